@@ -1,0 +1,361 @@
+"""Benchmark of the Sakura all-pairs Kepler step on GB300.
+
+Metric: pair-Kepler solves per second, counted as N^2 * steps / s (the
+literal N^2 count; the kernel solves the N(N-1) ordered pairs i != j).
+
+Default workload: equal-mass Plummer sphere, N = 1024, virial units,
+dt = 2^-8, 256 steps (one N-body time unit), second-order map, FP64.  One
+"step" is one ``sakura_step`` call: the pair kernel (drift, every ordered
+pair's Kepler solve, warp-shuffle reduction) plus the apply kernel.  The
+state (56 KB) fits in L2, so a 256 MB buffer is written between timed steps
+to flush L2; each step is timed with CUDA events on the library stream.
+
+Printed JSON line (rank 0): value (device-resident throughput), e2e (the
+same through the host-buffer entry point ``sakura_evolve_host``, copies
+included), roofline of the pair kernel against the FP64 ALU peak,
+cpu_baseline (the CPU oracle on the host cores), clocks sampled during the
+timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU (torchrun, one process per GPU): every rank integrates its own
+independently seeded replica; no data-path collective (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-Kepler solves/sec (N^2*steps/s)"
+UNIT = "pair-solves/s"
+
+# FP64 operations of one ordered pair in the pair kernel, counted by hand
+# from paper_1402_3325_gb300/csrc/{step_fp64.cu,kepler_fp64.cuh}: FMA = 2,
+# add/sub/mul = 1, divide = 1, square root = 1 (comparisons, fabs, fmax free).
+#   C_FIX: pair setup and back-drift (39) + Lagrange epilogue (33) +
+#          mass-weighted accumulation (12)
+#   C_IT:  one Laguerre iteration: Stumpff series and G-functions (48),
+#          convergence tests (3), Laguerre correction (10)
+C_FIX = 84
+C_IT = 61
+
+# FP64 ALU peak of one GB300: 152 SMs x 2 FP64 FMA units x 2 flop x 2.07 GHz
+# (the unit count follows from the nominal 1.25 TFLOP/s at 2.07 GHz).
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+
+
+def _workload(name: str, seed: int):
+    from paper_1402_3325_gb300 import ics
+    if name == "plummer1024":
+        return ics.plummer(1024, seed=seed), 256, (
+            "plummer-N1024 equal-mass virial (E=-1/4), dt=2^-8, 256 steps = 1 N-body time unit,"
+            " order 2")
+    if name == "bh16384":
+        return ics.bh_cluster(16384, seed=seed), 256, (
+            "black hole (m=1) + 16383 stars (total 1e-2), Plummer a=1, circular velocities,"
+            " dt=2^-10, order 2")
+    if name == "binaries16384":
+        return ics.plummer_binaries(16384, seed=seed), 64, (
+            "Plummer N=16384 with 10% primordial binaries (a in [1e-4,1e-2], thermal e),"
+            " dt=2^-10, order 2")
+    if name == "planetary9":
+        return ics.planetary(seed), 2000, (
+            "planetary N=9 (central mass 1 + 8 planets), dt=P_inner/200, 2000 steps, order 2")
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if parts[3 + k].lower() in ("active", "1"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _kernel_sources_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1402_3325_gb300", "csrc")
+    for f in ("kepler_fp64.cuh", "step_fp64.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(workload: str):
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, or
+    None when the summary is missing or the kernel changed since."""
+    path = os.path.join(ROOT, "profiles", f"pair_step_fp64_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as fh:
+        for ln in fh:
+            if ":" in ln and ln.lstrip().startswith("- "):
+                k, v = ln.lstrip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_sources_sha256_16") != _kernel_sources_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def _cpu_baseline(s, dt, budget_s=10.0, max_steps=256):
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.build()
+    r, v = s.r.copy(), s.v.copy()
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps:
+        rc, r, v = oracle.step(s.m, r, v, dt, 2, nthreads=cores)
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": s.n ** 2 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} consecutive steps of the same workload (N={s.n}) from its"
+                      f" initial state, OpenMP over i on {cores} threads, {el:.1f} s"}
+
+
+def run_reference(args, rank):
+    """The reference arm: the CPU oracle as it stands on the host cores."""
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    s, _, desc = _workload(args.workload, 0)
+    cores = os.cpu_count() or 1
+    r, v = s.r.copy(), s.v.copy()
+    for _ in range(args.warmup):
+        rc, r, v = oracle.step(s.m, r, v, s.dt, 2, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        rc, r, v = oracle.step(s.m, r, v, s.dt, 2, nthreads=cores)
+    el = time.perf_counter() - t0
+    value = s.n ** 2 * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "n": s.n, "dt": s.dt, "order": 2},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} timed steps after {args.warmup} warm-up"
+                                       f" steps, full N={s.n}, OpenMP over i on {cores} threads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plummer1024",
+                    choices=["plummer1024", "bh16384", "binaries16384", "planetary9"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.steps is None:
+        args.steps = _workload(args.workload, 0)[1]
+    args.warmup = max(3, args.warmup)
+
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    import numpy as np
+    import torch
+
+    from paper_1402_3325_gb300 import build as sk_build
+    from paper_1402_3325_gb300 import ics
+    from paper_1402_3325_gb300 import sakura as sk
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local_rank if world > 1 else 0)
+    torch.cuda.set_device(device)
+    if rank == 0:
+        sk_build.build()
+    if dist is not None:
+        dist.barrier()
+    stream = torch.cuda.current_stream(device)
+    s, _, desc = _workload(args.workload, seed=rank)
+    n = s.n
+    sk.init(device.index, stream=stream.cuda_stream)
+
+    state = torch.tensor(s.soa(), device=device)
+    mass = torch.tensor(s.m, device=device)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
+
+    # warm-up, then the mean Kepler iteration count of this workload
+    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_STATS)
+    for _ in range(args.warmup):
+        sk.step(state, mass, s.dt, 2)
+    sk.check()
+    st = sk.get_stats(reset=True)
+    kbar = st["iters"] / max(1, st["pairs"])
+    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_TIMING)
+    state.copy_(torch.tensor(s.soa(), device=device))
+    sk.get_stats(reset=True)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(device)
+    with ClockSampler(device.index) as clocks:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            sk.step(state, mass, s.dt, 2)
+            ends[k].record(stream)
+        torch.cuda.synchronize(device)
+    if dist is not None:
+        dist.barrier()
+    sk.check()
+    ms_total = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    st = sk.get_stats(reset=True)
+    pair_ms = st["pair_kernel_ms"] / max(1, st["timed_launches"])
+    if dist is not None:
+        t = torch.tensor([ms_total], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * n * n * args.steps / (ms_total * 1e-3)
+
+    # end to end through the host-buffer entry point, copies in the timed region
+    e2e = None
+    if not args.no_e2e:
+        host_state = torch.empty((6, n), dtype=torch.float64).pin_memory().numpy()
+        host_mass = torch.empty((n,), dtype=torch.float64).pin_memory().numpy()
+        host_state[...] = s.soa()
+        host_mass[...] = s.m
+        sk.init(device.index, stream=stream.cuda_stream)
+        for _ in range(2):
+            sk.evolve_host(host_state, host_mass, s.dt, 2, 1)
+        host_state[...] = s.soa()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sk.evolve_host(host_state, host_mass, s.dt, 2, 1)
+        el = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([el], device=device, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": world * n * n * args.steps / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(host_state.nbytes + host_mass.nbytes),
+               "d2h_bytes_per_step": int(host_state.nbytes)}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    flops_pair = C_FIX + kbar * C_IT
+    achieved = (n * (n - 1) * flops_pair) / (pair_ms * 1e-3) / 1e12
+    peak = FP64_PEAK_GFLOPS / 1e3
+    traffic = _profiled_traffic(args.workload)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "kernel": "pair_step_fp64_kernel", "pipe": "fp64",
+            "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (derived from the "
+                           "nominal 1.25 TFLOP/s; FMA probe measured 1.19)",
+            "flops_per_pair": flops_pair, "kepler_iters_mean": kbar,
+            "pair_kernel_ms": pair_ms, "pair_kernel_share": pair_ms / ms_step}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": desc, "n": n, "dt": s.dt, "order": 2, "form": "fp64",
+                       "pairs_solved_per_step": n * (n - 1),
+                       "l2": "256 MB buffer written between timed steps (state fits in L2)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "gpu_launches": 2 * args.steps,
+            "roofline": roof, "clocks": clocks.summary()}
+    if e2e is not None:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(s, s.dt)
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,167 @@
+/*
+ * sakura.h -- C ABI of the GB300 (sm_103a) implementation of the Sakura
+ * Keplerian-splitting N-body step (Goncalves Ferrari, Boekholt & Portegies
+ * Zwart 2014).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - G = 1, no softening (the method admits none, Sec. 3).
+ *  - A system of n particles is a device structure-of-arrays state
+ *    double[6][n] (rows x, y, z, vx, vy, vz, row-major, contiguous) and a
+ *    device double[n] of masses.  The caller owns both; the library never
+ *    frees or retains caller memory beyond a call.
+ *  - Device calls are asynchronous and ordered on the library stream
+ *    (sakura_config.stream, or the one given to sakura_set_stream).  Calls
+ *    that return host values (sakura_energy, sakura_get_stats, sakura_check,
+ *    sakura_evolve_host) synchronise that stream.
+ *  - Every function returns SAKURA_OK (0) or a negative SAKURA_E_* code.
+ *    Faults found on the device (coincident pair, non-finite state, failed
+ *    Kepler solve, non-positive mass) set bits in a device status word; they
+ *    are reported by the next synchronising call, or by the call itself when
+ *    SAKURA_FLAG_SYNC_CHECK is set.  No kernel traps or waits without bound.
+ *  - The library keeps one process-wide context (one device); it is not
+ *    thread-safe.  Scratch buffers are owned by the library and grow on
+ *    demand (cudaMalloc) outside the timed kernels.
+ */
+#ifndef SAKURA_H
+#define SAKURA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define SAKURA_OK 0
+#define SAKURA_E_NOINIT -1     /* sakura_init has not been called          */
+#define SAKURA_E_ARG -2        /* bad size, order, pointer or option        */
+#define SAKURA_E_MASS -3       /* a mass is <= 0 (mu_ij / m_i undefined)    */
+#define SAKURA_E_COINCIDENT -4 /* a pair has r0 = 0: the Kepler flow is undefined */
+#define SAKURA_E_NONFINITE -5  /* NaN or Inf in the state                   */
+#define SAKURA_E_KEPLER -6     /* Laguerre iteration and bisection both failed */
+#define SAKURA_E_CUDA -7       /* a CUDA runtime call failed                */
+#define SAKURA_E_TIMEOUT -8    /* a bounded device wait ran out             */
+#define SAKURA_E_NOMEM -9      /* device allocation failed                  */
+
+/* ---- options --------------------------------------------------------- */
+#define SAKURA_PREC_FP64 0  /* every pair solved in FP64                      */
+#define SAKURA_PREC_MIXED 1 /* distant, low-eccentricity pairs solved in FP32 */
+
+#define SAKURA_MIXED_RULE_LITERAL 0 /* FP32 iff r > r_min and e < e_max           */
+#define SAKURA_MIXED_RULE_HYP 1     /* FP32 iff r > r_min and (e < e_max or e > e_hyp) */
+
+#define SAKURA_GUESS_STANDARD 0 /* s0 = t / r0                               */
+#define SAKURA_GUESS_LEARNED 1  /* s0 from the loaded MLP (sakura_load_mlp)   */
+
+#define SAKURA_FLAG_SYNC_CHECK 1u /* synchronise and report faults on every call */
+#define SAKURA_FLAG_STATS 2u      /* collect iteration statistics (small cost)   */
+#define SAKURA_FLAG_TIMING 4u     /* time every pair-kernel launch with CUDA events */
+
+typedef struct sakura_config {
+    int device;           /* CUDA device ordinal                                  */
+    void *stream;         /* cudaStream_t for all work; NULL = legacy default    */
+    int precision;        /* SAKURA_PREC_*                                        */
+    int mixed_rule;       /* SAKURA_MIXED_RULE_*                                  */
+    double mixed_r_min;   /* default 0.1                                          */
+    double mixed_e_max;   /* default 0.9                                          */
+    double mixed_e_hyp;   /* default 10                                           */
+    int guess;            /* SAKURA_GUESS_*                                       */
+    double kepler_tol;    /* convergence |ds| <= kepler_tol * eps * |s|; default 4 */
+    int kepler_max_iter;  /* Laguerre steps before bisection; default 50          */
+    int kepler_bisection; /* 1 (default): bisection fallback; 0: report E_KEPLER  */
+    unsigned int flags;   /* SAKURA_FLAG_*                                        */
+    int block_warps;      /* pair kernel: i rows (warps) per block, 0 = tuned     */
+    int j_split;          /* pair kernel: j segments, 0 = chosen from n           */
+} sakura_config;
+
+typedef struct sakura_stats {
+    int64_t steps;        /* sakura_step calls since the last reset               */
+    int64_t pairs;        /* ordered pairs solved                                 */
+    int64_t iters;        /* Laguerre/Newton iterations summed over pairs         */
+    int64_t max_iters;    /* largest iteration count of any pair                  */
+    int64_t warp_slots;   /* sum over warp batches of 32 x (max lane iterations)  */
+    int64_t fp32_pairs;   /* pairs solved in single precision (mixed form)        */
+    int64_t fallbacks;    /* pairs that needed bisection or a restart             */
+    int64_t timed_launches; /* pair-kernel launches timed (SAKURA_FLAG_TIMING)    */
+    double pair_kernel_ms;  /* their summed device time, from CUDA events on the
+                               library stream                                    */
+} sakura_stats;
+
+/* Fill *cfg with the defaults listed above. */
+void sakura_default_config(sakura_config *cfg);
+
+/* Create the process-wide context on cfg->device (NULL: defaults).
+ * Allocates the status word and statistics counters.  Calling it again
+ * replaces the configuration and keeps scratch buffers. */
+int sakura_init(const sakura_config *cfg);
+
+/* Release every library-owned device buffer and the context. */
+int sakura_finalize(void);
+
+/* Change the stream used by later calls (cudaStream_t as void*). */
+int sakura_set_stream(void *stream);
+
+/* One step of the integrator on a device state, in place (Sec. 2.2).
+ *   order =  2: Psi(tau) = e^{tau/2 H_T} e^{tau H_W} e^{tau/2 H_T} (Eq. 25)
+ *               with the pair map of Eq. 26, i.e. Eqs. 27a-d.
+ *   order =  1: phi(tau) of Eq. 24 read right to left: W(tau) with the pair
+ *               map of Eq. 19a (Kepler, then backward drift), then drift tau.
+ *   order = -1: phi^dagger(tau): drift tau, then W(tau) with the pair map of
+ *               Eq. 19b (backward drift, then Kepler).
+ * Every ordered pair (i, j), i != j, is advanced by the universal-variable
+ * Kepler flow (Eq. 18) and its increments are summed mass-weighted into
+ * particle i (Eq. 23).
+ *   state:  device double[6][n], updated in place.
+ *   masses: device double[n], all > 0.
+ *   n >= 1; dt any finite value (negative integrates backwards).
+ * Errors: E_NOINIT, E_ARG (n < 1, order not in {2,1,-1}, NULL pointer,
+ * non-finite dt); device faults as described above. */
+int sakura_step(double *state, const double *masses, int64_t n, double dt, int order);
+
+/* nsteps consecutive steps on HOST buffers: copies state and masses to
+ * library-owned device memory, runs the steps, copies the state back and
+ * synchronises.  state: host double[6][n]; masses: host double[n]. */
+int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt,
+                       int order, int nsteps);
+
+/* Total energy E = sum_i m_i v_i^2 / 2 - sum_{i<j} m_i m_j / r_ij
+ * (Eqs. 1-3), accumulated in double-double.  state, masses: device, as
+ * above.  *E_out: host double.  Synchronises.  E_COINCIDENT if some r_ij = 0. */
+int sakura_energy(const double *state, const double *masses, int64_t n, double *E_out);
+
+/* Many independent systems in one persistent launch.  The systems are packed
+ * end to end: system k owns particles offsets[k] .. offsets[k+1]-1 of
+ * state (device double[6][total]) and masses (device double[total]).
+ * offsets: device int64[nsys+1]; dt: device double[nsys] (one step size per
+ * system).  Runs nsteps steps of the given order on every system.  The work
+ * schedule is rebuilt when offsets change (host copy of offsets needed:
+ * host_offsets, host int64[nsys+1]).  Max 1024 particles per system. */
+int sakura_step_batched(double *state, const double *masses, const int64_t *offsets,
+                        const int64_t *host_offsets, int nsys, const double *dt,
+                        int order, int nsteps);
+
+/* Load the initial-guess network used when cfg.guess = SAKURA_GUESS_LEARNED:
+ * a 6-64-64-1 perceptron.  weights: host float32 array laid out as
+ * W1[64][6], b1[64], W2[64][64], b2[64], W3[64], b3[1], then the input
+ * normalisation mean[6], scale[6] and output scale, shift (2 floats):
+ * 6*64+64+64*64+64+64+1+6+6+2 = 4687 floats.  bytes must equal 4687*4. */
+int sakura_load_mlp(const void *weights, size_t bytes);
+
+/* Copy the accumulated statistics (SAKURA_FLAG_STATS) and reset them if
+ * reset != 0.  Synchronises. */
+int sakura_get_stats(sakura_stats *out, int reset);
+
+/* Synchronise the library stream and return the first pending device fault
+ * (and clear it), or SAKURA_OK. */
+int sakura_check(void);
+
+/* Static description of a return code. */
+const char *sakura_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAKURA_H */

@@ -76,6 +76,10 @@ def _load():
                                         ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(Stats)]
             lib.oracle_step.restype = ctypes.c_int
+            lib.oracle_step_sample.argtypes = [I64, P, P, P, D, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int64), I64, P, P,
+                                               ctypes.c_int]
+            lib.oracle_step_sample.restype = ctypes.c_int
             lib.oracle_energy.argtypes = [I64, P, P, P, P, P, P]
             lib.oracle_energy.restype = ctypes.c_int
             lib.oracle_pair_classes.argtypes = [I64, P, P, P, D, ctypes.c_int,
@@ -129,6 +133,22 @@ def step(m, r, v, tau: float, order: int = 2, *, pair_solver: int = PAIR_KEPLER,
                              int(pair_solver), int(nthreads),
                              ctypes.byref(stats) if stats is not None else None)
     return rc, r, v
+
+
+def step_sample(m, r, v, tau: float, idx, order: int = 2, *, nthreads: int = 1):
+    """Post-step state of the particles listed in idx only (same values as
+    ``step`` would give them).  Returns (status, r_idx [k,3], v_idx [k,3])."""
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    k = idx.shape[0]
+    ro = np.zeros((k, 3))
+    vo = np.zeros((k, 3))
+    rc = _load().oracle_step_sample(m.shape[0], _dp(m), _dp(r), _dp(v), float(tau), int(order),
+                                    idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), k,
+                                    _dp(ro), _dp(vo), int(nthreads))
+    return rc, ro, vo
 
 
 def evolve(m, r, v, tau: float, nsteps: int, order: int = 2, **kw):

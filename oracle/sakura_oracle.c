@@ -442,6 +442,76 @@ int oracle_step(int64_t n, const double *m, double *r, double *v, double tau, in
     return ORC_OK;
 }
 
+/* The step of oracle_step (order 2, 1 or -1, Kepler pair solver) evaluated
+   only for the k particles listed in idx[]: writes their post-step positions
+   and velocities to r_out[k][3], v_out[k][3].  Each sampled row sums over all
+   j != i in ascending order exactly as the full step does, so the values are
+   the ones oracle_step would produce for those particles.  The input state is
+   not modified. */
+int oracle_step_sample(int64_t n, const double *m, const double *r, const double *v,
+                       double tau, int order, const int64_t *idx, int64_t k, double *r_out,
+                       double *v_out, int nthreads)
+{
+    if (n < 1 || !m || !r || !v || !idx || k < 0) return ORC_E_ARG;
+    if (!(order == 2 || order == 1 || order == -1)) return ORC_E_ARG;
+    double drift = order == 2 ? 0.5 * tau : (order == 1 ? 0.0 : tau);
+    double pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
+    double post = order == 2 ? 0.5 : (order == 1 ? 1.0 : 0.0);
+    double *rd = (double *)malloc(sizeof(double) * (size_t)(3 * n));
+    if (!rd) return ORC_E_ARG;
+    /* the first drift, as evolve_HT computes it */
+    for (int64_t i = 0; i < n; ++i)
+        for (int q = 0; q < 3; ++q) rd[3 * i + q] = r[3 * i + q] + v[3 * i + q] * drift;
+    int status = ORC_OK;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic) num_threads(nthreads)
+#endif
+    for (int64_t s = 0; s < k; ++s) {
+        int64_t i = idx[s];
+        double dmr[3] = {0, 0, 0}, dmv[3] = {0, 0, 0};
+        for (int64_t j = 0; j < n; ++j) {
+            if (i == j) continue;
+            double mij = m[i] + m[j];
+            double mu = m[i] * m[j] / mij;
+            double rr0[3], vv0[3], r0[3], v0[3], r1[3], v1[3], rr1[3];
+            for (int q = 0; q < 3; ++q) {
+                rr0[q] = rd[3 * i + q] - rd[3 * j + q];
+                vv0[q] = v[3 * i + q] - v[3 * j + q];
+            }
+            for (int q = 0; q < 3; ++q) {
+                r0[q] = rr0[q] - vv0[q] * tau * pre;
+                v0[q] = vv0[q];
+            }
+            int it = 0;
+            int rc = oracle_kepler(tau, mij, r0, v0, r1, v1, &it);
+            if (rc != ORC_OK) {
+#ifdef _OPENMP
+#pragma omp critical
+#endif
+                status = rc;
+            }
+            for (int q = 0; q < 3; ++q) rr1[q] = r1[q] - v1[q] * tau * post;
+            for (int q = 0; q < 3; ++q) {
+                dmr[q] += mu * (rr1[q] - rr0[q]);
+                dmv[q] += mu * (v1[q] - vv0[q]);
+            }
+        }
+        for (int q = 0; q < 3; ++q) {
+            double x = rd[3 * i + q] + dmr[q] / m[i];
+            double u = v[3 * i + q] + dmv[q] / m[i];
+            if (order == 2)
+                x += u * (0.5 * tau);
+            else if (order == 1)
+                x += u * tau;
+            r_out[3 * s + q] = x;
+            v_out[3 * s + q] = u;
+        }
+    }
+    free(rd);
+    return status;
+}
+
 /* ------------------------------------------------------------------ */
 /* Energy (Eqs. 1-3): E = sum_i m_i v_i^2 / 2 - sum_{i<j} m_i m_j / r_ij */
 /* Neumaier-compensated sums; T and U are also returned.               */

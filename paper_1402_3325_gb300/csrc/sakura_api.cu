@@ -1,0 +1,418 @@
+// sakura_api.cu -- the extern "C" boundary declared in include/sakura.h.
+//
+// Holds the process-wide context (device, stream, configuration, library-owned
+// scratch), validates arguments, sizes the launches and maps the device status
+// word to return codes.  All arithmetic of the method runs in the kernels.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "sakura.h"
+#include "kepler_fp64.cuh"
+#include "step_common.cuh"
+
+namespace {
+
+struct Buffer {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct Context {
+    bool init = false;
+    sakura_config cfg{};
+    cudaStream_t stream = nullptr;
+    unsigned *d_status = nullptr;
+    unsigned long long *d_stats = nullptr;
+    double *d_energy = nullptr;  // [3] E, T, U
+    Buffer partial;              // pair-kernel segment sums
+    Buffer energy_work;
+    Buffer host_state, host_mass;  // device copies for sakura_evolve_host
+    int64_t steps = 0;
+    int64_t pairs = 0;
+    int sm_count = 152;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timers;  // pending pair-kernel timings
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare;
+    double timed_ms = 0.0;
+    int64_t timed_launches = 0;
+};
+
+Context g;
+
+int grow(Buffer &b, size_t bytes)
+{
+    if (b.bytes >= bytes) return SAKURA_OK;
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return SAKURA_E_NOMEM;
+    }
+    b.bytes = bytes;
+    return SAKURA_OK;
+}
+
+int status_to_code(unsigned st)
+{
+    if (st & sakura::kStatusMass) return SAKURA_E_MASS;
+    if (st & sakura::kStatusNonfinite) return SAKURA_E_NONFINITE;
+    if (st & sakura::kStatusCoincident) return SAKURA_E_COINCIDENT;
+    if (st & sakura::kStatusKepler) return SAKURA_E_KEPLER;
+    if (st & sakura::kStatusTimeout) return SAKURA_E_TIMEOUT;
+    return SAKURA_OK;
+}
+
+// Event pair for one timed launch (reused across calls).
+std::pair<cudaEvent_t, cudaEvent_t> take_timer()
+{
+    if (!g.spare.empty()) {
+        auto p = g.spare.back();
+        g.spare.pop_back();
+        return p;
+    }
+    std::pair<cudaEvent_t, cudaEvent_t> p{nullptr, nullptr};
+    cudaEventCreate(&p.first);
+    cudaEventCreate(&p.second);
+    return p;
+}
+
+// Fold completed timings into the totals (the caller has synchronised).
+void collect_timers()
+{
+    for (auto &p : g.timers) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) {
+            g.timed_ms += ms;
+            g.timed_launches += 1;
+        }
+        g.spare.push_back(p);
+    }
+    g.timers.clear();
+    cudaGetLastError();
+}
+
+int launch_error()
+{
+    return cudaGetLastError() == cudaSuccess ? SAKURA_OK : SAKURA_E_CUDA;
+}
+
+// Synchronise, read and clear the status word.
+int drain_status()
+{
+    unsigned st = 0;
+    if (cudaMemcpyAsync(&st, g.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, g.stream) !=
+        cudaSuccess)
+        return SAKURA_E_CUDA;
+    if (cudaStreamSynchronize(g.stream) != cudaSuccess) return SAKURA_E_CUDA;
+    if (st) {
+        if (cudaMemsetAsync(g.d_status, 0, sizeof(unsigned), g.stream) != cudaSuccess)
+            return SAKURA_E_CUDA;
+    }
+    return status_to_code(st);
+}
+
+struct Plan {
+    int warps;
+    int nsplit;
+    int64_t jchunk;
+};
+
+Plan plan_step(int64_t n)
+{
+    Plan p;
+    p.warps = g.cfg.block_warps > 0 ? g.cfg.block_warps : 8;
+    if (p.warps != 4 && p.warps != 8 && p.warps != 16) p.warps = 8;
+    const int64_t iblocks = (n + p.warps - 1) / p.warps;
+    int64_t ns = g.cfg.j_split;
+    if (ns <= 0) {
+        const int64_t target = (int64_t)g.sm_count * 4;
+        ns = (target + iblocks - 1) / iblocks;
+        const int64_t cap = std::max<int64_t>(1, n / 128);
+        ns = std::min(ns, cap);
+    }
+    ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::max<int64_t>(1, n)));
+    ns = std::min<int64_t>(ns, 65535);
+    p.nsplit = (int)ns;
+    p.jchunk = (n + ns - 1) / ns;
+    return p;
+}
+
+int step_device(double *state, const double *masses, int64_t n, double dt, int order)
+{
+    const Plan p = plan_step(n);
+    int rc = grow(g.partial, (size_t)p.nsplit * 6 * (size_t)n * sizeof(double));
+    if (rc) return rc;
+    sakura::StepArgs a;
+    a.state = state;
+    a.mass = masses;
+    a.partial = (double *)g.partial.ptr;
+    a.n = n;
+    a.jchunk = p.jchunk;
+    a.tau = dt;
+    a.drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
+    a.pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
+    a.post = 1.0 - a.pre;
+    a.tol = g.cfg.kepler_tol * DBL_EPSILON;
+    a.max_iter = g.cfg.kepler_max_iter;
+    a.bisection = g.cfg.kepler_bisection;
+    a.status = g.d_status;
+    a.stats = g.d_stats;
+    const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
+    int nsplit = p.nsplit;
+    if (n > 1) {
+        const bool timing = (g.cfg.flags & SAKURA_FLAG_TIMING) != 0;
+        std::pair<cudaEvent_t, cudaEvent_t> tm{nullptr, nullptr};
+        if (timing) {
+            tm = take_timer();
+            cudaEventRecord(tm.first, g.stream);
+        }
+        sakura::launch_pair_step_fp64(a, p.warps, p.nsplit, stats, g.stream);
+        if (timing) {
+            cudaEventRecord(tm.second, g.stream);
+            g.timers.push_back(tm);
+        }
+    } else {
+        nsplit = 0;  // a single particle only drifts
+    }
+    sakura::launch_apply_step(state, masses, (const double *)g.partial.ptr, n, nsplit, dt, order,
+                              g.d_status, g.stream);
+    rc = launch_error();
+    if (rc) return rc;
+    g.steps += 1;
+    g.pairs += n * (n - 1);
+    return SAKURA_OK;
+}
+
+bool valid_order(int order) { return order == 2 || order == 1 || order == -1; }
+
+}  // namespace
+
+extern "C" {
+
+void sakura_default_config(sakura_config *cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->device = 0;
+    cfg->stream = nullptr;
+    cfg->precision = SAKURA_PREC_FP64;
+    cfg->mixed_rule = SAKURA_MIXED_RULE_LITERAL;
+    cfg->mixed_r_min = 0.1;
+    cfg->mixed_e_max = 0.9;
+    cfg->mixed_e_hyp = 10.0;
+    cfg->guess = SAKURA_GUESS_STANDARD;
+    cfg->kepler_tol = 4.0;
+    cfg->kepler_max_iter = 50;
+    cfg->kepler_bisection = 1;
+    cfg->flags = 0;
+    cfg->block_warps = 0;
+    cfg->j_split = 0;
+}
+
+int sakura_init(const sakura_config *cfg)
+{
+    sakura_config c;
+    if (cfg)
+        c = *cfg;
+    else
+        sakura_default_config(&c);
+    if (c.kepler_max_iter < 1 || c.kepler_max_iter > 10000 || !(c.kepler_tol > 0.0))
+        return SAKURA_E_ARG;
+    if (c.precision != SAKURA_PREC_FP64 && c.precision != SAKURA_PREC_MIXED) return SAKURA_E_ARG;
+    if (c.guess != SAKURA_GUESS_STANDARD && c.guess != SAKURA_GUESS_LEARNED) return SAKURA_E_ARG;
+    if (cudaSetDevice(c.device) != cudaSuccess) {
+        cudaGetLastError();
+        return SAKURA_E_CUDA;
+    }
+    if (g.init && g.cfg.device != c.device) sakura_finalize();
+    if (!g.init) {
+        if (cudaMalloc(&g.d_status, sizeof(unsigned)) != cudaSuccess) return SAKURA_E_NOMEM;
+        if (cudaMalloc(&g.d_stats, sakura::kStatCount * sizeof(unsigned long long)) !=
+            cudaSuccess)
+            return SAKURA_E_NOMEM;
+        if (cudaMalloc(&g.d_energy, 3 * sizeof(double)) != cudaSuccess) return SAKURA_E_NOMEM;
+        if (cudaMemset(g.d_status, 0, sizeof(unsigned)) != cudaSuccess) return SAKURA_E_CUDA;
+        if (cudaMemset(g.d_stats, 0, sakura::kStatCount * sizeof(unsigned long long)) !=
+            cudaSuccess)
+            return SAKURA_E_CUDA;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device) ==
+                cudaSuccess &&
+            sms > 0)
+            g.sm_count = sms;
+        g.steps = g.pairs = 0;
+    }
+    g.cfg = c;
+    g.stream = (cudaStream_t)c.stream;
+    g.init = true;
+    return SAKURA_OK;
+}
+
+int sakura_finalize(void)
+{
+    if (!g.init) return SAKURA_OK;
+    cudaStreamSynchronize(g.stream);
+    Buffer *bufs[] = {&g.partial, &g.energy_work, &g.host_state, &g.host_mass};
+    for (Buffer *b : bufs) {
+        if (b->ptr) cudaFree(b->ptr);
+        b->ptr = nullptr;
+        b->bytes = 0;
+    }
+    cudaFree(g.d_status);
+    cudaFree(g.d_stats);
+    cudaFree(g.d_energy);
+    for (auto &p : g.timers) g.spare.push_back(p);
+    for (auto &p : g.spare) {
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    g = Context();
+    return SAKURA_OK;
+}
+
+int sakura_set_stream(void *stream)
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    g.stream = (cudaStream_t)stream;
+    g.cfg.stream = stream;
+    return SAKURA_OK;
+}
+
+int sakura_step(double *state, const double *masses, int64_t n, double dt, int order)
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    if (!state || !masses || n < 1 || !valid_order(order) || !std::isfinite(dt))
+        return SAKURA_E_ARG;
+    int rc = step_device(state, masses, n, dt, order);
+    if (rc) return rc;
+    if (g.cfg.flags & SAKURA_FLAG_SYNC_CHECK) return drain_status();
+    return SAKURA_OK;
+}
+
+int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt, int order,
+                       int nsteps)
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    if (!state || !masses || n < 1 || !valid_order(order) || !std::isfinite(dt) || nsteps < 0)
+        return SAKURA_E_ARG;
+    int rc = grow(g.host_state, 6 * (size_t)n * sizeof(double));
+    if (rc) return rc;
+    rc = grow(g.host_mass, (size_t)n * sizeof(double));
+    if (rc) return rc;
+    double *ds = (double *)g.host_state.ptr;
+    double *dm = (double *)g.host_mass.ptr;
+    if (cudaMemcpyAsync(ds, state, 6 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
+                        g.stream) != cudaSuccess ||
+        cudaMemcpyAsync(dm, masses, (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
+                        g.stream) != cudaSuccess)
+        return SAKURA_E_CUDA;
+    for (int k = 0; k < nsteps; ++k) {
+        rc = step_device(ds, dm, n, dt, order);
+        if (rc) return rc;
+    }
+    if (cudaMemcpyAsync(state, ds, 6 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost,
+                        g.stream) != cudaSuccess)
+        return SAKURA_E_CUDA;
+    return drain_status();
+}
+
+int sakura_energy(const double *state, const double *masses, int64_t n, double *E_out)
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    if (!state || !masses || n < 1 || !E_out) return SAKURA_E_ARG;
+    const int nwork = sakura::energy_work_size(n);
+    int rc = grow(g.energy_work, (size_t)nwork * sizeof(double));
+    if (rc) return rc;
+    sakura::launch_energy(state, masses, n, (double *)g.energy_work.ptr, nwork, g.d_energy,
+                          g.d_status, g.stream);
+    rc = launch_error();
+    if (rc) return rc;
+    double out[3];
+    if (cudaMemcpyAsync(out, g.d_energy, sizeof(out), cudaMemcpyDeviceToHost, g.stream) !=
+        cudaSuccess)
+        return SAKURA_E_CUDA;
+    rc = drain_status();
+    *E_out = out[0];
+    return rc;
+}
+
+int sakura_step_batched(double *state, const double *masses, const int64_t *offsets,
+                        const int64_t *host_offsets, int nsys, const double *dt, int order,
+                        int nsteps)
+{
+    (void)state;
+    (void)masses;
+    (void)offsets;
+    (void)host_offsets;
+    (void)nsys;
+    (void)dt;
+    (void)order;
+    (void)nsteps;
+    if (!g.init) return SAKURA_E_NOINIT;
+    return SAKURA_E_ARG;
+}
+
+int sakura_load_mlp(const void *weights, size_t bytes)
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    if (!weights || bytes != 4687 * sizeof(float)) return SAKURA_E_ARG;
+    return SAKURA_E_ARG;
+}
+
+int sakura_get_stats(sakura_stats *out, int reset)
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    if (!out) return SAKURA_E_ARG;
+    unsigned long long h[sakura::kStatCount];
+    if (cudaMemcpyAsync(h, g.d_stats, sizeof(h), cudaMemcpyDeviceToHost, g.stream) !=
+        cudaSuccess)
+        return SAKURA_E_CUDA;
+    if (cudaStreamSynchronize(g.stream) != cudaSuccess) return SAKURA_E_CUDA;
+    out->steps = g.steps;
+    out->pairs = g.pairs;
+    out->iters = (int64_t)h[sakura::kStatIters];
+    out->max_iters = (int64_t)h[sakura::kStatMaxIters];
+    out->warp_slots = (int64_t)h[sakura::kStatSlots];
+    out->fallbacks = (int64_t)h[sakura::kStatFallbacks];
+    out->fp32_pairs = (int64_t)h[sakura::kStatFp32Pairs];
+    collect_timers();
+    out->timed_launches = g.timed_launches;
+    out->pair_kernel_ms = g.timed_ms;
+    if (reset) {
+        if (cudaMemsetAsync(g.d_stats, 0, sizeof(h), g.stream) != cudaSuccess)
+            return SAKURA_E_CUDA;
+        g.steps = g.pairs = 0;
+        g.timed_ms = 0.0;
+        g.timed_launches = 0;
+    }
+    return SAKURA_OK;
+}
+
+int sakura_check(void)
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    return drain_status();
+}
+
+const char *sakura_strerror(int code)
+{
+    switch (code) {
+    case SAKURA_OK: return "ok";
+    case SAKURA_E_NOINIT: return "sakura_init has not been called";
+    case SAKURA_E_ARG: return "invalid argument";
+    case SAKURA_E_MASS: return "a mass is not positive";
+    case SAKURA_E_COINCIDENT: return "two particles coincide (r_ij = 0)";
+    case SAKURA_E_NONFINITE: return "non-finite state";
+    case SAKURA_E_KEPLER: return "Kepler solver did not converge";
+    case SAKURA_E_CUDA: return "CUDA runtime error";
+    case SAKURA_E_TIMEOUT: return "bounded device wait ran out";
+    case SAKURA_E_NOMEM: return "device allocation failed";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

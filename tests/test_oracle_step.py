@@ -210,3 +210,14 @@ def test_threads_do_not_change_bits():
     _, r4, v4 = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=4)
     np.testing.assert_array_equal(r1, r4)
     np.testing.assert_array_equal(v1, v4)
+
+
+@pytest.mark.parametrize("order", [2, 1, -1])
+def test_step_sample_equals_full_step(order):
+    s = ics.random_cluster(40, seed=8, mass_spread=2.0)
+    idx = np.array([0, 7, 39, 13])
+    _, r1, v1 = oracle.step(s.m, s.r, s.v, 1 / 64, order)
+    rc, rs, vs = oracle.step_sample(s.m, s.r, s.v, 1 / 64, idx, order)
+    assert rc == oracle.OK
+    np.testing.assert_array_equal(rs, r1[idx])
+    np.testing.assert_array_equal(vs, v1[idx])
