@@ -157,6 +157,27 @@ int sakura_get_stats(sakura_stats *out, int reset);
  * (and clear it), or SAKURA_OK. */
 int sakura_check(void);
 
+/* The FP64 step of sakura_step (default Kepler controls: tolerance 4 eps,
+ * 50 Laguerre steps, bisection fallback) for callers that cannot allocate
+ * device memory: programs whose GPU memory is owned by another allocator
+ * (a framework's caching allocator that has reserved the device would make
+ * cudaMalloc fail) and latency-critical loops that must not call
+ * cudaMalloc/cudaFree.  The paper has no counterpart; this is an interface
+ * convenience.  It needs no sakura_init and allocates nothing: its scratch
+ * (row sums, 6 x SAKURA_NOALLOC_MAX_N doubles = 3 MiB) and its fault status
+ * word are file-scope device arrays that every GPU loading the library holds
+ * until the process exits.
+ *   state, masses: device arrays as for sakura_step; n <= SAKURA_NOALLOC_MAX_N
+ *   (larger n returns SAKURA_E_ARG); stream: cudaStream_t or NULL.
+ * Runs on the calling thread's current device and synchronises the stream
+ * before returning the first device fault of this call (or SAKURA_OK).
+ * The first call on a device looks up the arrays' device addresses; make it
+ * before any stream capture.  All calls share the arrays and keep the last
+ * call's contents; calls that overlap on the GPU race on them. */
+#define SAKURA_NOALLOC_MAX_N 65536
+int sakura_step_noalloc(double *state, const double *masses, int64_t n, double dt, int order,
+                        void *stream);
+
 /* Static description of a return code. */
 const char *sakura_strerror(int code);
 

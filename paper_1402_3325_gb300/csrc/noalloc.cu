@@ -1,0 +1,150 @@
+// noalloc.cu -- sakura_step_noalloc: the FP64 step without any device
+// allocation.
+//
+// Some callers cannot call cudaMalloc.  A host program whose device memory is
+// entirely held by another allocator (for example a framework's caching
+// allocator that has reserved the GPU) gets out-of-memory from it, and a
+// latency-critical loop cannot afford cudaMalloc/cudaFree, which may
+// synchronise the device.  For them this entry point runs the same pair and
+// apply kernels as sakura_step, but keeps the pair kernel's row-sum scratch
+// and the fault status word in file-scope device arrays that exist for as
+// long as the library is loaded.
+//
+// Limits and sharing rules:
+//   - n <= SAKURA_NOALLOC_MAX_N (65536); larger n returns SAKURA_E_ARG.
+//   - The scratch (6 x 65536 doubles = 3 MiB) and the status word are shared
+//     by every call on a device and keep the last call's contents.  Every
+//     scratch entry a call reads is written earlier in the same call; the
+//     status word is cleared at the start of each call.  Calls whose work
+//     overlaps on the GPU (other streams, other host threads) race on both.
+//   - The first call on a device looks up the arrays' device addresses with
+//     cudaGetSymbolAddress while that device is current; make that first call
+//     before any stream capture.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+
+#include "kepler_fp64.cuh"
+#include "sakura.h"
+#include "step_common.cuh"
+
+namespace {
+
+constexpr int64_t kMaxN = SAKURA_NOALLOC_MAX_N;
+constexpr int64_t kScratchDoubles = 6 * kMaxN;
+constexpr int kMaxDevices = 64;
+
+// The host-side names below are stand-ins for device memory: host code never
+// dereferences them and only passes the addresses returned by
+// cudaGetSymbolAddress to kernels.
+static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
+static __device__ __align__(256) unsigned g_noalloc_status[64];
+
+struct DeviceSymbols {
+    bool ready = false;
+    double *scratch = nullptr;
+    unsigned *status = nullptr;
+    int sm_count = 152;
+};
+
+DeviceSymbols g_dev[kMaxDevices];
+
+int setup_device(int dev, DeviceSymbols **out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return SAKURA_E_ARG;
+    DeviceSymbols &d = g_dev[dev];
+    if (!d.ready) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return SAKURA_E_CUDA;
+        }
+        d.scratch = (double *)p;
+        p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_status) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return SAKURA_E_CUDA;
+        }
+        d.status = (unsigned *)p;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            sms > 0)
+            d.sm_count = sms;
+        d.ready = true;
+    }
+    *out = &d;
+    return SAKURA_OK;
+}
+
+int code_from_status(unsigned st)
+{
+    if (st & sakura::kStatusMass) return SAKURA_E_MASS;
+    if (st & sakura::kStatusNonfinite) return SAKURA_E_NONFINITE;
+    if (st & sakura::kStatusCoincident) return SAKURA_E_COINCIDENT;
+    if (st & sakura::kStatusKepler) return SAKURA_E_KEPLER;
+    return SAKURA_OK;
+}
+
+}  // namespace
+
+extern "C" int sakura_step_noalloc(double *state, const double *masses, int64_t n, double dt,
+                                   int order, void *stream)
+{
+    if (!state || !masses || n < 1 || !std::isfinite(dt)) return SAKURA_E_ARG;
+    if (!(order == 2 || order == 1 || order == -1)) return SAKURA_E_ARG;
+    if (n > kMaxN) return SAKURA_E_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return SAKURA_E_CUDA;
+    }
+    DeviceSymbols *d = nullptr;
+    int rc = setup_device(dev, &d);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // j segments: enough blocks to fill the GPU, within the fixed scratch
+    const int warps = 8;
+    const int64_t iblocks = (n + warps - 1) / warps;
+    int64_t nsplit = ((int64_t)d->sm_count * 4 + iblocks - 1) / iblocks;
+    nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, n / 128));
+    nsplit = std::min<int64_t>(nsplit, kScratchDoubles / (6 * n));
+    nsplit = std::max<int64_t>(1, nsplit);
+
+    if (cudaMemsetAsync(d->status, 0, sizeof(unsigned), s) != cudaSuccess) {
+        cudaGetLastError();
+        return SAKURA_E_CUDA;
+    }
+    sakura::StepArgs a;
+    a.state = state;
+    a.mass = masses;
+    a.partial = d->scratch;
+    a.n = n;
+    a.jchunk = (n + nsplit - 1) / nsplit;
+    a.tau = dt;
+    a.drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
+    a.pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
+    a.post = 1.0 - a.pre;
+    a.tol = 4.0 * DBL_EPSILON;
+    a.max_iter = 50;
+    a.bisection = 1;
+    a.status = d->status;
+    a.stats = nullptr;
+    int used_split = (int)nsplit;
+    if (n > 1)
+        sakura::launch_pair_step_fp64(a, warps, used_split, false, s);
+    else
+        used_split = 0;
+    sakura::launch_apply_step(state, masses, d->scratch, n, used_split, dt, order, d->status, s);
+    if (cudaGetLastError() != cudaSuccess) return SAKURA_E_CUDA;
+    unsigned st = 0;
+    if (cudaMemcpyAsync(&st, d->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return SAKURA_E_CUDA;
+    }
+    return code_from_status(st);
+}

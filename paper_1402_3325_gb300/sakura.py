@@ -105,12 +105,14 @@ def load(path: str = LIB_PATH):
     lib.sakura_step_batched.argtypes = [P, P, P, P, I, P, I, I]
     lib.sakura_load_mlp.argtypes = [P, ctypes.c_size_t]
     lib.sakura_get_stats.argtypes = [ctypes.POINTER(Stats), I]
+    lib.sakura_step_noalloc.argtypes = [P, P, I64, D, I, P]
     lib.sakura_check.argtypes = []
     lib.sakura_strerror.argtypes = [I]
     lib.sakura_strerror.restype = ctypes.c_char_p
     for name in ("sakura_init", "sakura_finalize", "sakura_set_stream", "sakura_step",
                  "sakura_evolve_host", "sakura_energy", "sakura_step_batched",
-                 "sakura_load_mlp", "sakura_get_stats", "sakura_check"):
+                 "sakura_load_mlp", "sakura_get_stats", "sakura_check",
+                 "sakura_step_noalloc"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -177,6 +179,20 @@ def step(state, masses, dt: float, order: int = 2):
         raise ValueError("state must have shape (6, n)")
     _check(load().sakura_step(_ptr(state), _ptr(masses), n, float(dt), int(order)),
            "sakura_step")
+
+
+NOALLOC_MAX_N = 65536
+
+
+def step_noalloc(state, masses, dt: float, order: int = 2, stream=None):
+    """sakura_step without any device allocation (file-scope scratch, n <=
+    NOALLOC_MAX_N), for callers that cannot call cudaMalloc; synchronises."""
+    n = masses.shape[0]
+    if tuple(state.shape) != (6, n):
+        raise ValueError("state must have shape (6, n)")
+    s = ctypes.c_void_p(int(stream)) if stream is not None else None
+    _check(load().sakura_step_noalloc(_ptr(state), _ptr(masses), n, float(dt), int(order), s),
+           "sakura_step_noalloc")
 
 
 def evolve_host(state, masses, dt: float, order: int = 2, nsteps: int = 1):
