@@ -5,8 +5,9 @@ literal N^2 count; the kernel solves the N(N-1) ordered pairs i != j).
 
 Default workload: equal-mass Plummer sphere, N = 1024, virial units,
 dt = 2^-8, 256 steps (one N-body time unit), second-order map, FP64.  One
-"step" is one ``sakura_step`` call: the pair kernel (drift, every ordered
-pair's Kepler solve, warp-shuffle reduction) plus the apply kernel.  The
+"step" is one ``sakura_step`` call: the prep kernel (drift), the pair
+kernel (every ordered pair's Kepler solve, warp-shuffle row sums) and the
+apply kernel (Eqs. 27b-d).  The
 state (56 KB) fits in L2, so a 256 MB buffer is written between timed steps
 to flush L2; each step is timed with CUDA events on the library stream.
 
@@ -42,13 +43,21 @@ UNIT = "pair-solves/s"
 
 # FP64 operations of one ordered pair in the pair kernel, counted by hand
 # from paper_1402_3325_gb300/csrc/{step_fp64.cu,kepler_fp64.cuh}: FMA = 2,
-# add/sub/mul = 1, divide = 1, square root = 1 (comparisons, fabs, fmax free).
-#   C_FIX: pair setup and back-drift (39) + Lagrange epilogue (33) +
-#          mass-weighted accumulation (12)
-#   C_IT:  one Laguerre iteration: Stumpff series and G-functions (48),
-#          convergence tests (3), Laguerre correction (10)
-C_FIX = 84
-C_IT = 61
+# add/sub/mul = 1 (comparisons run on the integer pipe and are not counted).
+#   C_FIX  = relative state and m_ij (7) + setup: backward drift, r0 and 1/r0
+#            by seeded third-order refinement, eta0, v0^2, beta, zeta0 and the
+#            second-order guess (49) + Lagrange epilogue (27) + m_j-weighted
+#            accumulation (12)
+#   C_EVAL = one evaluation: beta s^2 (2), 3-term Stumpff series (12),
+#            G-functions (5), F, F', F'' (13), 1/F' (6), Newton step and
+#            convergence test (3)
+#   C_STEP = one Laguerre correction (6)
+# per pair: C_FIX + kbar * C_EVAL + (kbar - 1) * C_STEP, kbar = measured mean
+# evaluations.  ncu cross-check (profiles/pair_step_fp64_plummer1024.md):
+# 191 FP64 flops per pair executed, 4 % above this count.
+C_FIX = 95
+C_EVAL = 41
+C_STEP = 6
 
 # FP64 ALU peak of one GB300: 152 SMs x 2 FP64 FMA units x 2 flop x 2.07 GHz
 # (the unit count follows from the nominal 1.25 TFLOP/s at 2.07 GHz).
@@ -219,6 +228,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plummer1024",
                     choices=["plummer1024", "bh16384", "binaries16384", "planetary9"])
+    ap.add_argument("--guess", default="taylor", choices=["standard", "taylor"],
+                    help="Kepler initial guess: t/r0 or the second-order expansion")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -254,20 +265,21 @@ def main():
     stream = torch.cuda.current_stream(device)
     s, _, desc = _workload(args.workload, seed=rank)
     n = s.n
-    sk.init(device.index, stream=stream.cuda_stream)
+    guess = sk.GUESS_TAYLOR if args.guess == "taylor" else sk.GUESS_STANDARD
+    sk.init(device.index, stream=stream.cuda_stream, guess=guess)
 
     state = torch.tensor(s.soa(), device=device)
     mass = torch.tensor(s.m, device=device)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
 
     # warm-up, then the mean Kepler iteration count of this workload
-    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_STATS)
+    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_STATS, guess=guess)
     for _ in range(args.warmup):
         sk.step(state, mass, s.dt, 2)
     sk.check()
     st = sk.get_stats(reset=True)
     kbar = st["iters"] / max(1, st["pairs"])
-    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_TIMING)
+    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_TIMING, guess=guess)
     state.copy_(torch.tensor(s.soa(), device=device))
     sk.get_stats(reset=True)
 
@@ -303,7 +315,7 @@ def main():
         host_mass = torch.empty((n,), dtype=torch.float64).pin_memory().numpy()
         host_state[...] = s.soa()
         host_mass[...] = s.m
-        sk.init(device.index, stream=stream.cuda_stream)
+        sk.init(device.index, stream=stream.cuda_stream, guess=guess)
         for _ in range(2):
             sk.evolve_host(host_state, host_mass, s.dt, 2, 1)
         host_state[...] = s.soa()
@@ -326,7 +338,7 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    flops_pair = C_FIX + kbar * C_IT
+    flops_pair = C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP
     achieved = (n * (n - 1) * flops_pair) / (pair_ms * 1e-3) / 1e12
     peak = FP64_PEAK_GFLOPS / 1e3
     traffic = _profiled_traffic(args.workload)
@@ -342,10 +354,11 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": desc, "n": n, "dt": s.dt, "order": 2, "form": "fp64",
+                       "kepler_guess": args.guess,
                        "pairs_solved_per_step": n * (n - 1),
                        "l2": "256 MB buffer written between timed steps (state fits in L2)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 3 * args.steps,
             "roofline": roof, "clocks": clocks.summary()}
     if e2e is not None:
         line["e2e"] = e2e

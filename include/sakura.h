@@ -54,6 +54,7 @@ extern "C" {
 
 #define SAKURA_GUESS_STANDARD 0 /* s0 = t / r0                               */
 #define SAKURA_GUESS_LEARNED 1  /* s0 from the loaded MLP (sakura_load_mlp)   */
+#define SAKURA_GUESS_TAYLOR 2   /* s0 = (t/r0)(1 - eta0 t / (2 r0^2)): second order in t */
 
 #define SAKURA_FLAG_SYNC_CHECK 1u /* synchronise and report faults on every call */
 #define SAKURA_FLAG_STATS 2u      /* collect iteration statistics (small cost)   */
@@ -72,8 +73,9 @@ typedef struct sakura_config {
     int kepler_max_iter;  /* Laguerre steps before bisection; default 50          */
     int kepler_bisection; /* 1 (default): bisection fallback; 0: report E_KEPLER  */
     unsigned int flags;   /* SAKURA_FLAG_*                                        */
-    int block_warps;      /* pair kernel: i rows (warps) per block, 0 = tuned     */
-    int j_split;          /* pair kernel: j segments, 0 = chosen from n           */
+    int block_warps;      /* pair kernel: warps per block (4, 8, 16), 0 = 4       */
+    int grid_blocks;      /* pair kernel: blocks of the persistent grid, 0 = one
+                             wave of resident blocks                             */
 } sakura_config;
 
 typedef struct sakura_stats {
@@ -164,7 +166,8 @@ int sakura_check(void);
  * cudaMalloc fail) and latency-critical loops that must not call
  * cudaMalloc/cudaFree.  The paper has no counterpart; this is an interface
  * convenience.  It needs no sakura_init and allocates nothing: its scratch
- * (row sums, 6 x SAKURA_NOALLOC_MAX_N doubles = 3 MiB) and its fault status
+ * (drifted state and row sums, 20 x SAKURA_NOALLOC_MAX_N doubles = 10 MiB)
+ * and its fault status
  * word are file-scope device arrays that every GPU loading the library holds
  * until the process exits.
  *   state, masses: device arrays as for sakura_step; n <= SAKURA_NOALLOC_MAX_N

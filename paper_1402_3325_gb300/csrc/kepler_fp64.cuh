@@ -11,7 +11,10 @@
 // from the small Lagrange coefficients f-1, g-tau, fdot, gdot-1,
 //   delta_v = fdot r0 + (gdot-1) v0
 //   delta_r = ((f-1) - post*tau*fdot) r0 + ((g-tau) - post*tau*(gdot-1)) v0,
-// which never subtracts two nearly equal positions.
+// which never subtracts two nearly equal positions.  Every coefficient is
+// proportional to m = m_i + m_j except the period-reduction term (t - tau),
+// so the kernel forms delta / m and weights it by m_j: mu_ij delta / m_i =
+// m_j (delta / m), which is the Eq. 23 increment without a division.
 //
 // Kepler flow in the universal variable s (ds/dt = 1/r):
 //   t(s) = r0 s + eta0 G2(s) + zeta0 G3(s),  r(s) = r0 + eta0 G1 + zeta0 G2,
@@ -22,14 +25,35 @@
 // (Conway 1986), with a bracket safeguard and a bisection fallback.  F is
 // strictly increasing (F' = r > 0) so the root is unique.
 //
+// Laguerre step (n = 5, F' > 0):
+//   ds = 5F / (F' + 4 F' sqrt|1 - u|),  u = (5/4) F F'' / F'^2,
+// rewritten with q = F / F' (the Newton step) as ds = q (1 + k),
+// k = c / (1 - c), c = (4/5) u / (1 + sqrt(1 - u)) for |u| < 1/2 (and
+// k = 5 / (1 + 4 sqrt|1 - u|) - 1 otherwise, far from the root).  q is FP64;
+// k is a correction of size O(u) = O(F) and is formed in FP32, so its
+// rounding vanishes as F -> 0 and the iteration keeps its cubic convergence
+// to the FP64 root.
+//
+// Convergence: the Newton step q = F / F' is the first-order estimate of the
+// remaining |s - root|; a lane stops when |q| <= tol max(|s|, |t| / r), i.e.
+// |ds| <= 4 eps |s| or |F| <= 4 eps max(r |s|, |t|).
+//
 // Stumpff functions c_k(x) = sum_n (-x)^n / (k+2n)!: the argument is
-// quartered until |x| <= 0.1, the series for c2 and c3 is summed to 7 terms
-// (truncation < 1e-17 relative), c0 = 1 - x c2 and c1 = 1 - x c3, and the
-// quarterings are undone with the doubling identities
+// quartered until |x| <= 0.1, the series for c2 and c3 is summed with a
+// warp-uniform number of terms chosen from the largest |x| in the warp
+// (3 terms up to 1e-4, 4 up to 3e-3, 5 up to 2.5e-2, 6 up to 0.1; the first
+// omitted term is below 2^-55 relative), c0 = 1 - x c2, c1 = 1 - x c3, and
+// the quarterings are undone with the doubling identities
 //   c0(4x) = 1 - 4x c2(4x), c1(4x) = c0 c1, c2(4x) = c1^2 / 2,
 //   c3(4x) = (c2 + c0 c3) / 4.
-// No trigonometric or hyperbolic function is called, and the common case
-// (|x| <= 0.1) takes no branch.
+// No trigonometric or hyperbolic function is called.
+//
+// Reciprocals and reciprocal square roots use the hardware approximation
+// (rcp/rsqrt.approx.ftz.f64, relative error below 2^-19) refined by one
+// third-order step of the Newton-Raphson family (Householder order 2),
+//   y <- y (1 + e + e^2),          e = 1 - x y,
+//   y <- y (1 + e/2 + 3 e^2 / 8),  e = 1 - x y^2,
+// which takes the error from d to O(d^3).
 #pragma once
 
 #include <cstdint>
@@ -45,32 +69,118 @@ constexpr unsigned kStatusKepler = 4u;
 constexpr unsigned kStatusMass = 8u;
 constexpr unsigned kStatusTimeout = 16u;
 
+__device__ __forceinline__ double rcp_seed(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    return y;
+}
+
+__device__ __forceinline__ double rsqrt_seed(double x)
+{
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    return y;
+}
+
+// 1/x to about one ulp (x normal and finite): seed error d <= 2^-19, one
+// cubic step y (1 + e + e^2), e = 1 - x y, leaves O(d^3).
+__device__ __forceinline__ double rcp_nr(double x)
+{
+    const double y = rcp_seed(x);
+    const double e = fma(-x, y, 1.0);
+    return fma(y, fma(e, e, e), y);
+}
+
+// 1/sqrt(x) to about one ulp (x > 0 normal and finite): one cubic step
+// y (1 + e/2 + 3 e^2 / 8), e = 1 - x y^2, from a seed with error <= 2^-19.
+__device__ __forceinline__ double rsqrt_nr(double x)
+{
+    const double y = rsqrt_seed(x);
+    const double e = fma(-x, y * y, 1.0);
+    return fma(y * e, fma(0.375, e, 0.5), y);
+}
+
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Comparisons on IEEE bit patterns run on the integer pipe instead of the
+// narrow FP64 pipe.  For doubles that are not NaN, okey() is monotone:
+// a < b  <=>  okey(a) < okey(b).  magbits() is the pattern of |a|, monotone
+// in |a| (NaN compares above +inf).
+__device__ __forceinline__ long long okey(double a)
+{
+    const long long b = __double_as_longlong(a);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+__device__ __forceinline__ long long magbits(double a)
+{
+    return __double_as_longlong(a) & 0x7fffffffffffffffLL;
+}
+
+__device__ __forceinline__ bool is_neg(double a) { return __double_as_longlong(a) < 0; }
+
+constexpr long long kInfBits = 0x7ff0000000000000LL;
+constexpr long long kBits0p1 = 0x3fb999999999999aLL;  // 0.1
+
 struct Stumpff {
     double c0, c1, c2, c3;
 };
 
-__device__ __forceinline__ Stumpff stumpff_fp64(double x)
+// Number of series terms for c2 and c3 when every |x| in the warp has a
+// high word (sign, exponent, top mantissa bits) of at most hx: strictly
+// below the high word of 2^-14, 2^-9 and 2^-6 means |x| < 6.1e-5, 1.95e-3
+// and 1.56e-2, inside the 3-, 4- and 5-term limits above.
+__device__ __forceinline__ int stumpff_terms(unsigned hx)
+{
+    return hx < 0x3f100000u ? 3 : (hx < 0x3f600000u ? 4 : (hx < 0x3f900000u ? 5 : 6));
+}
+
+__device__ __forceinline__ unsigned abs_hiword(double x)
+{
+    return (unsigned)(magbits(x) >> 32);
+}
+
+// c0..c3 at x; nt: warp-uniform number of series terms (3..6) valid for the
+// reduced argument (see stumpff_terms).  Arguments with |x| > 0.1 are quartered first (per lane).
+__device__ __forceinline__ Stumpff stumpff_fp64(double x, int nt)
 {
     int k = 0;
-    while (fabs(x) > 0.1 && k < 80) {
+    while (magbits(x) > kBits0p1 && k < 80) {
         x *= 0.25;
         ++k;
     }
+    if (k > 0) nt = 6;
     const double y = -x;
-    // 1/(2n+2)! and 1/(2n+3)!, n = 0..6
-    double c2 = 1.0 / 87178291200.0;
-    c2 = fma(c2, y, 1.0 / 479001600.0);
-    c2 = fma(c2, y, 1.0 / 3628800.0);
-    c2 = fma(c2, y, 1.0 / 40320.0);
-    c2 = fma(c2, y, 1.0 / 720.0);
+    double c2, c3;
+    // Horner from the highest kept term; 1/(2n+2)! and 1/(2n+3)!
+    if (nt >= 6) {
+        c2 = fma(1.0 / 479001600.0, y, 1.0 / 3628800.0);
+        c3 = fma(1.0 / 6227020800.0, y, 1.0 / 39916800.0);
+        c2 = fma(c2, y, 1.0 / 40320.0);
+        c3 = fma(c3, y, 1.0 / 362880.0);
+        c2 = fma(c2, y, 1.0 / 720.0);
+        c3 = fma(c3, y, 1.0 / 5040.0);
+    } else if (nt == 5) {
+        c2 = fma(1.0 / 3628800.0, y, 1.0 / 40320.0);
+        c3 = fma(1.0 / 39916800.0, y, 1.0 / 362880.0);
+        c2 = fma(c2, y, 1.0 / 720.0);
+        c3 = fma(c3, y, 1.0 / 5040.0);
+    } else if (nt == 4) {
+        c2 = fma(1.0 / 40320.0, y, 1.0 / 720.0);
+        c3 = fma(1.0 / 362880.0, y, 1.0 / 5040.0);
+    } else {
+        c2 = 1.0 / 720.0;
+        c3 = 1.0 / 5040.0;
+    }
     c2 = fma(c2, y, 1.0 / 24.0);
-    c2 = fma(c2, y, 1.0 / 2.0);
-    double c3 = 1.0 / 1307674368000.0;
-    c3 = fma(c3, y, 1.0 / 6227020800.0);
-    c3 = fma(c3, y, 1.0 / 39916800.0);
-    c3 = fma(c3, y, 1.0 / 362880.0);
-    c3 = fma(c3, y, 1.0 / 5040.0);
     c3 = fma(c3, y, 1.0 / 120.0);
+    c2 = fma(c2, y, 0.5);
     c3 = fma(c3, y, 1.0 / 6.0);
     double c0 = fma(y, c2, 1.0);
     double c1 = fma(y, c3, 1.0);
@@ -93,164 +203,202 @@ struct KeplerParams {
     int bisection;    // 1: bisection fallback
 };
 
-struct PairResult {
-    double dr[3];
-    double dv[3];
+// Per-lane state of one pair's Kepler solve.
+struct PairSolve {
+    double x0, y0, z0, vx, vy, vz;  // Kepler input r0 (back-drifted) and v0
+    double r0, ir0, eta0, beta, zeta0, m, t;
+    double s, lo, hi;
+    double G1, G2, G3, Fp, ir;      // at the accepted s (ir = 1 / Fp)
     int iters;
-    int fallback;
+    bool done;
     unsigned status;
 };
 
-// Universal functions G0..G3 at s, and F, F', F''.
-struct KepEval {
-    double G0, G1, G2, G3, F, Fp, Fpp;
-};
-
-__device__ __forceinline__ KepEval kep_eval_fp64(double s, double beta, double r0, double eta0,
-                                                 double zeta0, double t)
+// Setup of one pair: backward drift, invariants, period reduction, guess.
+// rr0, vv0: relative state after the one-subscript drift; m: m_i + m_j.
+// guess: 0 = standard s0 = t/r0; 2 = second order in t, s0 = (t/r0)(1 -
+// eta0 t / (2 r0^2)), from ds/dt = 1/r and d2s/dt2 = -eta0/r0^3 at t = 0.
+__device__ __forceinline__ void pair_setup(PairSolve &p, double tau, double m, double rx,
+                                           double ry, double rz, double vx, double vy,
+                                           double vz, double pre, int guess)
 {
-    const Stumpff c = stumpff_fp64(beta * s * s);
-    KepEval e;
-    const double s2 = s * s;
-    e.G0 = c.c0;
-    e.G1 = s * c.c1;
-    e.G2 = s2 * c.c2;
-    e.G3 = s2 * s * c.c3;
-    e.F = fma(r0, s, fma(eta0, e.G2, fma(zeta0, e.G3, -t)));
-    e.Fp = fma(eta0, e.G1, fma(zeta0, e.G2, r0));
-    e.Fpp = fma(eta0, e.G0, zeta0 * e.G1);
-    return e;
+    const double ptau = pre * tau;
+    p.status = 0;
+    p.iters = 0;
+    p.m = m;
+    p.vx = vx;
+    p.vy = vy;
+    p.vz = vz;
+    p.x0 = fma(-ptau, vx, rx);
+    p.y0 = fma(-ptau, vy, ry);
+    p.z0 = fma(-ptau, vz, rz);
+    const double r0sq = fma(p.x0, p.x0, fma(p.y0, p.y0, p.z0 * p.z0));
+    p.G1 = p.G2 = p.G3 = 0.0;
+    const long long rb = __double_as_longlong(r0sq);
+    if (!(rb > 0 && rb < 0x7e37e43c8800759cLL)) {  // 0 < r0^2 < 1e300, not NaN
+        p.status = (r0sq == 0.0) ? kStatusCoincident : kStatusNonfinite;
+        p.done = true;
+        p.r0 = p.ir0 = 1.0;
+        p.Fp = p.ir = 1.0;
+        p.beta = p.eta0 = p.zeta0 = p.s = 0.0;
+        p.t = tau;
+        p.lo = p.hi = 0.0;
+        return;
+    }
+    p.ir0 = rsqrt_nr(r0sq);
+    p.r0 = r0sq * p.ir0;
+    p.Fp = p.r0;
+    p.ir = p.ir0;
+    p.eta0 = fma(p.x0, vx, fma(p.y0, vy, p.z0 * vz));
+    const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
+    p.beta = fma(2.0 * m, p.ir0, -v2);
+    p.zeta0 = fma(-p.beta, p.r0, m);
+    p.t = tau;
+    // bound orbit with |t| > P = 2 pi m / beta^1.5  <=>  t^2 beta^3 > (2 pi m)^2
+    if (__double_as_longlong(p.beta) > 0) {
+        const double b3 = p.beta * p.beta * p.beta;
+        const double tm = 2.0 * kPi * m;
+        if (okey(tau * tau * b3) > okey(tm * tm)) {
+            const double P = tm * rsqrt_nr(b3);
+            p.t = fmod(tau, P);
+        }
+    }
+    p.s = p.t * p.ir0;  // standard initial guess
+    if (guess == 2) {
+        const double h = 0.5 * p.s;
+        p.s = fma(-h * p.s, p.eta0 * p.ir0, p.s);
+    }
+    if (!is_neg(p.t)) {
+        p.lo = 0.0;
+        p.hi = __longlong_as_double(kInfBits);
+    } else {
+        p.lo = -__longlong_as_double(kInfBits);
+        p.hi = 0.0;
+    }
+    p.done = (magbits(p.t) == 0);
 }
 
-// Pair increments (delta_r, delta_v) of one ordered pair, see the file header.
-// rr0, vv0: relative state after the one-subscript drift; m: m_i + m_j.
-__device__ __forceinline__ PairResult pair_increment_fp64(double tau, double m, double rx,
-                                                          double ry, double rz, double vx,
-                                                          double vy, double vz, double pre,
-                                                          double post, const KeplerParams &kp)
+// One Laguerre iteration of a lane that is not done, at x = beta s^2; nt is
+// warp-uniform.  Returns true when the new iterate would leave the bracket
+// (the caller then applies pair_safeguard in a warp-uniform branch).
+__device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, int nt,
+                                             const KeplerParams &kp)
 {
-    PairResult out;
-    out.iters = 0;
-    out.fallback = 0;
-    out.status = 0;
-    // Eq. 17: backward drift before the Kepler flow
-    const double ptau = pre * tau;
-    const double x0 = fma(-ptau, vx, rx);
-    const double y0 = fma(-ptau, vy, ry);
-    const double z0 = fma(-ptau, vz, rz);
-    const double r0sq = fma(x0, x0, fma(y0, y0, z0 * z0));
-    if (!(r0sq > 0.0)) {
-        out.status = (r0sq == 0.0) ? kStatusCoincident : kStatusNonfinite;
-        for (int q = 0; q < 3; ++q) out.dr[q] = out.dv[q] = 0.0;
-        return out;
+    const double s = p.s;
+    const Stumpff c = stumpff_fp64(x, nt);
+    const double s2 = s * s;
+    const double G1 = s * c.c1;
+    const double G2 = s2 * c.c2;
+    const double G3 = s2 * s * c.c3;
+    const double F = fma(p.r0, s, fma(p.eta0, G2, fma(p.zeta0, G3, -p.t)));
+    const double Fp = fma(p.eta0, G1, fma(p.zeta0, G2, p.r0));
+    const double Fpp = fma(p.eta0, c.c0, p.zeta0 * G1);
+    const double ip = rcp_nr(Fp);
+    const double q = F * ip;
+    p.G1 = G1;
+    p.G2 = G2;
+    p.G3 = G3;
+    p.Fp = Fp;
+    p.ir = ip;
+    ++p.iters;
+    // |q| <= tol * max(|s|, |t| / r)
+    const long long sc = max(magbits(s), magbits(p.t * ip));
+    if (magbits(q) <= magbits(kp.tol * __longlong_as_double(sc))) {
+        p.done = true;
+        return false;
     }
-    const double r0 = sqrt(r0sq);
-    const double ir0 = 1.0 / r0;
-    const double eta0 = fma(x0, vx, fma(y0, vy, z0 * vz));
-    const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
-    const double beta = fma(2.0 * m, ir0, -v2);
-    const double zeta0 = fma(-beta, r0, m);
-    double t = tau;
-    if (beta > 0.0) {
-        const double P = 2.0 * kPi * m / (beta * sqrt(beta));
-        if (fabs(t) > P) t = fmod(t, P);
+    if (is_neg(F))
+        p.lo = s;
+    else
+        p.hi = s;
+    const float u = (float)(1.25 * q * (Fpp * ip));
+    const float r = sqrt_approx(fabsf(1.0f - u));
+    const float cf = __fdividef(0.8f * u, 1.0f + r);
+    const float k = fabsf(u) < 0.5f ? __fdividef(cf, 1.0f - cf)
+                                    : __fdividef(5.0f, fmaf(4.0f, r, 1.0f)) - 1.0f;
+    const double sn = s - fma(q, (double)k, q);
+    const long long ks = okey(sn);
+    if (ks > okey(p.lo) && ks < okey(p.hi)) {
+        p.s = sn;
+        return false;
     }
+    return true;
+}
 
-    KepEval e{0.0, 0.0, 0.0, 0.0, 0.0, r0, 0.0};
-    if (t != 0.0) {
-        double s = t * ir0;  // standard initial guess
-        double lo, hi;
-        if (t > 0.0) {
-            lo = 0.0;
-            hi = __longlong_as_double(0x7ff0000000000000LL);
-        } else {
-            lo = -__longlong_as_double(0x7ff0000000000000LL);
-            hi = 0.0;
-        }
-        bool done = false;
-        int it = 0;
-        for (; it < kp.max_iter; ++it) {
-            e = kep_eval_fp64(s, beta, r0, eta0, zeta0, t);
-            const double scale = fmax(fabs(t), r0 * fabs(s));
-            if (fabs(e.F) <= kp.tol * scale) {
-                done = true;
-                ++it;
-                break;
-            }
-            if (e.F < 0.0)
-                lo = s;
-            else
-                hi = s;
-            const double disc = fma(16.0 * e.Fp, e.Fp, -20.0 * e.F * e.Fpp);
-            const double den = e.Fp + copysign(sqrt(fabs(disc)), e.Fp);
-            const double ds = 5.0 * e.F / den;
-            double sn = s - ds;
-            if (fabs(ds) <= kp.tol * fabs(sn)) {
-                done = true;
-                ++it;
-                break;
-            }
-            if (!(sn > lo && sn < hi)) {
-                if (isinf(hi))
-                    sn = 2.0 * fmax(lo, s);
-                else if (isinf(lo))
-                    sn = 2.0 * fmin(hi, s);
-                else
-                    sn = 0.5 * (lo + hi);
-            }
-            s = sn;
-        }
-        out.iters = it;
-        if (!done) {
-            if (!kp.bisection) {
-                out.status |= kStatusKepler;
-            } else {
-                // expand an open bracket, then bisect to about two ulp
-                out.fallback = 1;
-                for (int q = 0; q < 2100 && isinf(hi); ++q) {
-                    const double c = 2.0 * fmax(lo, fabs(t) * ir0);
-                    e = kep_eval_fp64(c, beta, r0, eta0, zeta0, t);
-                    if (e.F < 0.0) lo = c; else hi = c;
-                }
-                for (int q = 0; q < 2100 && isinf(lo); ++q) {
-                    const double c = 2.0 * fmin(hi, -fabs(t) * ir0);
-                    e = kep_eval_fp64(c, beta, r0, eta0, zeta0, t);
-                    if (e.F > 0.0) hi = c; else lo = c;
-                }
-                double mid = 0.5 * (lo + hi);
-                for (int q = 0; q < 2200; ++q) {
-                    mid = 0.5 * (lo + hi);
-                    if (!(mid > lo && mid < hi)) break;
-                    if (hi - lo <= 2.2204460492503131e-16 * 2.0 * fmax(fabs(lo), fabs(hi))) break;
-                    e = kep_eval_fp64(mid, beta, r0, eta0, zeta0, t);
-                    if (e.F < 0.0) lo = mid;
-                    else if (e.F > 0.0) hi = mid;
-                    else break;
-                    ++out.iters;
-                }
-                e = kep_eval_fp64(mid, beta, r0, eta0, zeta0, t);
-                if (isinf(lo) || isinf(hi)) out.status |= kStatusKepler;
-            }
-        }
+// Replacement iterate when a Laguerre step left the bracket [lo, hi]:
+// double an open bracket's finite end, or bisect a closed one.
+__device__ __forceinline__ void pair_safeguard(PairSolve &p)
+{
+    if (magbits(p.hi) == kInfBits)
+        p.s = 2.0 * fmax(p.lo, p.s);
+    else if (magbits(p.lo) == kInfBits)
+        p.s = 2.0 * fmin(p.hi, p.s);
+    else
+        p.s = 0.5 * (p.lo + p.hi);
+}
+
+// F and its slope at s, with the G functions (bisection path; nt = 6).
+__device__ __forceinline__ double pair_eval(PairSolve &p, double s)
+{
+    const Stumpff c = stumpff_fp64(p.beta * s * s, 6);
+    const double s2 = s * s;
+    p.G1 = s * c.c1;
+    p.G2 = s2 * c.c2;
+    p.G3 = s2 * s * c.c3;
+    p.Fp = fma(p.eta0, p.G1, fma(p.zeta0, p.G2, p.r0));
+    p.ir = rcp_nr(p.Fp);
+    return fma(p.r0, s, fma(p.eta0, p.G2, fma(p.zeta0, p.G3, -p.t)));
+}
+
+// Bounded bisection on the bracket for a lane whose iteration did not
+// converge (rare); sets kStatusKepler if the bracket cannot be closed.
+__device__ __forceinline__ void pair_bisect(PairSolve &p)
+{
+    const double at = fabs(p.t) * p.ir0;
+    for (int q = 0; q < 2100 && isinf(p.hi); ++q) {
+        const double c = 2.0 * fmax(p.lo, at);
+        if (pair_eval(p, c) < 0.0) p.lo = c; else p.hi = c;
     }
-    // Lagrange coefficients in increment form
-    const double r = e.Fp;
-    const double ir = 1.0 / r;
-    const double mG2 = m * e.G2;
-    const double fm1 = -mG2 * ir0;
-    const double gmt = (t - tau) - m * e.G3;
-    const double fd = -m * e.G1 * ir0 * ir;
-    const double gdm1 = -mG2 * ir;
+    for (int q = 0; q < 2100 && isinf(p.lo); ++q) {
+        const double c = 2.0 * fmin(p.hi, -at);
+        if (pair_eval(p, c) > 0.0) p.hi = c; else p.lo = c;
+    }
+    double mid = 0.5 * (p.lo + p.hi);
+    for (int q = 0; q < 2200; ++q) {
+        mid = 0.5 * (p.lo + p.hi);
+        if (!(mid > p.lo && mid < p.hi)) break;
+        if (p.hi - p.lo <= 4.4408920985006262e-16 * fmax(fabs(p.lo), fabs(p.hi))) break;
+        const double F = pair_eval(p, mid);
+        if (F < 0.0) p.lo = mid;
+        else if (F > 0.0) p.hi = mid;
+        else break;
+        ++p.iters;
+    }
+    pair_eval(p, mid);
+    if (isinf(p.lo) || isinf(p.hi)) p.status |= kStatusKepler;
+    p.done = true;
+}
+
+// Increments divided by m = m_i + m_j: out[0..2] = delta_r / m,
+// out[3..5] = delta_v / m.
+__device__ __forceinline__ void pair_increment_over_m(const PairSolve &p, double tau, double post,
+                                                      double out[6])
+{
+    const double ir = p.ir;
+    const double fm1 = -p.G2 * p.ir0;
+    double gmt = -p.G3;
+    if (__double_as_longlong(p.t) != __double_as_longlong(tau)) gmt += (p.t - tau) * rcp_nr(p.m);
+    const double fd = -p.G1 * p.ir0 * ir;
+    const double gdm1 = -p.G2 * ir;
     const double qtau = post * tau;
     const double A = fma(-qtau, fd, fm1);
     const double B = fma(-qtau, gdm1, gmt);
-    out.dv[0] = fma(fd, x0, gdm1 * vx);
-    out.dv[1] = fma(fd, y0, gdm1 * vy);
-    out.dv[2] = fma(fd, z0, gdm1 * vz);
-    out.dr[0] = fma(A, x0, B * vx);
-    out.dr[1] = fma(A, y0, B * vy);
-    out.dr[2] = fma(A, z0, B * vz);
-    return out;
+    out[3] = fma(fd, p.x0, gdm1 * p.vx);
+    out[4] = fma(fd, p.y0, gdm1 * p.vy);
+    out[5] = fma(fd, p.z0, gdm1 * p.vz);
+    out[0] = fma(A, p.x0, B * p.vx);
+    out[1] = fma(A, p.y0, B * p.vy);
+    out[2] = fma(A, p.z0, B * p.vz);
 }
 
 }  // namespace sakura

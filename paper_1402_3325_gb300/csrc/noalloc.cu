@@ -12,7 +12,7 @@
 //
 // Limits and sharing rules:
 //   - n <= SAKURA_NOALLOC_MAX_N (65536); larger n returns SAKURA_E_ARG.
-//   - The scratch (6 x 65536 doubles = 3 MiB) and the status word are shared
+//   - The scratch (20 x 65536 doubles = 10 MiB) and the status word are shared
 //     by every call on a device and keep the last call's contents.  Every
 //     scratch entry a call reads is written earlier in the same call; the
 //     status word is cleared at the start of each call.  Calls whose work
@@ -33,7 +33,10 @@
 namespace {
 
 constexpr int64_t kMaxN = SAKURA_NOALLOC_MAX_N;
-constexpr int64_t kScratchDoubles = 6 * kMaxN;
+// drifted state X[7][n] plus the pair kernel's row partials: for W warps at
+// most (ceil(W/n) + 1) slots of 6 n doubles, i.e. 7n + 6W + 12n doubles;
+// 20 * kMaxN covers W up to 65536 warps.
+constexpr int64_t kScratchDoubles = 20 * kMaxN;
 constexpr int kMaxDevices = 64;
 
 // The host-side names below are stand-ins for device memory: host code never
@@ -105,39 +108,42 @@ extern "C" int sakura_step_noalloc(double *state, const double *masses, int64_t 
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
 
-    // j segments: enough blocks to fill the GPU, within the fixed scratch
-    const int warps = 8;
-    const int64_t iblocks = (n + warps - 1) / warps;
-    int64_t nsplit = ((int64_t)d->sm_count * 4 + iblocks - 1) / iblocks;
-    nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, n / 128));
-    nsplit = std::min<int64_t>(nsplit, kScratchDoubles / (6 * n));
-    nsplit = std::max<int64_t>(1, nsplit);
+    // persistent grid: one wave of resident blocks, within the fixed scratch
+    const int warps = 4;
+    const int64_t nb = (n + 31) / 32;
+    const int64_t B = n * nb;
+    int64_t blocks = (int64_t)d->sm_count * sakura::pair_step_fp64_blocks_per_sm(warps, false);
+    // at most one warp per 32-pair batch, so every slot of a row is written
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, B / warps));
+    while (blocks > 1 &&
+           7 * n + sakura::pair_step_slots(n, blocks * warps) * 6 * n > kScratchDoubles)
+        blocks /= 2;
+    const int64_t W = blocks * warps;
+    double *X = d->scratch;
+    double *partial = X + 7 * n;
 
     if (cudaMemsetAsync(d->status, 0, sizeof(unsigned), s) != cudaSuccess) {
         cudaGetLastError();
         return SAKURA_E_CUDA;
     }
+    const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
+    const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
+    sakura::launch_prep_step(state, masses, X, n, drift, d->status, s);
     sakura::StepArgs a;
-    a.state = state;
-    a.mass = masses;
-    a.partial = d->scratch;
+    a.X = X;
+    a.partial = partial;
     a.n = n;
-    a.jchunk = (n + nsplit - 1) / nsplit;
     a.tau = dt;
-    a.drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     a.pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
     a.post = 1.0 - a.pre;
     a.tol = 4.0 * DBL_EPSILON;
     a.max_iter = 50;
     a.bisection = 1;
+    a.guess = 0;
     a.status = d->status;
     a.stats = nullptr;
-    int used_split = (int)nsplit;
-    if (n > 1)
-        sakura::launch_pair_step_fp64(a, warps, used_split, false, s);
-    else
-        used_split = 0;
-    sakura::launch_apply_step(state, masses, d->scratch, n, used_split, dt, order, d->status, s);
+    if (n > 1) sakura::launch_pair_step_fp64(a, warps, (int)blocks, false, s);
+    sakura::launch_apply_step(state, X, partial, n, n > 1 ? W : 0, post_drift, d->status, s);
     if (cudaGetLastError() != cudaSuccess) return SAKURA_E_CUDA;
     unsigned st = 0;
     if (cudaMemcpyAsync(&st, d->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) !=

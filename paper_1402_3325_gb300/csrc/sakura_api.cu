@@ -7,6 +7,7 @@
 
 #include <cfloat>
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -117,52 +118,60 @@ int drain_status()
 
 struct Plan {
     int warps;
-    int nsplit;
-    int64_t jchunk;
+    int blocks;
+    int64_t W;  // warps in the persistent pair-kernel grid
 };
 
+// Launch shape of the persistent pair kernel: one wave of resident blocks
+// (or grid_blocks), never more warps than 32-pair batches: with W <= B every
+// warp owns at least one batch, so the slots of a row are all written.  (For
+// n <= 32 a row is a single batch and W may exceed B harmlessly.)
 Plan plan_step(int64_t n)
 {
     Plan p;
-    p.warps = g.cfg.block_warps > 0 ? g.cfg.block_warps : 8;
-    if (p.warps != 4 && p.warps != 8 && p.warps != 16) p.warps = 8;
-    const int64_t iblocks = (n + p.warps - 1) / p.warps;
-    int64_t ns = g.cfg.j_split;
-    if (ns <= 0) {
-        const int64_t target = (int64_t)g.sm_count * 4;
-        ns = (target + iblocks - 1) / iblocks;
-        const int64_t cap = std::max<int64_t>(1, n / 128);
-        ns = std::min(ns, cap);
+    p.warps = g.cfg.block_warps > 0 ? g.cfg.block_warps : 4;
+    if (p.warps != 4 && p.warps != 8 && p.warps != 16) p.warps = 4;
+    const int64_t nb = (n + 31) / 32;
+    const int64_t B = n * nb;
+    int64_t blocks = g.cfg.grid_blocks;
+    if (blocks <= 0) {
+        const int bps = sakura::pair_step_fp64_blocks_per_sm(
+            p.warps, (g.cfg.flags & SAKURA_FLAG_STATS) != 0);
+        blocks = (int64_t)g.sm_count * bps;
     }
-    ns = std::max<int64_t>(1, std::min<int64_t>(ns, std::max<int64_t>(1, n)));
-    ns = std::min<int64_t>(ns, 65535);
-    p.nsplit = (int)ns;
-    p.jchunk = (n + ns - 1) / ns;
+    blocks = std::min<int64_t>(blocks, std::max<int64_t>(1, B / p.warps));
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, 1 << 20));
+    p.blocks = (int)blocks;
+    p.W = blocks * p.warps;
     return p;
 }
 
 int step_device(double *state, const double *masses, int64_t n, double dt, int order)
 {
     const Plan p = plan_step(n);
-    int rc = grow(g.partial, (size_t)p.nsplit * 6 * (size_t)n * sizeof(double));
+    const int64_t slots = sakura::pair_step_slots(n, p.W);
+    int rc = grow(g.partial, (size_t)(7 * n + slots * 6 * n) * sizeof(double));
     if (rc) return rc;
+    double *X = (double *)g.partial.ptr;
+    double *partial = X + 7 * n;
+    const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
+    const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
+    sakura::launch_prep_step(state, masses, X, n, drift, g.d_status, g.stream);
     sakura::StepArgs a;
-    a.state = state;
-    a.mass = masses;
-    a.partial = (double *)g.partial.ptr;
+    a.X = X;
+    a.partial = partial;
     a.n = n;
-    a.jchunk = p.jchunk;
     a.tau = dt;
-    a.drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     a.pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
     a.post = 1.0 - a.pre;
     a.tol = g.cfg.kepler_tol * DBL_EPSILON;
     a.max_iter = g.cfg.kepler_max_iter;
     a.bisection = g.cfg.kepler_bisection;
+    a.guess = g.cfg.guess == SAKURA_GUESS_TAYLOR ? 2 : 0;
     a.status = g.d_status;
     a.stats = g.d_stats;
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
-    int nsplit = p.nsplit;
+    int64_t W = p.W;
     if (n > 1) {
         const bool timing = (g.cfg.flags & SAKURA_FLAG_TIMING) != 0;
         std::pair<cudaEvent_t, cudaEvent_t> tm{nullptr, nullptr};
@@ -170,16 +179,15 @@ int step_device(double *state, const double *masses, int64_t n, double dt, int o
             tm = take_timer();
             cudaEventRecord(tm.first, g.stream);
         }
-        sakura::launch_pair_step_fp64(a, p.warps, p.nsplit, stats, g.stream);
+        sakura::launch_pair_step_fp64(a, p.warps, p.blocks, stats, g.stream);
         if (timing) {
             cudaEventRecord(tm.second, g.stream);
             g.timers.push_back(tm);
         }
     } else {
-        nsplit = 0;  // a single particle only drifts
+        W = 0;  // a single particle only drifts
     }
-    sakura::launch_apply_step(state, masses, (const double *)g.partial.ptr, n, nsplit, dt, order,
-                              g.d_status, g.stream);
+    sakura::launch_apply_step(state, X, partial, n, W, post_drift, g.d_status, g.stream);
     rc = launch_error();
     if (rc) return rc;
     g.steps += 1;
@@ -210,7 +218,7 @@ void sakura_default_config(sakura_config *cfg)
     cfg->kepler_bisection = 1;
     cfg->flags = 0;
     cfg->block_warps = 0;
-    cfg->j_split = 0;
+    cfg->grid_blocks = 0;
 }
 
 int sakura_init(const sakura_config *cfg)
@@ -223,7 +231,9 @@ int sakura_init(const sakura_config *cfg)
     if (c.kepler_max_iter < 1 || c.kepler_max_iter > 10000 || !(c.kepler_tol > 0.0))
         return SAKURA_E_ARG;
     if (c.precision != SAKURA_PREC_FP64 && c.precision != SAKURA_PREC_MIXED) return SAKURA_E_ARG;
-    if (c.guess != SAKURA_GUESS_STANDARD && c.guess != SAKURA_GUESS_LEARNED) return SAKURA_E_ARG;
+    if (c.guess != SAKURA_GUESS_STANDARD && c.guess != SAKURA_GUESS_LEARNED &&
+        c.guess != SAKURA_GUESS_TAYLOR)
+        return SAKURA_E_ARG;
     if (cudaSetDevice(c.device) != cudaSuccess) {
         cudaGetLastError();
         return SAKURA_E_CUDA;

@@ -16,25 +16,30 @@ constexpr int kStatFp32Pairs = 4;
 constexpr int kStatCount = 8;
 
 struct StepArgs {
-    const double *state;  // [6][n] pre-step state (read only)
-    const double *mass;   // [n]
-    double *partial;      // [nsplit][6][n] per-segment row sums of mu * delta
+    const double *X;      // [7][n] drifted positions, velocities, masses (prep kernel)
+    double *partial;      // [slots][6][n] row sums of mu_ij delta / m_i, split by warp
     int64_t n;
-    int64_t jchunk;       // j segment length
     double tau;
-    double drift;         // one-subscript drift applied to loaded positions
     double pre, post;     // backward-drift fractions of the pair map
     double tol;           // Kepler tolerance (x DBL_EPSILON)
     int max_iter;
     int bisection;
+    int guess;            // 0 standard, 2 second-order analytic
     unsigned *status;
     unsigned long long *stats;
 };
 
-void launch_pair_step_fp64(const StepArgs &a, int warps, int nsplit, bool stats,
+// pair kernel: one persistent wave of `blocks` blocks of `warps` warps
+void launch_pair_step_fp64(const StepArgs &a, int warps, int blocks, bool stats,
                            cudaStream_t s);
-void launch_apply_step(double *state, const double *mass, const double *partial, int64_t n,
-                       int nsplit, double tau, int order, unsigned *status, cudaStream_t s);
+int pair_step_fp64_blocks_per_sm(int warps, bool stats);
+// number of partial-sum slots per row for W warps
+int pair_step_slots(int64_t n, int64_t W);
+void launch_prep_step(const double *state, const double *mass, double *X, int64_t n,
+                      double drift, unsigned *status, cudaStream_t s);
+// W = 0: no pair sums (n = 1)
+void launch_apply_step(double *state, const double *X, const double *partial, int64_t n,
+                       int64_t W, double post_drift, unsigned *status, cudaStream_t s);
 void launch_energy(const double *state, const double *mass, int64_t n, double *work,
                    int nwork, double *out, unsigned *status, cudaStream_t s);
 int energy_work_size(int64_t n);

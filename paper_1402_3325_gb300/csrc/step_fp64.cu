@@ -1,17 +1,24 @@
 // step_fp64.cu -- FP64 W-step kernels of the Sakura integrator.
 //
-// One step = pair kernel + apply kernel, both on the library stream.
+// One step = prep kernel + pair kernel + apply kernel, on the library stream.
 //
-// pair kernel: block = WARPS warps; warp w of block b owns row
-//   i = b * WARPS + w and block column y owns the j segment
-//   [y * jchunk, (y+1) * jchunk).  The block stages j-tiles of 256 particles
-//   (positions drifted on load, velocities, masses; 14 KB) in shared memory;
-//   lane l of a warp solves the pairs (i, j) with j = tile + l + 32k.  Each lane
-//   keeps six FP64 accumulators of mu_ij * (delta_r, delta_v) (Eq. 23); the
-//   warp reduces them with xor shuffles and lane 0 stores the row's partial
-//   sum for its segment in partial[y][6][n].  No atomics touch FP64 data.
-// apply kernel: sums the segments in a fixed order (deterministic) and
-//   applies Eqs. 27b-d (or the order-1 forms) to the state in place.
+// prep kernel: writes the drifted structure-of-arrays X[7][n] = (x, y, z
+//   after the one-subscript drift, vx, vy, vz, m) once per step (Eq. 27a or
+//   the order-1 forms), so no pair recomputes a drift.
+// pair kernel: a persistent launch of one wave of resident warps.  The
+//   ordered pairs are cut into B = n * ceil(n/32) batches (row i, 32
+//   consecutive j); warp w owns the contiguous batch range [w B / W,
+//   (w+1) B / W), so every warp gets the same number of batches (+-1) and
+//   crosses a row boundary about ceil(W/n) times at most.  Lane l of a batch
+//   solves the pair (i, j = 32 jb + l).  The Laguerre iterations of a batch
+//   run warp-synchronously (converged lanes idle; the Stumpff term count is
+//   chosen per warp).  Each lane keeps six FP64 accumulators of
+//   m_j (delta_r, delta_v) / m_ij = mu_ij (delta_r, delta_v) / m_i (Eq. 23);
+//   when the warp leaves a row it reduces them with xor shuffles and lane 0
+//   stores the row partial in slot k = w - owner(first batch of row i).  No
+//   atomics touch FP64 data.
+// apply kernel: sums a row's slots in slot order (deterministic for a given
+//   grid) and applies Eqs. 27b-d, or the order-1 forms, in place.
 #include <cuda_runtime.h>
 
 #include "kepler_fp64.cuh"
@@ -19,98 +26,138 @@
 
 namespace sakura {
 
+// Warp that owns batch b when B batches are split over W warps as
+// [w B / W, (w+1) B / W).
+__device__ __host__ __forceinline__ int64_t batch_owner(int64_t b, int64_t B, int64_t W)
+{
+    return ((b + 1) * W - 1) / B;
+}
+
+// X[7][n]: drifted positions, velocities, masses.
+__global__ void prep_step_kernel(const double *state, const double *mass, double *X, int64_t n,
+                                 double drift, unsigned *status)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double m = mass[i];
+    if (!(m > 0.0)) atomicOr(status, kStatusMass);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double v = state[(3 + q) * n + i];
+        X[q * n + i] = fma(v, drift, state[q * n + i]);
+        X[(3 + q) * n + i] = v;
+    }
+    X[6 * n + i] = m;
+}
+
 template <int WARPS, bool STATS>
 __global__ void __launch_bounds__(WARPS * 32)
     pair_step_fp64_kernel(StepArgs a)
 {
-    constexpr int kTile = 256;
-    __shared__ double sx[kTile], sy[kTile], sz[kTile], svx[kTile], svy[kTile], svz[kTile],
-        sm[kTile];
-    const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int64_t n = a.n;
-    const int64_t i = (int64_t)blockIdx.x * WARPS + warp;
-    const bool row = i < n;
-    const int64_t j0 = (int64_t)blockIdx.y * a.jchunk;
-    const int64_t j1 = min(n, j0 + a.jchunk);
+    const int64_t nb = (n + 31) >> 5;
+    const int64_t B = n * nb;
+    const int64_t W = (int64_t)gridDim.x * WARPS;
+    const int64_t w = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    const int64_t b0 = w * B / W;
+    const int64_t b1 = (w + 1) * B / W;
+    const double *X = a.X;
+    const KeplerParams kp{a.tol, a.max_iter, a.bisection};
 
-    double xi = 0, yi = 0, zi = 0, vxi = 0, vyi = 0, vzi = 0, mi = 1;
-    if (row) {
-        vxi = a.state[3 * n + i];
-        vyi = a.state[4 * n + i];
-        vzi = a.state[5 * n + i];
-        xi = fma(vxi, a.drift, a.state[i]);
-        yi = fma(vyi, a.drift, a.state[n + i]);
-        zi = fma(vzi, a.drift, a.state[2 * n + i]);
-        mi = a.mass[i];
-    }
-    double acc[6] = {0, 0, 0, 0, 0, 0};
     unsigned status = 0;
     long long it_sum = 0, slots = 0, fallbacks = 0;
     int it_max = 0;
-    const KeplerParams kp{a.tol, a.max_iter, a.bisection};
 
-    for (int64_t jt = j0; jt < j1; jt += kTile) {
-        __syncthreads();
-        for (int q = threadIdx.x; q < kTile; q += WARPS * 32) {
-            const int64_t j = jt + q;
-            if (j < j1) {
-                const double vx = a.state[3 * n + j], vy = a.state[4 * n + j],
-                             vz = a.state[5 * n + j];
-                svx[q] = vx;
-                svy[q] = vy;
-                svz[q] = vz;
-                sx[q] = fma(vx, a.drift, a.state[j]);
-                sy[q] = fma(vy, a.drift, a.state[n + j]);
-                sz[q] = fma(vz, a.drift, a.state[2 * n + j]);
-                sm[q] = a.mass[j];
+    int64_t i = b0 / nb;
+    int64_t jb = b0 - i * nb;
+    double xi = 0, yi = 0, zi = 0, vxi = 0, vyi = 0, vzi = 0, mi = 1;
+    if (b0 < b1) {
+        xi = X[i];
+        yi = X[n + i];
+        zi = X[2 * n + i];
+        vxi = X[3 * n + i];
+        vyi = X[4 * n + i];
+        vzi = X[5 * n + i];
+        mi = X[6 * n + i];
+    }
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t b = b0; b < b1; ++b) {
+        const int64_t j = (jb << 5) + lane;
+        const bool valid = (j < n) && (j != i);
+        PairSolve p;
+        double mj = 0.0;
+        if (valid) {
+            mj = X[6 * n + j];
+            pair_setup(p, a.tau, mi + mj, xi - X[j], yi - X[n + j], zi - X[2 * n + j],
+                       vxi - X[3 * n + j], vyi - X[4 * n + j], vzi - X[5 * n + j], a.pre, a.guess);
+        } else {
+            p.done = true;
+            p.beta = p.s = 0.0;
+            p.iters = 0;
+            p.status = 0;
+        }
+        // warp-synchronous Laguerre iterations: converged lanes idle
+        for (int it = 0; it < kp.max_iter; ++it) {
+            if (__all_sync(0xffffffffu, p.done)) break;
+            const double x = p.beta * p.s * p.s;
+            const unsigned hx = p.done ? 0u : abs_hiword(x);
+            const int nt = stumpff_terms(__reduce_max_sync(0xffffffffu, hx));
+            bool oob = false;
+            if (!p.done) oob = pair_iterate(p, x, nt, kp);
+            if (__any_sync(0xffffffffu, oob)) {
+                if (oob) pair_safeguard(p);
             }
         }
-        __syncthreads();
-        if (!row) continue;
-        const int cnt = (int)min((int64_t)kTile, j1 - jt);
-        // every lane runs the same trip count; invalid slots are predicated
-        for (int kb = 0; kb < cnt; kb += 32) {
-            const int k = kb + lane;
-            const int64_t j = jt + k;
-            const bool valid = (k < cnt) && (j != i);
-            int iters = 0;
-            if (valid) {
-                const double mj = sm[k];
-                const double mij = mi + mj;
-                const double mu = mi * mj / mij;
-                PairResult p = pair_increment_fp64(a.tau, mij, xi - sx[k], yi - sy[k],
-                                                   zi - sz[k], vxi - svx[k], vyi - svy[k],
-                                                   vzi - svz[k], a.pre, a.post, kp);
-                status |= p.status;
+        int fb = 0;
+        if (!p.done) {
+            if (kp.bisection) {
+                pair_bisect(p);
+                fb = 1;
+            } else {
+                p.status |= kStatusKepler;
+            }
+        }
+        if (valid) {
+            double d[6];
+            pair_increment_over_m(p, a.tau, a.post, d);
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    acc[q] = fma(mu, p.dr[q], acc[q]);
-                    acc[3 + q] = fma(mu, p.dv[q], acc[3 + q]);
+            for (int q = 0; q < 6; ++q) acc[q] = fma(mj, d[q], acc[q]);
+            status |= p.status;
+        }
+        if (STATS) {
+            const int iters = valid ? p.iters : 0;
+            it_sum += iters;
+            fallbacks += fb;
+            it_max = max(it_max, iters);
+            const int wmax = __reduce_max_sync(0xffffffffu, iters);
+            if (lane == 0) slots += 32LL * wmax;
+        }
+        // leaving row i: reduce and store its partial
+        if (++jb == nb || b + 1 == b1) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                double v = acc[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                acc[q] = 0.0;
+                if (lane == 0) {
+                    const int64_t k = w - batch_owner(i * nb, B, W);
+                    a.partial[(k * 6 + q) * n + i] = v;
                 }
-                iters = p.iters;
-                fallbacks += p.fallback;
             }
-            if (STATS) {
-                it_sum += iters;
-                it_max = max(it_max, iters);
-                const int wmax = __reduce_max_sync(0xffffffffu, iters);
-                if (lane == 0) slots += 32LL * wmax;
+            if (b + 1 < b1) {
+                ++i;
+                jb = 0;
+                xi = X[i];
+                yi = X[n + i];
+                zi = X[2 * n + i];
+                vxi = X[3 * n + i];
+                vyi = X[4 * n + i];
+                vzi = X[5 * n + i];
+                mi = X[6 * n + i];
             }
         }
-    }
-    // warp reduction of the six row sums
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        double v = acc[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        acc[q] = v;
-    }
-    if (row && lane == 0) {
-        double *dst = a.partial + (int64_t)blockIdx.y * 6 * n;
-#pragma unroll
-        for (int q = 0; q < 6; ++q) dst[q * n + i] = acc[q];
     }
     status = __reduce_or_sync(0xffffffffu, status);
     if (lane == 0 && status) atomicOr(a.status, status);
@@ -132,88 +179,105 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
 }
 
-// Eqs. 27b-d (order 2) and the first-order forms; sums segment partials in
-// segment order.
-__global__ void apply_step_kernel(double *state, const double *mass, const double *partial,
-                                  int64_t n, int nsplit, double tau, int order,
-                                  unsigned *status)
+// Eqs. 27b-d (order 2) and the first-order forms.  The slots of row i hold
+// sum_j m_j delta_ij / m_ij = sum_j mu_ij delta_ij / m_i (Eq. 23) split by
+// warp; they are added in slot order.  Positions come from X (after the
+// first drift), so  x_new = X_pos + dr + post_drift * v_new.
+__global__ void apply_step_kernel(double *state, const double *X, const double *partial,
+                                  int64_t n, int64_t W, double post_drift, unsigned *status)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double d[6] = {0, 0, 0, 0, 0, 0};
-    for (int s = 0; s < nsplit; ++s) {
-        const double *src = partial + (int64_t)s * 6 * n;
+    if (W > 0) {
+        const int64_t nb = (n + 31) >> 5;
+        const int64_t B = n * nb;
+        const int64_t k1 = batch_owner((i + 1) * nb - 1, B, W) - batch_owner(i * nb, B, W);
+        for (int64_t k = 0; k <= k1; ++k) {
 #pragma unroll
-        for (int q = 0; q < 6; ++q) d[q] += src[q * n + i];
+            for (int q = 0; q < 6; ++q) d[q] += partial[(k * 6 + q) * n + i];
+        }
     }
-    const double m = mass[i];
     unsigned st = 0;
-    if (!(m > 0.0)) st |= kStatusMass;
-    double x[3], v[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        x[q] = state[q * n + i];
-        v[q] = state[(3 + q) * n + i];
-    }
-    if (order == 2) {
-        const double h = 0.5 * tau;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const double xh = fma(v[q], h, x[q]);        // 27a
-            const double xt = xh + d[q] / m;             // 27b
-            const double v1 = v[q] + d[3 + q] / m;       // 27c
-            x[q] = fma(v1, h, xt);                       // 27d
-            v[q] = v1;
-        }
-    } else if (order == 1) {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const double xw = x[q] + d[q] / m;
-            const double vw = v[q] + d[3 + q] / m;
-            x[q] = fma(vw, tau, xw);
-            v[q] = vw;
-        }
-    } else {
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const double xd = fma(v[q], tau, x[q]);
-            x[q] = xd + d[q] / m;
-            v[q] = v[q] + d[3 + q] / m;
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        if (!isfinite(x[q]) || !isfinite(v[q])) st |= kStatusNonfinite;
-        state[q * n + i] = x[q];
-        state[(3 + q) * n + i] = v[q];
+        const double v1 = X[(3 + q) * n + i] + d[3 + q];   // 27c
+        const double xt = X[q * n + i] + d[q];             // 27b
+        const double x1 = fma(v1, post_drift, xt);         // 27d
+        if (!isfinite(x1) || !isfinite(v1)) st |= kStatusNonfinite;
+        state[q * n + i] = x1;
+        state[(3 + q) * n + i] = v1;
     }
     if (st) atomicOr(status, st);
 }
 
-void launch_pair_step_fp64(const StepArgs &a, int warps, int nsplit, bool stats,
+int pair_step_slots(int64_t n, int64_t W)
+{
+    return (int)((W + n - 1) / n + 1);
+}
+
+void launch_prep_step(const double *state, const double *mass, double *X, int64_t n,
+                      double drift, unsigned *status, cudaStream_t s)
+{
+    const int threads = 256;
+    prep_step_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(state, mass, X,
+                                                                                 n, drift, status);
+}
+
+void launch_pair_step_fp64(const StepArgs &a, int warps, int blocks, bool stats,
                            cudaStream_t s)
 {
-    const dim3 grid((unsigned)((a.n + warps - 1) / warps), (unsigned)nsplit);
+    const dim3 grid((unsigned)blocks);
 #define SAKURA_LAUNCH(W)                                                               \
     if (stats)                                                                         \
         pair_step_fp64_kernel<W, true><<<grid, W * 32, 0, s>>>(a);                     \
     else                                                                               \
         pair_step_fp64_kernel<W, false><<<grid, W * 32, 0, s>>>(a);
     switch (warps) {
-    case 4: SAKURA_LAUNCH(4) break;
+    case 8: SAKURA_LAUNCH(8) break;
     case 16: SAKURA_LAUNCH(16) break;
-    default: SAKURA_LAUNCH(8) break;
+    default: SAKURA_LAUNCH(4) break;
     }
 #undef SAKURA_LAUNCH
 }
 
-void launch_apply_step(double *state, const double *mass, const double *partial, int64_t n,
-                       int nsplit, double tau, int order, unsigned *status, cudaStream_t s)
+int pair_step_fp64_blocks_per_sm(int warps, bool stats)
+{
+    int b = 0;
+    cudaError_t e;
+    switch (warps) {
+    case 8:
+        e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        &b, pair_step_fp64_kernel<8, true>, 8 * 32, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        &b, pair_step_fp64_kernel<8, false>, 8 * 32, 0);
+        break;
+    case 16:
+        e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        &b, pair_step_fp64_kernel<16, true>, 16 * 32, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        &b, pair_step_fp64_kernel<16, false>, 16 * 32, 0);
+        break;
+    default:
+        e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        &b, pair_step_fp64_kernel<4, true>, 4 * 32, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        &b, pair_step_fp64_kernel<4, false>, 4 * 32, 0);
+        break;
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return b > 0 ? b : 1;
+}
+
+void launch_apply_step(double *state, const double *X, const double *partial, int64_t n,
+                       int64_t W, double post_drift, unsigned *status, cudaStream_t s)
 {
     const int threads = 256;
     const unsigned blocks = (unsigned)((n + threads - 1) / threads);
-    apply_step_kernel<<<blocks, threads, 0, s>>>(state, mass, partial, n, nsplit, tau, order,
-                                                 status);
+    apply_step_kernel<<<blocks, threads, 0, s>>>(state, X, partial, n, W, post_drift, status);
 }
 
 }  // namespace sakura

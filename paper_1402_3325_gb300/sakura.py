@@ -35,6 +35,7 @@ MIXED_RULE_LITERAL = 0
 MIXED_RULE_HYP = 1
 GUESS_STANDARD = 0
 GUESS_LEARNED = 1
+GUESS_TAYLOR = 2
 FLAG_SYNC_CHECK = 1
 FLAG_STATS = 2
 FLAG_TIMING = 4
@@ -57,7 +58,7 @@ class Config(ctypes.Structure):
         ("kepler_bisection", ctypes.c_int),
         ("flags", ctypes.c_uint),
         ("block_warps", ctypes.c_int),
-        ("j_split", ctypes.c_int),
+        ("grid_blocks", ctypes.c_int),
     ]
 
 

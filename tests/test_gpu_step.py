@@ -84,18 +84,42 @@ def test_step_matches_oracle(name, s, order):
     assert er <= TOL and ev <= TOL, (er, ev)
 
 
-def test_plummer_1024_step_matches_oracle():
+@pytest.mark.parametrize("guess", [sk.GUESS_STANDARD, sk.GUESS_TAYLOR])
+def test_plummer_1024_step_matches_oracle(guess):
     s = ics.plummer(1024, seed=0)
-    r, v = gpu_step(s, s.dt, 2)
+    with configured(guess=guess):
+        r, v = gpu_step(s, s.dt, 2)
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
     er, ev = rel_err(r, v, rr, vr)
     assert er <= TOL and ev <= TOL, (er, ev)
 
 
-@pytest.mark.parametrize("warps,split", [(4, 1), (8, 3), (16, 7), (8, 64)])
-def test_launch_shapes_match_oracle(warps, split):
+@pytest.mark.parametrize("order", [2, 1, -1])
+def test_taylor_guess_small_systems(order):
+    for name, s in SMALL[:6]:
+        with configured(guess=sk.GUESS_TAYLOR):
+            r, v = gpu_step(s, s.dt, order)
+        rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, order, nthreads=NCPU)
+        er, ev = rel_err(r, v, rr, vr)
+        assert er <= TOL and ev <= TOL, (name, er, ev)
+
+
+def test_taylor_guess_reduces_iterations():
+    s = ics.plummer(1024, seed=0)
+    its = {}
+    for guess in (sk.GUESS_STANDARD, sk.GUESS_TAYLOR):
+        with configured(guess=guess):
+            sk.get_stats(reset=True)
+            gpu_step(s, s.dt, 2)
+            st = sk.get_stats(reset=True)
+        its[guess] = st["iters"] / st["pairs"]
+    assert its[sk.GUESS_TAYLOR] < its[sk.GUESS_STANDARD] - 0.2
+
+
+@pytest.mark.parametrize("warps,blocks", [(4, 1), (8, 3), (16, 7), (4, 77), (8, 5000)])
+def test_launch_shapes_match_oracle(warps, blocks):
     s = ics.random_cluster(1000, seed=21, mass_spread=1.0)
-    with configured(block_warps=warps, j_split=split):
+    with configured(block_warps=warps, grid_blocks=blocks):
         r, v = gpu_step(s, s.dt, 2)
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
     er, ev = rel_err(r, v, rr, vr)
@@ -129,9 +153,11 @@ def test_full_size_bh_cluster_sampled():
     assert er <= TOL and ev <= TOL, (er, ev)
 
 
-def test_full_size_plummer_binaries_sampled():
+@pytest.mark.parametrize("guess", [sk.GUESS_STANDARD, sk.GUESS_TAYLOR])
+def test_full_size_plummer_binaries_sampled(guess):
     s = ics.plummer_binaries(16384, seed=0)
-    er, ev = _full_size_sample(s, seed=1)
+    with configured(guess=guess):
+        er, ev = _full_size_sample(s, seed=1)
     assert er <= TOL and ev <= TOL, (er, ev)
 
 
