@@ -230,6 +230,11 @@ def main():
                     choices=["plummer1024", "bh16384", "binaries16384", "planetary9"])
     ap.add_argument("--guess", default="taylor", choices=["standard", "taylor"],
                     help="Kepler initial guess: t/r0 or the second-order expansion")
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"],
+                    help="fp64: every pair in FP64; mixed: FP32 solves for the pairs the"
+                         " class rule admits, FP64 for the rest and all accumulation")
+    ap.add_argument("--mixed-rule", default="hyp", choices=["literal", "hyp"],
+                    help="literal: FP32 iff r > 0.1 and e < 0.9; hyp: ... or e > 10")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -266,20 +271,28 @@ def main():
     s, _, desc = _workload(args.workload, seed=rank)
     n = s.n
     guess = sk.GUESS_TAYLOR if args.guess == "taylor" else sk.GUESS_STANDARD
-    sk.init(device.index, stream=stream.cuda_stream, guess=guess)
+    form_opts = {}
+    if args.form == "mixed":
+        form_opts = dict(precision=sk.PREC_MIXED,
+                         mixed_rule=sk.MIXED_RULE_HYP if args.mixed_rule == "hyp"
+                         else sk.MIXED_RULE_LITERAL)
+    sk.init(device.index, stream=stream.cuda_stream, guess=guess, **form_opts)
 
     state = torch.tensor(s.soa(), device=device)
     mass = torch.tensor(s.m, device=device)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)
 
     # warm-up, then the mean Kepler iteration count of this workload
-    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_STATS, guess=guess)
+    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_STATS, guess=guess,
+            **form_opts)
     for _ in range(args.warmup):
         sk.step(state, mass, s.dt, 2)
     sk.check()
     st = sk.get_stats(reset=True)
     kbar = st["iters"] / max(1, st["pairs"])
-    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_TIMING, guess=guess)
+    fp32_share = st["fp32_pairs"] / max(1, st["pairs"])
+    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_TIMING, guess=guess,
+            **form_opts)
     state.copy_(torch.tensor(s.soa(), device=device))
     sk.get_stats(reset=True)
 
@@ -315,7 +328,7 @@ def main():
         host_mass = torch.empty((n,), dtype=torch.float64).pin_memory().numpy()
         host_state[...] = s.soa()
         host_mass[...] = s.m
-        sk.init(device.index, stream=stream.cuda_stream, guess=guess)
+        sk.init(device.index, stream=stream.cuda_stream, guess=guess, **form_opts)
         for _ in range(2):
             sk.evolve_host(host_state, host_mass, s.dt, 2, 1)
         host_state[...] = s.soa()
@@ -353,8 +366,9 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": desc, "n": n, "dt": s.dt, "order": 2, "form": "fp64",
+            "config": {"workload": desc, "n": n, "dt": s.dt, "order": 2, "form": args.form,
                        "kepler_guess": args.guess,
+                       "fp32_pair_share": fp32_share,
                        "pairs_solved_per_step": n * (n - 1),
                        "l2": "256 MB buffer written between timed steps (state fits in L2)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

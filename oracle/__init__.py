@@ -82,7 +82,7 @@ def _load():
             lib.oracle_step_sample.restype = ctypes.c_int
             lib.oracle_energy.argtypes = [I64, P, P, P, P, P, P]
             lib.oracle_energy.restype = ctypes.c_int
-            lib.oracle_pair_classes.argtypes = [I64, P, P, P, D, ctypes.c_int,
+            lib.oracle_pair_classes.argtypes = [I64, P, P, P, D, ctypes.c_int, ctypes.c_int,
                                                 D, D, D,
                                                 ctypes.POINTER(ctypes.c_uint8)]
             lib.oracle_pair_classes.restype = I64
@@ -175,16 +175,18 @@ def energy(m, r, v):
 
 
 def pair_classes(m, r, v, tau: float, rule: int = 0, r_min: float = 0.1,
-                 e_max: float = 0.9, e_hyp: float = 10.0, want_matrix: bool = False):
-    """Single-precision eligibility of every ordered pair (mixed-precision
-    form), decided in FP64.  Returns (count, matrix or None)."""
+                 e_max: float = 0.9, e_hyp: float = 10.0, want_matrix: bool = False,
+                 order: int = 2):
+    """Single-precision eligibility of every ordered pair of the step that
+    starts from (r, v) (mixed-precision form), decided in single precision
+    with a fixed operation order.  Returns (count, matrix or None)."""
     m = np.ascontiguousarray(m, dtype=np.float64)
     r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
     n = m.shape[0]
     mat = np.zeros((n, n), dtype=np.uint8) if want_matrix else None
     ptr = mat.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if want_matrix else None
-    cnt = _load().oracle_pair_classes(n, _dp(m), _dp(r), _dp(v), float(tau), int(rule),
+    cnt = _load().oracle_pair_classes(n, _dp(m), _dp(r), _dp(v), float(tau), int(order), int(rule),
                                       float(r_min), float(e_max), float(e_hyp), ptr)
     return int(cnt), mat
 

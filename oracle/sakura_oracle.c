@@ -562,51 +562,87 @@ int oracle_energy(int64_t n, const double *m, const double *r, const double *v,
 
 /* ------------------------------------------------------------------ */
 /* Precision class of each ordered pair for the mixed-precision form.  */
-/* The pair state is the Kepler input of Eq. 26 after the half drift   */
-/* (r0 = r_ij - tau/2 v_ij, v0 = v_ij).  FP64 decides:                  */
-/*   rule 0: single precision iff |r0| > r_min and e < e_max            */
-/*   rule 1: single precision iff |r0| > r_min and (e < e_max or        */
-/*           e > e_hyp)                                                  */
-/* with e^2 = 1 + 2 (v^2/2 - m/r) |r x v|^2 / m^2, m = m_i + m_j.        */
+/* The class is an integer decision taken in single precision; the     */
+/* operations and their order are fixed so that any implementation     */
+/* that follows them (with IEEE rounding and no contraction) takes the */
+/* same decision:                                                      */
+/*   x_d = x + v * drift          (double, the first drift of the step)*/
+/*   hi = (float)x_d, lo = (float)(x_d - (double)hi)                    */
+/*   dx = (hi_i - hi_j) + (lo_i - lo_j), du = (float)v_i - (float)v_j   */
+/*   x0 = dx - ptau * du,  ptau = (float)(pre * tau)                    */
+/*   r2 = (x0^2 + y0^2) + z0^2, v2, eta = r0.v0 likewise               */
+/*   m = (float)m_i + (float)m_j, h2 = r2 v2 - eta^2                    */
+/*   E = 0.5 v2 - m / sqrt(r2), e2 = 1 + ((2 E) h2) / (m m)             */
+/*   rule 0: single iff r2 > rmin2 and e2 < emax2                       */
+/*   rule 1: single iff r2 > rmin2 and (e2 < emax2 or e2 > ehyp2)       */
+/* with rmin2 = (float)(r_min^2) etc.  order selects (drift, pre):      */
+/* 2 -> (tau/2, 1/2), 1 -> (0, 0), -1 -> (tau, 1).                      */
 /* Writes one byte per ordered pair (row i, column j; diagonal 0) when  */
 /* cls != NULL and returns the number of single-precision pairs.        */
-/* The state r, v is the state at the start of the step (before the     */
-/* half drift), as passed to oracle_step with order 2.                  */
 /* ------------------------------------------------------------------ */
 int64_t oracle_pair_classes(int64_t n, const double *m, const double *r, const double *v,
-                            double tau, int rule, double r_min, double e_max,
+                            double tau, int order, int rule, double r_min, double e_max,
                             double e_hyp, uint8_t *cls)
 {
+    double drift = order == 2 ? 0.5 * tau : (order == 1 ? 0.0 : tau);
+    double pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
+    float ptau = (float)(pre * tau);
+    float rmin2 = (float)(r_min * r_min);
+    float emax2 = (float)(e_max * e_max);
+    float ehyp2 = (float)(e_hyp * e_hyp);
+    float *hi = (float *)malloc(sizeof(float) * (size_t)(3 * n));
+    float *lo = (float *)malloc(sizeof(float) * (size_t)(3 * n));
+    float *vf = (float *)malloc(sizeof(float) * (size_t)(3 * n));
+    float *mf = (float *)malloc(sizeof(float) * (size_t)n);
+    if (!hi || !lo || !vf || !mf) {
+        free(hi);
+        free(lo);
+        free(vf);
+        free(mf);
+        return -1;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        for (int q = 0; q < 3; ++q) {
+            double xd = r[3 * i + q] + v[3 * i + q] * drift;
+            float h = (float)xd;
+            hi[3 * i + q] = h;
+            lo[3 * i + q] = (float)(xd - (double)h);
+            vf[3 * i + q] = (float)v[3 * i + q];
+        }
+        mf[i] = (float)m[i];
+    }
     int64_t count = 0;
     for (int64_t i = 0; i < n; ++i)
         for (int64_t j = 0; j < n; ++j) {
             uint8_t c = 0;
             if (i != j) {
-                double mij = m[i] + m[j];
-                double x[3], u[3];
+                float x[3], u[3];
                 for (int q = 0; q < 3; ++q) {
-                    double ri = r[3 * i + q] + 0.5 * tau * v[3 * i + q];
-                    double rj = r[3 * j + q] + 0.5 * tau * v[3 * j + q];
-                    u[q] = v[3 * i + q] - v[3 * j + q];
-                    x[q] = (ri - rj) - 0.5 * tau * u[q];
+                    float d = (hi[3 * i + q] - hi[3 * j + q]) + (lo[3 * i + q] - lo[3 * j + q]);
+                    u[q] = vf[3 * i + q] - vf[3 * j + q];
+                    float pu = ptau * u[q];
+                    x[q] = d - pu;
                 }
-                double rr = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-                double v2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-                double hx = x[1] * u[2] - x[2] * u[1];
-                double hy = x[2] * u[0] - x[0] * u[2];
-                double hz = x[0] * u[1] - x[1] * u[0];
-                double h2 = hx * hx + hy * hy + hz * hz;
-                double en = 0.5 * v2 - mij / rr;
-                double e2 = 1.0 + 2.0 * en * h2 / (mij * mij);
-                double e = sqrt(fmax(e2, 0.0));
-                int far = rr > r_min;
-                int lowe = e < e_max;
-                int hyp = (rule == 1) && (e > e_hyp);
+                float r2 = (x[0] * x[0] + x[1] * x[1]) + x[2] * x[2];
+                float v2 = (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2];
+                float eta = (x[0] * u[0] + x[1] * u[1]) + x[2] * u[2];
+                float mm = mf[i] + mf[j];
+                float h2 = r2 * v2 - eta * eta;
+                float rr = sqrtf(r2);
+                float E = 0.5f * v2 - mm / rr;
+                float e2 = 1.0f + ((2.0f * E) * h2) / (mm * mm);
+                int far = r2 > rmin2;
+                int lowe = e2 < emax2;
+                int hyp = (rule == 1) && (e2 > ehyp2);
                 c = (uint8_t)(far && (lowe || hyp));
             }
             if (cls) cls[i * n + j] = c;
             count += c;
         }
+    free(hi);
+    free(lo);
+    free(vf);
+    free(mf);
     return count;
 }
 

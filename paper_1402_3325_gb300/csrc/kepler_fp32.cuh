@@ -1,0 +1,166 @@
+// kepler_fp32.cuh -- single-precision pair solve of the mixed-precision form.
+//
+// Same method as kepler_fp64.cuh (universal variable, Stumpff functions by
+// quartering and doubling, Laguerre n = 5 with the Newton-step convergence
+// test, increment form of the Eq. 26 pair map divided by m = m_i + m_j), in
+// FP32 throughout.  The test stops a lane when |F/F'| <= 4 eps32 max(|s|,
+// |t| |1/F'|), eps32 = 2^-23; a lane that has not converged after
+// kFp32MaxIter steps is handed to the FP64 solver.  Only pairs that the FP32
+// class rule admits (distant, low- or very-high-eccentricity pairs, whose
+// increments are small next to the state) come here; their increments are
+// accumulated in FP64 by the caller.
+//
+// The class rule is evaluated on the hi/lo float split of the drifted
+// positions with correctly rounded single-precision operations in a fixed
+// order (no contraction), so a CPU reference computes the same decisions.
+#pragma once
+
+#include <cstdint>
+
+namespace sakura {
+
+constexpr int kFp32MaxIter = 12;
+
+// Relative Kepler input of a pair in FP32 and the class decision.
+struct Pair32 {
+    float x0, y0, z0, vx, vy, vz;  // r0 (backward-drifted) and v0
+    float r2, v2, eta, m;
+    bool fp32;                      // admitted by the FP32 class rule
+};
+
+struct ClassRule {
+    float ptau;    // (float)(pre * tau)
+    float rmin2;   // (float)(r_min^2)
+    float emax2;   // (float)(e_max^2)
+    float ehyp2;   // (float)(e_hyp^2)
+    int rule;      // 0: r > r_min and e < e_max; 1: ... or e > e_hyp
+};
+
+// dx = (hi_i - hi_j) + (lo_i - lo_j) for each coordinate, dv in float,
+// r0 = dx - ptau dv, then e^2 = 1 + (2 E h^2) / m^2 with E = v^2/2 - m/r and
+// h^2 = r^2 v^2 - (r.v)^2.
+__device__ __forceinline__ void pair32_setup(Pair32 &p, const float hi_i[3], const float lo_i[3],
+                                             const float v_i[3], float m_i, const float hi_j[3],
+                                             const float lo_j[3], const float v_j[3], float m_j,
+                                             const ClassRule &cr)
+{
+    float x[3], u[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float d = __fadd_rn(__fsub_rn(hi_i[q], hi_j[q]), __fsub_rn(lo_i[q], lo_j[q]));
+        u[q] = __fsub_rn(v_i[q], v_j[q]);
+        x[q] = __fsub_rn(d, __fmul_rn(cr.ptau, u[q]));
+    }
+    p.x0 = x[0];
+    p.y0 = x[1];
+    p.z0 = x[2];
+    p.vx = u[0];
+    p.vy = u[1];
+    p.vz = u[2];
+    p.r2 = __fadd_rn(__fadd_rn(__fmul_rn(x[0], x[0]), __fmul_rn(x[1], x[1])), __fmul_rn(x[2], x[2]));
+    p.v2 = __fadd_rn(__fadd_rn(__fmul_rn(u[0], u[0]), __fmul_rn(u[1], u[1])), __fmul_rn(u[2], u[2]));
+    p.eta = __fadd_rn(__fadd_rn(__fmul_rn(x[0], u[0]), __fmul_rn(x[1], u[1])), __fmul_rn(x[2], u[2]));
+    p.m = __fadd_rn(m_i, m_j);
+    const float h2 = __fsub_rn(__fmul_rn(p.r2, p.v2), __fmul_rn(p.eta, p.eta));
+    const float r = __fsqrt_rn(p.r2);
+    const float E = __fsub_rn(__fmul_rn(0.5f, p.v2), __fdiv_rn(p.m, r));
+    const float e2 = __fadd_rn(1.0f, __fdiv_rn(__fmul_rn(__fmul_rn(2.0f, E), h2), __fmul_rn(p.m, p.m)));
+    const bool far = p.r2 > cr.rmin2;
+    const bool lowe = e2 < cr.emax2;
+    const bool hyp = (cr.rule == 1) && (e2 > cr.ehyp2);
+    p.fp32 = far && (lowe || hyp);
+}
+
+struct Stumpff32 {
+    float c0, c1, c2, c3;
+};
+
+__device__ __forceinline__ Stumpff32 stumpff_fp32(float x)
+{
+    int k = 0;
+    while (fabsf(x) > 0.1f && k < 40) {
+        x *= 0.25f;
+        ++k;
+    }
+    const float y = -x;
+    // 1/(2n+2)!, 1/(2n+3)!, n = 0..3 (first omitted term < 3e-11 relative)
+    float c2 = fmaf(fmaf(fmaf(1.0f / 40320.0f, y, 1.0f / 720.0f), y, 1.0f / 24.0f), y, 0.5f);
+    float c3 = fmaf(fmaf(fmaf(1.0f / 362880.0f, y, 1.0f / 5040.0f), y, 1.0f / 120.0f), y,
+                    1.0f / 6.0f);
+    float c0 = fmaf(y, c2, 1.0f);
+    float c1 = fmaf(y, c3, 1.0f);
+    for (; k > 0; --k) {
+        const float n3 = 0.25f * fmaf(c0, c3, c2);
+        const float n2 = 0.5f * c1 * c1;
+        const float n1 = c0 * c1;
+        x *= 4.0f;
+        c0 = fmaf(-x, n2, 1.0f);
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+    }
+    return {c0, c1, c2, c3};
+}
+
+// FP32 Kepler solve and increments divided by m; returns false when the
+// iteration did not converge (the pair then goes to the FP64 solver).
+// guess: 0 = t/r0, 2 = second order.  out[0..2] = delta_r/m,
+// out[3..5] = delta_v/m.
+__device__ __forceinline__ bool pair32_solve(const Pair32 &p, float tau, float post, int guess,
+                                             float out[6], int &iters)
+{
+    const float ir0 = rsqrtf(p.r2);
+    const float r0 = p.r2 * ir0;
+    const float beta = fmaf(2.0f * p.m, ir0, -p.v2);
+    const float zeta0 = fmaf(-beta, r0, p.m);
+    float t = tau;
+    if (beta > 0.0f) {
+        const float b3 = beta * beta * beta;
+        const float tm = 6.2831853f * p.m;
+        if (tau * tau * b3 > tm * tm) t = fmodf(tau, tm * rsqrtf(b3));
+    }
+    float s = t * ir0;
+    if (guess == 2) s = fmaf(-0.5f * s * s, p.eta * ir0, s);
+    float G1 = 0.0f, G2 = 0.0f, G3 = 0.0f, ir = ir0;
+    bool done = (t == 0.0f);
+    const float tol = 4.0f * 1.1920929e-7f;
+    iters = 0;
+    for (int it = 0; it < kFp32MaxIter && !done; ++it) {
+        const Stumpff32 c = stumpff_fp32(beta * s * s);
+        const float s2 = s * s;
+        G1 = s * c.c1;
+        G2 = s2 * c.c2;
+        G3 = s2 * s * c.c3;
+        const float F = fmaf(r0, s, fmaf(p.eta, G2, fmaf(zeta0, G3, -t)));
+        const float Fp = fmaf(p.eta, G1, fmaf(zeta0, G2, r0));
+        const float Fpp = fmaf(p.eta, c.c0, zeta0 * G1);
+        ir = __frcp_rn(Fp);
+        const float q = F * ir;
+        ++iters;
+        if (fabsf(q) <= tol * fmaxf(fabsf(s), fabsf(t * ir))) {
+            done = true;
+            break;
+        }
+        const float u = 1.25f * q * Fpp * ir;
+        const float den = 1.0f + 4.0f * sqrtf(fabsf(1.0f - u));
+        s = s - 5.0f * q * __frcp_rn(den);
+    }
+    if (!done) return false;
+    const float fm1 = -G2 * ir0;
+    float gmt = -G3;
+    if (t != tau) gmt += (t - tau) / p.m;
+    const float fd = -G1 * ir0 * ir;
+    const float gdm1 = -G2 * ir;
+    const float qtau = post * tau;
+    const float A = fmaf(-qtau, fd, fm1);
+    const float B = fmaf(-qtau, gdm1, gmt);
+    out[3] = fmaf(fd, p.x0, gdm1 * p.vx);
+    out[4] = fmaf(fd, p.y0, gdm1 * p.vy);
+    out[5] = fmaf(fd, p.z0, gdm1 * p.vz);
+    out[0] = fmaf(A, p.x0, B * p.vx);
+    out[1] = fmaf(A, p.y0, B * p.vy);
+    out[2] = fmaf(A, p.z0, B * p.vz);
+    return isfinite(out[0] + out[1] + out[2] + out[3] + out[4] + out[5]);
+}
+
+}  // namespace sakura

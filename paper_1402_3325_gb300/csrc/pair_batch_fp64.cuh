@@ -1,0 +1,64 @@
+// pair_batch_fp64.cuh -- one warp-wide batch of FP64 pair solves.
+#pragma once
+
+#include "kepler_fp64.cuh"
+#include "step_common.cuh"
+
+namespace sakura {
+
+// 32 ordered pairs (i, j_lane) of one row, one per lane; every lane of the
+// warp must call this (invalid lanes idle).  X is the drifted state
+// [7][n].  Adds m_j (delta_r, delta_v) / m_ij to acc (Eq. 23 with the
+// 1/m_i folded in), ORs device faults into status, and returns the lane's
+// Kepler evaluation count and whether it needed bisection.
+__device__ __forceinline__ void fp64_pair_batch(const double *X, int64_t n, int64_t j, bool valid,
+                                                double xi, double yi, double zi, double vxi,
+                                                double vyi, double vzi, double mi,
+                                                const StepArgs &a, const KeplerParams &kp,
+                                                double acc[6], unsigned &status, int &iters,
+                                                int &fb)
+{
+    PairSolve p;
+    double mj = 0.0;
+    if (valid) {
+        mj = X[6 * n + j];
+        pair_setup(p, a.tau, mi + mj, xi - X[j], yi - X[n + j], zi - X[2 * n + j],
+                   vxi - X[3 * n + j], vyi - X[4 * n + j], vzi - X[5 * n + j], a.pre, a.guess);
+    } else {
+        p.done = true;
+        p.beta = p.s = 0.0;
+        p.iters = 0;
+        p.status = 0;
+    }
+    // warp-synchronous Laguerre iterations: converged lanes idle
+    for (int it = 0; it < kp.max_iter; ++it) {
+        if (__all_sync(0xffffffffu, p.done)) break;
+        const double x = p.beta * p.s * p.s;
+        const unsigned hx = p.done ? 0u : abs_hiword(x);
+        const int nt = stumpff_terms(__reduce_max_sync(0xffffffffu, hx));
+        bool oob = false;
+        if (!p.done) oob = pair_iterate(p, x, nt, kp);
+        if (__any_sync(0xffffffffu, oob)) {
+            if (oob) pair_safeguard(p);
+        }
+    }
+    fb = 0;
+    if (!p.done) {
+        if (kp.bisection) {
+            pair_bisect(p);
+            fb = 1;
+        } else {
+            p.status |= kStatusKepler;
+        }
+    }
+    iters = valid ? p.iters : 0;
+    if (valid) {
+        double d[6];
+        pair_increment_over_m(p, a.tau, a.post, d);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) acc[q] = fma(mj, d[q], acc[q]);
+        status |= p.status;
+    }
+}
+
+}  // namespace sakura

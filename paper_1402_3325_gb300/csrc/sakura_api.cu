@@ -129,14 +129,17 @@ struct Plan {
 Plan plan_step(int64_t n)
 {
     Plan p;
+    const bool mixed = g.cfg.precision == SAKURA_PREC_MIXED;
     p.warps = g.cfg.block_warps > 0 ? g.cfg.block_warps : 4;
     if (p.warps != 4 && p.warps != 8 && p.warps != 16) p.warps = 4;
+    if (mixed) p.warps = 4;
     const int64_t nb = (n + 31) / 32;
     const int64_t B = n * nb;
     int64_t blocks = g.cfg.grid_blocks;
     if (blocks <= 0) {
-        const int bps = sakura::pair_step_fp64_blocks_per_sm(
-            p.warps, (g.cfg.flags & SAKURA_FLAG_STATS) != 0);
+        const bool st = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
+        const int bps = mixed ? sakura::pair_step_mixed_blocks_per_sm(st)
+                              : sakura::pair_step_fp64_blocks_per_sm(p.warps, st);
         blocks = (int64_t)g.sm_count * bps;
     }
     blocks = std::min<int64_t>(blocks, std::max<int64_t>(1, B / p.warps));
@@ -150,13 +153,21 @@ int step_device(double *state, const double *masses, int64_t n, double dt, int o
 {
     const Plan p = plan_step(n);
     const int64_t slots = sakura::pair_step_slots(n, p.W);
-    int rc = grow(g.partial, (size_t)(7 * n + slots * 6 * n) * sizeof(double));
+    const bool mixed = g.cfg.precision == SAKURA_PREC_MIXED;
+    // scratch: X[7][n] doubles, row partials [slots][6][n], then (mixed)
+    // X32[10][n] floats
+    const size_t doubles = (size_t)(7 * n + slots * 6 * n) + (mixed ? (size_t)(5 * n) : 0);
+    int rc = grow(g.partial, doubles * sizeof(double));
     if (rc) return rc;
     double *X = (double *)g.partial.ptr;
     double *partial = X + 7 * n;
+    float *X32 = (float *)(partial + slots * 6 * n);
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
-    sakura::launch_prep_step(state, masses, X, n, drift, g.d_status, g.stream);
+    if (mixed)
+        sakura::launch_prep_mixed(state, masses, X, X32, n, drift, g.d_status, g.stream);
+    else
+        sakura::launch_prep_step(state, masses, X, n, drift, g.d_status, g.stream);
     sakura::StepArgs a;
     a.X = X;
     a.partial = partial;
@@ -179,7 +190,20 @@ int step_device(double *state, const double *masses, int64_t n, double dt, int o
             tm = take_timer();
             cudaEventRecord(tm.first, g.stream);
         }
-        sakura::launch_pair_step_fp64(a, p.warps, p.blocks, stats, g.stream);
+        if (mixed) {
+            sakura::MixedArgs ma;
+            ma.X32 = X32;
+            ma.rule.ptau = (float)(a.pre * dt);
+            ma.rule.rmin2 = (float)(g.cfg.mixed_r_min * g.cfg.mixed_r_min);
+            ma.rule.emax2 = (float)(g.cfg.mixed_e_max * g.cfg.mixed_e_max);
+            ma.rule.ehyp2 = (float)(g.cfg.mixed_e_hyp * g.cfg.mixed_e_hyp);
+            ma.rule.rule = g.cfg.mixed_rule;
+            ma.tau32 = (float)dt;
+            ma.post32 = (float)a.post;
+            sakura::launch_pair_step_mixed(a, ma, p.blocks, stats, g.stream);
+        } else {
+            sakura::launch_pair_step_fp64(a, p.warps, p.blocks, stats, g.stream);
+        }
         if (timing) {
             cudaEventRecord(tm.second, g.stream);
             g.timers.push_back(tm);
@@ -231,6 +255,8 @@ int sakura_init(const sakura_config *cfg)
     if (c.kepler_max_iter < 1 || c.kepler_max_iter > 10000 || !(c.kepler_tol > 0.0))
         return SAKURA_E_ARG;
     if (c.precision != SAKURA_PREC_FP64 && c.precision != SAKURA_PREC_MIXED) return SAKURA_E_ARG;
+    if (c.mixed_rule != SAKURA_MIXED_RULE_LITERAL && c.mixed_rule != SAKURA_MIXED_RULE_HYP)
+        return SAKURA_E_ARG;
     if (c.guess != SAKURA_GUESS_STANDARD && c.guess != SAKURA_GUESS_LEARNED &&
         c.guess != SAKURA_GUESS_TAYLOR)
         return SAKURA_E_ARG;

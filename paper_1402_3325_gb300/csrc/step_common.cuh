@@ -5,6 +5,8 @@
 
 #include <cstdint>
 
+#include "kepler_fp32.cuh"
+
 namespace sakura {
 
 // indices into the device statistics counters
@@ -28,6 +30,19 @@ struct StepArgs {
     unsigned *status;
     unsigned long long *stats;
 };
+
+// extra arguments of the mixed-precision pair kernel
+struct MixedArgs {
+    const float *X32;     // [10][n] hi xyz, lo xyz, v xyz, m (floats)
+    ClassRule rule;       // FP32 class rule (kepler_fp32.cuh)
+    float tau32, post32;  // tau and the post-drift fraction in FP32
+};
+
+void launch_prep_mixed(const double *state, const double *mass, double *X, float *X32,
+                       int64_t n, double drift, unsigned *status, cudaStream_t s);
+void launch_pair_step_mixed(const StepArgs &a, const MixedArgs &ma, int blocks, bool stats,
+                            cudaStream_t s);
+int pair_step_mixed_blocks_per_sm(bool stats);
 
 // pair kernel: one persistent wave of `blocks` blocks of `warps` warps
 void launch_pair_step_fp64(const StepArgs &a, int warps, int blocks, bool stats,

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "kepler_fp64.cuh"
+#include "pair_batch_fp64.cuh"
 #include "step_common.cuh"
 
 namespace sakura {
@@ -85,48 +86,10 @@ __global__ void __launch_bounds__(WARPS * 32)
     for (int64_t b = b0; b < b1; ++b) {
         const int64_t j = (jb << 5) + lane;
         const bool valid = (j < n) && (j != i);
-        PairSolve p;
-        double mj = 0.0;
-        if (valid) {
-            mj = X[6 * n + j];
-            pair_setup(p, a.tau, mi + mj, xi - X[j], yi - X[n + j], zi - X[2 * n + j],
-                       vxi - X[3 * n + j], vyi - X[4 * n + j], vzi - X[5 * n + j], a.pre, a.guess);
-        } else {
-            p.done = true;
-            p.beta = p.s = 0.0;
-            p.iters = 0;
-            p.status = 0;
-        }
-        // warp-synchronous Laguerre iterations: converged lanes idle
-        for (int it = 0; it < kp.max_iter; ++it) {
-            if (__all_sync(0xffffffffu, p.done)) break;
-            const double x = p.beta * p.s * p.s;
-            const unsigned hx = p.done ? 0u : abs_hiword(x);
-            const int nt = stumpff_terms(__reduce_max_sync(0xffffffffu, hx));
-            bool oob = false;
-            if (!p.done) oob = pair_iterate(p, x, nt, kp);
-            if (__any_sync(0xffffffffu, oob)) {
-                if (oob) pair_safeguard(p);
-            }
-        }
-        int fb = 0;
-        if (!p.done) {
-            if (kp.bisection) {
-                pair_bisect(p);
-                fb = 1;
-            } else {
-                p.status |= kStatusKepler;
-            }
-        }
-        if (valid) {
-            double d[6];
-            pair_increment_over_m(p, a.tau, a.post, d);
-#pragma unroll
-            for (int q = 0; q < 6; ++q) acc[q] = fma(mj, d[q], acc[q]);
-            status |= p.status;
-        }
+        int iters = 0, fb = 0;
+        fp64_pair_batch(X, n, j, valid, xi, yi, zi, vxi, vyi, vzi, mi, a, kp, acc, status, iters,
+                        fb);
         if (STATS) {
-            const int iters = valid ? p.iters : 0;
             it_sum += iters;
             fallbacks += fb;
             it_max = max(it_max, iters);

@@ -1,0 +1,233 @@
+// step_mixed.cu -- mixed-precision W step: distant, weakly perturbing pairs in
+// FP32, everything else in FP64, all increments accumulated in FP64.
+//
+// prep kernel: the drift in FP64 (x + v drift, rounded twice, as a plain CPU
+//   loop computes it), the FP64 drifted state X[7][n], and a float copy
+//   X32[10][n] = (hi x, y, z, lo x, y, z, vx, vy, vz, m) with x = hi + lo,
+//   hi = fl32(x), lo = fl32(x - hi), so FP32 pair differences keep the
+//   accuracy of the separation rather than of the coordinate.
+// pair kernel: the persistent batch partition of the FP64 kernel.  For each
+//   batch every lane forms its pair's FP32 Kepler input and class (class rule
+//   in kepler_fp32.cuh); FP32-class lanes solve in FP32 and add
+//   m_j * delta/m_ij to the FP64 row accumulators; the other pairs are
+//   compacted into a per-warp shared-memory queue and solved 32 at a time by
+//   the FP64 batch solver, so a few close pairs never make a whole warp run
+//   the FP64 path half-empty.  The queue is drained at every row end.
+#include <cuda_runtime.h>
+
+#include "kepler_fp32.cuh"
+#include "kepler_fp64.cuh"
+#include "pair_batch_fp64.cuh"
+#include "step_common.cuh"
+
+namespace sakura {
+
+__device__ __host__ __forceinline__ int64_t mixed_owner(int64_t b, int64_t B, int64_t W)
+{
+    return ((b + 1) * W - 1) / B;
+}
+
+__global__ void prep_mixed_kernel(const double *state, const double *mass, double *X, float *X32,
+                                  int64_t n, double drift, unsigned *status)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double m = mass[i];
+    if (!(m > 0.0)) atomicOr(status, kStatusMass);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double v = state[(3 + q) * n + i];
+        const double x = __dadd_rn(state[q * n + i], __dmul_rn(v, drift));
+        const float hi = __double2float_rn(x);
+        const float lo = __double2float_rn(__dsub_rn(x, (double)hi));
+        X[q * n + i] = x;
+        X[(3 + q) * n + i] = v;
+        X32[q * n + i] = hi;
+        X32[(3 + q) * n + i] = lo;
+        X32[(6 + q) * n + i] = __double2float_rn(v);
+    }
+    X[6 * n + i] = m;
+    X32[9 * n + i] = __double2float_rn(m);
+}
+
+template <int WARPS, bool STATS>
+__global__ void __launch_bounds__(WARPS * 32)
+    pair_step_mixed_kernel(StepArgs a, MixedArgs ma)
+{
+    __shared__ int queue[WARPS][64];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int *qw = queue[wib];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t n = a.n;
+    const int64_t nb = (n + 31) >> 5;
+    const int64_t B = n * nb;
+    const int64_t W = (int64_t)gridDim.x * WARPS;
+    const int64_t w = (int64_t)blockIdx.x * WARPS + wib;
+    const int64_t b0 = w * B / W;
+    const int64_t b1 = (w + 1) * B / W;
+    const double *X = a.X;
+    const float *X32 = ma.X32;
+    const KeplerParams kp{a.tol, a.max_iter, a.bisection};
+
+    unsigned status = 0;
+    long long it_sum = 0, slots = 0, fallbacks = 0, n32 = 0;
+    int it_max = 0;
+    int tail = 0;  // warp-uniform queue length
+
+    int64_t i = b0 / nb;
+    int64_t jb = b0 - i * nb;
+    double xi = 0, yi = 0, zi = 0, vxi = 0, vyi = 0, vzi = 0, mi = 1;
+    float hi_i[3] = {0, 0, 0}, lo_i[3] = {0, 0, 0}, v_i[3] = {0, 0, 0}, mfi = 1.0f;
+    auto load_row = [&](int64_t r) {
+        xi = X[r];
+        yi = X[n + r];
+        zi = X[2 * n + r];
+        vxi = X[3 * n + r];
+        vyi = X[4 * n + r];
+        vzi = X[5 * n + r];
+        mi = X[6 * n + r];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            hi_i[q] = X32[q * n + r];
+            lo_i[q] = X32[(3 + q) * n + r];
+            v_i[q] = X32[(6 + q) * n + r];
+        }
+        mfi = X32[9 * n + r];
+    };
+    if (b0 < b1) load_row(i);
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+
+    auto run_fp64 = [&](int64_t jq, bool vq) {
+        int iters = 0, fb = 0;
+        fp64_pair_batch(X, n, jq, vq, xi, yi, zi, vxi, vyi, vzi, mi, a, kp, acc, status, iters,
+                        fb);
+        if (STATS) {
+            it_sum += iters;
+            fallbacks += fb;
+            it_max = max(it_max, iters);
+            const int wmax = __reduce_max_sync(0xffffffffu, iters);
+            if (lane == 0) slots += 32LL * wmax;
+        }
+    };
+
+    for (int64_t b = b0; b < b1; ++b) {
+        const int64_t j = (jb << 5) + lane;
+        const bool valid = (j < n) && (j != i);
+        bool solved32 = false;
+        if (valid) {
+            float hi_j[3], lo_j[3], v_j[3];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                hi_j[q] = X32[q * n + j];
+                lo_j[q] = X32[(3 + q) * n + j];
+                v_j[q] = X32[(6 + q) * n + j];
+            }
+            Pair32 p;
+            pair32_setup(p, hi_i, lo_i, v_i, mfi, hi_j, lo_j, v_j, X32[9 * n + j], ma.rule);
+            if (p.fp32) {
+                float d[6];
+                int it32 = 0;
+                solved32 = pair32_solve(p, ma.tau32, ma.post32, a.guess, d, it32);
+                if (solved32) {
+                    const double mj = X[6 * n + j];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) acc[q] = fma(mj, (double)d[q], acc[q]);
+                }
+            }
+        }
+        if (STATS) n32 += solved32 ? 1 : 0;
+        // every other valid pair joins the warp's FP64 queue
+        const bool need64 = valid && !solved32;
+        const unsigned mask = __ballot_sync(0xffffffffu, need64);
+        if (need64) qw[tail + __popc(mask & lt_mask)] = (int)j;
+        tail += __popc(mask);
+        __syncwarp();
+        if (tail >= 32) {
+            run_fp64(qw[lane], true);
+            __syncwarp();
+            if (lane < tail - 32) qw[lane] = qw[32 + lane];
+            __syncwarp();
+            tail -= 32;
+        }
+        // leaving row i: drain the queue, reduce and store the row partial
+        if (++jb == nb || b + 1 == b1) {
+            if (tail > 0) {
+                const bool vq = lane < tail;
+                run_fp64(vq ? qw[lane] : 0, vq);
+                __syncwarp();
+                tail = 0;
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                double v = acc[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                acc[q] = 0.0;
+                if (lane == 0) {
+                    const int64_t k = w - mixed_owner(i * nb, B, W);
+                    a.partial[(k * 6 + q) * n + i] = v;
+                }
+            }
+            if (b + 1 < b1) {
+                ++i;
+                jb = 0;
+                load_row(i);
+            }
+        }
+    }
+    status = __reduce_or_sync(0xffffffffu, status);
+    if (lane == 0 && status) atomicOr(a.status, status);
+    if (STATS) {
+        long long s1 = it_sum, s2 = slots, s3 = fallbacks, s4 = n32;
+        int mx = it_max;
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+            s4 += __shfl_xor_sync(0xffffffffu, s4, o);
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) {
+            atomicAdd(&a.stats[kStatIters], (unsigned long long)s1);
+            atomicAdd(&a.stats[kStatSlots], (unsigned long long)s2);
+            atomicAdd(&a.stats[kStatFallbacks], (unsigned long long)s3);
+            atomicAdd(&a.stats[kStatFp32Pairs], (unsigned long long)s4);
+            atomicMax(&a.stats[kStatMaxIters], (unsigned long long)mx);
+        }
+    }
+}
+
+void launch_prep_mixed(const double *state, const double *mass, double *X, float *X32,
+                       int64_t n, double drift, unsigned *status, cudaStream_t s)
+{
+    const int threads = 256;
+    prep_mixed_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
+        state, mass, X, X32, n, drift, status);
+}
+
+void launch_pair_step_mixed(const StepArgs &a, const MixedArgs &ma, int blocks, bool stats,
+                            cudaStream_t s)
+{
+    if (stats)
+        pair_step_mixed_kernel<4, true><<<blocks, 128, 0, s>>>(a, ma);
+    else
+        pair_step_mixed_kernel<4, false><<<blocks, 128, 0, s>>>(a, ma);
+}
+
+int pair_step_mixed_blocks_per_sm(bool stats)
+{
+    int b = 0;
+    const cudaError_t e =
+        stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, pair_step_mixed_kernel<4, true>,
+                                                              128, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &b, pair_step_mixed_kernel<4, false>, 128, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return b > 0 ? b : 1;
+}
+
+}  // namespace sakura

@@ -1,0 +1,119 @@
+"""GPU tests of the mixed-precision form (FP32 solves for distant, weakly
+perturbing pairs; FP64 for the rest and for all accumulation).
+
+* The number of pairs solved in FP32 equals the oracle's single-precision
+  class count exactly (same decision, same precision, same operation order).
+* With a class rule that admits no pair, every pair goes through the per-warp
+  FP64 queue and the step matches the FP64 oracle to 1e-12.
+* Otherwise one step stays within the stated bound of the FP64 oracle
+  (per-particle relative error, metric of the FP64 tests).
+"""
+import contextlib
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1402_3325_gb300 import ics
+from paper_1402_3325_gb300 import sakura as sk
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+NCPU = os.cpu_count() or 1
+STEP_BOUND = 1e-8   # per-particle relative error of one mixed step vs the FP64 oracle
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1402_3325_gb300 import build
+    build.build()
+    sk.init(0, flags=sk.FLAG_STATS)
+    yield
+    sk.finalize()
+
+
+@contextlib.contextmanager
+def mixed(**opts):
+    sk.init(0, flags=sk.FLAG_STATS, precision=sk.PREC_MIXED, **opts)
+    try:
+        yield
+    finally:
+        sk.init(0, flags=sk.FLAG_STATS)
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def step_gpu(s, order=2, nsteps=1):
+    st = dev(s.soa())
+    m = dev(s.m)
+    sk.get_stats(reset=True)
+    for _ in range(nsteps):
+        sk.step(st, m, s.dt, order)
+    sk.check()
+    stats = sk.get_stats(reset=True)
+    r, v = ics.from_soa(st.cpu().numpy())
+    return r, v, stats
+
+
+def rel_err(r, v, rr, vr):
+    R = np.sqrt((rr ** 2).sum(1).mean())
+    V = np.sqrt((vr ** 2).sum(1).mean())
+    er = np.linalg.norm(r - rr, axis=1) / np.maximum(np.linalg.norm(rr, axis=1), R)
+    ev = np.linalg.norm(v - vr, axis=1) / np.maximum(np.linalg.norm(vr, axis=1), V)
+    return float(er.max()), float(ev.max())
+
+
+CASES = [
+    ("bh2048-literal", lambda: ics.bh_cluster(2048, seed=3), 0),
+    ("bh2048-hyp", lambda: ics.bh_cluster(2048, seed=3), 1),
+    ("plummer1024-hyp", lambda: ics.plummer(1024, seed=5), 1),
+    ("random300-hyp", lambda: ics.random_cluster(300, seed=7, mass_spread=2.0), 1),
+]
+
+
+@pytest.mark.parametrize("name,make,rule", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("order", [2, -1])
+def test_mixed_class_count_and_accuracy(name, make, rule, order):
+    s = make()
+    with mixed(mixed_rule=rule, guess=sk.GUESS_TAYLOR):
+        r, v, st = step_gpu(s, order)
+    cnt, _ = oracle.pair_classes(s.m, s.r, s.v, s.dt, rule=rule, order=order)
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, order, nthreads=NCPU)
+    er, ev = rel_err(r, v, rr, vr)
+    print(f"{name} order {order}: fp32 pairs {st['fp32_pairs']} / {st['pairs']}"
+          f" (oracle {cnt}), err r {er:.2e} v {ev:.2e}")
+    assert st["fp32_pairs"] == cnt
+    assert er <= STEP_BOUND and ev <= STEP_BOUND
+
+
+def test_mixed_without_fp32_pairs_is_fp64_exact():
+    # r_min larger than the system: every pair takes the FP64 queue
+    s = ics.random_cluster(700, seed=11, mass_spread=2.0)
+    with mixed(mixed_r_min=1e6):
+        r, v, st = step_gpu(s, 2)
+    assert st["fp32_pairs"] == 0
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
+    er, ev = rel_err(r, v, rr, vr)
+    assert er <= 1e-12 and ev <= 1e-12, (er, ev)
+
+
+def test_mixed_energy_drift_bh_cluster():
+    # BH cluster, hyperbolic rule: 16 steps of the mixed and the FP64 form
+    # from the same start; energies from the oracle's compensated sum
+    s = ics.bh_cluster(2048, seed=2)
+    E0 = oracle.energy(s.m, s.r, s.v)[0]
+    with mixed(mixed_rule=1, guess=sk.GUESS_TAYLOR):
+        rm, vm, stm = step_gpu(s, 2, nsteps=16)
+    rf, vf, _ = step_gpu(s, 2, nsteps=16)
+    Em = oracle.energy(s.m, rm, vm)[0]
+    Ef = oracle.energy(s.m, rf, vf)[0]
+    print(f"dE/E fp64 {abs(Ef / E0 - 1):.3e} mixed {abs(Em / E0 - 1):.3e}"
+          f" |Em-Ef|/|E| {abs(Em - Ef) / abs(E0):.3e} fp32 share"
+          f" {stm['fp32_pairs'] / stm['pairs']:.3f}")
+    assert abs(Em - Ef) <= 1e-9 * abs(E0)
