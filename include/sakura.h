@@ -59,6 +59,9 @@ extern "C" {
 #define SAKURA_FLAG_SYNC_CHECK 1u /* synchronise and report faults on every call */
 #define SAKURA_FLAG_STATS 2u      /* collect iteration statistics (small cost)   */
 #define SAKURA_FLAG_TIMING 4u     /* time every pair-kernel launch with CUDA events */
+#define SAKURA_FLAG_NO_AUTOTUNE 8u /* batched path: skip the block-shape autotuner  */
+
+#define SAKURA_BATCH_MAX_N 64     /* largest system of sakura_step_batched       */
 
 typedef struct sakura_config {
     int device;           /* CUDA device ordinal                                  */
@@ -133,16 +136,29 @@ int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt
  * above.  *E_out: host double.  Synchronises.  E_COINCIDENT if some r_ij = 0. */
 int sakura_energy(const double *state, const double *masses, int64_t n, double *E_out);
 
-/* Many independent systems in one persistent launch.  The systems are packed
- * end to end: system k owns particles offsets[k] .. offsets[k+1]-1 of
- * state (device double[6][total]) and masses (device double[total]).
- * offsets: device int64[nsys+1]; dt: device double[nsys] (one step size per
- * system).  Runs nsteps steps of the given order on every system.  The work
- * schedule is rebuilt when offsets change (host copy of offsets needed:
- * host_offsets, host int64[nsys+1]).  Max 1024 particles per system. */
+/* Many independent systems in one persistent launch (the paper's method
+ * applied to each system separately).  The systems are packed end to end:
+ * system k owns particles offsets[k] .. offsets[k+1]-1 of state (device
+ * double[6][total], total = offsets[nsys]) and masses (device double[total]).
+ *   offsets: device int64[nsys+1]; host_offsets: the same values on the host
+ *   (used to build the work schedule, rebuilt when they change);
+ *   dt: device double[nsys], one step size per system.
+ * Runs nsteps steps of the given order (2, 1, -1) on every system, state
+ * updated in place.  A warp runs all steps of its systems with the state in
+ * shared memory; the launch is a CUDA graph (counter reset + kernel), built
+ * once per (buffers, schedule, nsteps, order, block shape) and replayed.  The
+ * first call with a new schedule times the candidate block shapes (1, 2, 4, 8
+ * warps) on a scratch copy and keeps the fastest unless
+ * SAKURA_FLAG_NO_AUTOTUNE is set or cfg.block_warps / cfg.grid_blocks fix it.
+ * Systems need 1 <= N <= SAKURA_BATCH_MAX_N particles (else SAKURA_E_ARG). */
 int sakura_step_batched(double *state, const double *masses, const int64_t *offsets,
-                        const int64_t *host_offsets, int nsys, const double *dt,
-                        int order, int nsteps);
+                        const int64_t *host_offsets, int nsys, const double *dt, int order,
+                        int nsteps);
+
+/* The block shape the batched autotuner chose (warps per block, blocks) and
+ * the time in ms it measured for 1, 2, 4 and 8 warps per block.
+ * SAKURA_E_ARG if no batched call has been tuned yet. */
+int sakura_batched_tuning(int *warps, int *blocks, double times_ms[4]);
 
 /* Load the initial-guess network used when cfg.guess = SAKURA_GUESS_LEARNED:
  * a 6-64-64-1 perceptron.  weights: host float32 array laid out as

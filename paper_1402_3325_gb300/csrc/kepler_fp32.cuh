@@ -120,7 +120,10 @@ __device__ __forceinline__ bool pair32_solve(const Pair32 &p, float tau, float p
         if (tau * tau * b3 > tm * tm) t = fmodf(tau, tm * rsqrtf(b3));
     }
     float s = t * ir0;
-    if (guess == 2) s = fmaf(-0.5f * s * s, p.eta * ir0, s);
+    if (guess == 2) {
+        const float c = 0.5f * s * (p.eta * ir0);
+        if (fabsf(c) < 0.5f) s = fmaf(-c, s, s);
+    }
     float G1 = 0.0f, G2 = 0.0f, G3 = 0.0f, ir = ir0;
     bool done = (t == 0.0f);
     const float tol = 4.0f * 1.1920929e-7f;

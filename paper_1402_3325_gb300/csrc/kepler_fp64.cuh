@@ -217,7 +217,9 @@ struct PairSolve {
 // Setup of one pair: backward drift, invariants, period reduction, guess.
 // rr0, vv0: relative state after the one-subscript drift; m: m_i + m_j.
 // guess: 0 = standard s0 = t/r0; 2 = second order in t, s0 = (t/r0)(1 -
-// eta0 t / (2 r0^2)), from ds/dt = 1/r and d2s/dt2 = -eta0/r0^3 at t = 0.
+// eta0 t / (2 r0^2)), from ds/dt = 1/r and d2s/dt2 = -eta0/r0^3 at t = 0;
+// when the correction exceeds 1/2 in size (fast radial motion over the
+// step) the expansion is not trusted and the standard guess is used.
 __device__ __forceinline__ void pair_setup(PairSolve &p, double tau, double m, double rx,
                                            double ry, double rz, double vx, double vy,
                                            double vz, double pre, int guess)
@@ -265,8 +267,8 @@ __device__ __forceinline__ void pair_setup(PairSolve &p, double tau, double m, d
     }
     p.s = p.t * p.ir0;  // standard initial guess
     if (guess == 2) {
-        const double h = 0.5 * p.s;
-        p.s = fma(-h * p.s, p.eta0 * p.ir0, p.s);
+        const double c = 0.5 * p.s * (p.eta0 * p.ir0);  // eta0 t / (2 r0^2)
+        if (magbits(c) < 0x3fe0000000000000LL) p.s = fma(-c, p.s, p.s);  // |c| < 1/2
     }
     if (!is_neg(p.t)) {
         p.lo = 0.0;
@@ -301,6 +303,15 @@ __device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, int nt,
     p.Fp = Fp;
     p.ir = ip;
     ++p.iters;
+    // an iterate so far out that the G functions overflowed: the root lies
+    // between it and the origin, so it bounds the bracket on its side
+    if ((__double_as_longlong(F) & kInfBits) == kInfBits) {
+        if (is_neg(s))
+            p.lo = s;
+        else
+            p.hi = s;
+        return true;
+    }
     // |q| <= tol * max(|s|, |t| / r)
     const long long sc = max(magbits(s), magbits(p.t * ip));
     if (magbits(q) <= magbits(kp.tol * __longlong_as_double(sc))) {

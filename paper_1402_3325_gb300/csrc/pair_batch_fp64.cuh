@@ -6,6 +6,39 @@
 
 namespace sakura {
 
+// Warp-synchronous FP64 solve of 32 pairs, one per lane, whose setup is
+// done (lanes with p.done == true at entry idle).  Every lane of the warp must
+// call this.  tau, post: this lane's step and post-drift fraction.  Writes
+// the increments divided by m_ij to d (only meaningful when valid), returns
+// the lane's evaluation count and whether it needed bisection.
+__device__ __forceinline__ void fp64_solve_warp(PairSolve &p, bool valid, double tau,
+                                                double post, const KeplerParams &kp,
+                                                double d[6], int &iters, int &fb)
+{
+    for (int it = 0; it < kp.max_iter; ++it) {
+        if (__all_sync(0xffffffffu, p.done)) break;
+        const double x = p.beta * p.s * p.s;
+        const unsigned hx = p.done ? 0u : abs_hiword(x);
+        const int nt = stumpff_terms(__reduce_max_sync(0xffffffffu, hx));
+        bool oob = false;
+        if (!p.done) oob = pair_iterate(p, x, nt, kp);
+        if (__any_sync(0xffffffffu, oob)) {
+            if (oob) pair_safeguard(p);
+        }
+    }
+    fb = 0;
+    if (!p.done) {
+        if (kp.bisection) {
+            pair_bisect(p);
+            fb = 1;
+        } else {
+            p.status |= kStatusKepler;
+        }
+    }
+    iters = valid ? p.iters : 0;
+    if (valid) pair_increment_over_m(p, tau, post, d);
+}
+
 // 32 ordered pairs (i, j_lane) of one row, one per lane; every lane of the
 // warp must call this (invalid lanes idle).  X is the drifted state
 // [7][n].  Adds m_j (delta_r, delta_v) / m_ij to acc (Eq. 23 with the
@@ -30,31 +63,9 @@ __device__ __forceinline__ void fp64_pair_batch(const double *X, int64_t n, int6
         p.iters = 0;
         p.status = 0;
     }
-    // warp-synchronous Laguerre iterations: converged lanes idle
-    for (int it = 0; it < kp.max_iter; ++it) {
-        if (__all_sync(0xffffffffu, p.done)) break;
-        const double x = p.beta * p.s * p.s;
-        const unsigned hx = p.done ? 0u : abs_hiword(x);
-        const int nt = stumpff_terms(__reduce_max_sync(0xffffffffu, hx));
-        bool oob = false;
-        if (!p.done) oob = pair_iterate(p, x, nt, kp);
-        if (__any_sync(0xffffffffu, oob)) {
-            if (oob) pair_safeguard(p);
-        }
-    }
-    fb = 0;
-    if (!p.done) {
-        if (kp.bisection) {
-            pair_bisect(p);
-            fb = 1;
-        } else {
-            p.status |= kStatusKepler;
-        }
-    }
-    iters = valid ? p.iters : 0;
+    double d[6];
+    fp64_solve_warp(p, valid, a.tau, a.post, kp, d, iters, fb);
     if (valid) {
-        double d[6];
-        pair_increment_over_m(p, a.tau, a.post, d);
 #pragma unroll
         for (int q = 0; q < 6; ++q) acc[q] = fma(mj, d[q], acc[q]);
         status |= p.status;

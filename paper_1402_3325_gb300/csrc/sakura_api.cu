@@ -13,6 +13,7 @@
 
 #include "sakura.h"
 #include "kepler_fp64.cuh"
+#include "step_batched.cuh"
 #include "step_common.cuh"
 
 namespace {
@@ -20,6 +21,21 @@ namespace {
 struct Buffer {
     void *ptr = nullptr;
     size_t bytes = 0;
+};
+
+// Cached state of the batched ensemble path.
+struct BatchCache {
+    std::vector<int64_t> host_offsets;  // schedule key
+    Buffer task_begin, task_sys, counter, tune_state;
+    int ntasks = 0;
+    int warps = 4;
+    int blocks = 0;
+    bool tuned = false;
+    cudaGraphExec_t exec = nullptr;
+    sakura::BatchArgs graph_args{};
+    int graph_warps = 0, graph_blocks = 0;
+    bool graph_stats = false;
+    double tuned_ms[4] = {0, 0, 0, 0};
 };
 
 struct Context {
@@ -39,6 +55,7 @@ struct Context {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare;
     double timed_ms = 0.0;
     int64_t timed_launches = 0;
+    BatchCache batch;
 };
 
 Context g;
@@ -292,7 +309,10 @@ int sakura_finalize(void)
 {
     if (!g.init) return SAKURA_OK;
     cudaStreamSynchronize(g.stream);
-    Buffer *bufs[] = {&g.partial, &g.energy_work, &g.host_state, &g.host_mass};
+    if (g.batch.exec) cudaGraphExecDestroy(g.batch.exec);
+    Buffer *bufs[] = {&g.partial,          &g.energy_work,      &g.host_state,
+                      &g.host_mass,        &g.batch.task_begin, &g.batch.task_sys,
+                      &g.batch.counter,    &g.batch.tune_state};
     for (Buffer *b : bufs) {
         if (b->ptr) cudaFree(b->ptr);
         b->ptr = nullptr;
@@ -380,16 +400,157 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
                         const int64_t *host_offsets, int nsys, const double *dt, int order,
                         int nsteps)
 {
-    (void)state;
-    (void)masses;
-    (void)offsets;
-    (void)host_offsets;
-    (void)nsys;
-    (void)dt;
-    (void)order;
-    (void)nsteps;
     if (!g.init) return SAKURA_E_NOINIT;
-    return SAKURA_E_ARG;
+    if (!state || !masses || !offsets || !host_offsets || !dt || nsys < 1 || nsteps < 0 ||
+        !valid_order(order))
+        return SAKURA_E_ARG;
+    if (host_offsets[0] != 0) return SAKURA_E_ARG;
+    for (int k = 0; k < nsys; ++k) {
+        const int64_t nk = host_offsets[k + 1] - host_offsets[k];
+        if (nk < 1 || nk > SAKURA_BATCH_MAX_N) return SAKURA_E_ARG;
+    }
+    if (nsteps == 0) return SAKURA_OK;
+    BatchCache &bc = g.batch;
+    int rc;
+    const bool new_schedule =
+        bc.host_offsets.size() != (size_t)nsys + 1 ||
+        !std::equal(bc.host_offsets.begin(), bc.host_offsets.end(), host_offsets);
+    if (new_schedule) {
+        std::vector<int> tb, ts;
+        sakura::build_batch_schedule(host_offsets, nsys, tb, ts);
+        if ((rc = grow(bc.task_begin, tb.size() * sizeof(int)))) return rc;
+        if ((rc = grow(bc.task_sys, ts.size() * sizeof(int)))) return rc;
+        if ((rc = grow(bc.counter, sizeof(int)))) return rc;
+        if (cudaMemcpyAsync(bc.task_begin.ptr, tb.data(), tb.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, g.stream) != cudaSuccess ||
+            cudaMemcpyAsync(bc.task_sys.ptr, ts.data(), ts.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, g.stream) != cudaSuccess ||
+            cudaStreamSynchronize(g.stream) != cudaSuccess)
+            return SAKURA_E_CUDA;
+        bc.host_offsets.assign(host_offsets, host_offsets + nsys + 1);
+        bc.ntasks = (int)tb.size() - 1;
+        bc.tuned = false;
+        if (bc.exec) cudaGraphExecDestroy(bc.exec);
+        bc.exec = nullptr;
+    }
+    const int64_t total = host_offsets[nsys];
+    const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
+    sakura::BatchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.state = state;
+    a.mass = masses;
+    a.offsets = offsets;
+    a.dt = dt;
+    a.task_begin = (const int *)bc.task_begin.ptr;
+    a.task_sys = (const int *)bc.task_sys.ptr;
+    a.ntasks = bc.ntasks;
+    a.counter = (int *)bc.counter.ptr;
+    a.total = total;
+    a.nsteps = nsteps;
+    a.drift_frac = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
+    a.post_drift_frac = order == 2 ? 0.5 : (order == 1 ? 1.0 : 0.0);
+    a.pre = a.drift_frac;
+    a.post = 1.0 - a.pre;
+    a.tol = g.cfg.kepler_tol * DBL_EPSILON;
+    a.max_iter = g.cfg.kepler_max_iter;
+    a.bisection = g.cfg.kepler_bisection;
+    a.guess = g.cfg.guess == SAKURA_GUESS_TAYLOR ? 2 : 0;
+    a.status = g.d_status;
+    a.stats = g.d_stats;
+
+    // autotune the block shape once per schedule, on a scratch copy
+    static const int kCand[4] = {1, 2, 4, 8};
+    if (!bc.tuned) {
+        bc.warps = g.cfg.block_warps > 0 ? g.cfg.block_warps : 4;
+        if (bc.warps != 1 && bc.warps != 2 && bc.warps != 4 && bc.warps != 8) bc.warps = 4;
+        bc.blocks = g.cfg.grid_blocks > 0 ? g.cfg.grid_blocks
+                                          : g.sm_count * sakura::batched_blocks_per_sm(bc.warps,
+                                                                                      stats);
+        if (!(g.cfg.flags & SAKURA_FLAG_NO_AUTOTUNE) && g.cfg.block_warps <= 0 &&
+            g.cfg.grid_blocks <= 0) {
+            if ((rc = grow(bc.tune_state, 6 * (size_t)total * sizeof(double)))) return rc;
+            sakura::BatchArgs t = a;
+            t.state = (double *)bc.tune_state.ptr;
+            t.nsteps = 1;
+            t.stats = g.d_stats;
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            double best = 1e300;
+            for (int c = 0; c < 4; ++c) {
+                const int w = kCand[c];
+                const int blocks = g.sm_count * sakura::batched_blocks_per_sm(w, false);
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; ++rep) {  // first launch warms up
+                    cudaMemcpyAsync(t.state, state, 6 * (size_t)total * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, g.stream);
+                    cudaMemsetAsync(t.counter, 0, sizeof(int), g.stream);
+                    cudaEventRecord(e0, g.stream);
+                    sakura::launch_batched(t, w, blocks, false, g.stream);
+                    cudaEventRecord(e1, g.stream);
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&ms, e0, e1);
+                }
+                bc.tuned_ms[c] = ms;
+                if (ms < best) {
+                    best = ms;
+                    bc.warps = w;
+                    bc.blocks = blocks;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (cudaGetLastError() != cudaSuccess) return SAKURA_E_CUDA;
+            // the tuning launches touched only the scratch copy; clear their
+            // status bits and statistics
+            cudaMemsetAsync(g.d_status, 0, sizeof(unsigned), g.stream);
+            cudaMemsetAsync(g.d_stats, 0, sakura::kStatCount * sizeof(unsigned long long),
+                            g.stream);
+        }
+        if (stats)
+            bc.blocks = g.sm_count * sakura::batched_blocks_per_sm(bc.warps, true);
+        bc.tuned = true;
+    }
+    // (re)build the graph when anything it captured changed
+    const bool same = bc.exec && bc.graph_warps == bc.warps && bc.graph_blocks == bc.blocks &&
+                      bc.graph_stats == stats &&
+                      std::memcmp(&bc.graph_args, &a, sizeof(a)) == 0;
+    if (!same) {
+        if (bc.exec) cudaGraphExecDestroy(bc.exec);
+        bc.exec = nullptr;
+        if (sakura::build_batched_graph(a, bc.warps, bc.blocks, stats, &bc.exec) != cudaSuccess) {
+            cudaGetLastError();
+            return SAKURA_E_CUDA;
+        }
+        bc.graph_args = a;
+        bc.graph_warps = bc.warps;
+        bc.graph_blocks = bc.blocks;
+        bc.graph_stats = stats;
+    }
+    if (cudaGraphLaunch(bc.exec, g.stream) != cudaSuccess) {
+        cudaGetLastError();
+        return SAKURA_E_CUDA;
+    }
+    g.steps += nsteps;
+    int64_t pairs = 0;
+    for (int k = 0; k < nsys; ++k) {
+        const int64_t nk = host_offsets[k + 1] - host_offsets[k];
+        pairs += nk * (nk - 1);
+    }
+    g.pairs += pairs * nsteps;
+    if (g.cfg.flags & SAKURA_FLAG_SYNC_CHECK) return drain_status();
+    return SAKURA_OK;
+}
+
+int sakura_batched_tuning(int *warps, int *blocks, double times_ms[4])
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    if (!g.batch.tuned) return SAKURA_E_ARG;
+    if (warps) *warps = g.batch.warps;
+    if (blocks) *blocks = g.batch.blocks;
+    if (times_ms)
+        for (int c = 0; c < 4; ++c) times_ms[c] = g.batch.tuned_ms[c];
+    return SAKURA_OK;
 }
 
 int sakura_load_mlp(const void *weights, size_t bytes)

@@ -1,0 +1,317 @@
+// step_batched.cu -- many independent small systems in one persistent launch.
+//
+// The systems of an ensemble never interact, so a warp can take a system (or
+// several small ones) and run all requested steps on it without any
+// synchronisation beyond its own lanes: the state lives in shared memory for
+// the whole launch.
+//
+// Schedule (built on the host when the offsets change): systems with N > 32
+// get a warp each (lane l owns rows l and l + 32); systems with N <= 32 are
+// packed first-fit-decreasing into warps with at most 32 particles in total
+// (one row per lane).  Tasks are sorted by cost and handed out through an
+// atomic counter (dynamic longest-first).
+//
+// Per step, per warp: each lane drifts its rows (Eq. 27a), then the lanes walk
+// their rows' j in ascending order in lockstep; every position of that walk is
+// one warp-synchronous FP64 Kepler solve of 32 pairs (same solver as the
+// single-system kernel); each lane accumulates m_j delta / m_ij for its rows
+// in registers (Eq. 23), and after a __syncwarp applies Eqs. 27b-d to its
+// rows in shared memory.  Each system keeps its own dt.
+//
+// The counter reset and the launch form a CUDA graph that is built once per
+// (buffers, schedule, nsteps, order, launch shape) and replayed.  A small
+// autotuner times the candidate block shapes on a scratch copy of the state
+// the first time a schedule is used.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cfloat>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "kepler_fp64.cuh"
+#include "pair_batch_fp64.cuh"
+#include "step_common.cuh"
+#include "step_batched.cuh"
+
+namespace sakura {
+
+constexpr int kBatchMaxN = 64;
+
+template <int WARPS, bool STATS>
+__global__ void __launch_bounds__(WARPS * 32)
+    batched_kernel(BatchArgs a)
+{
+    __shared__ double sh[WARPS][7][kBatchMaxN];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    double(*S)[kBatchMaxN] = sh[wib];
+    const int64_t tot = a.total;
+    const KeplerParams kp{a.tol, a.max_iter, a.bisection};
+    unsigned status = 0;
+    long long it_sum = 0, slots = 0, fallbacks = 0;
+    int it_max = 0;
+
+    while (true) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(a.counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= a.ntasks) break;
+        const int sb = a.task_begin[t], se = a.task_begin[t + 1];
+        int my_sys = -1, my_base = 0, my_N = 0, my_row = 0;
+        int base = 0;
+        for (int q = sb; q < se; ++q) {
+            const int k = a.task_sys[q];
+            const int64_t o0 = a.offsets[k];
+            const int Nk = (int)(a.offsets[k + 1] - o0);
+            for (int pi = lane; pi < Nk; pi += 32) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) S[c][base + pi] = a.state[c * tot + o0 + pi];
+                const double m = a.mass[o0 + pi];
+                if (!(m > 0.0)) status |= kStatusMass;
+                S[6][base + pi] = m;
+            }
+            if (Nk > 32) {
+                my_sys = k;
+                my_row = lane;
+                my_base = 0;
+                my_N = Nk;
+            } else if (lane >= base && lane < base + Nk) {
+                my_sys = k;
+                my_row = lane - base;
+                my_base = base;
+                my_N = Nk;
+            }
+            base += Nk;
+        }
+        __syncwarp();
+        const int nrows = my_sys < 0 ? 0 : (my_N > 32 ? (lane + 32 < my_N ? 2 : 1) : 1);
+        const double tau = my_sys >= 0 ? a.dt[my_sys] : 0.0;
+        const double drift = a.drift_frac * tau;
+        const double post_drift = a.post_drift_frac * tau;
+        const int mylen = nrows * (my_N - 1);
+        const int maxlen = __reduce_max_sync(0xffffffffu, mylen > 0 ? mylen : 0);
+
+        for (int step = 0; step < a.nsteps; ++step) {
+            for (int r = 0; r < nrows; ++r) {
+                const int i = my_base + my_row + 32 * r;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) S[c][i] = fma(S[3 + c][i], drift, S[c][i]);
+            }
+            __syncwarp();
+            double acc0[6] = {0, 0, 0, 0, 0, 0}, acc1[6] = {0, 0, 0, 0, 0, 0};
+            int r = 0, jp = 0;
+            for (int jj = 0; jj < maxlen; ++jj) {
+                const bool valid = jj < mylen;
+                PairSolve p;
+                double mj = 0.0;
+                if (valid) {
+                    const int il = my_row + 32 * r;
+                    const int jl = jp + (jp >= il ? 1 : 0);
+                    const int i = my_base + il, j = my_base + jl;
+                    mj = S[6][j];
+                    pair_setup(p, tau, S[6][i] + mj, S[0][i] - S[0][j], S[1][i] - S[1][j],
+                               S[2][i] - S[2][j], S[3][i] - S[3][j], S[4][i] - S[4][j],
+                               S[5][i] - S[5][j], a.pre, a.guess);
+                } else {
+                    p.done = true;
+                    p.beta = p.s = 0.0;
+                    p.iters = 0;
+                    p.status = 0;
+                }
+                double d[6];
+                int iters = 0, fb = 0;
+                fp64_solve_warp(p, valid, tau, a.post, kp, d, iters, fb);
+                if (valid) {
+                    if (r == 0) {
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) acc0[q] = fma(mj, d[q], acc0[q]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) acc1[q] = fma(mj, d[q], acc1[q]);
+                    }
+                    status |= p.status;
+                    if (++jp == my_N - 1) {
+                        jp = 0;
+                        ++r;
+                    }
+                }
+                if (STATS) {
+                    it_sum += iters;
+                    fallbacks += fb;
+                    it_max = max(it_max, iters);
+                    const int wmax = __reduce_max_sync(0xffffffffu, iters);
+                    if (lane == 0) slots += 32LL * wmax;
+                }
+            }
+            __syncwarp();
+            for (int rr = 0; rr < nrows; ++rr) {
+                const int i = my_base + my_row + 32 * rr;
+                const double *dd = rr == 0 ? acc0 : acc1;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double v1 = S[3 + c][i] + dd[3 + c];
+                    S[c][i] = fma(v1, post_drift, S[c][i] + dd[c]);
+                    S[3 + c][i] = v1;
+                }
+            }
+            __syncwarp();
+        }
+        // write the task's systems back
+        base = 0;
+        for (int q = sb; q < se; ++q) {
+            const int k = a.task_sys[q];
+            const int64_t o0 = a.offsets[k];
+            const int Nk = (int)(a.offsets[k + 1] - o0);
+            for (int pi = lane; pi < Nk; pi += 32) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    const double x = S[c][base + pi];
+                    if (!isfinite(x)) status |= kStatusNonfinite;
+                    a.state[c * tot + o0 + pi] = x;
+                }
+            }
+            base += Nk;
+        }
+        __syncwarp();
+    }
+    status = __reduce_or_sync(0xffffffffu, status);
+    if (lane == 0 && status) atomicOr(a.status, status);
+    if (STATS) {
+        long long s1 = it_sum, s2 = slots, s3 = fallbacks;
+        int mx = it_max;
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) {
+            atomicAdd(&a.stats[kStatIters], (unsigned long long)s1);
+            atomicAdd(&a.stats[kStatSlots], (unsigned long long)s2);
+            atomicAdd(&a.stats[kStatFallbacks], (unsigned long long)s3);
+            atomicMax(&a.stats[kStatMaxIters], (unsigned long long)mx);
+        }
+    }
+}
+
+namespace {
+
+template <int W>
+const void *kernel_ptr(bool stats)
+{
+    return stats ? (const void *)batched_kernel<W, true> : (const void *)batched_kernel<W, false>;
+}
+
+const void *batched_kernel_ptr(int warps, bool stats)
+{
+    switch (warps) {
+    case 1: return kernel_ptr<1>(stats);
+    case 2: return kernel_ptr<2>(stats);
+    case 8: return kernel_ptr<8>(stats);
+    default: return kernel_ptr<4>(stats);
+    }
+}
+
+}  // namespace
+
+int batched_blocks_per_sm(int warps, bool stats)
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_kernel_ptr(warps, stats),
+                                                      warps * 32, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return b > 0 ? b : 1;
+}
+
+// Schedule: systems with N > 32 alone, the others packed first-fit-decreasing
+// into warps of at most 32 particles; tasks sorted by cost (lockstep length
+// (N-1) x rows per lane) so the atomic counter hands out the longest first.
+void build_batch_schedule(const int64_t *offsets, int nsys, std::vector<int> &task_begin,
+                          std::vector<int> &task_sys)
+{
+    std::vector<int> order(nsys);
+    std::iota(order.begin(), order.end(), 0);
+    auto size = [&](int k) { return (int)(offsets[k + 1] - offsets[k]); };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return size(a) > size(b); });
+    struct Bin {
+        int cap;
+        int cost;
+        std::vector<int> sys;
+    };
+    std::vector<Bin> bins;
+    for (int k : order) {
+        const int N = size(k);
+        if (N > 32) {
+            bins.push_back({0, (N - 1) * 2, {k}});
+            continue;
+        }
+        bool placed = false;
+        // first fit over the most recent bins (sizes are sorted, so earlier
+        // bins are nearly full)
+        const int from = std::max(0, (int)bins.size() - 64);
+        for (int b = from; b < (int)bins.size(); ++b) {
+            if (bins[b].cap >= N && !bins[b].sys.empty() && size(bins[b].sys[0]) <= 32) {
+                bins[b].cap -= N;
+                bins[b].sys.push_back(k);
+                bins[b].cost = std::max(bins[b].cost, N - 1);
+                placed = true;
+                break;
+            }
+        }
+        if (!placed) bins.push_back({32 - N, N - 1, {k}});
+    }
+    std::stable_sort(bins.begin(), bins.end(),
+                     [](const Bin &a, const Bin &b) { return a.cost > b.cost; });
+    task_begin.assign(1, 0);
+    task_sys.clear();
+    for (const Bin &b : bins) {
+        for (int k : b.sys) task_sys.push_back(k);
+        task_begin.push_back((int)task_sys.size());
+    }
+}
+
+void launch_batched(const BatchArgs &a, int warps, int blocks, bool stats, cudaStream_t s)
+{
+    void *args[] = {(void *)&a};
+    cudaLaunchKernel(batched_kernel_ptr(warps, stats), dim3(blocks), dim3(warps * 32), args, 0,
+                     s);
+}
+
+cudaError_t build_batched_graph(const BatchArgs &a, int warps, int blocks, bool stats,
+                                cudaGraphExec_t *exec)
+{
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaMemsetParams mp;
+    std::memset(&mp, 0, sizeof(mp));
+    mp.dst = (void *)a.counter;
+    mp.value = 0;
+    mp.elementSize = sizeof(int);
+    mp.width = 1;
+    mp.height = 1;
+    mp.pitch = sizeof(int);
+    cudaGraphNode_t mset = nullptr, kern = nullptr;
+    e = cudaGraphAddMemsetNode(&mset, graph, nullptr, 0, &mp);
+    if (e == cudaSuccess) {
+        BatchArgs copy = a;
+        void *args[] = {(void *)&copy};
+        cudaKernelNodeParams kpar;
+        std::memset(&kpar, 0, sizeof(kpar));
+        kpar.func = (void *)batched_kernel_ptr(warps, stats);
+        kpar.gridDim = dim3(blocks);
+        kpar.blockDim = dim3(warps * 32);
+        kpar.sharedMemBytes = 0;
+        kpar.kernelParams = args;
+        e = cudaGraphAddKernelNode(&kern, graph, &mset, 1, &kpar);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    return e;
+}
+
+}  // namespace sakura

@@ -39,6 +39,8 @@ GUESS_TAYLOR = 2
 FLAG_SYNC_CHECK = 1
 FLAG_STATS = 2
 FLAG_TIMING = 4
+FLAG_NO_AUTOTUNE = 8
+BATCH_MAX_N = 64
 
 MLP_FLOATS = 6 * 64 + 64 + 64 * 64 + 64 + 64 + 1 + 6 + 6 + 2
 
@@ -107,13 +109,15 @@ def load(path: str = LIB_PATH):
     lib.sakura_load_mlp.argtypes = [P, ctypes.c_size_t]
     lib.sakura_get_stats.argtypes = [ctypes.POINTER(Stats), I]
     lib.sakura_step_noalloc.argtypes = [P, P, I64, D, I, P]
+    lib.sakura_batched_tuning.argtypes = [ctypes.POINTER(I), ctypes.POINTER(I),
+                                          ctypes.POINTER(D)]
     lib.sakura_check.argtypes = []
     lib.sakura_strerror.argtypes = [I]
     lib.sakura_strerror.restype = ctypes.c_char_p
     for name in ("sakura_init", "sakura_finalize", "sakura_set_stream", "sakura_step",
                  "sakura_evolve_host", "sakura_energy", "sakura_step_batched",
                  "sakura_load_mlp", "sakura_get_stats", "sakura_check",
-                 "sakura_step_noalloc"):
+                 "sakura_step_noalloc", "sakura_batched_tuning"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -223,6 +227,16 @@ def step_batched(state, masses, offsets, host_offsets, dt, order: int = 2, nstep
     _check(load().sakura_step_batched(_ptr(state), _ptr(masses), _ptr(offsets),
                                       host_offsets.ctypes.data, nsys, _ptr(dt), int(order),
                                       int(nsteps)), "sakura_step_batched")
+
+
+def batched_tuning():
+    """(warps per block, blocks, {warps: ms}) chosen by the batched autotuner."""
+    w = ctypes.c_int()
+    b = ctypes.c_int()
+    t = (ctypes.c_double * 4)()
+    _check(load().sakura_batched_tuning(ctypes.byref(w), ctypes.byref(b), t),
+           "sakura_batched_tuning")
+    return w.value, b.value, {k: t[c] for c, k in enumerate((1, 2, 4, 8))}
 
 
 def load_mlp(weights):
