@@ -232,7 +232,8 @@ def run_ensemble(args, rank, world, device, stream, dist):
 
     from paper_1402_3325_gb300 import sakura as sk
     ens, _, desc = _workload(args.workload, seed=rank)
-    guess = sk.GUESS_TAYLOR if args.guess == "taylor" else sk.GUESS_STANDARD
+    guess = {"taylor": sk.GUESS_TAYLOR, "standard": sk.GUESS_STANDARD,
+             "learned": sk.GUESS_LEARNED}[args.guess]
     sizes = ens.offsets[1:] - ens.offsets[:-1]
     n2 = int((sizes * sizes).sum())
     st = torch.tensor(ens.state, device=device)
@@ -240,6 +241,9 @@ def run_ensemble(args, rank, world, device, stream, dist):
     off = torch.tensor(ens.offsets, device=device)
     dt = torch.tensor(ens.dt, device=device)
     sk.init(device.index, stream=stream.cuda_stream, guess=guess, flags=sk.FLAG_STATS)
+    if args.guess == "learned":
+        from paper_1402_3325_gb300 import learned
+        learned.load_default()
     sk.step_batched(st, m, off, ens.offsets, dt, 2, args.warmup)   # schedule, autotune
     sk.check()
     stt = sk.get_stats(reset=True)
@@ -311,8 +315,9 @@ def main():
     ap.add_argument("--workload", default="plummer1024",
                     choices=["plummer1024", "bh16384", "binaries16384", "planetary9",
                              "ensemble4096"])
-    ap.add_argument("--guess", default="taylor", choices=["standard", "taylor"],
-                    help="Kepler initial guess: t/r0 or the second-order expansion")
+    ap.add_argument("--guess", default="taylor", choices=["standard", "taylor", "learned"],
+                    help="Kepler initial guess: t/r0, the second-order expansion, or the"
+                         " expansion refined by the trained network")
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: every pair in FP64; mixed: FP32 solves for the pairs the"
                          " class rule admits, FP64 for the rest and all accumulation")
@@ -355,13 +360,17 @@ def main():
         return run_ensemble(args, rank, world, device, stream, dist)
     s, _, desc = _workload(args.workload, seed=rank)
     n = s.n
-    guess = sk.GUESS_TAYLOR if args.guess == "taylor" else sk.GUESS_STANDARD
+    guess = {"taylor": sk.GUESS_TAYLOR, "standard": sk.GUESS_STANDARD,
+             "learned": sk.GUESS_LEARNED}[args.guess]
     form_opts = {}
     if args.form == "mixed":
         form_opts = dict(precision=sk.PREC_MIXED,
                          mixed_rule=sk.MIXED_RULE_HYP if args.mixed_rule == "hyp"
                          else sk.MIXED_RULE_LITERAL)
     sk.init(device.index, stream=stream.cuda_stream, guess=guess, **form_opts)
+    if args.guess == "learned":
+        from paper_1402_3325_gb300 import learned
+        learned.load_default()
 
     state = torch.tensor(s.soa(), device=device)
     mass = torch.tensor(s.m, device=device)

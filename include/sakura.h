@@ -160,12 +160,63 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
  * SAKURA_E_ARG if no batched call has been tuned yet. */
 int sakura_batched_tuning(int *warps, int *blocks, double times_ms[4]);
 
-/* Load the initial-guess network used when cfg.guess = SAKURA_GUESS_LEARNED:
- * a 6-64-64-1 perceptron.  weights: host float32 array laid out as
+/* ---- learned initial guess ------------------------------------------
+ * The paper leaves the Kepler solver's starting value open (Sec. 2.3 only
+ * names a universal-variable solver).  With cfg.guess = SAKURA_GUESS_LEARNED
+ * the second-order guess s_T2 is refined by a 6-64-64-1 tanh perceptron:
+ *   s0 = s_T2 exp(w g(x)), w = q/(1+q), q = tau'^2 (1 + eta'^2 + |beta'|),
+ * tau' = |t| sqrt(m/r0^3), eta' = sign(t) eta0/sqrt(m r0), beta' = beta r0/m,
+ * x = (log tau', asinh eta', asinh beta', tanh(eta' tau'), tanh(beta' tau'^2),
+ * w) normalised, g clamped to [-4, 4]; a warp of 32 pairs that all have
+ * w <= 1e-4 keeps s_T2 without evaluating the network.  The convergence test, the bracket and
+ * the bisection fallback are unchanged, so results do not depend on the
+ * network.  Inference runs inside the pair kernels with BF16 mma.sync (FP32
+ * accumulation), weights in shared memory.  Training runs on the GPU with the
+ * kernels below (FP32). */
+
+/* Load the network: weights is a host float32 array laid out as
  * W1[64][6], b1[64], W2[64][64], b2[64], W3[64], b3[1], then the input
- * normalisation mean[6], scale[6] and output scale, shift (2 floats):
- * 6*64+64+64*64+64+64+1+6+6+2 = 4687 floats.  bytes must equal 4687*4. */
+ * normalisation mean[6], scale[6] and the output scale, shift (2 floats):
+ * 6*64+64+64*64+64+64+1+6+6+2 = 4687 floats.  bytes must equal 4687*4; all
+ * values finite and the six input scales > 0 (else SAKURA_E_ARG).
+ * Synchronises.  Steps with SAKURA_GUESS_LEARNED before a load return
+ * SAKURA_E_ARG. */
 int sakura_load_mlp(const void *weights, size_t bytes);
+
+/* Training data from the method itself: for the ordered pairs
+ * pair_ids[k] = i * n + j (device int64[count]) of the step of order `order`
+ * that starts from state (device double[6][n]) with masses (device double[n]),
+ * runs each pair's FP64 Kepler solve (Eq. 18, standard guess) and writes the
+ * features (device float[count][6]) and the target g = log(s / s_T2) / w
+ * (device float[count]); iters (device int[count] or NULL) receives the
+ * evaluations the standard guess needed.  Synchronises; device faults are
+ * returned. */
+int sakura_sample_pairs(const double *state, const double *masses, int64_t n, double dt,
+                        int order, const int64_t *pair_ids, int64_t count, float *features,
+                        float *targets, int *iters);
+
+/* Mean squared error of the network with FP32 parameters params (device
+ * float[4673], layout as the first 4673 floats of the load blob) on a batch
+ * of raw features (device float[batch][6]) normalised by norm (device
+ * float[12]: mean[6], scale[6]) against targets (device float[batch]); writes
+ * the gradient (device float[4673]) and the loss (device float[1]).
+ * Synchronises. */
+int sakura_mlp_grad(const float *params, const float *norm, const float *features,
+                    const float *targets, int64_t batch, float *grad, float *loss);
+
+/* Adam training (lr, beta1 = 0.9, beta2 = 0.999) of params (device
+ * float[4673], updated in place) for `epochs` passes over nsamples samples in
+ * consecutive minibatches of `batch` (shuffle the data beforehand).  losses:
+ * device float[epochs * (nsamples / batch)] receiving each minibatch loss, or
+ * NULL.  Synchronises. */
+int sakura_mlp_train(float *params, const float *norm, const float *features,
+                     const float *targets, int64_t nsamples, int64_t batch, int epochs, float lr,
+                     float *losses);
+
+/* The loaded network's output g (after output scaling and clamping) for raw
+ * features (device float[count][6]) into out (device float[count]), with the
+ * same BF16 warp inference the pair kernels use.  Synchronises. */
+int sakura_mlp_eval(const float *features, int64_t count, float *out);
 
 /* Copy the accumulated statistics (SAKURA_FLAG_STATS) and reset them if
  * reset != 0.  Synchronises. */

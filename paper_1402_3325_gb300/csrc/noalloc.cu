@@ -140,6 +140,7 @@ extern "C" int sakura_step_noalloc(double *state, const double *masses, int64_t 
     a.max_iter = 50;
     a.bisection = 1;
     a.guess = 0;
+    a.mlp = nullptr;
     a.status = d->status;
     a.stats = nullptr;
     if (n > 1) sakura::launch_pair_step_fp64(a, warps, (int)blocks, false, s);

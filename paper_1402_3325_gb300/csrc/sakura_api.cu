@@ -13,6 +13,7 @@
 
 #include "sakura.h"
 #include "kepler_fp64.cuh"
+#include "mlp_infer.cuh"
 #include "step_batched.cuh"
 #include "step_common.cuh"
 
@@ -31,6 +32,7 @@ struct BatchCache {
     int warps = 4;
     int blocks = 0;
     bool tuned = false;
+    bool tuned_learned = false;
     cudaGraphExec_t exec = nullptr;
     sakura::BatchArgs graph_args{};
     int graph_warps = 0, graph_blocks = 0;
@@ -56,6 +58,8 @@ struct Context {
     double timed_ms = 0.0;
     int64_t timed_launches = 0;
     BatchCache batch;
+    Buffer mlp, mlp_blob, mlp_scratch, mlp_adam;  // learned-guess network and training
+    bool mlp_loaded = false;
 };
 
 Context g;
@@ -155,8 +159,9 @@ Plan plan_step(int64_t n)
     int64_t blocks = g.cfg.grid_blocks;
     if (blocks <= 0) {
         const bool st = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
+        const bool learned = g.cfg.guess == SAKURA_GUESS_LEARNED;
         const int bps = mixed ? sakura::pair_step_mixed_blocks_per_sm(st)
-                              : sakura::pair_step_fp64_blocks_per_sm(p.warps, st);
+                              : sakura::pair_step_fp64_blocks_per_sm(p.warps, st, learned);
         blocks = (int64_t)g.sm_count * bps;
     }
     blocks = std::min<int64_t>(blocks, std::max<int64_t>(1, B / p.warps));
@@ -196,6 +201,9 @@ int step_device(double *state, const double *masses, int64_t n, double dt, int o
     a.max_iter = g.cfg.kepler_max_iter;
     a.bisection = g.cfg.kepler_bisection;
     a.guess = g.cfg.guess == SAKURA_GUESS_TAYLOR ? 2 : 0;
+    a.mlp = (g.cfg.guess == SAKURA_GUESS_LEARNED && !mixed)
+                ? (const sakura::MlpWeights *)g.mlp.ptr
+                : nullptr;
     a.status = g.d_status;
     a.stats = g.d_stats;
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
@@ -312,7 +320,8 @@ int sakura_finalize(void)
     if (g.batch.exec) cudaGraphExecDestroy(g.batch.exec);
     Buffer *bufs[] = {&g.partial,          &g.energy_work,      &g.host_state,
                       &g.host_mass,        &g.batch.task_begin, &g.batch.task_sys,
-                      &g.batch.counter,    &g.batch.tune_state};
+                      &g.batch.counter,    &g.batch.tune_state, &g.mlp,
+                      &g.mlp_blob,         &g.mlp_scratch,      &g.mlp_adam};
     for (Buffer *b : bufs) {
         if (b->ptr) cudaFree(b->ptr);
         b->ptr = nullptr;
@@ -343,6 +352,7 @@ int sakura_step(double *state, const double *masses, int64_t n, double dt, int o
     if (!g.init) return SAKURA_E_NOINIT;
     if (!state || !masses || n < 1 || !valid_order(order) || !std::isfinite(dt))
         return SAKURA_E_ARG;
+    if (g.cfg.guess == SAKURA_GUESS_LEARNED && !g.mlp_loaded) return SAKURA_E_ARG;
     int rc = step_device(state, masses, n, dt, order);
     if (rc) return rc;
     if (g.cfg.flags & SAKURA_FLAG_SYNC_CHECK) return drain_status();
@@ -353,6 +363,7 @@ int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt
                        int nsteps)
 {
     if (!g.init) return SAKURA_E_NOINIT;
+    if (g.cfg.guess == SAKURA_GUESS_LEARNED && !g.mlp_loaded) return SAKURA_E_ARG;
     if (!state || !masses || n < 1 || !valid_order(order) || !std::isfinite(dt) || nsteps < 0)
         return SAKURA_E_ARG;
     int rc = grow(g.host_state, 6 * (size_t)n * sizeof(double));
@@ -410,6 +421,7 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
         if (nk < 1 || nk > SAKURA_BATCH_MAX_N) return SAKURA_E_ARG;
     }
     if (nsteps == 0) return SAKURA_OK;
+    if (g.cfg.guess == SAKURA_GUESS_LEARNED && !g.mlp_loaded) return SAKURA_E_ARG;
     BatchCache &bc = g.batch;
     int rc;
     const bool new_schedule =
@@ -430,6 +442,7 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
         bc.host_offsets.assign(host_offsets, host_offsets + nsys + 1);
         bc.ntasks = (int)tb.size() - 1;
         bc.tuned = false;
+        bc.tuned_learned = false;
         if (bc.exec) cudaGraphExecDestroy(bc.exec);
         bc.exec = nullptr;
     }
@@ -455,17 +468,19 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
     a.max_iter = g.cfg.kepler_max_iter;
     a.bisection = g.cfg.kepler_bisection;
     a.guess = g.cfg.guess == SAKURA_GUESS_TAYLOR ? 2 : 0;
+    a.mlp = g.cfg.guess == SAKURA_GUESS_LEARNED ? (const sakura::MlpWeights *)g.mlp.ptr : nullptr;
     a.status = g.d_status;
     a.stats = g.d_stats;
+    const bool learned = a.mlp != nullptr;
 
     // autotune the block shape once per schedule, on a scratch copy
     static const int kCand[4] = {1, 2, 4, 8};
     if (!bc.tuned) {
         bc.warps = g.cfg.block_warps > 0 ? g.cfg.block_warps : 4;
         if (bc.warps != 1 && bc.warps != 2 && bc.warps != 4 && bc.warps != 8) bc.warps = 4;
-        bc.blocks = g.cfg.grid_blocks > 0 ? g.cfg.grid_blocks
-                                          : g.sm_count * sakura::batched_blocks_per_sm(bc.warps,
-                                                                                      stats);
+        bc.blocks = g.cfg.grid_blocks > 0
+                        ? g.cfg.grid_blocks
+                        : g.sm_count * sakura::batched_blocks_per_sm(bc.warps, stats, learned);
         if (!(g.cfg.flags & SAKURA_FLAG_NO_AUTOTUNE) && g.cfg.block_warps <= 0 &&
             g.cfg.grid_blocks <= 0) {
             if ((rc = grow(bc.tune_state, 6 * (size_t)total * sizeof(double)))) return rc;
@@ -479,7 +494,7 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
             double best = 1e300;
             for (int c = 0; c < 4; ++c) {
                 const int w = kCand[c];
-                const int blocks = g.sm_count * sakura::batched_blocks_per_sm(w, false);
+                const int blocks = g.sm_count * sakura::batched_blocks_per_sm(w, false, learned);
                 float ms = 0.f;
                 for (int rep = 0; rep < 2; ++rep) {  // first launch warms up
                     cudaMemcpyAsync(t.state, state, 6 * (size_t)total * sizeof(double),
@@ -508,10 +523,17 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
                             g.stream);
         }
         if (stats)
-            bc.blocks = g.sm_count * sakura::batched_blocks_per_sm(bc.warps, true);
+            bc.blocks = g.sm_count * sakura::batched_blocks_per_sm(bc.warps, true, learned);
         bc.tuned = true;
     }
     // (re)build the graph when anything it captured changed
+    if (bc.tuned_learned != learned) {
+        // occupancy differs with the network in shared memory
+        bc.blocks = g.cfg.grid_blocks > 0
+                        ? g.cfg.grid_blocks
+                        : g.sm_count * sakura::batched_blocks_per_sm(bc.warps, stats, learned);
+        bc.tuned_learned = learned;
+    }
     const bool same = bc.exec && bc.graph_warps == bc.warps && bc.graph_blocks == bc.blocks &&
                       bc.graph_stats == stats &&
                       std::memcmp(&bc.graph_args, &a, sizeof(a)) == 0;
@@ -556,8 +578,107 @@ int sakura_batched_tuning(int *warps, int *blocks, double times_ms[4])
 int sakura_load_mlp(const void *weights, size_t bytes)
 {
     if (!g.init) return SAKURA_E_NOINIT;
-    if (!weights || bytes != 4687 * sizeof(float)) return SAKURA_E_ARG;
-    return SAKURA_E_ARG;
+    if (!weights || bytes != (size_t)sakura::kMlpBlob * sizeof(float)) return SAKURA_E_ARG;
+    const float *w = (const float *)weights;
+    for (int k = 0; k < sakura::kMlpBlob; ++k)
+        if (!std::isfinite(w[k])) return SAKURA_E_ARG;
+    for (int k = 0; k < 6; ++k)
+        if (!(w[sakura::kMlpParams + 6 + k] > 0.0f)) return SAKURA_E_ARG;  // input scales
+    int rc;
+    if ((rc = grow(g.mlp, sizeof(sakura::MlpWeights)))) return rc;
+    if ((rc = grow(g.mlp_blob, bytes))) return rc;
+    if (cudaMemcpyAsync(g.mlp_blob.ptr, weights, bytes, cudaMemcpyHostToDevice, g.stream) !=
+        cudaSuccess)
+        return SAKURA_E_CUDA;
+    sakura::launch_mlp_pack((const float *)g.mlp_blob.ptr, (sakura::MlpWeights *)g.mlp.ptr,
+                            g.stream);
+    if (cudaStreamSynchronize(g.stream) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return SAKURA_E_CUDA;
+    g.mlp_loaded = true;
+    return SAKURA_OK;
+}
+
+int sakura_sample_pairs(const double *state, const double *masses, int64_t n, double dt,
+                        int order, const int64_t *pair_ids, int64_t count, float *features,
+                        float *targets, int *iters)
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    if (!state || !masses || !pair_ids || !features || !targets || n < 2 || count < 0 ||
+        !valid_order(order) || !std::isfinite(dt))
+        return SAKURA_E_ARG;
+    if (count == 0) return SAKURA_OK;
+    // the drifted state X[7][n] in the head of the step scratch
+    int rc = grow(g.partial, (size_t)7 * n * sizeof(double));
+    if (rc) return rc;
+    double *X = (double *)g.partial.ptr;
+    const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
+    const double pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
+    sakura::launch_prep_step(state, masses, X, n, drift, g.d_status, g.stream);
+    sakura::launch_sample_pairs(X, n, dt, pre, pair_ids, count, features, targets, iters,
+                                g.cfg.kepler_tol * DBL_EPSILON, g.d_status, g.stream);
+    if (launch_error()) return SAKURA_E_CUDA;
+    return drain_status();
+}
+
+int sakura_mlp_grad(const float *params, const float *norm, const float *features,
+                    const float *targets, int64_t batch, float *grad, float *loss)
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    if (!params || !norm || !features || !targets || !grad || !loss || batch < 1)
+        return SAKURA_E_ARG;
+    int rc = grow(g.mlp_scratch, sakura::mlp_grad_scratch_floats(batch) * sizeof(float));
+    if (rc) return rc;
+    sakura::launch_mlp_grad(params, norm, features, targets, batch, (float *)g.mlp_scratch.ptr,
+                            grad, loss, g.stream);
+    if (launch_error()) return SAKURA_E_CUDA;
+    return cudaStreamSynchronize(g.stream) == cudaSuccess ? SAKURA_OK : SAKURA_E_CUDA;
+}
+
+int sakura_mlp_train(float *params, const float *norm, const float *features,
+                     const float *targets, int64_t nsamples, int64_t batch, int epochs, float lr,
+                     float *losses)
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    if (!params || !norm || !features || !targets || nsamples < 1 || batch < 1 || epochs < 0 ||
+        !(lr > 0.0f))
+        return SAKURA_E_ARG;
+    batch = std::min(batch, nsamples);
+    const int P = sakura::kMlpParams;
+    int rc = grow(g.mlp_scratch, sakura::mlp_grad_scratch_floats(batch) * sizeof(float));
+    if (rc) return rc;
+    if ((rc = grow(g.mlp_adam, (size_t)(3 * P + 1) * sizeof(float)))) return rc;
+    float *m = (float *)g.mlp_adam.ptr, *v = m + P, *gr = v + P, *lossbuf = gr + P;
+    if (cudaMemsetAsync(m, 0, 2 * P * sizeof(float), g.stream) != cudaSuccess)
+        return SAKURA_E_CUDA;
+    const int64_t per_epoch = nsamples / batch;
+    int64_t t = 0;
+    double b1t = 1.0, b2t = 1.0;
+    for (int e = 0; e < epochs; ++e) {
+        for (int64_t k = 0; k < per_epoch; ++k) {
+            const int64_t off = k * batch;
+            float *lp = losses ? losses + t : lossbuf;
+            sakura::launch_mlp_grad(params, norm, features + off * 6, targets + off, batch,
+                                    (float *)g.mlp_scratch.ptr, gr, lp, g.stream);
+            ++t;
+            b1t *= 0.9;
+            b2t *= 0.999;
+            sakura::launch_adam(params, m, v, gr, lr, (float)b1t, (float)b2t, g.stream);
+        }
+    }
+    if (launch_error()) return SAKURA_E_CUDA;
+    return cudaStreamSynchronize(g.stream) == cudaSuccess ? SAKURA_OK : SAKURA_E_CUDA;
+}
+
+int sakura_mlp_eval(const float *features, int64_t count, float *out)
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    if (!g.mlp_loaded) return SAKURA_E_ARG;
+    if (!features || !out || count < 0) return SAKURA_E_ARG;
+    if (count == 0) return SAKURA_OK;
+    sakura::launch_mlp_eval((const sakura::MlpWeights *)g.mlp.ptr, features, count, out,
+                            g.stream);
+    if (launch_error()) return SAKURA_E_CUDA;
+    return cudaStreamSynchronize(g.stream) == cudaSuccess ? SAKURA_OK : SAKURA_E_CUDA;
 }
 
 int sakura_get_stats(sakura_stats *out, int reset)

@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "kepler_fp64.cuh"
+#include "mlp_infer.cuh"
 #include "pair_batch_fp64.cuh"
 #include "step_common.cuh"
 #include "step_batched.cuh"
@@ -39,11 +40,15 @@ namespace sakura {
 
 constexpr int kBatchMaxN = 64;
 
-template <int WARPS, bool STATS>
+template <int WARPS, bool STATS, bool LEARNED>
 __global__ void __launch_bounds__(WARPS * 32)
     batched_kernel(BatchArgs a)
 {
     __shared__ double sh[WARPS][7][kBatchMaxN];
+    extern __shared__ __align__(16) unsigned char dsm[];
+    MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(dsm);
+    __nv_bfloat16 *mlpStage = reinterpret_cast<__nv_bfloat16 *>(dsm + sizeof(MlpWeights));
+    if (LEARNED) mlp_load_shared(*mlpW, a.mlp);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     double(*S)[kBatchMaxN] = sh[wib];
@@ -113,13 +118,14 @@ __global__ void __launch_bounds__(WARPS * 32)
                     mj = S[6][j];
                     pair_setup(p, tau, S[6][i] + mj, S[0][i] - S[0][j], S[1][i] - S[1][j],
                                S[2][i] - S[2][j], S[3][i] - S[3][j], S[4][i] - S[4][j],
-                               S[5][i] - S[5][j], a.pre, a.guess);
+                               S[5][i] - S[5][j], a.pre, LEARNED ? 2 : a.guess);
                 } else {
                     p.done = true;
                     p.beta = p.s = 0.0;
                     p.iters = 0;
                     p.status = 0;
                 }
+                if (LEARNED) learned_guess_warp(p, valid, *mlpW, mlpStage + wib * 32 * 16);
                 double d[6];
                 int iters = 0, fb = 0;
                 fp64_solve_warp(p, valid, tau, a.post, kp, d, iters, fb);
@@ -199,28 +205,39 @@ __global__ void __launch_bounds__(WARPS * 32)
 namespace {
 
 template <int W>
-const void *kernel_ptr(bool stats)
+const void *kernel_ptr(bool stats, bool learned)
 {
-    return stats ? (const void *)batched_kernel<W, true> : (const void *)batched_kernel<W, false>;
+    if (learned)
+        return stats ? (const void *)batched_kernel<W, true, true>
+                     : (const void *)batched_kernel<W, false, true>;
+    return stats ? (const void *)batched_kernel<W, true, false>
+                 : (const void *)batched_kernel<W, false, false>;
 }
 
-const void *batched_kernel_ptr(int warps, bool stats)
+const void *batched_kernel_ptr(int warps, bool stats, bool learned)
 {
     switch (warps) {
-    case 1: return kernel_ptr<1>(stats);
-    case 2: return kernel_ptr<2>(stats);
-    case 8: return kernel_ptr<8>(stats);
-    default: return kernel_ptr<4>(stats);
+    case 1: return kernel_ptr<1>(stats, learned);
+    case 2: return kernel_ptr<2>(stats, learned);
+    case 8: return kernel_ptr<8>(stats, learned);
+    default: return kernel_ptr<4>(stats, learned);
     }
+}
+
+size_t batched_dyn_smem(int warps, bool learned)
+{
+    return learned ? sizeof(MlpWeights) + (size_t)warps * 32 * 16 * 2 : 0;
 }
 
 }  // namespace
 
-int batched_blocks_per_sm(int warps, bool stats)
+int batched_blocks_per_sm(int warps, bool stats, bool learned)
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_kernel_ptr(warps, stats),
-                                                      warps * 32, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_kernel_ptr(warps, stats, learned),
+                                                      warps * 32,
+                                                      batched_dyn_smem(warps, learned)) !=
+        cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
@@ -276,9 +293,10 @@ void build_batch_schedule(const int64_t *offsets, int nsys, std::vector<int> &ta
 
 void launch_batched(const BatchArgs &a, int warps, int blocks, bool stats, cudaStream_t s)
 {
+    const bool learned = a.mlp != nullptr;
     void *args[] = {(void *)&a};
-    cudaLaunchKernel(batched_kernel_ptr(warps, stats), dim3(blocks), dim3(warps * 32), args, 0,
-                     s);
+    cudaLaunchKernel(batched_kernel_ptr(warps, stats, learned), dim3(blocks), dim3(warps * 32),
+                     args, batched_dyn_smem(warps, learned), s);
 }
 
 cudaError_t build_batched_graph(const BatchArgs &a, int warps, int blocks, bool stats,
@@ -302,10 +320,10 @@ cudaError_t build_batched_graph(const BatchArgs &a, int warps, int blocks, bool 
         void *args[] = {(void *)&copy};
         cudaKernelNodeParams kpar;
         std::memset(&kpar, 0, sizeof(kpar));
-        kpar.func = (void *)batched_kernel_ptr(warps, stats);
+        kpar.func = (void *)batched_kernel_ptr(warps, stats, a.mlp != nullptr);
         kpar.gridDim = dim3(blocks);
         kpar.blockDim = dim3(warps * 32);
-        kpar.sharedMemBytes = 0;
+        kpar.sharedMemBytes = (unsigned)batched_dyn_smem(warps, a.mlp != nullptr);
         kpar.kernelParams = args;
         e = cudaGraphAddKernelNode(&kern, graph, &mset, 1, &kpar);
     }

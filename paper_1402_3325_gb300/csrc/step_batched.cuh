@@ -8,6 +8,8 @@
 
 namespace sakura {
 
+struct MlpWeights;
+
 struct BatchArgs {
     double *state;            // [6][total] SoA of all systems, updated in place
     const double *mass;       // [total]
@@ -26,11 +28,12 @@ struct BatchArgs {
     int max_iter;
     int bisection;
     int guess;
+    const MlpWeights *mlp;    // learned guess network, or nullptr
     unsigned *status;
     unsigned long long *stats;
 };
 
-int batched_blocks_per_sm(int warps, bool stats);
+int batched_blocks_per_sm(int warps, bool stats, bool learned = false);
 void build_batch_schedule(const int64_t *offsets, int nsys, std::vector<int> &task_begin,
                           std::vector<int> &task_sys);
 void launch_batched(const BatchArgs &a, int warps, int blocks, bool stats, cudaStream_t s);

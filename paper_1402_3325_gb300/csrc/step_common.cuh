@@ -9,6 +9,8 @@
 
 namespace sakura {
 
+struct MlpWeights;
+
 // indices into the device statistics counters
 constexpr int kStatIters = 0;
 constexpr int kStatMaxIters = 1;
@@ -27,6 +29,7 @@ struct StepArgs {
     int max_iter;
     int bisection;
     int guess;            // 0 standard, 2 second-order analytic
+    const MlpWeights *mlp; // learned guess network (device), or nullptr
     unsigned *status;
     unsigned long long *stats;
 };
@@ -47,7 +50,20 @@ int pair_step_mixed_blocks_per_sm(bool stats);
 // pair kernel: one persistent wave of `blocks` blocks of `warps` warps
 void launch_pair_step_fp64(const StepArgs &a, int warps, int blocks, bool stats,
                            cudaStream_t s);
-int pair_step_fp64_blocks_per_sm(int warps, bool stats);
+int pair_step_fp64_blocks_per_sm(int warps, bool stats, bool learned = false);
+
+// learned-guess network: data, training and evaluation (mlp.cu)
+void launch_sample_pairs(const double *X, int64_t n, double tau, double pre, const int64_t *ids,
+                         int64_t count, float *feat, float *target, int *iters, double tol,
+                         unsigned *status, cudaStream_t s);
+void launch_mlp_grad(const float *P, const float *norm, const float *feat, const float *target,
+                     int64_t B, float *scratch, float *grad, float *loss, cudaStream_t s);
+size_t mlp_grad_scratch_floats(int64_t B);
+void launch_adam(float *P, float *m, float *v, const float *g, float lr, float b1t, float b2t,
+                 cudaStream_t s);
+void launch_mlp_pack(const float *blob, MlpWeights *W, cudaStream_t s);
+void launch_mlp_eval(const MlpWeights *W, const float *feat, int64_t count, float *out,
+                     cudaStream_t s);
 // number of partial-sum slots per row for W warps
 int pair_step_slots(int64_t n, int64_t W);
 void launch_prep_step(const double *state, const double *mass, double *X, int64_t n,

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include "kepler_fp64.cuh"
+#include "mlp_infer.cuh"
 #include "pair_batch_fp64.cuh"
 #include "step_common.cuh"
 
@@ -51,10 +52,15 @@ __global__ void prep_step_kernel(const double *state, const double *mass, double
     X[6 * n + i] = m;
 }
 
-template <int WARPS, bool STATS>
+template <int WARPS, bool STATS, bool LEARNED>
 __global__ void __launch_bounds__(WARPS * 32)
     pair_step_fp64_kernel(StepArgs a)
 {
+    // learned guess: network and per-warp staging in dynamic shared memory
+    extern __shared__ __align__(16) unsigned char dsm[];
+    MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(dsm);
+    __nv_bfloat16 *mlpStage = reinterpret_cast<__nv_bfloat16 *>(dsm + sizeof(MlpWeights));
+    if (LEARNED) mlp_load_shared(*mlpW, a.mlp);
     const int lane = threadIdx.x & 31;
     const int64_t n = a.n;
     const int64_t nb = (n + 31) >> 5;
@@ -87,8 +93,13 @@ __global__ void __launch_bounds__(WARPS * 32)
         const int64_t j = (jb << 5) + lane;
         const bool valid = (j < n) && (j != i);
         int iters = 0, fb = 0;
-        fp64_pair_batch(X, n, j, valid, xi, yi, zi, vxi, vyi, vzi, mi, a, kp, acc, status, iters,
-                        fb);
+        if (LEARNED)
+            fp64_pair_batch<true>(X, n, j, valid, xi, yi, zi, vxi, vyi, vzi, mi, a, kp, acc,
+                                  status, iters, fb, mlpW,
+                                  mlpStage + (threadIdx.x >> 5) * 32 * 16);
+        else
+            fp64_pair_batch<false>(X, n, j, valid, xi, yi, zi, vxi, vyi, vzi, mi, a, kp, acc,
+                                   status, iters, fb);
         if (STATS) {
             it_sum += iters;
             fallbacks += fb;
@@ -187,48 +198,49 @@ void launch_prep_step(const double *state, const double *mass, double *X, int64_
                                                                                  n, drift, status);
 }
 
+namespace {
+
+template <int W>
+const void *fp64_kernel_ptr(bool stats, bool learned)
+{
+    if (learned)
+        return stats ? (const void *)pair_step_fp64_kernel<W, true, true>
+                     : (const void *)pair_step_fp64_kernel<W, false, true>;
+    return stats ? (const void *)pair_step_fp64_kernel<W, true, false>
+                 : (const void *)pair_step_fp64_kernel<W, false, false>;
+}
+
+const void *fp64_kernel(int warps, bool stats, bool learned)
+{
+    switch (warps) {
+    case 8: return fp64_kernel_ptr<8>(stats, learned);
+    case 16: return fp64_kernel_ptr<16>(stats, learned);
+    default: return fp64_kernel_ptr<4>(stats, learned);
+    }
+}
+
+}  // namespace
+
+size_t learned_smem(int warps) { return sizeof(MlpWeights) + (size_t)warps * 32 * 16 * 2; }
+
 void launch_pair_step_fp64(const StepArgs &a, int warps, int blocks, bool stats,
                            cudaStream_t s)
 {
-    const dim3 grid((unsigned)blocks);
-#define SAKURA_LAUNCH(W)                                                               \
-    if (stats)                                                                         \
-        pair_step_fp64_kernel<W, true><<<grid, W * 32, 0, s>>>(a);                     \
-    else                                                                               \
-        pair_step_fp64_kernel<W, false><<<grid, W * 32, 0, s>>>(a);
-    switch (warps) {
-    case 8: SAKURA_LAUNCH(8) break;
-    case 16: SAKURA_LAUNCH(16) break;
-    default: SAKURA_LAUNCH(4) break;
-    }
-#undef SAKURA_LAUNCH
+    if (warps != 8 && warps != 16) warps = 4;
+    const bool learned = a.mlp != nullptr;
+    void *args[] = {(void *)&a};
+    cudaLaunchKernel(fp64_kernel(warps, stats, learned), dim3(blocks), dim3(warps * 32), args,
+                     learned ? learned_smem(warps) : 0, s);
 }
 
-int pair_step_fp64_blocks_per_sm(int warps, bool stats)
+int pair_step_fp64_blocks_per_sm(int warps, bool stats, bool learned)
 {
+    if (warps != 8 && warps != 16) warps = 4;
     int b = 0;
-    cudaError_t e;
-    switch (warps) {
-    case 8:
-        e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        &b, pair_step_fp64_kernel<8, true>, 8 * 32, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        &b, pair_step_fp64_kernel<8, false>, 8 * 32, 0);
-        break;
-    case 16:
-        e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        &b, pair_step_fp64_kernel<16, true>, 16 * 32, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        &b, pair_step_fp64_kernel<16, false>, 16 * 32, 0);
-        break;
-    default:
-        e = stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        &b, pair_step_fp64_kernel<4, true>, 4 * 32, 0)
-                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                        &b, pair_step_fp64_kernel<4, false>, 4 * 32, 0);
-        break;
-    }
-    if (e != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fp64_kernel(warps, stats, learned),
+                                                      warps * 32,
+                                                      learned ? learned_smem(warps) : 0) !=
+        cudaSuccess) {
         cudaGetLastError();
         return 1;
     }

@@ -109,6 +109,10 @@ def load(path: str = LIB_PATH):
     lib.sakura_load_mlp.argtypes = [P, ctypes.c_size_t]
     lib.sakura_get_stats.argtypes = [ctypes.POINTER(Stats), I]
     lib.sakura_step_noalloc.argtypes = [P, P, I64, D, I, P]
+    lib.sakura_sample_pairs.argtypes = [P, P, I64, D, I, P, I64, P, P, P]
+    lib.sakura_mlp_grad.argtypes = [P, P, P, P, I64, P, P]
+    lib.sakura_mlp_train.argtypes = [P, P, P, P, I64, I64, I, ctypes.c_float, P]
+    lib.sakura_mlp_eval.argtypes = [P, I64, P]
     lib.sakura_batched_tuning.argtypes = [ctypes.POINTER(I), ctypes.POINTER(I),
                                           ctypes.POINTER(D)]
     lib.sakura_check.argtypes = []
@@ -117,7 +121,8 @@ def load(path: str = LIB_PATH):
     for name in ("sakura_init", "sakura_finalize", "sakura_set_stream", "sakura_step",
                  "sakura_evolve_host", "sakura_energy", "sakura_step_batched",
                  "sakura_load_mlp", "sakura_get_stats", "sakura_check",
-                 "sakura_step_noalloc", "sakura_batched_tuning"):
+                 "sakura_step_noalloc", "sakura_batched_tuning", "sakura_sample_pairs",
+                 "sakura_mlp_grad", "sakura_mlp_train", "sakura_mlp_eval"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -244,6 +249,57 @@ def load_mlp(weights):
     import numpy as np
     w = np.ascontiguousarray(weights, dtype=np.float32)
     _check(load().sakura_load_mlp(w.ctypes.data, w.nbytes), "sakura_load_mlp")
+
+
+MLP_PARAMS = 4673
+
+
+def sample_pairs(state, masses, dt: float, pair_ids, order: int = 2, want_iters: bool = False):
+    """Features [count, 6], targets [count] (and iterations) of the given
+    ordered pairs (device int64 tensor of i * n + j), as CUDA tensors."""
+    import torch
+    n = masses.shape[0]
+    count = int(pair_ids.shape[0])
+    feat = torch.empty((count, 6), dtype=torch.float32, device=state.device)
+    tgt = torch.empty((count,), dtype=torch.float32, device=state.device)
+    its = torch.empty((count,), dtype=torch.int32, device=state.device) if want_iters else None
+    _check(load().sakura_sample_pairs(_ptr(state), _ptr(masses), n, float(dt), int(order),
+                                      _ptr(pair_ids), count, _ptr(feat), _ptr(tgt),
+                                      _ptr(its) if its is not None else None),
+           "sakura_sample_pairs")
+    return (feat, tgt, its) if want_iters else (feat, tgt)
+
+
+def mlp_grad(params, norm, features, targets):
+    """(loss, gradient) of the network on one batch; all CUDA float32 tensors."""
+    import torch
+    grad = torch.empty_like(params)
+    loss = torch.empty((1,), dtype=torch.float32, device=params.device)
+    _check(load().sakura_mlp_grad(_ptr(params), _ptr(norm), _ptr(features), _ptr(targets),
+                                  int(targets.shape[0]), _ptr(grad), _ptr(loss)),
+           "sakura_mlp_grad")
+    return float(loss.item()), grad
+
+
+def mlp_train(params, norm, features, targets, batch: int, epochs: int, lr: float):
+    """Adam training in place; returns the minibatch losses (CUDA tensor)."""
+    import torch
+    ns = int(targets.shape[0])
+    steps = epochs * (ns // min(batch, ns))
+    losses = torch.empty((max(1, steps),), dtype=torch.float32, device=params.device)
+    _check(load().sakura_mlp_train(_ptr(params), _ptr(norm), _ptr(features), _ptr(targets), ns,
+                                   int(batch), int(epochs), float(lr), _ptr(losses)),
+           "sakura_mlp_train")
+    return losses[:steps]
+
+
+def mlp_eval(features):
+    """Output of the loaded network for raw features (CUDA float32 [k, 6])."""
+    import torch
+    out = torch.empty((features.shape[0],), dtype=torch.float32, device=features.device)
+    _check(load().sakura_mlp_eval(_ptr(features), int(features.shape[0]), _ptr(out)),
+           "sakura_mlp_eval")
+    return out
 
 
 def get_stats(reset: bool = False) -> dict:
