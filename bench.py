@@ -58,6 +58,8 @@ UNIT = "pair-solves/s"
 C_FIX = 95
 C_EVAL = 41
 C_STEP = 6
+# the symmetric mode adds the column accumulation (6 FMA) to every solve
+C_SYM = 12
 
 # FP64 ALU peak of one GB300: 152 SMs x 2 FP64 FMA units x 2 flop x 2.07 GHz
 # (the unit count follows from the nominal 1.25 TFLOP/s at 2.07 GHz).
@@ -147,19 +149,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _kernel_sources_hash() -> str:
+def _kernel_sources_hash(kernel: str = "pair_step_sym") -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1402_3325_gb300", "csrc")
-    for f in ("kepler_fp64.cuh", "step_fp64.cu"):
+    main = {"pair_step_sym": "step_sym.cu", "pair_step_fp64": "step_fp64.cu"}.get(kernel,
+                                                                               "step_fp64.cu")
+    for f in ("kepler_fp64.cuh", "pair_batch_fp64.cuh", main):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic(workload: str):
+def _profiled_traffic(workload: str, kernel: str):
     """DRAM bytes per pair-kernel launch from the committed ncu summary, or
     None when the summary is missing or the kernel changed since."""
-    path = os.path.join(ROOT, "profiles", f"pair_step_fp64_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -168,7 +172,7 @@ def _profiled_traffic(workload: str):
             if ":" in ln and ln.lstrip().startswith("- "):
                 k, v = ln.lstrip()[2:].split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_sources_sha256_16") != _kernel_sources_hash():
+    if vals.get("kernel_sources_sha256_16") != _kernel_sources_hash(kernel):
         return None
     try:
         return float(vals["dram_bytes_per_launch"])
@@ -318,6 +322,9 @@ def main():
     ap.add_argument("--guess", default="taylor", choices=["standard", "taylor", "learned"],
                     help="Kepler initial guess: t/r0, the second-order expansion, or the"
                          " expansion refined by the trained network")
+    ap.add_argument("--pairs", default="symmetric", choices=["symmetric", "ordered"],
+                    help="symmetric: each unordered pair solved once (Newton's third law);"
+                         " ordered: every ordered pair solved")
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"],
                     help="fp64: every pair in FP64; mixed: FP32 solves for the pairs the"
                          " class rule admits, FP64 for the rest and all accumulation")
@@ -362,9 +369,10 @@ def main():
     n = s.n
     guess = {"taylor": sk.GUESS_TAYLOR, "standard": sk.GUESS_STANDARD,
              "learned": sk.GUESS_LEARNED}[args.guess]
-    form_opts = {}
+    form_opts = {"pair_mode": sk.PAIRS_SYMMETRIC if args.pairs == "symmetric"
+                 else sk.PAIRS_ORDERED}
     if args.form == "mixed":
-        form_opts = dict(precision=sk.PREC_MIXED,
+        form_opts.update(precision=sk.PREC_MIXED,
                          mixed_rule=sk.MIXED_RULE_HYP if args.mixed_rule == "hyp"
                          else sk.MIXED_RULE_LITERAL)
     sk.init(device.index, stream=stream.cuda_stream, guess=guess, **form_opts)
@@ -383,7 +391,8 @@ def main():
         sk.step(state, mass, s.dt, 2)
     sk.check()
     st = sk.get_stats(reset=True)
-    kbar = st["iters"] / max(1, st["pairs"])
+    kbar = st["iters"] / max(1, st["solves"])
+    solves_per_pair = st["solves"] / max(1, st["pairs"])
     fp32_share = st["fp32_pairs"] / max(1, st["pairs"])
     sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_TIMING, guess=guess,
             **form_opts)
@@ -445,28 +454,36 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    flops_pair = C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP
-    achieved = (n * (n - 1) * flops_pair) / (pair_ms * 1e-3) / 1e12
+    symmetric = args.pairs == "symmetric" and args.form == "fp64"
+    flops_solve = C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP + (C_SYM if symmetric else 0)
+    solves = n * (n - 1) * solves_per_pair
+    achieved = solves * flops_solve / (pair_ms * 1e-3) / 1e12
     peak = FP64_PEAK_GFLOPS / 1e3
-    traffic = _profiled_traffic(args.workload)
+    traffic = _profiled_traffic(args.workload,
+                                "pair_step_sym" if symmetric else "pair_step_fp64")
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
-            "kernel": "pair_step_fp64_kernel", "pipe": "fp64",
+            "kernel": "pair_step_sym_kernel" if symmetric else (
+                "pair_step_mixed_kernel" if args.form == "mixed" else "pair_step_fp64_kernel"),
+            "pipe": "fp64",
             "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (derived from the "
                            "nominal 1.25 TFLOP/s; FMA probe measured 1.19)",
-            "flops_per_pair": flops_pair, "kepler_iters_mean": kbar,
+            "flops_per_solve": flops_solve, "kepler_evals_per_solve": kbar,
+            "solves_per_step": solves,
             "pair_kernel_ms": pair_ms, "pair_kernel_share": pair_ms / ms_step}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": desc, "n": n, "dt": s.dt, "order": 2, "form": args.form,
+                       "pairs": args.pairs if args.form == "fp64" else "ordered",
                        "kepler_guess": args.guess,
                        "fp32_pair_share": fp32_share,
                        "pairs_solved_per_step": n * (n - 1),
                        "l2": "256 MB buffer written between timed steps (state fits in L2)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "gpu_launches": 3 * args.steps,
+            "solves_per_pair": solves_per_pair,
             "roofline": roof, "clocks": clocks.summary()}
     if e2e is not None:
         line["e2e"] = e2e

@@ -52,6 +52,10 @@ extern "C" {
 #define SAKURA_MIXED_RULE_LITERAL 0 /* FP32 iff r > r_min and e < e_max           */
 #define SAKURA_MIXED_RULE_HYP 1     /* FP32 iff r > r_min and (e < e_max or e > e_hyp) */
 
+#define SAKURA_PAIRS_ORDERED 0   /* solve every ordered pair (i, j), i != j         */
+#define SAKURA_PAIRS_SYMMETRIC 1 /* solve every unordered pair once and apply it to
+                                    both particles (Newton's third law)            */
+
 #define SAKURA_GUESS_STANDARD 0 /* s0 = t / r0                               */
 #define SAKURA_GUESS_LEARNED 1  /* s0 from the loaded MLP (sakura_load_mlp)   */
 #define SAKURA_GUESS_TAYLOR 2   /* s0 = (t/r0)(1 - eta0 t / (2 r0^2)): second order in t */
@@ -79,6 +83,8 @@ typedef struct sakura_config {
     int block_warps;      /* pair kernel: warps per block (4, 8, 16), 0 = 4       */
     int grid_blocks;      /* pair kernel: blocks of the persistent grid, 0 = one
                              wave of resident blocks                             */
+    int pair_mode;        /* SAKURA_PAIRS_* for the FP64 step (default symmetric;
+                             ordered when the tile partials would pass 16 GB)   */
 } sakura_config;
 
 typedef struct sakura_stats {
@@ -89,6 +95,8 @@ typedef struct sakura_stats {
     int64_t warp_slots;   /* sum over warp batches of 32 x (max lane iterations)  */
     int64_t fp32_pairs;   /* pairs solved in single precision (mixed form)        */
     int64_t fallbacks;    /* pairs that needed bisection or a restart             */
+    int64_t solves;       /* Kepler solves performed (pairs / 2 + diagonal-tile
+                             pairs in the symmetric mode)                        */
     int64_t timed_launches; /* pair-kernel launches timed (SAKURA_FLAG_TIMING)    */
     double pair_kernel_ms;  /* their summed device time, from CUDA events on the
                                library stream                                    */
@@ -117,7 +125,11 @@ int sakura_set_stream(void *stream);
  *               Eq. 19b (backward drift, then Kepler).
  * Every ordered pair (i, j), i != j, is advanced by the universal-variable
  * Kepler flow (Eq. 18) and its increments are summed mass-weighted into
- * particle i (Eq. 23).
+ * particle i (Eq. 23).  With cfg.pair_mode = SAKURA_PAIRS_SYMMETRIC (the
+ * default) each unordered pair is solved once, its two ordered increments
+ * being exact negatives; the library scratch then grows to at most
+ * 8 x 6 x 8 ceil(n/32) n bytes (12 MB at n = 1024, 400 MB at 16384), and
+ * above 16 GB the ordered kernel is used.
  *   state:  device double[6][n], updated in place.
  *   masses: device double[n], all > 0.
  *   n >= 1; dt any finite value (negative integrates backwards).

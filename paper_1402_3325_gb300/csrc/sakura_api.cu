@@ -52,6 +52,7 @@ struct Context {
     Buffer host_state, host_mass;  // device copies for sakura_evolve_host
     int64_t steps = 0;
     int64_t pairs = 0;
+    int64_t solves = 0;
     int sm_count = 152;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> timers;  // pending pair-kernel timings
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare;
@@ -171,8 +172,79 @@ Plan plan_step(int64_t n)
     return p;
 }
 
+// Unordered pairs once (Newton's third law): systolic 32 x 32 tiles.
+int step_device_sym(double *state, const double *masses, int64_t n, double dt, int order)
+{
+    const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
+    const bool learned = g.cfg.guess == SAKURA_GUESS_LEARNED;
+    const int64_t nb = (n + 31) / 32;
+    const int64_t tiles = nb * (nb + 1) / 2;
+    const int bps = sakura::pair_step_sym_blocks_per_sm(stats, learned);
+    const int64_t resident = (int64_t)g.sm_count * bps * 4;
+    // step ranges per tile: enough items for every resident warp (each range
+    // adds nb slots of partials for the apply kernel to read)
+    int S = 1;
+    while (S < 8 && tiles * S < resident) S *= 2;
+    const int64_t items = tiles * S;
+    int64_t blocks = g.cfg.grid_blocks > 0 ? g.cfg.grid_blocks : (int64_t)g.sm_count * bps;
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (items + 3) / 4));
+    const int64_t nslots = nb * S;
+    int rc = grow(g.partial, (size_t)(7 * n + nslots * 6 * n) * sizeof(double));
+    if (rc) return rc;
+    double *X = (double *)g.partial.ptr;
+    double *partial = X + 7 * n;
+    const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
+    const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
+    sakura::launch_prep_step(state, masses, X, n, drift, g.d_status, g.stream);
+    sakura::StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.X = X;
+    a.partial = partial;
+    a.n = n;
+    a.tau = dt;
+    a.pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
+    a.post = 1.0 - a.pre;
+    a.tol = g.cfg.kepler_tol * DBL_EPSILON;
+    a.max_iter = g.cfg.kepler_max_iter;
+    a.bisection = g.cfg.kepler_bisection;
+    a.guess = g.cfg.guess == SAKURA_GUESS_TAYLOR ? 2 : 0;
+    a.mlp = learned ? (const sakura::MlpWeights *)g.mlp.ptr : nullptr;
+    a.status = g.d_status;
+    a.stats = g.d_stats;
+    const bool timing = (g.cfg.flags & SAKURA_FLAG_TIMING) != 0;
+    std::pair<cudaEvent_t, cudaEvent_t> tm{nullptr, nullptr};
+    if (timing) {
+        tm = take_timer();
+        cudaEventRecord(tm.first, g.stream);
+    }
+    sakura::launch_pair_step_sym(a, S, items, (int)blocks, stats, g.stream);
+    if (timing) {
+        cudaEventRecord(tm.second, g.stream);
+        g.timers.push_back(tm);
+    }
+    sakura::launch_apply_sym(state, X, partial, n, nslots, post_drift, g.d_status, g.stream);
+    rc = launch_error();
+    if (rc) return rc;
+    g.steps += 1;
+    g.pairs += n * (n - 1);
+    int64_t diag = 0;  // ordered pairs inside diagonal tiles
+    for (int64_t b = 0; b < nb; ++b) {
+        const int64_t nbk = std::min<int64_t>(32, n - 32 * b);
+        diag += nbk * (nbk - 1);
+    }
+    g.solves += (n * (n - 1) - diag) / 2 + diag;
+    return SAKURA_OK;
+}
+
+// The symmetric mode keeps 32 n (n/32 + 1) doubles of tile partials; beyond
+// kSymMaxBytes the ordered-pair kernel (O(n) scratch) is used instead.
+constexpr double kSymMaxBytes = 16.0 * 1024 * 1024 * 1024;
+
 int step_device(double *state, const double *masses, int64_t n, double dt, int order)
 {
+    if (g.cfg.pair_mode == SAKURA_PAIRS_SYMMETRIC && g.cfg.precision == SAKURA_PREC_FP64 &&
+        n > 1 && 8.0 * 6.0 * 8.0 * (double)((n + 31) / 32) * (double)n <= kSymMaxBytes)
+        return step_device_sym(state, masses, n, dt, order);
     const Plan p = plan_step(n);
     const int64_t slots = sakura::pair_step_slots(n, p.W);
     const bool mixed = g.cfg.precision == SAKURA_PREC_MIXED;
@@ -241,6 +313,7 @@ int step_device(double *state, const double *masses, int64_t n, double dt, int o
     if (rc) return rc;
     g.steps += 1;
     g.pairs += n * (n - 1);
+    g.solves += n * (n - 1);
     return SAKURA_OK;
 }
 
@@ -268,6 +341,7 @@ void sakura_default_config(sakura_config *cfg)
     cfg->flags = 0;
     cfg->block_warps = 0;
     cfg->grid_blocks = 0;
+    cfg->pair_mode = SAKURA_PAIRS_SYMMETRIC;
 }
 
 int sakura_init(const sakura_config *cfg)
@@ -281,6 +355,8 @@ int sakura_init(const sakura_config *cfg)
         return SAKURA_E_ARG;
     if (c.precision != SAKURA_PREC_FP64 && c.precision != SAKURA_PREC_MIXED) return SAKURA_E_ARG;
     if (c.mixed_rule != SAKURA_MIXED_RULE_LITERAL && c.mixed_rule != SAKURA_MIXED_RULE_HYP)
+        return SAKURA_E_ARG;
+    if (c.pair_mode != SAKURA_PAIRS_ORDERED && c.pair_mode != SAKURA_PAIRS_SYMMETRIC)
         return SAKURA_E_ARG;
     if (c.guess != SAKURA_GUESS_STANDARD && c.guess != SAKURA_GUESS_LEARNED &&
         c.guess != SAKURA_GUESS_TAYLOR)
@@ -305,7 +381,7 @@ int sakura_init(const sakura_config *cfg)
                 cudaSuccess &&
             sms > 0)
             g.sm_count = sms;
-        g.steps = g.pairs = 0;
+        g.steps = g.pairs = g.solves = 0;
     }
     g.cfg = c;
     g.stream = (cudaStream_t)c.stream;
@@ -560,6 +636,7 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
         pairs += nk * (nk - 1);
     }
     g.pairs += pairs * nsteps;
+    g.solves += pairs * nsteps;
     if (g.cfg.flags & SAKURA_FLAG_SYNC_CHECK) return drain_status();
     return SAKURA_OK;
 }
@@ -692,6 +769,7 @@ int sakura_get_stats(sakura_stats *out, int reset)
     if (cudaStreamSynchronize(g.stream) != cudaSuccess) return SAKURA_E_CUDA;
     out->steps = g.steps;
     out->pairs = g.pairs;
+    out->solves = g.solves;
     out->iters = (int64_t)h[sakura::kStatIters];
     out->max_iters = (int64_t)h[sakura::kStatMaxIters];
     out->warp_slots = (int64_t)h[sakura::kStatSlots];
@@ -703,7 +781,7 @@ int sakura_get_stats(sakura_stats *out, int reset)
     if (reset) {
         if (cudaMemsetAsync(g.d_stats, 0, sizeof(h), g.stream) != cudaSuccess)
             return SAKURA_E_CUDA;
-        g.steps = g.pairs = 0;
+        g.steps = g.pairs = g.solves = 0;
         g.timed_ms = 0.0;
         g.timed_launches = 0;
     }

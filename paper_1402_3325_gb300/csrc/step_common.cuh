@@ -64,6 +64,13 @@ void launch_adam(float *P, float *m, float *v, const float *g, float lr, float b
 void launch_mlp_pack(const float *blob, MlpWeights *W, cudaStream_t s);
 void launch_mlp_eval(const MlpWeights *W, const float *feat, int64_t count, float *out,
                      cudaStream_t s);
+// symmetric (Newton's third law) pair kernel: items = tiles * S
+int pair_step_sym_blocks_per_sm(bool stats, bool learned);
+void launch_pair_step_sym(const StepArgs &a, int S, int64_t items, int blocks, bool stats,
+                          cudaStream_t s);
+void launch_apply_sym(double *state, const double *X, const double *partial, int64_t n,
+                      int64_t nslots, double post_drift, unsigned *status, cudaStream_t s);
+
 // number of partial-sum slots per row for W warps
 int pair_step_slots(int64_t n, int64_t W);
 void launch_prep_step(const double *state, const double *mass, double *X, int64_t n,

@@ -1,0 +1,255 @@
+// step_sym.cu -- FP64 W step solving every unordered pair once (Newton's third
+// law, which the paper leaves to future implementations, Sec. 2.1).
+//
+// The increments of the ordered pairs (i, j) and (j, i) are exact negatives
+// of each other: every scalar of the solve (r0^2, eta0 = r0.v0, v0^2, beta,
+// zeta0, s, G_k) is unchanged when (r0, v0) -> (-r0, -v0), IEEE negation and
+// round-to-nearest are symmetric, and the increments are linear in (r0, v0).
+// So each pair is solved once and adds  m_j delta/m_ij  to particle i and
+// -m_i delta/m_ij  to particle j (Eq. 23 with 1/m_i folded in).
+//
+// Work: 32 x 32 tiles (row block I, column block J), I <= J, optionally cut
+// into S step ranges.  A warp takes one (tile, range) item.  Lane l owns row
+// i = 32 I + l; at step k it solves the pair with column c = (l + k) mod 32,
+// so the 32 lanes always hold 32 different columns.  Row sums stay in the
+// lane; column sums travel with their column: after each step every lane
+// takes the column accumulator of lane l + 1 (warp shuffle), so the
+// accumulator of column (l + k) mod 32 is in lane l at step k.  Diagonal tiles
+// (I = J) solve their ordered pairs (i != j) and keep only row sums.
+// Partials go to part[slot][6][n] with slot = other_block * S + range: the
+// row sums of tile (I, J) to slot (J, h) of the rows, the column sums to slot
+// (I, h) of the columns.  Every (slot, particle) is written exactly once and
+// the apply kernel adds a particle's nb * S slots in a fixed order
+// (deterministic, no atomics).
+#include <cuda_runtime.h>
+
+#include "kepler_fp64.cuh"
+#include "mlp_infer.cuh"
+#include "pair_batch_fp64.cuh"
+#include "step_common.cuh"
+
+namespace sakura {
+
+__device__ __forceinline__ void tile_of(int64_t t, int64_t &I, int64_t &J)
+{
+    int64_t j = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((j + 1) * (j + 2) / 2 <= t) ++j;
+    while (j * (j + 1) / 2 > t) --j;
+    J = j;
+    I = t - j * (j + 1) / 2;
+}
+
+template <bool STATS, bool LEARNED>
+__global__ void __launch_bounds__(128)
+    pair_step_sym_kernel(StepArgs a, int S, int64_t items)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(dsm);
+    __nv_bfloat16 *mlpStage = reinterpret_cast<__nv_bfloat16 *>(dsm + sizeof(MlpWeights));
+    if (LEARNED) mlp_load_shared(*mlpW, a.mlp);
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t n = a.n;
+    const int64_t W = (int64_t)gridDim.x * 4;
+    const int64_t w = (int64_t)blockIdx.x * 4 + wib;
+    const double *X = a.X;
+    const KeplerParams kp{a.tol, a.max_iter, a.bisection};
+    unsigned status = 0;
+    long long it_sum = 0, slots = 0, fallbacks = 0;
+    int it_max = 0;
+
+    for (int64_t item = w * items / W; item < (w + 1) * items / W; ++item) {
+        const int64_t tile = item / S;
+        const int h = (int)(item - tile * S);
+        int64_t I, J;
+        tile_of(tile, I, J);
+        const bool diag = I == J;
+        const int k0 = h * 32 / S, k1 = (h + 1) * 32 / S;
+        const int64_t i = 32 * I + lane;
+        const bool irow = i < n;
+        double xi = 0, yi = 0, zi = 0, vxi = 0, vyi = 0, vzi = 0, mi = 1;
+        if (irow) {
+            xi = X[i];
+            yi = X[n + i];
+            zi = X[2 * n + i];
+            vxi = X[3 * n + i];
+            vyi = X[4 * n + i];
+            vzi = X[5 * n + i];
+            mi = X[6 * n + i];
+        }
+        double racc[6] = {0, 0, 0, 0, 0, 0}, cacc[6] = {0, 0, 0, 0, 0, 0};
+        for (int k = k0; k < k1; ++k) {
+            const int c = (lane + k) & 31;
+            const int64_t j = 32 * J + c;
+            const bool valid = irow && j < n && (!diag || c != lane);
+            PairSolve p;
+            double mj = 0.0;
+            if (valid) {
+                mj = X[6 * n + j];
+                pair_setup(p, a.tau, mi + mj, xi - X[j], yi - X[n + j], zi - X[2 * n + j],
+                           vxi - X[3 * n + j], vyi - X[4 * n + j], vzi - X[5 * n + j], a.pre,
+                           LEARNED ? 2 : a.guess);
+            } else {
+                p.done = true;
+                p.beta = p.s = 0.0;
+                p.iters = 0;
+                p.status = 0;
+            }
+            if (LEARNED) learned_guess_warp(p, valid, *mlpW, mlpStage + wib * 32 * 16);
+            double d[6];
+            int iters = 0, fb = 0;
+            fp64_solve_warp(p, valid, a.tau, a.post, kp, d, iters, fb);
+            if (valid) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    racc[q] = fma(mj, d[q], racc[q]);
+                    cacc[q] = fma(-mi, d[q], cacc[q]);
+                }
+                status |= p.status;
+            }
+            if (STATS) {
+                it_sum += iters;
+                fallbacks += fb;
+                it_max = max(it_max, iters);
+                const int wmax = __reduce_max_sync(0xffffffffu, iters);
+                if (lane == 0) slots += 32LL * wmax;
+            }
+            if (!diag && k + 1 < k1) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) cacc[q] = __shfl_sync(0xffffffffu, cacc[q], (lane + 1) & 31);
+            }
+        }
+        // row sums of rows i to slot (J, h); column sums to slot (I, h)
+        if (irow) {
+            double *dst = a.partial + (J * S + h) * 6 * n;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) dst[q * n + i] = racc[q];
+        }
+        if (!diag) {
+            const int64_t j = 32 * J + ((lane + k1 - 1) & 31);
+            if (j < n) {
+                double *dst = a.partial + (I * S + h) * 6 * n;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) dst[q * n + j] = cacc[q];
+            }
+        }
+    }
+    status = __reduce_or_sync(0xffffffffu, status);
+    if (lane == 0 && status) atomicOr(a.status, status);
+    if (STATS) {
+        long long s1 = it_sum, s2 = slots, s3 = fallbacks;
+        int mx = it_max;
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) {
+            atomicAdd(&a.stats[kStatIters], (unsigned long long)s1);
+            atomicAdd(&a.stats[kStatSlots], (unsigned long long)s2);
+            atomicAdd(&a.stats[kStatFallbacks], (unsigned long long)s3);
+            atomicMax(&a.stats[kStatMaxIters], (unsigned long long)mx);
+        }
+    }
+}
+
+// Eqs. 27b-d with the nslots slots of each particle added in a fixed order:
+// a block takes 32 particles (one per lane); its kApplyWarps warps sum the
+// slots k = w, w + kApplyWarps, ... of those particles (coalesced loads), and
+// warp 0 adds the warps' sums in warp order and applies the update.
+constexpr int kApplyWarps = 16;
+
+__global__ void __launch_bounds__(32 * kApplyWarps)
+    apply_sym_kernel(double *state, const double *X, const double *partial, int64_t n,
+                     int64_t nslots, double post_drift, unsigned *status)
+{
+    __shared__ double red[kApplyWarps][6][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+    double d[6] = {0, 0, 0, 0, 0, 0};
+    if (i < n) {
+        // four interleaved partial sums per component keep more loads in flight
+        double e[4][6] = {};
+        int64_t k = wid;
+        for (; k + 3 * kApplyWarps < nslots; k += 4 * kApplyWarps) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+                    e[u][q] += partial[((k + u * kApplyWarps) * 6 + q) * n + i];
+        }
+        for (; k < nslots; k += kApplyWarps) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) e[0][q] += partial[(k * 6 + q) * n + i];
+        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) d[q] = (e[0][q] + e[1][q]) + (e[2][q] + e[3][q]);
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) red[wid][q][lane] = d[q];
+    __syncthreads();
+    if (wid != 0 || i >= n) return;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        double t = red[0][q][lane];
+        for (int w = 1; w < kApplyWarps; ++w) t += red[w][q][lane];
+        d[q] = t;
+    }
+    unsigned st = 0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double v1 = X[(3 + q) * n + i] + d[3 + q];
+        const double x1 = fma(v1, post_drift, X[q * n + i] + d[q]);
+        if (!isfinite(x1) || !isfinite(v1)) st |= kStatusNonfinite;
+        state[q * n + i] = x1;
+        state[(3 + q) * n + i] = v1;
+    }
+    if (st) atomicOr(status, st);
+}
+
+namespace {
+
+const void *sym_kernel(bool stats, bool learned)
+{
+    if (learned)
+        return stats ? (const void *)pair_step_sym_kernel<true, true>
+                     : (const void *)pair_step_sym_kernel<false, true>;
+    return stats ? (const void *)pair_step_sym_kernel<true, false>
+                 : (const void *)pair_step_sym_kernel<false, false>;
+}
+
+size_t sym_smem(bool learned) { return learned ? sizeof(MlpWeights) + 4 * 32 * 16 * 2 : 0; }
+
+}  // namespace
+
+int pair_step_sym_blocks_per_sm(bool stats, bool learned)
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sym_kernel(stats, learned), 128,
+                                                      sym_smem(learned)) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return b > 0 ? b : 1;
+}
+
+void launch_pair_step_sym(const StepArgs &a, int S, int64_t items, int blocks, bool stats,
+                          cudaStream_t s)
+{
+    const bool learned = a.mlp != nullptr;
+    int Sv = S;
+    int64_t it = items;
+    void *args[] = {(void *)&a, (void *)&Sv, (void *)&it};
+    cudaLaunchKernel(sym_kernel(stats, learned), dim3(blocks), dim3(128), args, sym_smem(learned),
+                     s);
+}
+
+void launch_apply_sym(double *state, const double *X, const double *partial, int64_t n,
+                      int64_t nslots, double post_drift, unsigned *status, cudaStream_t s)
+{
+    apply_sym_kernel<<<(unsigned)((n + 31) / 32), 32 * kApplyWarps, 0, s>>>(
+        state, X, partial, n, nslots, post_drift, status);
+}
+
+}  // namespace sakura

@@ -29,6 +29,8 @@ E_CUDA = -7
 E_TIMEOUT = -8
 E_NOMEM = -9
 
+PAIRS_ORDERED = 0
+PAIRS_SYMMETRIC = 1
 PREC_FP64 = 0
 PREC_MIXED = 1
 MIXED_RULE_LITERAL = 0
@@ -61,13 +63,14 @@ class Config(ctypes.Structure):
         ("flags", ctypes.c_uint),
         ("block_warps", ctypes.c_int),
         ("grid_blocks", ctypes.c_int),
+        ("pair_mode", ctypes.c_int),
     ]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in
                 ("steps", "pairs", "iters", "max_iters", "warp_slots", "fp32_pairs",
-                 "fallbacks", "timed_launches")] + [("pair_kernel_ms", ctypes.c_double)]
+                 "fallbacks", "solves", "timed_launches")] + [("pair_kernel_ms", ctypes.c_double)]
 
     def as_dict(self):
         d = {k: int(getattr(self, k)) for k, _ in self._fields_[:-1]}

@@ -40,6 +40,7 @@ def test_default_config_values(lib):
     c = sk.default_config()
     assert c.kepler_tol == 4.0 and c.kepler_max_iter == 50 and c.kepler_bisection == 1
     assert c.mixed_r_min == 0.1 and c.mixed_e_max == 0.9 and c.mixed_e_hyp == 10.0
+    assert c.pair_mode == sk.PAIRS_SYMMETRIC
     assert ctypes.sizeof(sk.Config) >= 80
 
 

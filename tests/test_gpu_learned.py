@@ -121,9 +121,9 @@ def test_learned_guess_cuts_iterations_and_keeps_parity(trained):
     std, _, _ = _stats_for(system, sk.GUESS_STANDARD)
     tay, _, _ = _stats_for(system, sk.GUESS_TAYLOR)
     lrn, r, v = _stats_for(system, sk.GUESS_LEARNED, blob)
-    m_std = std["iters"] / std["pairs"]
-    m_lrn = lrn["iters"] / lrn["pairs"]
-    print(f"mean evaluations standard {m_std:.4f} taylor {tay['iters'] / tay['pairs']:.4f}"
+    m_std = std["iters"] / std["solves"]
+    m_lrn = lrn["iters"] / lrn["solves"]
+    print(f"mean evaluations standard {m_std:.4f} taylor {tay['iters'] / tay['solves']:.4f}"
           f" learned {m_lrn:.4f}; max {std['max_iters']} / {tay['max_iters']} /"
           f" {lrn['max_iters']}")
     assert m_lrn < m_std - 0.01

@@ -77,7 +77,8 @@ SMALL = systems_small()
 @pytest.mark.parametrize("order", [2, 1, -1])
 @pytest.mark.parametrize("name,s", SMALL, ids=[n for n, _ in SMALL])
 def test_step_matches_oracle(name, s, order):
-    r, v = gpu_step(s, s.dt, order)
+    with configured(pair_mode=sk.PAIRS_ORDERED):
+        r, v = gpu_step(s, s.dt, order)
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, order, nthreads=NCPU)
     assert rc == oracle.OK
     er, ev = rel_err(r, v, rr, vr)
@@ -87,7 +88,7 @@ def test_step_matches_oracle(name, s, order):
 @pytest.mark.parametrize("guess", [sk.GUESS_STANDARD, sk.GUESS_TAYLOR])
 def test_plummer_1024_step_matches_oracle(guess):
     s = ics.plummer(1024, seed=0)
-    with configured(guess=guess):
+    with configured(guess=guess, pair_mode=sk.PAIRS_ORDERED):
         r, v = gpu_step(s, s.dt, 2)
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
     er, ev = rel_err(r, v, rr, vr)
@@ -97,7 +98,7 @@ def test_plummer_1024_step_matches_oracle(guess):
 @pytest.mark.parametrize("order", [2, 1, -1])
 def test_taylor_guess_small_systems(order):
     for name, s in SMALL[:6]:
-        with configured(guess=sk.GUESS_TAYLOR):
+        with configured(guess=sk.GUESS_TAYLOR, pair_mode=sk.PAIRS_ORDERED):
             r, v = gpu_step(s, s.dt, order)
         rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, order, nthreads=NCPU)
         er, ev = rel_err(r, v, rr, vr)
@@ -112,14 +113,14 @@ def test_taylor_guess_reduces_iterations():
             sk.get_stats(reset=True)
             gpu_step(s, s.dt, 2)
             st = sk.get_stats(reset=True)
-        its[guess] = st["iters"] / st["pairs"]
+        its[guess] = st["iters"] / st["solves"]
     assert its[sk.GUESS_TAYLOR] < its[sk.GUESS_STANDARD] - 0.2
 
 
 @pytest.mark.parametrize("warps,blocks", [(4, 1), (8, 3), (16, 7), (4, 77), (8, 5000)])
 def test_launch_shapes_match_oracle(warps, blocks):
     s = ics.random_cluster(1000, seed=21, mass_spread=1.0)
-    with configured(block_warps=warps, grid_blocks=blocks):
+    with configured(block_warps=warps, grid_blocks=blocks, pair_mode=sk.PAIRS_ORDERED):
         r, v = gpu_step(s, s.dt, 2)
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
     er, ev = rel_err(r, v, rr, vr)
@@ -149,14 +150,15 @@ def _full_size_sample(s, k=48, seed=0):
 
 
 def test_full_size_bh_cluster_sampled():
-    er, ev = _full_size_sample(ics.bh_cluster(16384, seed=0))
+    with configured(pair_mode=sk.PAIRS_ORDERED):
+        er, ev = _full_size_sample(ics.bh_cluster(16384, seed=0))
     assert er <= TOL and ev <= TOL, (er, ev)
 
 
 @pytest.mark.parametrize("guess", [sk.GUESS_STANDARD, sk.GUESS_TAYLOR])
 def test_full_size_plummer_binaries_sampled(guess):
     s = ics.plummer_binaries(16384, seed=0)
-    with configured(guess=guess):
+    with configured(guess=guess, pair_mode=sk.PAIRS_ORDERED):
         er, ev = _full_size_sample(s, seed=1)
     assert er <= TOL and ev <= TOL, (er, ev)
 
@@ -191,10 +193,11 @@ def test_evolve_host_equals_device_steps():
 
 
 def test_stats_count_pairs_and_iterations():
-    sk.get_stats(reset=True)
     s = ics.random_cluster(200, seed=9)
-    gpu_step(s, s.dt, 2, nsteps=2)
-    st = sk.get_stats(reset=True)
+    with configured(pair_mode=sk.PAIRS_ORDERED):
+        sk.get_stats(reset=True)
+        gpu_step(s, s.dt, 2, nsteps=2)
+        st = sk.get_stats(reset=True)
     assert st["steps"] == 2 and st["pairs"] == 2 * 200 * 199
     assert st["iters"] >= st["pairs"] and st["warp_slots"] >= st["iters"]
     assert 1 <= st["max_iters"] <= 50
@@ -253,3 +256,44 @@ def test_argument_errors():
     assert lib.sakura_step(sk._ptr(state), sk._ptr(mass), 4, 0.1, 3) == sk.E_ARG
     assert lib.sakura_step(None, sk._ptr(mass), 4, 0.1, 2) == sk.E_ARG
     assert lib.sakura_step(sk._ptr(state), sk._ptr(mass), 4, float("nan"), 2) == sk.E_ARG
+
+
+# --- symmetric mode: every unordered pair solved once (Newton's third law) ---
+
+@pytest.mark.parametrize("order", [2, 1, -1])
+@pytest.mark.parametrize("name,s", SMALL, ids=[n for n, _ in SMALL])
+def test_symmetric_step_matches_oracle(name, s, order):
+    with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=sk.GUESS_TAYLOR):
+        r, v = gpu_step(s, s.dt, order)
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, order, nthreads=NCPU)
+    er, ev = rel_err(r, v, rr, vr)
+    assert er <= TOL and ev <= TOL, (er, ev)
+
+
+@pytest.mark.parametrize("blocks", [0, 1, 7, 300])
+def test_symmetric_plummer_1024_and_grid_shapes(blocks):
+    s = ics.plummer(1024, seed=0)
+    with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=sk.GUESS_TAYLOR, grid_blocks=blocks):
+        r, v = gpu_step(s, s.dt, 2)
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
+    er, ev = rel_err(r, v, rr, vr)
+    assert er <= TOL and ev <= TOL, (er, ev)
+
+
+def test_symmetric_full_size_binaries_sampled():
+    s = ics.plummer_binaries(16384, seed=0)
+    with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=sk.GUESS_TAYLOR):
+        er, ev = _full_size_sample(s, seed=2)
+    assert er <= TOL and ev <= TOL, (er, ev)
+
+
+def test_symmetric_counts_solves():
+    n = 100  # blocks of 32, 32, 32, 4
+    s = ics.random_cluster(n, seed=9)
+    with configured(pair_mode=sk.PAIRS_SYMMETRIC):
+        sk.get_stats(reset=True)
+        gpu_step(s, s.dt, 2)
+        st = sk.get_stats(reset=True)
+    diag = 3 * 32 * 31 + 4 * 3
+    assert st["pairs"] == n * (n - 1)
+    assert st["solves"] == (n * (n - 1) - diag) // 2 + diag
