@@ -31,6 +31,8 @@
  *     e^{tau H_T}.  order = -1 is the adjoint phi^dagger: drift tau, then W(tau)
  *     with pair map Eq. 19b (backward drift tau, then Kepler tau).
  *   - Energy sums use Neumaier compensated summation.
+ *   - Orders 4, 6, 8 (the paper only says that higher orders come from
+ *     compositions, Sec. 2.2): Yoshida's triple jump of the second-order map.
  *
  * Parity status: every exported function here is pinned by tests/ against
  * closed forms, high-precision (mpmath) classical Kepler solutions, an
@@ -407,11 +409,36 @@ static int evolve_HW(double tau, int64_t n, const double *m, double *r, double *
     return status;
 }
 
+int oracle_step(int64_t n, const double *m, double *r, double *v, double tau, int order,
+                int pair_solver, int nthreads, oracle_stats *st);
+
+/* Orders 4, 6 and 8: the paper (Sec. 2.2, after Eqs. 19a-b) builds higher
+ * orders by composing the symmetric second-order map, as in symplectic
+ * integrators (Yoshida 1990).  Yoshida's triple jump raises a symmetric map
+ * S of order 2k - 2 to order 2k:
+ *     S_2k(tau) = S(x1 tau) S(x0 tau) S(x1 tau),
+ *     x1 = 1 / (2 - 2^(1/(2k-1))),  x0 = -2^(1/(2k-1)) / (2 - 2^(1/(2k-1))),
+ * the three maps applied left to right in time (the outer two are equal, so
+ * the reading of the operator order does not matter). */
+static int step_triple_jump(int64_t n, const double *m, double *r, double *v, double tau,
+                            int order, int pair_solver, int nthreads, oracle_stats *st)
+{
+    const double c = pow(2.0, 1.0 / (double)(order - 1));
+    const double x1 = 1.0 / (2.0 - c);
+    const double x0 = -c / (2.0 - c);
+    int rc = oracle_step(n, m, r, v, x1 * tau, order - 2, pair_solver, nthreads, st);
+    if (rc == ORC_OK) rc = oracle_step(n, m, r, v, x0 * tau, order - 2, pair_solver, nthreads, st);
+    if (rc == ORC_OK) rc = oracle_step(n, m, r, v, x1 * tau, order - 2, pair_solver, nthreads, st);
+    return rc;
+}
+
 /* One step of the integrator on m[n], r[n][3], v[n][3] in place.
  *   order =  2: Psi(tau) = D(tau/2) W(tau) D(tau/2), pair map Eq. 26 (Eq. 25,
  *               Eqs. 27a-d, the paper's listing).
  *   order =  1: phi(tau) = W(tau; Eq. 19a) followed by D(tau).
  *   order = -1: phi^dagger(tau) = D(tau) followed by W(tau; Eq. 19b).
+ *   order =  4, 6, 8: the triple-jump composition of the order below
+ *               (3, 9 or 27 second-order steps, step_triple_jump).
  * pair_solver selects the two-body map inside W: ORC_PAIR_KEPLER (Eq. 18) or
  * ORC_PAIR_DKD (the Eq. 28 substitute).  nthreads: OpenMP threads for the i
  * loop (results do not depend on it).  stats may be NULL. */
@@ -419,6 +446,8 @@ int oracle_step(int64_t n, const double *m, double *r, double *v, double tau, in
                 int pair_solver, int nthreads, oracle_stats *st)
 {
     if (n < 1 || !m || !r || !v) return ORC_E_ARG;
+    if (order == 4 || order == 6 || order == 8)
+        return step_triple_jump(n, m, r, v, tau, order, pair_solver, nthreads, st);
     if (!(order == 2 || order == 1 || order == -1)) return ORC_E_ARG;
     for (int64_t i = 0; i < n; ++i)
         if (!(m[i] > 0.0)) return ORC_E_MASS;

@@ -10,7 +10,11 @@ Expected values come from outside the oracle:
   * second-order convergence against scipy's DOP853 at tight tolerance;
   * time symmetry: exact for N = 2 and for the Eq. 28 limit, O(tau^4) for
     N > 2 (non-commuting pair maps, Eq. 21);
-  * qualitative: planetary energy error far below leapfrog's (Sec. 3.1).
+  * qualitative: planetary energy error far below leapfrog's (Sec. 3.1);
+  * orders 4, 6, 8 (triple-jump compositions, Sec. 2.2): exact for N = 2;
+    fourth and sixth order in the Eq. 28 limit, where the base map is an
+    exactly symmetric leapfrog; third order with Kepler pair maps for N > 2,
+    whose time-symmetry defect is O(tau^4).
 """
 import math
 
@@ -193,9 +197,70 @@ def test_planetary_energy_far_better_than_leapfrog():
     assert worst_s < worst_l / 30
 
 
+@pytest.mark.parametrize("order", [4, 6, 8])
+@pytest.mark.parametrize("tau", [0.37, -0.2, 3.9])
+def test_composed_two_body_step_is_exact(order, tau):
+    # every second-order sub-step is the exact two-body flow for N = 2, so the
+    # composition is exact too if and only if its time weights sum to one
+    pytest.importorskip("mpmath")
+    from classical_kepler import kepler_classical_f64
+    m, r, v = _binary()
+    rc, r1, v1 = oracle.step(m, r, v, tau, order)
+    assert rc == oracle.OK
+    M = m.sum()
+    R = (m[:, None] * r).sum(0) / M
+    V = (m[:, None] * v).sum(0) / M
+    rr, vv = kepler_classical_f64(tau, M, r[0] - r[1], v[0] - v[1])
+    rr, vv = np.array(rr), np.array(vv)
+    exp_r = np.stack([R + tau * V + m[1] / M * rr, R + tau * V - m[0] / M * rr])
+    exp_v = np.stack([V + m[1] / M * vv, V - m[0] / M * vv])
+    assert np.abs(r1 - exp_r).max() <= 2e-14 * max(1.0, abs(tau)) * (order - 1)
+    assert np.abs(v1 - exp_v).max() <= 2e-14 * (order - 1)
+
+
+def _triple():
+    m = np.array([0.5, 0.4, 0.1])
+    r = np.array([[0.05, 0, 0], [-0.0625, 0, 0], [1.5, 0.3, 0]])
+    vin = math.sqrt(0.9 / 0.1125)
+    v = np.array([[0, 0.4 * vin / 0.9, 0], [0, -0.5 * vin / 0.9, 0], [0, 0.75, 0.05]])
+    return m, r, v
+
+
+def _convergence(order, ks, pair_solver=oracle.PAIR_KEPLER):
+    m, r, v = _triple()
+    rref = _reference(m, r, v, 1.0)
+    errs = []
+    for k in ks:
+        rc, r1, _ = oracle.evolve(m, r, v, 2.0 ** -k, 2 ** k, order, pair_solver=pair_solver)
+        assert rc == oracle.OK
+        errs.append(np.abs(r1 - rref).max())
+    return [a / b for a, b in zip(errs, errs[1:])]
+
+
+def test_composition_orders_in_the_symmetric_dkd_limit():
+    # in the Eq. 28 limit the second-order map is the DKD leapfrog, which is
+    # exactly time-symmetric: the triple jump must then give order 4 and 6
+    # (error ratios 16 and 64 per halving), which pins its weights
+    q4 = _convergence(4, (6, 7, 8), oracle.PAIR_DKD)
+    assert 11 < q4[0] < 20 and 13 < q4[1] < 19, q4
+    q6 = _convergence(6, (6, 7, 8), oracle.PAIR_DKD)
+    assert q6[0] > 30 and q6[1] > 45, q6
+
+
+def test_composition_of_kepler_pair_maps_is_third_order():
+    # with Kepler pair maps the second-order step is time-symmetric only up
+    # to O(tau^4) for N > 2 (pair maps computed from one state do not
+    # commute, Eq. 21), and the triple jump cancels odd-order terms only:
+    # the composed step is third order (ratio 8), not fourth
+    q4 = _convergence(4, (6, 7, 8))
+    assert 7.0 < q4[0] < 9.0 and 7.0 < q4[1] < 9.0, q4
+
+
 def test_step_argument_errors():
     m, r, v = _binary()
     assert oracle.step(m, r, v, 0.1, 3)[0] == oracle.E_ARG
+    assert oracle.step(m, r, v, 0.1, 5)[0] == oracle.E_ARG
+    assert oracle.step(m, r, v, 0.1, 10)[0] == oracle.E_ARG
     assert oracle.step(np.array([1.0, 0.0]), r, v, 0.1, 2)[0] == oracle.E_MASS
     rn = r.copy()
     rn[0, 0] = np.nan
