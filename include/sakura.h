@@ -88,8 +88,10 @@ typedef struct sakura_config {
 } sakura_config;
 
 typedef struct sakura_stats {
-    int64_t steps;        /* sakura_step calls since the last reset               */
-    int64_t pairs;        /* ordered pairs solved                                 */
+    int64_t steps;        /* second-order (or first-order) maps applied since the
+                             last reset: one per order-2/1/-1 step, 3 / 9 / 27
+                             per step of order 4 / 6 / 8                         */
+    int64_t pairs;        /* ordered pairs advanced (per map applied)            */
     int64_t iters;        /* Laguerre/Newton iterations summed over pairs         */
     int64_t max_iters;    /* largest iteration count of any pair                  */
     int64_t warp_slots;   /* sum over warp batches of 32 x (max lane iterations)  */
@@ -123,6 +125,14 @@ int sakura_set_stream(void *stream);
  *               map of Eq. 19a (Kepler, then backward drift), then drift tau.
  *   order = -1: phi^dagger(tau): drift tau, then W(tau) with the pair map of
  *               Eq. 19b (backward drift, then Kepler).
+ *   order = 4, 6, 8: Yoshida's triple jump of the order below, down to
+ *               order-2 maps: S_2k(tau) = S_2k-2(x1 tau) S_2k-2(x0 tau)
+ *               S_2k-2(x1 tau), x1 = 1/(2 - 2^(1/(2k-1))), x0 = 1 - 2 x1
+ *               (the composition route to higher orders of Sec. 2.2); 3, 9
+ *               or 27 order-2 maps per step.  The order-2 map is
+ *               time-symmetric only up to O(tau^4) for N > 2, so the
+ *               composed steps converge at third order there (exactly for
+ *               N = 2).
  * Every ordered pair (i, j), i != j, is advanced by the universal-variable
  * Kepler flow (Eq. 18) and its increments are summed mass-weighted into
  * particle i (Eq. 23).  With cfg.pair_mode = SAKURA_PAIRS_SYMMETRIC (the
@@ -133,13 +143,14 @@ int sakura_set_stream(void *stream);
  *   state:  device double[6][n], updated in place.
  *   masses: device double[n], all > 0.
  *   n >= 1; dt any finite value (negative integrates backwards).
- * Errors: E_NOINIT, E_ARG (n < 1, order not in {2,1,-1}, NULL pointer,
- * non-finite dt); device faults as described above. */
+ * Errors: E_NOINIT, E_ARG (n < 1, order not in {2,1,-1,4,6,8}, NULL
+ * pointer, non-finite dt); device faults as described above. */
 int sakura_step(double *state, const double *masses, int64_t n, double dt, int order);
 
 /* nsteps consecutive steps on HOST buffers: copies state and masses to
  * library-owned device memory, runs the steps, copies the state back and
- * synchronises.  state: host double[6][n]; masses: host double[n]. */
+ * synchronises.  state: host double[6][n]; masses: host double[n].  order
+ * as for sakura_step. */
 int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt,
                        int order, int nsteps);
 
@@ -155,7 +166,7 @@ int sakura_energy(const double *state, const double *masses, int64_t n, double *
  *   offsets: device int64[nsys+1]; host_offsets: the same values on the host
  *   (used to build the work schedule, rebuilt when they change);
  *   dt: device double[nsys], one step size per system.
- * Runs nsteps steps of the given order (2, 1, -1) on every system, state
+ * Runs nsteps steps of the given order (2, 1, -1, 4, 6, 8) on every system, state
  * updated in place.  A warp runs all steps of its systems with the state in
  * shared memory; the launch is a CUDA graph (counter reset + kernel), built
  * once per (buffers, schedule, nsteps, order, block shape) and replayed.  The

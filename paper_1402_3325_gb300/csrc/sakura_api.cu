@@ -319,6 +319,50 @@ int step_device(double *state, const double *masses, int64_t n, double dt, int o
 
 bool valid_order(int order) { return order == 2 || order == 1 || order == -1; }
 
+bool valid_step_order(int order)
+{
+    return valid_order(order) || order == 4 || order == 6 || order == 8;
+}
+
+// Sub-steps of one step of the given order: the map itself for orders 2, 1
+// and -1; for orders 4, 6 and 8 Yoshida's triple jump applied to the order
+// below, S_2k(t) = S_2k-2(x1 t) S_2k-2(x0 t) S_2k-2(x1 t) with
+// x1 = 1 / (2 - 2^(1/(2k-1))) and x0 = 1 - 2 x1, down to second-order steps
+// (the paper's route to higher orders, Sec. 2.2).  Writes the time weights
+// (3, 9 or 27 of them) and the order of each sub-step; returns the count.
+int substeps(int order, double *w, int *sub_order)
+{
+    int cnt = 1;
+    w[0] = 1.0;
+    *sub_order = order;
+    if (!(order == 4 || order == 6 || order == 8)) return cnt;
+    *sub_order = 2;
+    for (int k = 4; k <= order; k += 2) {
+        const double c = std::pow(2.0, 1.0 / (double)(k - 1));
+        const double x1 = 1.0 / (2.0 - c);
+        const double x[3] = {x1, 1.0 - 2.0 * x1, x1};
+        double nw[sakura::kMaxSubsteps];
+        int m = 0;
+        for (int q = 0; q < 3; ++q)
+            for (int i = 0; i < cnt; ++i) nw[m++] = x[q] * w[i];
+        cnt = m;
+        std::memcpy(w, nw, cnt * sizeof(double));
+    }
+    return cnt;
+}
+
+int step_composed(double *state, const double *masses, int64_t n, double dt, int order)
+{
+    double w[sakura::kMaxSubsteps];
+    int so;
+    const int cnt = substeps(order, w, &so);
+    for (int u = 0; u < cnt; ++u) {
+        const int rc = step_device(state, masses, n, w[u] * dt, so);
+        if (rc) return rc;
+    }
+    return SAKURA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -426,10 +470,10 @@ int sakura_set_stream(void *stream)
 int sakura_step(double *state, const double *masses, int64_t n, double dt, int order)
 {
     if (!g.init) return SAKURA_E_NOINIT;
-    if (!state || !masses || n < 1 || !valid_order(order) || !std::isfinite(dt))
+    if (!state || !masses || n < 1 || !valid_step_order(order) || !std::isfinite(dt))
         return SAKURA_E_ARG;
     if (g.cfg.guess == SAKURA_GUESS_LEARNED && !g.mlp_loaded) return SAKURA_E_ARG;
-    int rc = step_device(state, masses, n, dt, order);
+    int rc = step_composed(state, masses, n, dt, order);
     if (rc) return rc;
     if (g.cfg.flags & SAKURA_FLAG_SYNC_CHECK) return drain_status();
     return SAKURA_OK;
@@ -440,7 +484,8 @@ int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt
 {
     if (!g.init) return SAKURA_E_NOINIT;
     if (g.cfg.guess == SAKURA_GUESS_LEARNED && !g.mlp_loaded) return SAKURA_E_ARG;
-    if (!state || !masses || n < 1 || !valid_order(order) || !std::isfinite(dt) || nsteps < 0)
+    if (!state || !masses || n < 1 || !valid_step_order(order) || !std::isfinite(dt) ||
+        nsteps < 0)
         return SAKURA_E_ARG;
     int rc = grow(g.host_state, 6 * (size_t)n * sizeof(double));
     if (rc) return rc;
@@ -454,7 +499,7 @@ int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt
                         g.stream) != cudaSuccess)
         return SAKURA_E_CUDA;
     for (int k = 0; k < nsteps; ++k) {
-        rc = step_device(ds, dm, n, dt, order);
+        rc = step_composed(ds, dm, n, dt, order);
         if (rc) return rc;
     }
     if (cudaMemcpyAsync(state, ds, 6 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost,
@@ -489,7 +534,7 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
 {
     if (!g.init) return SAKURA_E_NOINIT;
     if (!state || !masses || !offsets || !host_offsets || !dt || nsys < 1 || nsteps < 0 ||
-        !valid_order(order))
+        !valid_step_order(order))
         return SAKURA_E_ARG;
     if (host_offsets[0] != 0) return SAKURA_E_ARG;
     for (int k = 0; k < nsys; ++k) {
@@ -536,8 +581,10 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
     a.counter = (int *)bc.counter.ptr;
     a.total = total;
     a.nsteps = nsteps;
-    a.drift_frac = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
-    a.post_drift_frac = order == 2 ? 0.5 : (order == 1 ? 1.0 : 0.0);
+    int so;
+    a.nsub = substeps(order, a.sub, &so);
+    a.drift_frac = so == 2 ? 0.5 : (so == 1 ? 0.0 : 1.0);
+    a.post_drift_frac = so == 2 ? 0.5 : (so == 1 ? 1.0 : 0.0);
     a.pre = a.drift_frac;
     a.post = 1.0 - a.pre;
     a.tol = g.cfg.kepler_tol * DBL_EPSILON;
@@ -629,14 +676,14 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
         cudaGetLastError();
         return SAKURA_E_CUDA;
     }
-    g.steps += nsteps;
+    g.steps += (int64_t)nsteps * a.nsub;
     int64_t pairs = 0;
     for (int k = 0; k < nsys; ++k) {
         const int64_t nk = host_offsets[k + 1] - host_offsets[k];
         pairs += nk * (nk - 1);
     }
-    g.pairs += pairs * nsteps;
-    g.solves += pairs * nsteps;
+    g.pairs += pairs * nsteps * a.nsub;
+    g.solves += pairs * nsteps * a.nsub;
     if (g.cfg.flags & SAKURA_FLAG_SYNC_CHECK) return drain_status();
     return SAKURA_OK;
 }

@@ -92,13 +92,15 @@ __global__ void __launch_bounds__(WARPS * 32)
         }
         __syncwarp();
         const int nrows = my_sys < 0 ? 0 : (my_N > 32 ? (lane + 32 < my_N ? 2 : 1) : 1);
-        const double tau = my_sys >= 0 ? a.dt[my_sys] : 0.0;
-        const double drift = a.drift_frac * tau;
-        const double post_drift = a.post_drift_frac * tau;
+        const double dt = my_sys >= 0 ? a.dt[my_sys] : 0.0;
         const int mylen = nrows * (my_N - 1);
         const int maxlen = __reduce_max_sync(0xffffffffu, mylen > 0 ? mylen : 0);
 
-        for (int step = 0; step < a.nsteps; ++step) {
+        for (int64_t sub = 0; sub < (int64_t)a.nsteps * a.nsub; ++sub) {
+            // sub-step sub % nsub of the composition (one sub-step for orders 2, 1, -1)
+            const double tau = dt * a.sub[(int)(sub % a.nsub)];
+            const double drift = a.drift_frac * tau;
+            const double post_drift = a.post_drift_frac * tau;
             for (int r = 0; r < nrows; ++r) {
                 const int i = my_base + my_row + 32 * r;
 #pragma unroll

@@ -10,6 +10,8 @@ namespace sakura {
 
 struct MlpWeights;
 
+constexpr int kMaxSubsteps = 27;
+
 struct BatchArgs {
     double *state;            // [6][total] SoA of all systems, updated in place
     const double *mass;       // [total]
@@ -21,6 +23,8 @@ struct BatchArgs {
     int *counter;             // work counter, zeroed before the launch
     int64_t total;            // particles in all systems (row stride of state)
     int nsteps;
+    int nsub;                 // sub-steps per step: 1, or 3 / 9 / 27 for orders 4 / 6 / 8
+    double sub[kMaxSubsteps]; // time weight of each sub-step (the composition)
     double drift_frac;        // first drift / tau (order 2: 1/2, 1: 0, -1: 1)
     double post_drift_frac;   // last drift / tau (order 2: 1/2, 1: 1, -1: 0)
     double pre, post;         // backward-drift fractions of the pair map
