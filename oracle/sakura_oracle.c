@@ -145,13 +145,17 @@ static double kep_solve(const kep_t *k, const oracle_kepler_opts *o, int *iters,
     double lo, hi;
     int n_it = 0;
 
-    /* Bracket the unique root: F(0) = -t and F'(s) = r(s) > 0. */
+    /* Bracket the unique root: F(0) = -t and F'(s) = r(s) > 0.  F grows
+       without bound away from 0 on the side of the root, so where its
+       evaluation overflows (inf, or inf - inf on a strongly hyperbolic orbit
+       whose guess lies far beyond the root) s is past the root: a
+       non-finite F counts as "past the root" in every test below. */
     if (k->t > 0.0) {
         lo = 0.0;
         hi = s;
         for (int d = 0; d < 400; ++d) {
             kep_eval(k, hi, G, &F, &Fp, &Fpp);
-            if (F >= 0.0) break;
+            if (!(F < 0.0)) break;
             lo = hi;
             hi *= 2.0;
         }
@@ -160,7 +164,7 @@ static double kep_solve(const kep_t *k, const oracle_kepler_opts *o, int *iters,
         lo = s;
         for (int d = 0; d < 400; ++d) {
             kep_eval(k, lo, G, &F, &Fp, &Fpp);
-            if (F <= 0.0) break;
+            if (!(F > 0.0)) break;
             hi = lo;
             lo *= 2.0;
         }
@@ -170,6 +174,15 @@ static double kep_solve(const kep_t *k, const oracle_kepler_opts *o, int *iters,
     for (int it = 0; it < o->max_iter; ++it) {
         kep_eval(k, s, G, &F, &Fp, &Fpp);
         ++n_it;
+        if (!isfinite(F) || !isfinite(Fp) || !isfinite(Fpp)) {
+            /* overflow: s lies past the root; bisect towards it */
+            if (s > 0.0)
+                hi = s;
+            else
+                lo = s;
+            s = 0.5 * (lo + hi);
+            continue;
+        }
         if (F == 0.0) {
             *iters = n_it;
             *ok = 1;
@@ -209,7 +222,12 @@ static double kep_solve(const kep_t *k, const oracle_kepler_opts *o, int *iters,
         if (hi - lo <= 2.0 * eps * fmax(fabs(lo), fabs(hi))) break;
         kep_eval(k, mid, G, &F, &Fp, &Fpp);
         ++n_it;
-        if (F < 0.0)
+        if (!isfinite(F)) {
+            if (mid > 0.0)
+                hi = mid;
+            else
+                lo = mid;
+        } else if (F < 0.0)
             lo = mid;
         else if (F > 0.0)
             hi = mid;

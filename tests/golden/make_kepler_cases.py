@@ -53,6 +53,15 @@ def cases():
     # tight binary over many periods (a ~ 1e-4, P < dt)
     out.append(_case("tight-binary", 2.0 ** -10, 2.0 / 16384, [1e-4, 2e-5, 0.0],
                      [0.0, 1.15, 0.1]))
+    # fast, strongly hyperbolic star pairs whose standard guess t / r0 lies so
+    # far past the root that the G-functions overflow there (sqrt(-beta) t / r0
+    # > 710): approaching, receding, and backward in time
+    out.append(_case("hyperbolic-guess-overflow-approach", 1e-3, 2e-6, [9e-5, 2e-5, -1e-5],
+                     [-60.0, 25.0, 18.0]))
+    out.append(_case("hyperbolic-guess-overflow-recede", 1e-3, 2e-6, [9e-5, 2e-5, -1e-5],
+                     [120.0, -50.0, -36.0]))
+    out.append(_case("hyperbolic-guess-overflow-backward", -1e-3, 2e-6, [9e-5, 2e-5, -1e-5],
+                     [-60.0, 25.0, 18.0]))
     # random mix
     for k in range(12):
         m = float(10 ** rng.uniform(-6, 0.5))

@@ -84,12 +84,17 @@ def test_two_body_invariants_conserved(case):
     assert rc == oracle.OK
     e0, h0, a0 = _invariants(m, case["r0"], case["v0"])
     e1, h1, a1 = _invariants(m, r1, v1)
-    escale = 0.5 * case["v0"] @ case["v0"] + m / np.linalg.norm(case["r0"])
+    # round-off of evaluating an invariant is relative to the magnitudes of
+    # the state it is evaluated at: take the larger of the two states (a fast
+    # flyby ends a thousand times farther out than it starts)
+    r0n, v0n = np.linalg.norm(case["r0"]), np.linalg.norm(case["v0"])
+    r1n, v1n = np.linalg.norm(r1), np.linalg.norm(v1)
+    escale = max(0.5 * v0n ** 2 + m / r0n, 0.5 * v1n ** 2 + m / r1n)
     tol = 1e-12 if "multirev" in case["name"] or "parabolic" in case["name"] else 1e-13
     assert abs(e1 - e0) <= tol * escale
-    hscale = np.linalg.norm(case["r0"]) * np.linalg.norm(case["v0"])
+    hscale = max(r0n * v0n, r1n * v1n)
     assert np.abs(h1 - h0).max() <= tol * hscale
-    assert np.abs(a1 - a0).max() <= tol * max(m, hscale * np.linalg.norm(case["v0"]))
+    assert np.abs(a1 - a0).max() <= tol * max(m, hscale * max(v0n, v1n))
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c["name"] for c in CASES])
