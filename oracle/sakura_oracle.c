@@ -200,6 +200,13 @@ static double kep_solve(const kep_t *k, const oracle_kepler_opts *o, int *iters,
             hi = s;
         double disc = (nl - 1.0) * (nl - 1.0) * Fp * Fp - nl * (nl - 1.0) * F * Fpp;
         double den = Fp + copysign(sqrt(fabs(disc)), Fp);
+        if (!isfinite(disc) || !isfinite(den) || den == 0.0) {
+            /* F' = r(s) so large that its square overflows: s lies far past
+               the root (at the root r is the pair's separation), and the
+               Laguerre step would round to zero; bisect instead */
+            s = 0.5 * (lo + hi);
+            continue;
+        }
         double ds = nl * F / den;
         double snew = s - ds;
         if (fabs(ds) <= o->tol_eps * eps * fabs(snew)) {

@@ -62,6 +62,17 @@ def cases():
                      [120.0, -50.0, -36.0]))
     out.append(_case("hyperbolic-guess-overflow-backward", -1e-3, 2e-6, [9e-5, 2e-5, -1e-5],
                      [-60.0, 25.0, 18.0]))
+    # close flyby (impact parameter 1.5e-5, ending 0.42 apart) whose guess
+    # lies 2e4 / sqrt(-beta) past the root, where r(s) = F' is so large that
+    # the Laguerre discriminant overflows
+    out.append(_case("close-flyby-guess-far-past-root", 1e-3, 2e-6, [1.6e-5, -1.1e-5, 4e-6],
+                     [-300.0, 180.0, 250.0]))
+    # nearly head-on flyby (a pair of a fast star swarm) on which the Laguerre
+    # step from far past the root once rounded to zero and was taken for
+    # convergence
+    out.append(_case("close-flyby-discriminant-overflow", 1e-3, 2e-6,
+                     [-5.918864792495962e-06, 4.702523318676603e-05, 0.00044838192387707486],
+                     [-34.92845080444039, -206.30318962125773, -252.43950821240344]))
     # random mix
     for k in range(12):
         m = float(10 ** rng.uniform(-6, 0.5))

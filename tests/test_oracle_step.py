@@ -256,6 +256,23 @@ def test_composition_of_kepler_pair_maps_is_third_order():
     assert 7.0 < q4[0] < 9.0 and 7.0 < q4[1] < 9.0, q4
 
 
+def test_fast_swarm_step_is_nearly_free_motion():
+    # stars of mass 1e-6 within 5e-4 of each other at speeds ~400: every
+    # pair is a fast flyby whose deflection is tiny (tan(theta/2) = m / (b v^2)),
+    # and for most pairs the standard guess lies far past the root; the step
+    # must stay close to straight-line motion and conserve momentum
+    rng = np.random.default_rng(0)
+    n = 64
+    m = np.full(n, 1e-6)
+    r = rng.uniform(-2.5e-4, 2.5e-4, (n, 3))
+    v = rng.normal(0.0, 300.0, (n, 3))
+    rc, r1, v1 = oracle.step(m, r, v, 1e-3, 2)
+    assert rc == oracle.OK
+    assert np.abs(r1 - (r + 1e-3 * v)).max() < 1e-5
+    assert np.abs(v1 - v).max() < 1e-1
+    assert np.abs((m[:, None] * (v1 - v)).sum(0)).max() < 1e-15
+
+
 def test_step_argument_errors():
     m, r, v = _binary()
     assert oracle.step(m, r, v, 0.1, 3)[0] == oracle.E_ARG
