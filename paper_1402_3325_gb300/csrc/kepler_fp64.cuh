@@ -127,6 +127,7 @@ __device__ __forceinline__ bool is_neg(double a) { return __double_as_longlong(a
 
 constexpr long long kInfBits = 0x7ff0000000000000LL;
 constexpr long long kBits0p1 = 0x3fb999999999999aLL;  // 0.1
+constexpr long long kBits2p1000 = 0x7e70000000000000LL;  // 2^1000
 
 struct Stumpff {
     double c0, c1, c2, c3;
@@ -303,9 +304,11 @@ __device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, int nt,
     p.Fp = Fp;
     p.ir = ip;
     ++p.iters;
-    // an iterate so far out that the G functions overflowed: the root lies
-    // between it and the origin, so it bounds the bracket on its side
-    if ((__double_as_longlong(F) & kInfBits) == kInfBits) {
+    // an iterate so far out that the G functions overflowed, or that r(s) =
+    // F' passed 2^1000 (its reciprocal would flush to zero and fake
+    // convergence): r at the root is the pair's separation, so the root lies
+    // between the iterate and the origin and the iterate bounds the bracket
+    if ((__double_as_longlong(F) & kInfBits) == kInfBits || magbits(Fp) >= kBits2p1000) {
         if (is_neg(s))
             p.lo = s;
         else
@@ -382,7 +385,9 @@ __device__ __forceinline__ void pair_bisect(PairSolve &p)
         const double F = pair_eval(p, mid);
         if (F < 0.0) p.lo = mid;
         else if (F > 0.0) p.hi = mid;
-        else break;
+        else if (F == 0.0) break;
+        else if (is_neg(mid)) p.lo = mid;  // overflow: mid lies past the root
+        else p.hi = mid;
         ++p.iters;
     }
     pair_eval(p, mid);

@@ -212,6 +212,37 @@ def bh_cluster(n: int = 16384, seed: int = 0, *, m_bh=1.0, m_cluster=1e-2) -> Sy
     return System(m, r, v, 2.0 ** -10, f"bh-cluster-N{n}-seed{seed}")
 
 
+def plummer_bh(n: int = 128, q: float = 1e6, seed: int = 0) -> System:
+    """The paper's large-N test (Sec. 3.2): a Plummer sphere of n - 1
+    equal-mass stars with a black hole of q times a star's mass at rest at
+    its centre, total mass 1, in virial equilibrium.  Star positions follow
+    the Plummer profile at the N-body-unit scale 3 pi / 16; each star's speed
+    is x v_esc(r), with x drawn from the Plummer speed distribution
+    x^2 (1 - x^2)^(7/2) and v_esc the escape speed of the combined potential
+    (stars plus black hole), in an isotropic direction.  The system is moved
+    to its centre-of-mass frame and the velocities alone are scaled to
+    2T = -W, so the stars orbit at radii of order one whatever q is.  q = 1
+    makes the black hole an ordinary star.  dt = 1e-4."""
+    rng = np.random.default_rng(seed)
+    k = n - 1
+    m_star = 1.0 / (k + q)
+    m_bh = q * m_star
+    a = 3.0 * math.pi / 16.0
+    rs, rad = _plummer_positions(rng, k)
+    x = _plummer_speeds(rng, rad) / (math.sqrt(2.0) * (1.0 + rad * rad) ** (-0.25))
+    rs, rad = rs * a, rad * a
+    vesc = np.sqrt(2.0 * (k * m_star / np.sqrt(rad * rad + a * a) + m_bh / rad))
+    vs = (x * vesc)[:, None] * _isotropic(rng, k)
+    m = np.concatenate([[m_bh], np.full(k, m_star)])
+    r = np.concatenate([np.zeros((1, 3)), rs])
+    v = np.concatenate([np.zeros((1, 3)), vs])
+    r, v = _com_frame(m, r, v)
+    W = potential_energy(m, r)
+    T = 0.5 * float((m * (v * v).sum(1)).sum())
+    v = v * math.sqrt(-0.5 * W / T)
+    return System(m, r, v, 1e-4, f"plummer-bh-N{n}-q{q:g}-seed{seed}")
+
+
 def plummer_binaries(n: int = 16384, seed: int = 0, *, f_bin: float = 0.1,
                      a_lo=1e-4, a_hi=1e-2) -> System:
     """Plummer cluster of n equal-mass (1/n) particles of which a fraction

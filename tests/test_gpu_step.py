@@ -258,6 +258,29 @@ def test_argument_errors():
     assert lib.sakura_step(sk._ptr(state), sk._ptr(mass), 4, float("nan"), 2) == sk.E_ARG
 
 
+def _fast_swarm(n=64, seed=0):
+    # stars of mass 1e-6 in a cube of side 5e-4 at speeds ~300: for most pairs
+    # the standard guess t / r0 lies so far past the root (sqrt(-beta) t / r0
+    # ~ 10^3) that the G functions overflow there
+    rng = np.random.default_rng(seed)
+    m = np.full(n, 1e-6)
+    r = rng.uniform(-2.5e-4, 2.5e-4, (n, 3))
+    v = rng.normal(0.0, 300.0, (n, 3))
+    return ics.System(m, r, v, 1e-3, "fast-swarm")
+
+
+@pytest.mark.parametrize("pairs", [sk.PAIRS_ORDERED, sk.PAIRS_SYMMETRIC])
+@pytest.mark.parametrize("guess", [sk.GUESS_STANDARD, sk.GUESS_TAYLOR])
+def test_fast_hyperbolic_pairs_with_overflowing_guess(guess, pairs):
+    s = _fast_swarm()
+    with configured(guess=guess, pair_mode=pairs):
+        r, v = gpu_step(s, s.dt, 2)
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
+    assert rc == oracle.OK
+    er, ev = rel_err(r, v, rr, vr)
+    assert er <= TOL and ev <= TOL, (er, ev)
+
+
 # --- symmetric mode: every unordered pair solved once (Newton's third law) ---
 
 @pytest.mark.parametrize("order", [2, 1, -1])
