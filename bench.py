@@ -325,9 +325,11 @@ def main():
     ap.add_argument("--pairs", default="symmetric", choices=["symmetric", "ordered"],
                     help="symmetric: each unordered pair solved once (Newton's third law);"
                          " ordered: every ordered pair solved")
-    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"],
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed", "df64"],
                     help="fp64: every pair in FP64; mixed: FP32 solves for the pairs the"
-                         " class rule admits, FP64 for the rest and all accumulation")
+                         " class rule admits, FP64 for the rest and all accumulation;"
+                         " df64: every pair to FP64 accuracy in double-word arithmetic on"
+                         " the FP32 pipe (symmetric pairs)")
     ap.add_argument("--mixed-rule", default="hyp", choices=["literal", "hyp"],
                     help="literal: FP32 iff r > 0.1 and e < 0.9; hyp: ... or e > 10")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -371,6 +373,8 @@ def main():
              "learned": sk.GUESS_LEARNED}[args.guess]
     form_opts = {"pair_mode": sk.PAIRS_SYMMETRIC if args.pairs == "symmetric"
                  else sk.PAIRS_ORDERED}
+    if args.form == "df64":
+        form_opts.update(precision=sk.PREC_DF64)
     if args.form == "mixed":
         form_opts.update(precision=sk.PREC_MIXED,
                          mixed_rule=sk.MIXED_RULE_HYP if args.mixed_rule == "hyp"

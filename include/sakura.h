@@ -48,6 +48,18 @@ extern "C" {
 /* ---- options --------------------------------------------------------- */
 #define SAKURA_PREC_FP64 0  /* every pair solved in FP64                      */
 #define SAKURA_PREC_MIXED 1 /* distant, low-eccentricity pairs solved in FP32 */
+#define SAKURA_PREC_DF64 2  /* every pair solved to FP64 accuracy in double-word
+                               ("double-float") arithmetic on the FP32 pipe:
+                               an FP32 Laguerre phase, one double-word
+                               correction and the increments in double-word
+                               form; pairs outside single-precision range,
+                               bound orbits whose step exceeds 0.9 of the
+                               period and unconverged pairs are solved in
+                               FP64.  Symmetric pair mode only (else as
+                               FP64); the initial guess is the second-order
+                               one (SAKURA_GUESS_LEARNED included).  Results
+                               match the FP64 form to about 2^-46 relative
+                               per pair.                                       */
 
 #define SAKURA_MIXED_RULE_LITERAL 0 /* FP32 iff r > r_min and e < e_max           */
 #define SAKURA_MIXED_RULE_HYP 1     /* FP32 iff r > r_min and (e < e_max or e > e_hyp) */
@@ -95,7 +107,8 @@ typedef struct sakura_stats {
     int64_t iters;        /* Laguerre/Newton iterations summed over pairs         */
     int64_t max_iters;    /* largest iteration count of any pair                  */
     int64_t warp_slots;   /* sum over warp batches of 32 x (max lane iterations)  */
-    int64_t fp32_pairs;   /* pairs solved in single precision (mixed form)        */
+    int64_t fp32_pairs;   /* pairs solved on the FP32 pipe: in single precision
+                             (mixed form) or in double-word arithmetic (df64)  */
     int64_t fallbacks;    /* pairs that needed bisection or a restart             */
     int64_t solves;       /* Kepler solves performed (pairs / 2 + diagonal-tile
                              pairs in the symmetric mode)                        */

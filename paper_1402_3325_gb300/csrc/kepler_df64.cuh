@@ -1,0 +1,342 @@
+// kepler_df64.cuh -- the pair map of Eq. 26 with the Kepler flow of Eq. 18
+// computed on the FP32 pipe to FP64 accuracy.
+//
+// Same method as kepler_fp64.cuh (universal variable s, F(s) = r0 s +
+// eta0 G2 + zeta0 G3 - t, Stumpff functions by series with quartering and
+// doubling, Laguerre steps of order 5 (Conway 1986), increments divided by
+// m = m_i + m_j), organised in two phases:
+//
+//   1. FP32: the Kepler input from the leading float of each exact
+//      double-word difference, then Laguerre iterations in single precision
+//      until |F/F'| <= 4 eps32 max(|s|, |t/F'|) (k32_solve).  This finds the
+//      root to about 1e-7.
+//   2. Double-word (df64.cuh): the Kepler input (backward drift, r0, 1/r0,
+//      eta0, beta, zeta0), F, F' and F'' at s in double-word arithmetic and
+//      one Laguerre correction ds = q (1 + k), q = F / F' in double-word form
+//      and the small Laguerre factor k in float.  When |ds| <= 2^-20
+//      max(|s|, |t/F'|) the truncation error of the cubically convergent
+//      step is far below 2^-48 and G1..G3 and F' are carried to s - ds by their
+//      Taylor series (dG_k/ds = G_{k-1}, G_0 = c0, dG_0/ds = -beta G1), with
+//      first-order terms in double-word form; otherwise s - ds is evaluated
+//      again (at most kDwMaxEval evaluations).
+//
+// A pair is solved this way only where single precision has the range for
+// it (class test in dw_admit): 1e-30 < r0^2, v^2, m < 1e30, a bound orbit
+// whose step is below 0.9 of its period (no reduction of t modulo the
+// period), a converged FP32 phase and |beta s^2| <= 256 (hyperbolic G
+// functions below e^16).  The caller solves every other pair with the FP64
+// solver.  Every admitted increment is accurate to a few units of 2^-48
+// relative, so the results match the FP64 solver within the per-step parity
+// bound.
+#pragma once
+
+#include <cmath>
+
+#include "df64.cuh"
+
+namespace sakura {
+
+constexpr int kDwMaxEval = 3;
+constexpr int kDwFp32MaxIter = 12;
+
+// double-word 1/(2n+2)! and 1/(2n+3)! (hi, lo), split from the exact values
+#define SAKURA_DW_INV6 dw{0x1.555556p-3f, -0x1.555556p-28f}
+#define SAKURA_DW_INV24 dw{0x1.555556p-5f, -0x1.555556p-30f}
+#define SAKURA_DW_INV720 dw{0x1.6c16c2p-10f, -0x1.27d27ep-35f}
+#define SAKURA_DW_INV120 dw{0x1.111112p-7f, -0x1.dddddep-32f}
+#define SAKURA_DW_INV5040 dw{0x1.a01a02p-13f, -0x1.7f97fap-39f}
+
+// --------------------------------------------------------------------------
+// phase 1: single precision
+
+struct K32 {
+    float s;      // root estimate
+    float x;      // beta s^2 at the estimate
+    float beta;
+    bool ok;      // converged (and finite)
+    int iters;
+};
+
+DW_HD float stumpff32_terms(float x, float &c0, float &c1, float &c2)
+{
+    int k = 0;
+    while (fabsf(x) > 0.1f && k < 40) {
+        x *= 0.25f;
+        ++k;
+    }
+    const float y = -x;
+    float s2 = fmaf(fmaf(fmaf(1.0f / 40320.0f, y, 1.0f / 720.0f), y, 1.0f / 24.0f), y, 0.5f);
+    float s3 = fmaf(fmaf(fmaf(1.0f / 362880.0f, y, 1.0f / 5040.0f), y, 1.0f / 120.0f), y,
+                    1.0f / 6.0f);
+    float s0 = fmaf(y, s2, 1.0f);
+    float s1 = fmaf(y, s3, 1.0f);
+    for (; k > 0; --k) {
+        const float n3 = 0.25f * fmaf(s0, s3, s2);
+        const float n2 = 0.5f * s1 * s1;
+        const float n1 = s0 * s1;
+        x *= 4.0f;
+        s0 = fmaf(-x, n2, 1.0f);
+        s1 = n1;
+        s2 = n2;
+        s3 = n3;
+    }
+    c0 = s0;
+    c1 = s1;
+    c2 = s2;
+    return s3;
+}
+
+// Laguerre iterations in FP32 from the standard (guess 0) or second-order
+// (guess 2) initial value.
+DW_HD K32 k32_solve(float r0, float ir0, float eta, float beta, float zeta,
+                                         float t, int guess)
+{
+    K32 o;
+    o.beta = beta;
+    float s = t * ir0;
+    if (guess == 2) {
+        const float c = 0.5f * s * (eta * ir0);
+        if (fabsf(c) < 0.5f) s = fmaf(-c, s, s);
+    }
+    const float tol = 4.0f * 1.1920929e-7f;
+    o.ok = false;
+    o.iters = 0;
+    for (int it = 0; it < kDwFp32MaxIter; ++it) {
+        float c0, c1, c2;
+        const float c3 = stumpff32_terms(beta * s * s, c0, c1, c2);
+        const float s2 = s * s;
+        const float G1 = s * c1, G2 = s2 * c2, G3 = s2 * s * c3;
+        const float F = fmaf(r0, s, fmaf(eta, G2, fmaf(zeta, G3, -t)));
+        const float Fp = fmaf(eta, G1, fmaf(zeta, G2, r0));
+        const float Fpp = fmaf(eta, c0, zeta * G1);
+        const float ir = 1.0f / Fp;
+        const float q = F * ir;
+        ++o.iters;
+        if (!(fabsf(q) <= 1e30f)) break;  // overflow or NaN
+        if (fabsf(q) <= tol * fmaxf(fabsf(s), fabsf(t * ir))) {
+            o.ok = true;
+            break;
+        }
+        const float u = 1.25f * q * Fpp * ir;
+        const float den = 1.0f + 4.0f * sqrtf(fabsf(1.0f - u));
+        s = s - 5.0f * q / den;
+    }
+    o.s = s;
+    o.x = beta * s * s;
+    o.ok = o.ok && (fabsf(o.x) <= 256.0f) && fabsf(s) <= 3.0e38f;
+    return o;
+}
+
+// --------------------------------------------------------------------------
+// phase 2: double-word
+
+struct PairDW {
+    dw x0, y0, z0;   // backward-drifted relative position (Kepler input)
+    dw vx, vy, vz;   // relative velocity
+    dw m;            // m_i + m_j
+    dw r0, ir0, eta0, beta, zeta0;
+};
+
+// Relative state from exact double-word differences rr, vv; ptau = pre tau.
+DW_HD void dw_setup(PairDW &p, const dw rr[3], const dw vv[3], dw m, dw ptau)
+{
+    p.vx = vv[0];
+    p.vy = vv[1];
+    p.vz = vv[2];
+    p.x0 = dw_sub(rr[0], dw_mul(ptau, vv[0]));
+    p.y0 = dw_sub(rr[1], dw_mul(ptau, vv[1]));
+    p.z0 = dw_sub(rr[2], dw_mul(ptau, vv[2]));
+    p.m = m;
+    const dw r2 = dw_add(dw_add(dw_sqr(p.x0), dw_sqr(p.y0)), dw_sqr(p.z0));
+    p.ir0 = dw_rsqrt(r2);
+    p.r0 = dw_mul(r2, p.ir0);
+    p.eta0 = dw_add(dw_add(dw_mul(p.x0, p.vx), dw_mul(p.y0, p.vy)), dw_mul(p.z0, p.vz));
+    const dw v2 = dw_add(dw_add(dw_sqr(p.vx), dw_sqr(p.vy)), dw_sqr(p.vz));
+    p.beta = dw_sub(dw_scale(dw_mul(m, p.ir0), 2.0f), v2);
+    p.zeta0 = dw_sub(m, dw_mul(p.beta, p.r0));
+}
+
+// c0..c3 at x in double-word form.  big (warp-uniform): some |x| of the warp
+// exceeds 2^-8, so three double-word Horner steps are used (else two, which
+// keep the float tail's error below 2^-49 for |x| < 2^-8); arguments above
+// 0.1 are quartered first and doubled back.
+struct StumpffDW {
+    dw c0, c1, c2, c3;
+};
+
+DW_HD StumpffDW stumpff_dw(dw x, bool big)
+{
+    int k = 0;
+    while (fabsf(x.h) > 0.1f && k < 16) {
+        x = dw_scale(x, 0.25f);
+        ++k;
+    }
+    const dw y = dw_neg(x);
+    const float yf = y.h;
+    // c2 = 1/2 + y (1/24 + y (1/720 + y (1/40320 + ...))), c3 likewise from
+    // 1/6: the inner terms in float, the outer two or three in double-word
+    dw c2, c3;
+    if (big) {
+        const float t2 = fmaf(fmaf(1.0f / 479001600.0f, yf, 1.0f / 3628800.0f), yf,
+                              1.0f / 40320.0f);
+        const float t3 = fmaf(fmaf(1.0f / 6227020800.0f, yf, 1.0f / 39916800.0f), yf,
+                              1.0f / 362880.0f);
+        c2 = dw_add(dw_mul(y, dw_add(SAKURA_DW_INV720, dw_mul_f(y, t2))), SAKURA_DW_INV24);
+        c3 = dw_add(dw_mul(y, dw_add(SAKURA_DW_INV5040, dw_mul_f(y, t3))), SAKURA_DW_INV120);
+    } else {
+        const float t2 = fmaf(fmaf(1.0f / 3628800.0f, yf, 1.0f / 40320.0f), yf, 1.0f / 720.0f);
+        const float t3 = fmaf(fmaf(1.0f / 39916800.0f, yf, 1.0f / 362880.0f), yf,
+                              1.0f / 5040.0f);
+        c2 = dw_add(dw_mul_f(y, t2), SAKURA_DW_INV24);
+        c3 = dw_add(dw_mul_f(y, t3), SAKURA_DW_INV120);
+    }
+    c2 = dw_add_f(dw_mul(y, c2), 0.5f);
+    c3 = dw_add(dw_mul(y, c3), SAKURA_DW_INV6);
+    dw c0 = dw_add_f(dw_mul(y, c2), 1.0f);
+    dw c1 = dw_add_f(dw_mul(y, c3), 1.0f);
+    for (; k > 0; --k) {
+        const dw n3 = dw_scale(dw_add(dw_mul(c0, c3), c2), 0.25f);
+        const dw n2 = dw_scale(dw_sqr(c1), 0.5f);
+        const dw n1 = dw_mul(c0, c1);
+        x = dw_scale(x, 4.0f);
+        c0 = dw_add_f(dw_neg(dw_mul(x, n2)), 1.0f);
+        c1 = n1;
+        c2 = n2;
+        c3 = n3;
+    }
+    return {c0, c1, c2, c3};
+}
+
+struct EvalDW {
+    dw G1, G2, G3, c0, Fp, Fpp;
+    dw ds;         // Laguerre correction: the root is s - ds
+    bool conv;     // |ds| small enough for the Taylor carry
+};
+
+DW_HD EvalDW dw_eval(const PairDW &p, dw s, dw t, bool big)
+{
+    EvalDW e;
+    const dw s2 = dw_sqr(s);
+    const StumpffDW c = stumpff_dw(dw_mul(p.beta, s2), big);
+    e.c0 = c.c0;
+    e.G1 = dw_mul(s, c.c1);
+    e.G2 = dw_mul(s2, c.c2);
+    e.G3 = dw_mul(dw_mul(s2, s), c.c3);
+    const dw F = dw_sub(dw_add(dw_add(dw_mul(p.r0, s), dw_mul(p.eta0, e.G2)),
+                               dw_mul(p.zeta0, e.G3)),
+                        t);
+    e.Fp = dw_add(dw_add(p.r0, dw_mul(p.eta0, e.G1)), dw_mul(p.zeta0, e.G2));
+    e.Fpp = dw_add(dw_mul(p.eta0, c.c0), dw_mul(p.zeta0, e.G1));
+    const dw q = dw_mul(F, dw_rcp(e.Fp));
+    // Laguerre factor of order 5 in float: ds = q (1 + k)
+    const float u = 1.25f * q.h * (e.Fpp.h / e.Fp.h);
+    const float r = sqrtf(fabsf(1.0f - u));
+    const float cf = 0.8f * u / (1.0f + r);
+    const float k = fabsf(u) < 0.5f ? cf / (1.0f - cf) : 5.0f / fmaf(4.0f, r, 1.0f) - 1.0f;
+    e.ds = dw_add_f(q, q.h * k);
+    const float sc = fmaxf(fabsf(s.h), fabsf(t.h / e.Fp.h));
+    e.conv = fabsf(e.ds.h) <= 0x1p-20f * sc;
+    return e;
+}
+
+// Carry G1..G3 and F' = r from s to s - ds (|ds| <= 2^-20 |s|): first-order
+// terms in double-word form, second-order terms in float.
+DW_HD void dw_carry(EvalDW &e, const PairDW &p)
+{
+    const dw d = e.ds;
+    const float h2 = 0.5f * d.h * d.h;
+    const dw G0 = e.c0;
+    const float Gm1 = -p.beta.h * e.G1.h;             // dG0/ds
+    const float F3 = fmaf(-p.eta0.h * p.beta.h, e.G1.h, p.zeta0.h * G0.h);  // dF''/ds
+    e.G3 = dw_add_f(dw_sub(e.G3, dw_mul(d, e.G2)), h2 * e.G1.h);
+    e.G2 = dw_add_f(dw_sub(e.G2, dw_mul(d, e.G1)), h2 * G0.h);
+    e.G1 = dw_add_f(dw_sub(e.G1, dw_mul(d, G0)), h2 * Gm1);
+    e.Fp = dw_add_f(dw_sub(e.Fp, dw_mul(d, e.Fpp)), h2 * F3);
+}
+
+// Increments of the pair map (Eq. 26, increment form) divided by m, from
+// the G functions and r = F' at the root; qtau = post tau.
+DW_HD void dw_increment_over_m(const PairDW &p, const EvalDW &e, dw qtau,
+                                                    dw out[6])
+{
+    const dw ir = dw_rcp(e.Fp);
+    const dw fm1 = dw_neg(dw_mul(e.G2, p.ir0));
+    const dw gmt = dw_neg(e.G3);
+    const dw fd = dw_neg(dw_mul(dw_mul(e.G1, p.ir0), ir));
+    const dw gdm1 = dw_neg(dw_mul(e.G2, ir));
+    const dw A = dw_sub(fm1, dw_mul(qtau, fd));
+    const dw B = dw_sub(gmt, dw_mul(qtau, gdm1));
+    out[3] = dw_add(dw_mul(fd, p.x0), dw_mul(gdm1, p.vx));
+    out[4] = dw_add(dw_mul(fd, p.y0), dw_mul(gdm1, p.vy));
+    out[5] = dw_add(dw_mul(fd, p.z0), dw_mul(gdm1, p.vz));
+    out[0] = dw_add(dw_mul(A, p.x0), dw_mul(B, p.vx));
+    out[1] = dw_add(dw_mul(A, p.y0), dw_mul(B, p.vy));
+    out[2] = dw_add(dw_mul(A, p.z0), dw_mul(B, p.vz));
+}
+
+// Phase 1 with the class test: the float Kepler input from the leading
+// parts of the exact differences rr, vv (ptau32 = (float)(pre tau),
+// t32 = (float)tau), the range and period conditions, and the FP32 solve.
+DW_HD K32 dw_phase1(const dw rr[3], const dw vv[3], dw m, float ptau32, float t32, int guess)
+{
+    float x[3], u[3];
+    for (int q = 0; q < 3; ++q) {
+        u[q] = vv[q].h;
+        x[q] = fmaf(-ptau32, u[q], rr[q].h);
+    }
+    const float r2 = fmaf(x[0], x[0], fmaf(x[1], x[1], x[2] * x[2]));
+    const float v2 = fmaf(u[0], u[0], fmaf(u[1], u[1], u[2] * u[2]));
+    const float eta = fmaf(x[0], u[0], fmaf(x[1], u[1], x[2] * u[2]));
+    const bool range = r2 > 1e-30f && r2 < 1e30f && v2 < 1e30f && m.h > 1e-30f && m.h < 1e30f;
+    K32 o;
+    o.ok = false;
+    o.iters = 0;
+    o.s = 0.0f;
+    o.x = 0.0f;
+    o.beta = 0.0f;
+    if (!range) return o;
+    const float ir0 = 1.0f / sqrtf(r2);
+    const float r0 = r2 * ir0;
+    const float beta = fmaf(2.0f * m.h, ir0, -v2);
+    const float zeta = fmaf(-beta, r0, m.h);
+    // a bound orbit whose step exceeds 0.9 of its period needs t reduced
+    // modulo the period: FP64 solver
+    if (beta > 0.0f) {
+        const float b3 = beta * beta * beta;
+        const float tm = 6.2831853f * 0.9f * m.h;
+        if (t32 * t32 * b3 >= tm * tm) return o;
+    }
+    return k32_solve(r0, ir0, eta, beta, zeta, t32, guess);
+}
+
+// Phase 2 for an admitted pair: setup, evaluations from s32, Taylor carry
+// and increments over m.  Returns false when kDwMaxEval evaluations did not
+// reach the carry condition (the caller then uses the FP64 solver).
+DW_HD bool dw_phase2(const dw rr[3], const dw vv[3], dw m, dw ptau, dw t, dw qtau, float s32,
+                     bool big, dw out[6], int &evals)
+{
+    PairDW p;
+    dw_setup(p, rr, vv, m, ptau);
+    dw s = dw_from(s32);
+    EvalDW e;
+    evals = 0;
+    for (;;) {
+        e = dw_eval(p, s, t, big);
+        ++evals;
+        if (e.conv) break;
+        if (evals >= kDwMaxEval) return false;
+        s = dw_sub(s, e.ds);
+    }
+    dw_carry(e, p);
+    dw_increment_over_m(p, e, qtau, out);
+    return true;
+}
+
+// acc += p with renormalisation
+DW_HD void dw_acc(dw &acc, dw p)
+{
+    const dw s = two_sum(acc.h, p.h);
+    acc = fast_two_sum(s.h, fadd(s.l, fadd(acc.l, p.l)));
+}
+
+}  // namespace sakura

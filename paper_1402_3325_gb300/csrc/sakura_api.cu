@@ -172,14 +172,23 @@ Plan plan_step(int64_t n)
     return p;
 }
 
-// Unordered pairs once (Newton's third law): systolic 32 x 32 tiles.
-int step_device_sym(double *state, const double *masses, int64_t n, double dt, int order)
+sakura::dw split_dw(double d)
+{
+    const float h = (float)d;
+    return {h, (float)(d - (double)h)};
+}
+
+// Unordered pairs once (Newton's third law): systolic 32 x 32 tiles; df64:
+// the pair solves in double-word arithmetic (step_df64.cu).
+int step_device_sym(double *state, const double *masses, int64_t n, double dt, int order,
+                    bool df64)
 {
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
-    const bool learned = g.cfg.guess == SAKURA_GUESS_LEARNED;
+    const bool learned = !df64 && g.cfg.guess == SAKURA_GUESS_LEARNED;
     const int64_t nb = (n + 31) / 32;
     const int64_t tiles = nb * (nb + 1) / 2;
-    const int bps = sakura::pair_step_sym_blocks_per_sm(stats, learned);
+    const int bps = df64 ? sakura::pair_step_df64_blocks_per_sm(stats)
+                         : sakura::pair_step_sym_blocks_per_sm(stats, learned);
     const int64_t resident = (int64_t)g.sm_count * bps * 4;
     // step ranges per tile: enough items for every resident warp (each range
     // adds nb slots of partials for the apply kernel to read)
@@ -189,13 +198,20 @@ int step_device_sym(double *state, const double *masses, int64_t n, double dt, i
     int64_t blocks = g.cfg.grid_blocks > 0 ? g.cfg.grid_blocks : (int64_t)g.sm_count * bps;
     blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (items + 3) / 4));
     const int64_t nslots = nb * S;
-    int rc = grow(g.partial, (size_t)(7 * n + nslots * 6 * n) * sizeof(double));
+    // scratch: X[7][n] doubles, tile partials [nslots][6][n] (doubles, or
+    // double-words of two floats), then (df64) X3[20][n] floats
+    int rc = grow(g.partial, (size_t)(7 * n + nslots * 6 * n + (df64 ? 10 * n : 0)) *
+                                 sizeof(double));
     if (rc) return rc;
     double *X = (double *)g.partial.ptr;
     double *partial = X + 7 * n;
+    float *X3 = (float *)(partial + nslots * 6 * n);
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
-    sakura::launch_prep_step(state, masses, X, n, drift, g.d_status, g.stream);
+    if (df64)
+        sakura::launch_prep_df64(state, masses, X, X3, n, drift, g.d_status, g.stream);
+    else
+        sakura::launch_prep_step(state, masses, X, n, drift, g.d_status, g.stream);
     sakura::StepArgs a;
     std::memset(&a, 0, sizeof(a));
     a.X = X;
@@ -217,12 +233,26 @@ int step_device_sym(double *state, const double *masses, int64_t n, double dt, i
         tm = take_timer();
         cudaEventRecord(tm.first, g.stream);
     }
-    sakura::launch_pair_step_sym(a, S, items, (int)blocks, stats, g.stream);
+    if (df64) {
+        sakura::DwArgs da;
+        da.X3 = X3;
+        da.ptau32 = (float)(a.pre * dt);
+        da.t32 = (float)dt;
+        da.ptau = split_dw(a.pre * dt);
+        da.t = split_dw(dt);
+        da.qtau = split_dw(a.post * dt);
+        sakura::launch_pair_step_df64(a, da, S, items, (int)blocks, stats, g.stream);
+    } else {
+        sakura::launch_pair_step_sym(a, S, items, (int)blocks, stats, g.stream);
+    }
     if (timing) {
         cudaEventRecord(tm.second, g.stream);
         g.timers.push_back(tm);
     }
-    sakura::launch_apply_sym(state, X, partial, n, nslots, post_drift, g.d_status, g.stream);
+    if (df64)
+        sakura::launch_apply_df64(state, X, partial, n, nslots, post_drift, g.d_status, g.stream);
+    else
+        sakura::launch_apply_sym(state, X, partial, n, nslots, post_drift, g.d_status, g.stream);
     rc = launch_error();
     if (rc) return rc;
     g.steps += 1;
@@ -242,9 +272,10 @@ constexpr double kSymMaxBytes = 16.0 * 1024 * 1024 * 1024;
 
 int step_device(double *state, const double *masses, int64_t n, double dt, int order)
 {
-    if (g.cfg.pair_mode == SAKURA_PAIRS_SYMMETRIC && g.cfg.precision == SAKURA_PREC_FP64 &&
+    if (g.cfg.pair_mode == SAKURA_PAIRS_SYMMETRIC && g.cfg.precision != SAKURA_PREC_MIXED &&
         n > 1 && 8.0 * 6.0 * 8.0 * (double)((n + 31) / 32) * (double)n <= kSymMaxBytes)
-        return step_device_sym(state, masses, n, dt, order);
+        return step_device_sym(state, masses, n, dt, order,
+                               g.cfg.precision == SAKURA_PREC_DF64);
     const Plan p = plan_step(n);
     const int64_t slots = sakura::pair_step_slots(n, p.W);
     const bool mixed = g.cfg.precision == SAKURA_PREC_MIXED;
@@ -397,7 +428,9 @@ int sakura_init(const sakura_config *cfg)
         sakura_default_config(&c);
     if (c.kepler_max_iter < 1 || c.kepler_max_iter > 10000 || !(c.kepler_tol > 0.0))
         return SAKURA_E_ARG;
-    if (c.precision != SAKURA_PREC_FP64 && c.precision != SAKURA_PREC_MIXED) return SAKURA_E_ARG;
+    if (c.precision != SAKURA_PREC_FP64 && c.precision != SAKURA_PREC_MIXED &&
+        c.precision != SAKURA_PREC_DF64)
+        return SAKURA_E_ARG;
     if (c.mixed_rule != SAKURA_MIXED_RULE_LITERAL && c.mixed_rule != SAKURA_MIXED_RULE_HYP)
         return SAKURA_E_ARG;
     if (c.pair_mode != SAKURA_PAIRS_ORDERED && c.pair_mode != SAKURA_PAIRS_SYMMETRIC)

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 
+#include "df64.cuh"
 #include "kepler_fp32.cuh"
 
 namespace sakura {
@@ -46,6 +47,21 @@ void launch_prep_mixed(const double *state, const double *mass, double *X, float
 void launch_pair_step_mixed(const StepArgs &a, const MixedArgs &ma, int blocks, bool stats,
                             cudaStream_t s);
 int pair_step_mixed_blocks_per_sm(bool stats);
+
+// extra arguments of the double-word pair kernel
+struct DwArgs {
+    const float *X3;      // [20][n] three-float drifted state, double-word masses
+    float ptau32, t32;    // (float)(pre tau), (float)tau for the FP32 phase
+    dw ptau, t, qtau;     // pre tau, tau and post tau as double-words
+};
+
+void launch_prep_df64(const double *state, const double *mass, double *X, float *X3, int64_t n,
+                      double drift, unsigned *status, cudaStream_t s);
+void launch_pair_step_df64(const StepArgs &a, const DwArgs &da, int S, int64_t items, int blocks,
+                           bool stats, cudaStream_t s);
+void launch_apply_df64(double *state, const double *X, const void *partial, int64_t n,
+                       int64_t nslots, double post_drift, unsigned *status, cudaStream_t s);
+int pair_step_df64_blocks_per_sm(bool stats);
 
 // pair kernel: one persistent wave of `blocks` blocks of `warps` warps
 void launch_pair_step_fp64(const StepArgs &a, int warps, int blocks, bool stats,

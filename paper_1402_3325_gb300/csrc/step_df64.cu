@@ -1,0 +1,376 @@
+// step_df64.cu -- the W step with every unordered pair solved once (Newton's
+// third law, as step_sym.cu) and the Kepler solves done in double-word
+// arithmetic on the FP32 pipe (kepler_df64.cuh), to FP64 accuracy.
+//
+// prep kernel: the FP64 drift of Eq. 27a (as prep_step_kernel), the FP64
+//   drifted state X[7][n] and its exact three-float form X3[20][n]
+//   (rows 3q..3q+2: component q of x, y, z, vx, vy, vz split as d0 + d1 + d2;
+//   rows 18, 19: the mass as a double-word).
+// pair kernel: the systolic 32 x 32 tiles of step_sym.cu.  Each lane forms
+//   its pair's exact double-word differences (tf_diff), runs the FP32 phase
+//   and class test, and the admitted lanes run the double-word phase; the
+//   row and column sums are kept as renormalised double-words.  A pair the
+//   class test rejects (or whose double-word phase does not converge) joins
+//   a per-warp shared-memory queue that is solved 32 at a time by the FP64
+//   batch solver; each result is added to its row owner and to the lane that
+//   holds its column at that moment, in queue order (deterministic).
+//   Partial sums go out as double-words (float2) to the slots of step_sym.cu.
+// apply kernel: Eqs. 27b-d with the slots added in double-word arithmetic
+//   and converted to FP64 once per particle.
+#include <cuda_runtime.h>
+
+#include "df64.cuh"
+#include "kepler_df64.cuh"
+#include "kepler_fp64.cuh"
+#include "pair_batch_fp64.cuh"
+#include "step_common.cuh"
+
+namespace sakura {
+
+__global__ void prep_df64_kernel(const double *state, const double *mass, double *X, float *X3,
+                                 int64_t n, double drift, unsigned *status)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double m = mass[i];
+    if (!(m > 0.0)) atomicOr(status, kStatusMass);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        double x;
+        if (q < 3) {
+            x = fma(state[(3 + q) * n + i], drift, state[q * n + i]);
+        } else {
+            x = state[q * n + i];
+        }
+        X[q * n + i] = x;
+        float d0, d1, d2;
+        tf_split(x, d0, d1, d2);
+        X3[(3 * q) * n + i] = d0;
+        X3[(3 * q + 1) * n + i] = d1;
+        X3[(3 * q + 2) * n + i] = d2;
+    }
+    X[6 * n + i] = m;
+    const float mh = __double2float_rn(m);
+    X3[18 * n + i] = mh;
+    X3[19 * n + i] = __double2float_rn(m - (double)mh);
+}
+
+__device__ __forceinline__ dw dw_from_double(double x)
+{
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(128)
+    pair_step_sym_df64_kernel(StepArgs a, DwArgs da, int S, int64_t items)
+{
+    __shared__ int queue[4][64];
+    __shared__ double qres[4][32][12];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int *qw = queue[wib];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t n = a.n;
+    const int64_t W = (int64_t)gridDim.x * 4;
+    const int64_t w = (int64_t)blockIdx.x * 4 + wib;
+    const float *X3 = da.X3;
+    const KeplerParams kp{a.tol, a.max_iter, a.bisection};
+    const int guess = a.guess == 1 ? 2 : a.guess;
+    unsigned status = 0;
+    long long it_sum = 0, slots = 0, fallbacks = 0, ndw = 0;
+    int it_max = 0;
+
+    for (int64_t item = w * items / W; item < (w + 1) * items / W; ++item) {
+        const int64_t tile = item / S;
+        const int h = (int)(item - tile * S);
+        int64_t I, J;
+        {
+            int64_t jj = (int64_t)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+            while ((jj + 1) * (jj + 2) / 2 <= tile) ++jj;
+            while (jj * (jj + 1) / 2 > tile) --jj;
+            J = jj;
+            I = tile - jj * (jj + 1) / 2;
+        }
+        const bool diag = I == J;
+        const int k0 = h * 32 / S, k1 = (h + 1) * 32 / S;
+        const int64_t i = 32 * I + lane;
+        const bool irow = i < n;
+        float xi[18];
+        dw mi = {1.0f, 0.0f};
+#pragma unroll
+        for (int q = 0; q < 18; ++q) xi[q] = irow ? X3[q * n + i] : 0.0f;
+        if (irow) mi = {X3[18 * n + i], X3[19 * n + i]};
+        dw racc[6], cacc[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) racc[q] = cacc[q] = dw{0.0f, 0.0f};
+        int tail = 0;
+
+        // FP64 solve of queue entries 0..cnt-1 at step kc, results added to
+        // the row owners and the lanes holding the columns, in queue order
+        auto flush = [&](int kc, int cnt) {
+            const bool vq = lane < cnt;
+            const int e = vq ? qw[lane] : 0;
+            const int64_t iq = 32 * I + (e & 31), jq = 32 * J + (e >> 5);
+            PairSolve p;
+            double miq = 0.0, mjq = 0.0;
+            if (vq) {
+                const double *X = a.X;
+                miq = X[6 * n + iq];
+                mjq = X[6 * n + jq];
+                pair_setup(p, a.tau, miq + mjq, X[iq] - X[jq], X[n + iq] - X[n + jq],
+                           X[2 * n + iq] - X[2 * n + jq], X[3 * n + iq] - X[3 * n + jq],
+                           X[4 * n + iq] - X[4 * n + jq], X[5 * n + iq] - X[5 * n + jq], a.pre,
+                           guess);
+            } else {
+                p.done = true;
+                p.beta = p.s = 0.0;
+                p.iters = 0;
+                p.status = 0;
+            }
+            double d[6];
+            int iters = 0, fb = 0;
+            fp64_solve_warp(p, vq, a.tau, a.post, kp, d, iters, fb);
+            if (vq) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    qres[wib][lane][q] = mjq * d[q];
+                    qres[wib][lane][6 + q] = -miq * d[q];
+                }
+                status |= p.status;
+            }
+            if (STATS) {
+                it_sum += iters;
+                fallbacks += fb;
+                it_max = max(it_max, iters);
+                const int wmax = __reduce_max_sync(0xffffffffu, iters);
+                if (lane == 0) slots += 32LL * wmax;
+            }
+            __syncwarp();
+            const int mycol = (lane + kc) & 31;
+            for (int q = 0; q < cnt; ++q) {
+                const int eq = qw[q];
+                if ((eq & 31) == lane) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) dw_acc(racc[c], dw_from_double(qres[wib][q][c]));
+                }
+                if (!diag && (eq >> 5) == mycol) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c)
+                        dw_acc(cacc[c], dw_from_double(qres[wib][q][6 + c]));
+                }
+            }
+            __syncwarp();
+        };
+
+        for (int k = k0; k < k1; ++k) {
+            const int c = (lane + k) & 31;
+            const int64_t j = 32 * J + c;
+            const bool valid = irow && j < n && (!diag || c != lane);
+            dw rr[3], vv[3], mj = {0.0f, 0.0f};
+            K32 o;
+            o.ok = false;
+            o.x = 0.0f;
+            o.s = 0.0f;
+            o.iters = 0;
+            if (valid) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    rr[q] = tf_diff(xi[3 * q], xi[3 * q + 1], xi[3 * q + 2], X3[(3 * q) * n + j],
+                                    X3[(3 * q + 1) * n + j], X3[(3 * q + 2) * n + j]);
+                    vv[q] = tf_diff(xi[9 + 3 * q], xi[10 + 3 * q], xi[11 + 3 * q],
+                                    X3[(9 + 3 * q) * n + j], X3[(10 + 3 * q) * n + j],
+                                    X3[(11 + 3 * q) * n + j]);
+                }
+                mj = {X3[18 * n + j], X3[19 * n + j]};
+                o = dw_phase1(rr, vv, dw_add(mi, mj), da.ptau32, da.t32, guess);
+            }
+            const bool big = __any_sync(0xffffffffu, o.ok && fabsf(o.x) > 0x1p-8f);
+            bool solved = false;
+            int evals = 0;
+            dw d[6];
+            if (o.ok)
+                solved = dw_phase2(rr, vv, dw_add(mi, mj), da.ptau, da.t, da.qtau, o.s, big, d,
+                                   evals);
+            if (solved) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    dw_acc(racc[q], dw_mul(mj, d[q]));
+                    dw_acc(cacc[q], dw_mul(dw_neg(mi), d[q]));
+                }
+            }
+            if (STATS) {
+                const int it = o.iters + evals;
+                it_sum += it;
+                it_max = max(it_max, it);
+                ndw += solved ? 1 : 0;
+                const int wmax = __reduce_max_sync(0xffffffffu, it);
+                if (lane == 0) slots += 32LL * wmax;
+            }
+            const bool need64 = valid && !solved;
+            const unsigned mask = __ballot_sync(0xffffffffu, need64);
+            if (need64) qw[tail + __popc(mask & lt_mask)] = lane | (c << 5);
+            tail += __popc(mask);
+            __syncwarp();
+            if (tail >= 32) {
+                flush(k, 32);
+                if (lane < tail - 32) qw[lane] = qw[32 + lane];
+                __syncwarp();
+                tail -= 32;
+            }
+            if (!diag && k + 1 < k1) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    cacc[q].h = __shfl_sync(0xffffffffu, cacc[q].h, (lane + 1) & 31);
+                    cacc[q].l = __shfl_sync(0xffffffffu, cacc[q].l, (lane + 1) & 31);
+                }
+            }
+        }
+        if (tail > 0) flush(k1 - 1, tail);
+        // row sums of rows i to slot (J, h); column sums to slot (I, h)
+        float2 *part = reinterpret_cast<float2 *>(a.partial);
+        if (irow) {
+            float2 *dst = part + (J * S + h) * 6 * n;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) dst[q * n + i] = make_float2(racc[q].h, racc[q].l);
+        }
+        if (!diag) {
+            const int64_t jc = 32 * J + ((lane + k1 - 1) & 31);
+            if (jc < n) {
+                float2 *dst = part + (I * S + h) * 6 * n;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) dst[q * n + jc] = make_float2(cacc[q].h, cacc[q].l);
+            }
+        }
+    }
+    status = __reduce_or_sync(0xffffffffu, status);
+    if (lane == 0 && status) atomicOr(a.status, status);
+    if (STATS) {
+        long long s1 = it_sum, s2 = slots, s3 = fallbacks, s4 = ndw;
+        int mx = it_max;
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+            s4 += __shfl_xor_sync(0xffffffffu, s4, o);
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) {
+            atomicAdd(&a.stats[kStatIters], (unsigned long long)s1);
+            atomicAdd(&a.stats[kStatSlots], (unsigned long long)s2);
+            atomicAdd(&a.stats[kStatFallbacks], (unsigned long long)s3);
+            atomicAdd(&a.stats[kStatFp32Pairs], (unsigned long long)s4);
+            atomicMax(&a.stats[kStatMaxIters], (unsigned long long)mx);
+        }
+    }
+}
+
+// Eqs. 27b-d: a block takes 32 particles (one per lane); its kApplyWarps
+// warps add the double-word slots k = w, w + kApplyWarps, ... of those
+// particles, warp 0 adds the warps' sums in warp order, converts to FP64 and
+// applies the update.
+constexpr int kApplyDwWarps = 16;
+
+__global__ void __launch_bounds__(32 * kApplyDwWarps)
+    apply_df64_kernel(double *state, const double *X, const float2 *partial, int64_t n,
+                      int64_t nslots, double post_drift, unsigned *status)
+{
+    __shared__ float2 red[kApplyDwWarps][6][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+    dw d[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) d[q] = dw{0.0f, 0.0f};
+    if (i < n) {
+        int64_t k = wid;
+        for (; k + kApplyDwWarps < nslots; k += 2 * kApplyDwWarps) {
+            float2 v0[6], v1[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                v0[q] = partial[(k * 6 + q) * n + i];
+                v1[q] = partial[((k + kApplyDwWarps) * 6 + q) * n + i];
+            }
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                dw_acc(d[q], dw{v0[q].x, v0[q].y});
+                dw_acc(d[q], dw{v1[q].x, v1[q].y});
+            }
+        }
+        for (; k < nslots; k += kApplyDwWarps) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const float2 v = partial[(k * 6 + q) * n + i];
+                dw_acc(d[q], dw{v.x, v.y});
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) red[wid][q][lane] = make_float2(d[q].h, d[q].l);
+    __syncthreads();
+    if (wid != 0 || i >= n) return;
+    double dd[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        dw t = {red[0][q][lane].x, red[0][q][lane].y};
+        for (int w = 1; w < kApplyDwWarps; ++w)
+            t = dw_add(t, dw{red[w][q][lane].x, red[w][q][lane].y});
+        dd[q] = (double)t.h + (double)t.l;
+    }
+    unsigned st = 0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double v1 = X[(3 + q) * n + i] + dd[3 + q];
+        const double x1 = fma(v1, post_drift, X[q * n + i] + dd[q]);
+        if (!isfinite(x1) || !isfinite(v1)) st |= kStatusNonfinite;
+        state[q * n + i] = x1;
+        state[(3 + q) * n + i] = v1;
+    }
+    if (st) atomicOr(status, st);
+}
+
+namespace {
+
+const void *df64_kernel(bool stats)
+{
+    return stats ? (const void *)pair_step_sym_df64_kernel<true>
+                 : (const void *)pair_step_sym_df64_kernel<false>;
+}
+
+}  // namespace
+
+int pair_step_df64_blocks_per_sm(bool stats)
+{
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, df64_kernel(stats), 128, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return b > 0 ? b : 1;
+}
+
+void launch_prep_df64(const double *state, const double *mass, double *X, float *X3, int64_t n,
+                      double drift, unsigned *status, cudaStream_t s)
+{
+    const int threads = 256;
+    prep_df64_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
+        state, mass, X, X3, n, drift, status);
+}
+
+void launch_pair_step_df64(const StepArgs &a, const DwArgs &da, int S, int64_t items, int blocks,
+                           bool stats, cudaStream_t s)
+{
+    int Sv = S;
+    int64_t it = items;
+    void *args[] = {(void *)&a, (void *)&da, (void *)&Sv, (void *)&it};
+    cudaLaunchKernel(df64_kernel(stats), dim3(blocks), dim3(128), args, 0, s);
+}
+
+void launch_apply_df64(double *state, const double *X, const void *partial, int64_t n,
+                       int64_t nslots, double post_drift, unsigned *status, cudaStream_t s)
+{
+    apply_df64_kernel<<<(unsigned)((n + 31) / 32), 32 * kApplyDwWarps, 0, s>>>(
+        state, X, reinterpret_cast<const float2 *>(partial), n, nslots, post_drift, status);
+}
+
+}  // namespace sakura

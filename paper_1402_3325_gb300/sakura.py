@@ -33,6 +33,7 @@ PAIRS_ORDERED = 0
 PAIRS_SYMMETRIC = 1
 PREC_FP64 = 0
 PREC_MIXED = 1
+PREC_DF64 = 2
 MIXED_RULE_LITERAL = 0
 MIXED_RULE_HYP = 1
 GUESS_STANDARD = 0
