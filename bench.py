@@ -1,23 +1,28 @@
 """Benchmark of the Sakura all-pairs Kepler step on GB300.
 
 Metric: pair-Kepler solves per second, counted as N^2 * steps / s (the
-literal N^2 count; the kernel solves the N(N-1) ordered pairs i != j).
+literal N^2 count; the kernel solves each of the N(N-1)/2 unordered pairs
+once and applies it to both particles).
 
 Default workload: equal-mass Plummer sphere, N = 1024, virial units,
 dt = 2^-8, 256 steps (one N-body time unit), second-order map, FP64.  One
-"step" is one ``sakura_step`` call: the prep kernel (drift), the pair
-kernel (every ordered pair's Kepler solve, warp-shuffle row sums) and the
-apply kernel (Eqs. 27b-d).  The
-state (56 KB) fits in L2, so a 256 MB buffer is written between timed steps
-to flush L2; each step is timed with CUDA events on the library stream.
+"step" is one ``sakura_step`` call: the prep kernel (drift, Eq. 27a), the
+pair kernel (every unordered pair's Kepler solve on systolic 32 x 32 tiles)
+and the apply kernel (Eqs. 27b-d).  The state (56 KB) fits in L2, so a
+256 MB buffer is written between timed steps to flush L2; each step is
+timed with CUDA events on the library stream.
 
-Printed JSON line (rank 0): value (device-resident throughput), e2e (the
-same through the host-buffer entry point ``sakura_evolve_host``, copies
-included), roofline of the pair kernel against the FP64 ALU peak,
-cpu_baseline (the CPU oracle on the host cores), clocks sampled during the
-timed region.
+Printed JSON line (rank 0): value (device-resident throughput of the plain
+FP64 form), e2e (the same through the host-buffer entry point
+``sakura_evolve_host``, copies included), roofline of the pair kernel
+against the FP64 ALU peak, variants.df64 (the same workload in the
+double-word form: FP64-accurate pair solves on the FP32 pipe, against the
+FP32 peak), cpu_baseline (the CPU oracle on the host cores), clocks sampled
+during the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload plummer1024|bh16384|binaries16384|planetary9|ensemble4096]
+                    [--form fp64|mixed|df64] [--pairs symmetric|ordered]
 
 Multi-GPU (torchrun, one process per GPU): every rank integrates its own
 independently seeded replica; no data-path collective (weak scaling).
@@ -64,6 +69,14 @@ C_SYM = 12
 # FP64 ALU peak of one GB300: 152 SMs x 2 FP64 FMA units x 2 flop x 2.07 GHz
 # (the unit count follows from the nominal 1.25 TFLOP/s at 2.07 GHz).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# FP32 pipe peak of one GB300: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+
+# FP32 operations (FMA = 2) of one double-word pair solve, counted by running
+# the library's double-word code on the host with an operation tally over the
+# pairs of each workload's first step (tests/df64_flop_count.py; a CPU test
+# checks these figures against the current code)
+DF64_FLOPS_PER_SOLVE = {"plummer1024": 2039.0, "bh16384": 2016.1, "binaries16384": 2017.2}
 
 
 def _workload(name: str, seed: int):
@@ -152,9 +165,10 @@ class ClockSampler:
 def _kernel_sources_hash(kernel: str = "pair_step_sym") -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1402_3325_gb300", "csrc")
-    main = {"pair_step_sym": "step_sym.cu", "pair_step_fp64": "step_fp64.cu"}.get(kernel,
-                                                                               "step_fp64.cu")
-    for f in ("kepler_fp64.cuh", "pair_batch_fp64.cuh", main):
+    files = {"pair_step_sym": ["step_sym.cu"], "pair_step_fp64": ["step_fp64.cu"],
+             "pair_step_sym_df64": ["df64.cuh", "kepler_df64.cuh", "step_df64.cu"]}.get(
+                 kernel, ["step_fp64.cu"])
+    for f in ["kepler_fp64.cuh", "pair_batch_fp64.cuh"] + files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -310,6 +324,54 @@ def run_ensemble(args, rank, world, device, stream, dist):
     return 0
 
 
+def _variant_df64(args, sk, s, device, stream, flush, guess):
+    """The same workload and step count in the double-word form (FP64-accurate
+    pair solves on the FP32 pipe), timed the same way; reported beside the
+    plain FP64 headline."""
+    import torch
+    n = s.n
+    opts = dict(pair_mode=sk.PAIRS_SYMMETRIC, precision=sk.PREC_DF64)
+    mass = torch.tensor(s.m, device=device)
+    state = torch.tensor(s.soa(), device=device)
+    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_STATS, guess=guess, **opts)
+    for _ in range(args.warmup):
+        sk.step(state, mass, s.dt, 2)
+    sk.check()
+    st = sk.get_stats(reset=True)
+    spp = st["solves"] / max(1, st["pairs"])
+    share = st["fp32_pairs"] / max(1, st["solves"])
+    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_TIMING, guess=guess, **opts)
+    state.copy_(torch.tensor(s.soa(), device=device))
+    sk.get_stats(reset=True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize(device)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        sk.step(state, mass, s.dt, 2)
+        ends[k].record(stream)
+    torch.cuda.synchronize(device)
+    sk.check()
+    ms_total = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    st = sk.get_stats(reset=True)
+    pair_ms = st["pair_kernel_ms"] / max(1, st["timed_launches"])
+    flops = DF64_FLOPS_PER_SOLVE.get(args.workload)
+    solves = n * (n - 1) * spp
+    achieved = solves * flops / (pair_ms * 1e-3) / 1e12 if flops else None
+    peak = FP32_PEAK_GFLOPS / 1e3
+    return {"value": n * n * args.steps / (ms_total * 1e-3), "unit": UNIT,
+            "ms_per_step": ms_total / args.steps,
+            "dtype": "f32 double-word (pair solves) + f64 (drift, sums, fallback pairs)",
+            "parity": "same 1e-12 per-step bound against the FP64 oracle as the FP64 form",
+            "double_word_solve_share": share,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if achieved else None,
+                         "traffic": _profiled_traffic(args.workload, "pair_step_sym_df64"),
+                         "kernel": "pair_step_sym_df64_kernel", "pipe": "fp32",
+                         "flops_per_solve": flops, "pair_kernel_ms": pair_ms}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -332,6 +394,8 @@ def main():
                          " the FP32 pipe (symmetric pairs)")
     ap.add_argument("--mixed-rule", default="hyp", choices=["literal", "hyp"],
                     help="literal: FP32 iff r > 0.1 and e < 0.9; hyp: ... or e > 10")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the double-word form reported beside the FP64 headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -458,29 +522,38 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    symmetric = args.pairs == "symmetric" and args.form == "fp64"
-    flops_solve = C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP + (C_SYM if symmetric else 0)
+    symmetric = args.pairs == "symmetric" and args.form in ("fp64", "df64")
     solves = n * (n - 1) * solves_per_pair
-    achieved = solves * flops_solve / (pair_ms * 1e-3) / 1e12
-    peak = FP64_PEAK_GFLOPS / 1e3
-    traffic = _profiled_traffic(args.workload,
-                                "pair_step_sym" if symmetric else "pair_step_fp64")
+    if args.form == "df64":
+        flops_solve = DF64_FLOPS_PER_SOLVE.get(args.workload)
+        peak = FP32_PEAK_GFLOPS / 1e3
+        kname, pipe = "pair_step_sym_df64", "fp32"
+        peak_source = ("152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; flops per solve counted"
+                       " by running the double-word code on the host with an operation tally")
+    else:
+        flops_solve = C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP + (C_SYM if symmetric else 0)
+        peak = FP64_PEAK_GFLOPS / 1e3
+        kname = "pair_step_sym" if symmetric else (
+            "pair_step_mixed" if args.form == "mixed" else "pair_step_fp64")
+        pipe = "fp64"
+        peak_source = ("152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (derived from the nominal"
+                       " 1.25 TFLOP/s; FMA probe measured 1.19)")
+    achieved = (solves * flops_solve / (pair_ms * 1e-3) / 1e12) if flops_solve else None
+    traffic = _profiled_traffic(args.workload, kname)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic,
-            "kernel": "pair_step_sym_kernel" if symmetric else (
-                "pair_step_mixed_kernel" if args.form == "mixed" else "pair_step_fp64_kernel"),
-            "pipe": "fp64",
-            "peak_source": "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (derived from the "
-                           "nominal 1.25 TFLOP/s; FMA probe measured 1.19)",
+            "frac": achieved / peak if achieved else None, "traffic": traffic,
+            "kernel": kname + "_kernel", "pipe": pipe, "peak_source": peak_source,
             "flops_per_solve": flops_solve, "kepler_evals_per_solve": kbar,
             "solves_per_step": solves,
             "pair_kernel_ms": pair_ms, "pair_kernel_share": pair_ms / ms_step}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": ("f32 double-word (pair solves) + f64 (drift, sums, fallback pairs)"
+                      if args.form == "df64" else "f64"),
             "data": "synthetic",
             "config": {"workload": desc, "n": n, "dt": s.dt, "order": 2, "form": args.form,
-                       "pairs": args.pairs if args.form == "fp64" else "ordered",
+                       "pairs": args.pairs if args.form in ("fp64", "df64") else "ordered",
                        "kepler_guess": args.guess,
                        "fp32_pair_share": fp32_share,
                        "pairs_solved_per_step": n * (n - 1),
@@ -491,6 +564,9 @@ def main():
             "roofline": roof, "clocks": clocks.summary()}
     if e2e is not None:
         line["e2e"] = e2e
+    if (args.form == "fp64" and args.pairs == "symmetric" and not args.no_variants and
+            args.workload in DF64_FLOPS_PER_SOLVE):
+        line["variants"] = {"df64": _variant_df64(args, sk, s, device, stream, flush, guess)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(s, s.dt)
     print(json.dumps(line))

@@ -39,6 +39,17 @@ struct dw {
     float h, l;
 };
 
+#if !defined(__CUDA_ARCH__) && defined(SAKURA_DW_COUNT)
+// host build only: tally of floating-point operations (FMA = 2) and of
+// special-function approximations, for counting the work of one solve
+extern long long sakura_dw_flops, sakura_dw_mufu;
+#define SAKURA_DW_TALLY(k) (sakura_dw_flops += (k))
+#define SAKURA_DW_MUFU() (++sakura_dw_mufu)
+#else
+#define SAKURA_DW_TALLY(k) ((void)0)
+#define SAKURA_DW_MUFU() ((void)0)
+#endif
+
 #if defined(__CUDA_ARCH__)
 DW_HD float fadd(float a, float b) { return __fadd_rn(a, b); }
 DW_HD float fsub(float a, float b) { return __fsub_rn(a, b); }
@@ -57,13 +68,48 @@ DW_HD float rsqrt_approx(float x)
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+DW_HD float fsqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 #else
-DW_HD float fadd(float a, float b) { return a + b; }
-DW_HD float fsub(float a, float b) { return a - b; }
-DW_HD float fmul(float a, float b) { return a * b; }
-DW_HD float ffma(float a, float b, float c) { return std::fmaf(a, b, c); }
-DW_HD float rcp_approx(float x) { return 1.0f / x; }
-DW_HD float rsqrt_approx(float x) { return 1.0f / std::sqrt(x); }
+DW_HD float fadd(float a, float b)
+{
+    SAKURA_DW_TALLY(1);
+    return a + b;
+}
+DW_HD float fsub(float a, float b)
+{
+    SAKURA_DW_TALLY(1);
+    return a - b;
+}
+DW_HD float fmul(float a, float b)
+{
+    SAKURA_DW_TALLY(1);
+    return a * b;
+}
+DW_HD float ffma(float a, float b, float c)
+{
+    SAKURA_DW_TALLY(2);
+    return std::fmaf(a, b, c);
+}
+DW_HD float rcp_approx(float x)
+{
+    SAKURA_DW_MUFU();
+    return 1.0f / x;
+}
+DW_HD float rsqrt_approx(float x)
+{
+    SAKURA_DW_MUFU();
+    return 1.0f / std::sqrt(x);
+}
+DW_HD float fsqrt_approx(float x)
+{
+    SAKURA_DW_MUFU();
+    return std::sqrt(x);
+}
 #endif
 
 DW_HD dw two_sum(float a, float b)

@@ -61,21 +61,21 @@ DW_HD float stumpff32_terms(float x, float &c0, float &c1, float &c2)
 {
     int k = 0;
     while (fabsf(x) > 0.1f && k < 40) {
-        x *= 0.25f;
+        x = fmul(x, 0.25f);
         ++k;
     }
     const float y = -x;
-    float s2 = fmaf(fmaf(fmaf(1.0f / 40320.0f, y, 1.0f / 720.0f), y, 1.0f / 24.0f), y, 0.5f);
-    float s3 = fmaf(fmaf(fmaf(1.0f / 362880.0f, y, 1.0f / 5040.0f), y, 1.0f / 120.0f), y,
+    float s2 = ffma(ffma(ffma(1.0f / 40320.0f, y, 1.0f / 720.0f), y, 1.0f / 24.0f), y, 0.5f);
+    float s3 = ffma(ffma(ffma(1.0f / 362880.0f, y, 1.0f / 5040.0f), y, 1.0f / 120.0f), y,
                     1.0f / 6.0f);
-    float s0 = fmaf(y, s2, 1.0f);
-    float s1 = fmaf(y, s3, 1.0f);
+    float s0 = ffma(y, s2, 1.0f);
+    float s1 = ffma(y, s3, 1.0f);
     for (; k > 0; --k) {
-        const float n3 = 0.25f * fmaf(s0, s3, s2);
-        const float n2 = 0.5f * s1 * s1;
-        const float n1 = s0 * s1;
-        x *= 4.0f;
-        s0 = fmaf(-x, n2, 1.0f);
+        const float n3 = fmul(0.25f, ffma(s0, s3, s2));
+        const float n2 = fmul(fmul(0.5f, s1), s1);
+        const float n1 = fmul(s0, s1);
+        x = fmul(x, 4.0f);
+        s0 = ffma(-x, n2, 1.0f);
         s1 = n1;
         s2 = n2;
         s3 = n3;
@@ -87,42 +87,42 @@ DW_HD float stumpff32_terms(float x, float &c0, float &c1, float &c2)
 }
 
 // Laguerre iterations in FP32 from the standard (guess 0) or second-order
-// (guess 2) initial value.
-DW_HD K32 k32_solve(float r0, float ir0, float eta, float beta, float zeta,
-                                         float t, int guess)
+// (guess 2) initial value (approximate reciprocals: this phase only needs
+// the root to about 1e-7).
+DW_HD K32 k32_solve(float r0, float ir0, float eta, float beta, float zeta, float t, int guess)
 {
     K32 o;
     o.beta = beta;
-    float s = t * ir0;
+    float s = fmul(t, ir0);
     if (guess == 2) {
-        const float c = 0.5f * s * (eta * ir0);
-        if (fabsf(c) < 0.5f) s = fmaf(-c, s, s);
+        const float c = fmul(fmul(0.5f, s), fmul(eta, ir0));
+        if (fabsf(c) < 0.5f) s = ffma(-c, s, s);
     }
     const float tol = 4.0f * 1.1920929e-7f;
     o.ok = false;
     o.iters = 0;
     for (int it = 0; it < kDwFp32MaxIter; ++it) {
         float c0, c1, c2;
-        const float c3 = stumpff32_terms(beta * s * s, c0, c1, c2);
-        const float s2 = s * s;
-        const float G1 = s * c1, G2 = s2 * c2, G3 = s2 * s * c3;
-        const float F = fmaf(r0, s, fmaf(eta, G2, fmaf(zeta, G3, -t)));
-        const float Fp = fmaf(eta, G1, fmaf(zeta, G2, r0));
-        const float Fpp = fmaf(eta, c0, zeta * G1);
-        const float ir = 1.0f / Fp;
-        const float q = F * ir;
+        const float s2 = fmul(s, s);
+        const float c3 = stumpff32_terms(fmul(beta, s2), c0, c1, c2);
+        const float G1 = fmul(s, c1), G2 = fmul(s2, c2), G3 = fmul(fmul(s2, s), c3);
+        const float F = ffma(r0, s, ffma(eta, G2, ffma(zeta, G3, -t)));
+        const float Fp = ffma(eta, G1, ffma(zeta, G2, r0));
+        const float Fpp = ffma(eta, c0, fmul(zeta, G1));
+        const float ir = rcp_approx(Fp);
+        const float q = fmul(F, ir);
         ++o.iters;
         if (!(fabsf(q) <= 1e30f)) break;  // overflow or NaN
-        if (fabsf(q) <= tol * fmaxf(fabsf(s), fabsf(t * ir))) {
+        if (fabsf(q) <= fmul(tol, fmaxf(fabsf(s), fabsf(fmul(t, ir))))) {
             o.ok = true;
             break;
         }
-        const float u = 1.25f * q * Fpp * ir;
-        const float den = 1.0f + 4.0f * sqrtf(fabsf(1.0f - u));
-        s = s - 5.0f * q / den;
+        const float u = fmul(fmul(1.25f, q), fmul(Fpp, ir));
+        const float den = ffma(4.0f, fsqrt_approx(fabsf(fsub(1.0f, u))), 1.0f);
+        s = fsub(s, fmul(fmul(5.0f, q), rcp_approx(den)));
     }
     o.s = s;
-    o.x = beta * s * s;
+    o.x = fmul(fmul(beta, s), s);
     o.ok = o.ok && (fabsf(o.x) <= 256.0f) && fabsf(s) <= 3.0e38f;
     return o;
 }
@@ -177,15 +177,15 @@ DW_HD StumpffDW stumpff_dw(dw x, bool big)
     // 1/6: the inner terms in float, the outer two or three in double-word
     dw c2, c3;
     if (big) {
-        const float t2 = fmaf(fmaf(1.0f / 479001600.0f, yf, 1.0f / 3628800.0f), yf,
+        const float t2 = ffma(ffma(1.0f / 479001600.0f, yf, 1.0f / 3628800.0f), yf,
                               1.0f / 40320.0f);
-        const float t3 = fmaf(fmaf(1.0f / 6227020800.0f, yf, 1.0f / 39916800.0f), yf,
+        const float t3 = ffma(ffma(1.0f / 6227020800.0f, yf, 1.0f / 39916800.0f), yf,
                               1.0f / 362880.0f);
         c2 = dw_add(dw_mul(y, dw_add(SAKURA_DW_INV720, dw_mul_f(y, t2))), SAKURA_DW_INV24);
         c3 = dw_add(dw_mul(y, dw_add(SAKURA_DW_INV5040, dw_mul_f(y, t3))), SAKURA_DW_INV120);
     } else {
-        const float t2 = fmaf(fmaf(1.0f / 3628800.0f, yf, 1.0f / 40320.0f), yf, 1.0f / 720.0f);
-        const float t3 = fmaf(fmaf(1.0f / 39916800.0f, yf, 1.0f / 362880.0f), yf,
+        const float t2 = ffma(ffma(1.0f / 3628800.0f, yf, 1.0f / 40320.0f), yf, 1.0f / 720.0f);
+        const float t3 = ffma(ffma(1.0f / 39916800.0f, yf, 1.0f / 362880.0f), yf,
                               1.0f / 5040.0f);
         c2 = dw_add(dw_mul_f(y, t2), SAKURA_DW_INV24);
         c3 = dw_add(dw_mul_f(y, t3), SAKURA_DW_INV120);
@@ -227,15 +227,17 @@ DW_HD EvalDW dw_eval(const PairDW &p, dw s, dw t, bool big)
                         t);
     e.Fp = dw_add(dw_add(p.r0, dw_mul(p.eta0, e.G1)), dw_mul(p.zeta0, e.G2));
     e.Fpp = dw_add(dw_mul(p.eta0, c.c0), dw_mul(p.zeta0, e.G1));
-    const dw q = dw_mul(F, dw_rcp(e.Fp));
+    const dw ir = dw_rcp(e.Fp);
+    const dw q = dw_mul(F, ir);
     // Laguerre factor of order 5 in float: ds = q (1 + k)
-    const float u = 1.25f * q.h * (e.Fpp.h / e.Fp.h);
-    const float r = sqrtf(fabsf(1.0f - u));
-    const float cf = 0.8f * u / (1.0f + r);
-    const float k = fabsf(u) < 0.5f ? cf / (1.0f - cf) : 5.0f / fmaf(4.0f, r, 1.0f) - 1.0f;
-    e.ds = dw_add_f(q, q.h * k);
-    const float sc = fmaxf(fabsf(s.h), fabsf(t.h / e.Fp.h));
-    e.conv = fabsf(e.ds.h) <= 0x1p-20f * sc;
+    const float u = fmul(fmul(1.25f, q.h), fmul(e.Fpp.h, ir.h));
+    const float r = fsqrt_approx(fabsf(fsub(1.0f, u)));
+    const float cf = fmul(fmul(0.8f, u), rcp_approx(fadd(1.0f, r)));
+    const float k = fabsf(u) < 0.5f ? fmul(cf, rcp_approx(fsub(1.0f, cf)))
+                                    : fsub(fmul(5.0f, rcp_approx(ffma(4.0f, r, 1.0f))), 1.0f);
+    e.ds = dw_add_f(q, fmul(q.h, k));
+    const float sc = fmaxf(fabsf(s.h), fabsf(fmul(t.h, ir.h)));
+    e.conv = fabsf(e.ds.h) <= fmul(0x1p-20f, sc);
     return e;
 }
 
@@ -244,14 +246,14 @@ DW_HD EvalDW dw_eval(const PairDW &p, dw s, dw t, bool big)
 DW_HD void dw_carry(EvalDW &e, const PairDW &p)
 {
     const dw d = e.ds;
-    const float h2 = 0.5f * d.h * d.h;
+    const float h2 = fmul(fmul(0.5f, d.h), d.h);
     const dw G0 = e.c0;
-    const float Gm1 = -p.beta.h * e.G1.h;             // dG0/ds
-    const float F3 = fmaf(-p.eta0.h * p.beta.h, e.G1.h, p.zeta0.h * G0.h);  // dF''/ds
-    e.G3 = dw_add_f(dw_sub(e.G3, dw_mul(d, e.G2)), h2 * e.G1.h);
-    e.G2 = dw_add_f(dw_sub(e.G2, dw_mul(d, e.G1)), h2 * G0.h);
-    e.G1 = dw_add_f(dw_sub(e.G1, dw_mul(d, G0)), h2 * Gm1);
-    e.Fp = dw_add_f(dw_sub(e.Fp, dw_mul(d, e.Fpp)), h2 * F3);
+    const float Gm1 = fmul(-p.beta.h, e.G1.h);  // dG0/ds
+    const float F3 = ffma(fmul(-p.eta0.h, p.beta.h), e.G1.h, fmul(p.zeta0.h, G0.h));  // dF''/ds
+    e.G3 = dw_add_f(dw_sub(e.G3, dw_mul(d, e.G2)), fmul(h2, e.G1.h));
+    e.G2 = dw_add_f(dw_sub(e.G2, dw_mul(d, e.G1)), fmul(h2, G0.h));
+    e.G1 = dw_add_f(dw_sub(e.G1, dw_mul(d, G0)), fmul(h2, Gm1));
+    e.Fp = dw_add_f(dw_sub(e.Fp, dw_mul(d, e.Fpp)), fmul(h2, F3));
 }
 
 // Increments of the pair map (Eq. 26, increment form) divided by m, from
@@ -282,11 +284,11 @@ DW_HD K32 dw_phase1(const dw rr[3], const dw vv[3], dw m, float ptau32, float t3
     float x[3], u[3];
     for (int q = 0; q < 3; ++q) {
         u[q] = vv[q].h;
-        x[q] = fmaf(-ptau32, u[q], rr[q].h);
+        x[q] = ffma(-ptau32, u[q], rr[q].h);
     }
-    const float r2 = fmaf(x[0], x[0], fmaf(x[1], x[1], x[2] * x[2]));
-    const float v2 = fmaf(u[0], u[0], fmaf(u[1], u[1], u[2] * u[2]));
-    const float eta = fmaf(x[0], u[0], fmaf(x[1], u[1], x[2] * u[2]));
+    const float r2 = ffma(x[0], x[0], ffma(x[1], x[1], fmul(x[2], x[2])));
+    const float v2 = ffma(u[0], u[0], ffma(u[1], u[1], fmul(u[2], u[2])));
+    const float eta = ffma(x[0], u[0], ffma(x[1], u[1], fmul(x[2], u[2])));
     const bool range = r2 > 1e-30f && r2 < 1e30f && v2 < 1e30f && m.h > 1e-30f && m.h < 1e30f;
     K32 o;
     o.ok = false;
@@ -295,16 +297,16 @@ DW_HD K32 dw_phase1(const dw rr[3], const dw vv[3], dw m, float ptau32, float t3
     o.x = 0.0f;
     o.beta = 0.0f;
     if (!range) return o;
-    const float ir0 = 1.0f / sqrtf(r2);
-    const float r0 = r2 * ir0;
-    const float beta = fmaf(2.0f * m.h, ir0, -v2);
-    const float zeta = fmaf(-beta, r0, m.h);
+    const float ir0 = rsqrt_approx(r2);
+    const float r0 = fmul(r2, ir0);
+    const float beta = ffma(fmul(2.0f, m.h), ir0, -v2);
+    const float zeta = ffma(-beta, r0, m.h);
     // a bound orbit whose step exceeds 0.9 of its period needs t reduced
     // modulo the period: FP64 solver
     if (beta > 0.0f) {
-        const float b3 = beta * beta * beta;
-        const float tm = 6.2831853f * 0.9f * m.h;
-        if (t32 * t32 * b3 >= tm * tm) return o;
+        const float b3 = fmul(fmul(beta, beta), beta);
+        const float tm = fmul(6.2831853f * 0.9f, m.h);
+        if (fmul(fmul(t32, t32), b3) >= fmul(tm, tm)) return o;
     }
     return k32_solve(r0, ir0, eta, beta, zeta, t32, guess);
 }

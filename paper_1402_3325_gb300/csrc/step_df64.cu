@@ -212,11 +212,14 @@ __global__ void __launch_bounds__(128)
             if (need64) qw[tail + __popc(mask & lt_mask)] = lane | (c << 5);
             tail += __popc(mask);
             __syncwarp();
-            if (tail >= 32) {
-                flush(k, 32);
-                if (lane < tail - 32) qw[lane] = qw[32 + lane];
+            // solve the queue 32 at a time, and drain it at the item's last
+            // step (one call site keeps the FP64 solver's code single)
+            while (tail >= 32 || (k + 1 == k1 && tail > 0)) {
+                const int cnt = min(tail, 32);
+                flush(k, cnt);
+                if (lane < tail - cnt) qw[lane] = qw[cnt + lane];
                 __syncwarp();
-                tail -= 32;
+                tail -= cnt;
             }
             if (!diag && k + 1 < k1) {
 #pragma unroll
@@ -226,7 +229,6 @@ __global__ void __launch_bounds__(128)
                 }
             }
         }
-        if (tail > 0) flush(k1 - 1, tail);
         // row sums of rows i to slot (J, h); column sums to slot (I, h)
         float2 *part = reinterpret_cast<float2 *>(a.partial);
         if (irow) {
@@ -265,67 +267,58 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-// Eqs. 27b-d: a block takes 32 particles (one per lane); its kApplyWarps
-// warps add the double-word slots k = w, w + kApplyWarps, ... of those
-// particles, warp 0 adds the warps' sums in warp order, converts to FP64 and
-// applies the update.
+// Eqs. 27b-d: block (x, y) takes 32 particles (one per lane) and the
+// component pair (y, 3 + y); its kApplyDwWarps warps add the double-word
+// slots k = w, w + kApplyDwWarps, ... of those particles, warp 0 adds the
+// warps' sums in warp order, converts to FP64 and applies the update.
 constexpr int kApplyDwWarps = 16;
 
 __global__ void __launch_bounds__(32 * kApplyDwWarps)
     apply_df64_kernel(double *state, const double *X, const float2 *partial, int64_t n,
                       int64_t nslots, double post_drift, unsigned *status)
 {
-    __shared__ float2 red[kApplyDwWarps][6][32];
+    __shared__ float2 red[kApplyDwWarps][2][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int q = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * 32 + lane;
-    dw d[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) d[q] = dw{0.0f, 0.0f};
+    dw dr = {0.0f, 0.0f}, dv = {0.0f, 0.0f};
     if (i < n) {
+        dw er1 = {0.0f, 0.0f}, ev1 = {0.0f, 0.0f};
         int64_t k = wid;
         for (; k + kApplyDwWarps < nslots; k += 2 * kApplyDwWarps) {
-            float2 v0[6], v1[6];
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                v0[q] = partial[(k * 6 + q) * n + i];
-                v1[q] = partial[((k + kApplyDwWarps) * 6 + q) * n + i];
-            }
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                dw_acc(d[q], dw{v0[q].x, v0[q].y});
-                dw_acc(d[q], dw{v1[q].x, v1[q].y});
-            }
+            const float2 a0 = partial[(k * 6 + q) * n + i];
+            const float2 b0 = partial[(k * 6 + 3 + q) * n + i];
+            const float2 a1 = partial[((k + kApplyDwWarps) * 6 + q) * n + i];
+            const float2 b1 = partial[((k + kApplyDwWarps) * 6 + 3 + q) * n + i];
+            dw_acc(dr, dw{a0.x, a0.y});
+            dw_acc(dv, dw{b0.x, b0.y});
+            dw_acc(er1, dw{a1.x, a1.y});
+            dw_acc(ev1, dw{b1.x, b1.y});
         }
         for (; k < nslots; k += kApplyDwWarps) {
-#pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                const float2 v = partial[(k * 6 + q) * n + i];
-                dw_acc(d[q], dw{v.x, v.y});
-            }
+            const float2 a0 = partial[(k * 6 + q) * n + i];
+            const float2 b0 = partial[(k * 6 + 3 + q) * n + i];
+            dw_acc(dr, dw{a0.x, a0.y});
+            dw_acc(dv, dw{b0.x, b0.y});
         }
+        dr = dw_add(dr, er1);
+        dv = dw_add(dv, ev1);
     }
-#pragma unroll
-    for (int q = 0; q < 6; ++q) red[wid][q][lane] = make_float2(d[q].h, d[q].l);
+    red[wid][0][lane] = make_float2(dr.h, dr.l);
+    red[wid][1][lane] = make_float2(dv.h, dv.l);
     __syncthreads();
     if (wid != 0 || i >= n) return;
-    double dd[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        dw t = {red[0][q][lane].x, red[0][q][lane].y};
-        for (int w = 1; w < kApplyDwWarps; ++w)
-            t = dw_add(t, dw{red[w][q][lane].x, red[w][q][lane].y});
-        dd[q] = (double)t.h + (double)t.l;
+    dw tr = {red[0][0][lane].x, red[0][0][lane].y};
+    dw tv = {red[0][1][lane].x, red[0][1][lane].y};
+    for (int w = 1; w < kApplyDwWarps; ++w) {
+        tr = dw_add(tr, dw{red[w][0][lane].x, red[w][0][lane].y});
+        tv = dw_add(tv, dw{red[w][1][lane].x, red[w][1][lane].y});
     }
-    unsigned st = 0;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const double v1 = X[(3 + q) * n + i] + dd[3 + q];
-        const double x1 = fma(v1, post_drift, X[q * n + i] + dd[q]);
-        if (!isfinite(x1) || !isfinite(v1)) st |= kStatusNonfinite;
-        state[q * n + i] = x1;
-        state[(3 + q) * n + i] = v1;
-    }
-    if (st) atomicOr(status, st);
+    const double v1 = X[(3 + q) * n + i] + ((double)tv.h + (double)tv.l);
+    const double x1 = fma(v1, post_drift, X[q * n + i] + ((double)tr.h + (double)tr.l));
+    if (!isfinite(x1) || !isfinite(v1)) atomicOr(status, kStatusNonfinite);
+    state[q * n + i] = x1;
+    state[(3 + q) * n + i] = v1;
 }
 
 namespace {
@@ -369,7 +362,7 @@ void launch_pair_step_df64(const StepArgs &a, const DwArgs &da, int S, int64_t i
 void launch_apply_df64(double *state, const double *X, const void *partial, int64_t n,
                        int64_t nslots, double post_drift, unsigned *status, cudaStream_t s)
 {
-    apply_df64_kernel<<<(unsigned)((n + 31) / 32), 32 * kApplyDwWarps, 0, s>>>(
+    apply_df64_kernel<<<dim3((unsigned)((n + 31) / 32), 3), 32 * kApplyDwWarps, 0, s>>>(
         state, X, reinterpret_cast<const float2 *>(partial), n, nslots, post_drift, status);
 }
 

@@ -154,58 +154,54 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-// Eqs. 27b-d with the nslots slots of each particle added in a fixed order:
-// a block takes 32 particles (one per lane); its kApplyWarps warps sum the
-// slots k = w, w + kApplyWarps, ... of those particles (coalesced loads), and
-// warp 0 adds the warps' sums in warp order and applies the update.
+// Eqs. 27b-d with the nslots slots of each particle added in a fixed order.
+// Block (x, y) takes 32 particles (one per lane) and the component pair
+// (y, 3 + y), so that a step's partials are read by 3 n / 32 blocks; its
+// kApplyWarps warps sum the slots k = w, w + kApplyWarps, ... (coalesced
+// loads, four interleaved sums each) and warp 0 adds the warps' sums in
+// warp order and applies the update of x_y and v_y.
 constexpr int kApplyWarps = 16;
 
 __global__ void __launch_bounds__(32 * kApplyWarps)
     apply_sym_kernel(double *state, const double *X, const double *partial, int64_t n,
                      int64_t nslots, double post_drift, unsigned *status)
 {
-    __shared__ double red[kApplyWarps][6][32];
+    __shared__ double red[kApplyWarps][2][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int q = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * 32 + lane;
-    double d[6] = {0, 0, 0, 0, 0, 0};
+    double dr = 0.0, dv = 0.0;
     if (i < n) {
-        // four interleaved partial sums per component keep more loads in flight
-        double e[4][6] = {};
+        double er[4] = {0, 0, 0, 0}, ev[4] = {0, 0, 0, 0};
         int64_t k = wid;
         for (; k + 3 * kApplyWarps < nslots; k += 4 * kApplyWarps) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int q = 0; q < 6; ++q)
-                    e[u][q] += partial[((k + u * kApplyWarps) * 6 + q) * n + i];
+            for (int u = 0; u < 4; ++u) {
+                er[u] += partial[((k + u * kApplyWarps) * 6 + q) * n + i];
+                ev[u] += partial[((k + u * kApplyWarps) * 6 + 3 + q) * n + i];
+            }
         }
         for (; k < nslots; k += kApplyWarps) {
-#pragma unroll
-            for (int q = 0; q < 6; ++q) e[0][q] += partial[(k * 6 + q) * n + i];
+            er[0] += partial[(k * 6 + q) * n + i];
+            ev[0] += partial[(k * 6 + 3 + q) * n + i];
         }
-#pragma unroll
-        for (int q = 0; q < 6; ++q) d[q] = (e[0][q] + e[1][q]) + (e[2][q] + e[3][q]);
+        dr = (er[0] + er[1]) + (er[2] + er[3]);
+        dv = (ev[0] + ev[1]) + (ev[2] + ev[3]);
     }
-#pragma unroll
-    for (int q = 0; q < 6; ++q) red[wid][q][lane] = d[q];
+    red[wid][0][lane] = dr;
+    red[wid][1][lane] = dv;
     __syncthreads();
     if (wid != 0 || i >= n) return;
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        double t = red[0][q][lane];
-        for (int w = 1; w < kApplyWarps; ++w) t += red[w][q][lane];
-        d[q] = t;
+    double tr = red[0][0][lane], tv = red[0][1][lane];
+    for (int w = 1; w < kApplyWarps; ++w) {
+        tr += red[w][0][lane];
+        tv += red[w][1][lane];
     }
-    unsigned st = 0;
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const double v1 = X[(3 + q) * n + i] + d[3 + q];
-        const double x1 = fma(v1, post_drift, X[q * n + i] + d[q]);
-        if (!isfinite(x1) || !isfinite(v1)) st |= kStatusNonfinite;
-        state[q * n + i] = x1;
-        state[(3 + q) * n + i] = v1;
-    }
-    if (st) atomicOr(status, st);
+    const double v1 = X[(3 + q) * n + i] + tv;
+    const double x1 = fma(v1, post_drift, X[q * n + i] + tr);
+    if (!isfinite(x1) || !isfinite(v1)) atomicOr(status, kStatusNonfinite);
+    state[q * n + i] = x1;
+    state[(3 + q) * n + i] = v1;
 }
 
 namespace {
@@ -248,7 +244,7 @@ void launch_pair_step_sym(const StepArgs &a, int S, int64_t items, int blocks, b
 void launch_apply_sym(double *state, const double *X, const double *partial, int64_t n,
                       int64_t nslots, double post_drift, unsigned *status, cudaStream_t s)
 {
-    apply_sym_kernel<<<(unsigned)((n + 31) / 32), 32 * kApplyWarps, 0, s>>>(
+    apply_sym_kernel<<<dim3((unsigned)((n + 31) / 32), 3), 32 * kApplyWarps, 0, s>>>(
         state, X, partial, n, nslots, post_drift, status);
 }
 

@@ -6,6 +6,14 @@
 
 using sakura::dw;
 
+#if defined(SAKURA_DW_COUNT)
+namespace sakura {
+long long sakura_dw_flops = 0, sakura_dw_mufu = 0;
+}
+using sakura::sakura_dw_flops;
+using sakura::sakura_dw_mufu;
+#endif
+
 extern "C" {
 
 // op: 0 add, 1 sub, 2 add_f, 3 mul, 4 mul_f, 5 sqr, 6 rcp, 7 rsqrt
@@ -70,6 +78,50 @@ void dw_pair_batch(long n, const double *rv, const double *m, double tau, double
         for (int q = 0; q < 6; ++q) out[6 * k + q] = (double)d[q].h + (double)d[q].l;
     }
 }
+
+#if defined(SAKURA_DW_COUNT)
+// Floating-point work of the pair kernel for each pair (ri, rj, vi, vj as
+// doubles after the drift): the six exact differences, the FP32 phase, the
+// double-word phase and the two weighted double-word accumulations.
+// Returns the flops (FMA = 2) and approximations summed over the admitted
+// pairs and their count.
+void dw_count_pairs(long n, const double *xi, const double *xj, const double *mi,
+                    const double *mj, double tau, double pre, double post, int guess,
+                    double *flops, double *mufu, long *admitted)
+{
+    *flops = 0.0;
+    *mufu = 0.0;
+    *admitted = 0;
+    for (long k = 0; k < n; ++k) {
+        sakura_dw_flops = 0;
+        sakura_dw_mufu = 0;
+        dw rr[3], vv[3];
+        for (int q = 0; q < 6; ++q) {
+            float a0, a1, a2, b0, b1, b2;
+            sakura::tf_split(xi[6 * k + q], a0, a1, a2);
+            sakura::tf_split(xj[6 * k + q], b0, b1, b2);
+            (q < 3 ? rr[q] : vv[q - 3]) = sakura::tf_diff(a0, a1, a2, b0, b1, b2);
+        }
+        const dw ma = to_dw(mi[k]), mb = to_dw(mj[k]);
+        const dw m = sakura::dw_add(ma, mb);
+        const sakura::K32 o = sakura::dw_phase1(rr, vv, m, (float)(pre * tau), (float)tau, guess);
+        if (!o.ok) continue;
+        dw d[6];
+        int ev = 0;
+        if (!sakura::dw_phase2(rr, vv, m, to_dw(pre * tau), to_dw(tau), to_dw(post * tau), o.s,
+                               std::fabs(o.x) > 0x1p-8f, d, ev))
+            continue;
+        dw racc[6] = {}, cacc[6] = {};
+        for (int q = 0; q < 6; ++q) {
+            sakura::dw_acc(racc[q], sakura::dw_mul(mb, d[q]));
+            sakura::dw_acc(cacc[q], sakura::dw_mul(sakura::dw_neg(ma), d[q]));
+        }
+        *flops += (double)sakura_dw_flops;
+        *mufu += (double)sakura_dw_mufu;
+        ++*admitted;
+    }
+}
+#endif
 
 // exact difference of doubles through their three-float form
 void tf_diff_batch(long n, const double *a, const double *b, float *zh, float *zl)

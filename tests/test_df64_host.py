@@ -228,3 +228,20 @@ def test_double_word_pair_map_is_close_to_fp64_accuracy(lib, order):
         edw = max(np.abs(out[k, :3] * m[k] - dr).max() / sr, np.abs(out[k, 3:] * m[k] - dv).max() / sv)
         worst = max(worst, edw / max(1024 * e64, 2.0 ** -44))
     assert worst <= 1.0, worst
+
+
+def test_bench_flop_counts_are_current(tmp_path):
+    """bench.py's per-solve FP32 work of the double-word form must be the
+    count of the current code (tests/df64_flop_count.py)."""
+    import importlib.util
+    import sys
+    sys.path.insert(0, HERE)
+    import df64_flop_count as dfc
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(os.path.dirname(HERE),
+                                                                        "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    lib = dfc.build(str(tmp_path))
+    for name, s in dfc.workloads().items():
+        f, _, _ = dfc.count(lib, s)
+        assert abs(f - bench.DF64_FLOPS_PER_SOLVE[name]) <= 0.5, (name, f)
