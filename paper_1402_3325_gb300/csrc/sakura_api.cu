@@ -189,15 +189,13 @@ int step_device_sym(double *state, const double *masses, int64_t n, double dt, i
     const int64_t tiles = nb * (nb + 1) / 2;
     const int bps = df64 ? sakura::pair_step_df64_blocks_per_sm(stats)
                          : sakura::pair_step_sym_blocks_per_sm(stats, learned);
-    const int64_t resident = (int64_t)g.sm_count * bps * 4;
-    // step ranges per tile: enough items for every resident warp (each range
-    // adds nb slots of partials for the apply kernel to read)
-    int S = 1;
-    while (S < 8 && tiles * S < resident) S *= 2;
-    const int64_t items = tiles * S;
+    // contiguous tile-step ranges for W <= T warps (step_common.cuh)
+    const int64_t T = tiles * 32;
     int64_t blocks = g.cfg.grid_blocks > 0 ? g.cfg.grid_blocks : (int64_t)g.sm_count * bps;
-    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, (items + 3) / 4));
-    const int64_t nslots = nb * S;
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, T / 4));
+    const int64_t W = blocks * 4;
+    const int Smax = (int)((32 * W + T - 1) / T + 1);
+    const int64_t nslots = nb * Smax;
     // scratch: X[7][n] doubles, tile partials [nslots][6][n] (doubles, or
     // double-words of two floats), then (df64) X3[20][n] floats
     int rc = grow(g.partial, (size_t)(7 * n + nslots * 6 * n + (df64 ? 10 * n : 0)) *
@@ -241,18 +239,20 @@ int step_device_sym(double *state, const double *masses, int64_t n, double dt, i
         da.ptau = split_dw(a.pre * dt);
         da.t = split_dw(dt);
         da.qtau = split_dw(a.post * dt);
-        sakura::launch_pair_step_df64(a, da, S, items, (int)blocks, stats, g.stream);
+        sakura::launch_pair_step_df64(a, da, Smax, T, (int)blocks, stats, g.stream);
     } else {
-        sakura::launch_pair_step_sym(a, S, items, (int)blocks, stats, g.stream);
+        sakura::launch_pair_step_sym(a, Smax, T, (int)blocks, stats, g.stream);
     }
     if (timing) {
         cudaEventRecord(tm.second, g.stream);
         g.timers.push_back(tm);
     }
     if (df64)
-        sakura::launch_apply_df64(state, X, partial, n, nslots, post_drift, g.d_status, g.stream);
+        sakura::launch_apply_df64(state, X, partial, n, Smax, W, T, post_drift, g.d_status,
+                                  g.stream);
     else
-        sakura::launch_apply_sym(state, X, partial, n, nslots, post_drift, g.d_status, g.stream);
+        sakura::launch_apply_sym(state, X, partial, n, Smax, W, T, post_drift, g.d_status,
+                                 g.stream);
     rc = launch_error();
     if (rc) return rc;
     g.steps += 1;

@@ -48,6 +48,37 @@ void launch_pair_step_mixed(const StepArgs &a, const MixedArgs &ma, int blocks, 
                             cudaStream_t s);
 int pair_step_mixed_blocks_per_sm(bool stats);
 
+// Tiling of the symmetric (Newton's third law) kernels, step_sym.cu and
+// step_df64.cu.  Tile t = J (J + 1) / 2 + I covers row block I and column
+// block J, I <= J < nb; its 32 systolic steps are the tile-steps
+// 32 t .. 32 t + 31 of T = 32 tiles.  Warp w of W takes the contiguous
+// tile-steps [w T / W, (w + 1) T / W) (W <= T, so no range is empty), so every
+// warp gets T / W steps to within one.  The warp's piece of a tile is that
+// tile's segment number w - sym_owner(32 t); its row sums go to slot
+// J Smax + segment of the rows' particles and its column sums to slot
+// I Smax + segment of the columns' particles; Smax = ceil(32 W / T) + 1 bounds
+// the segments of any tile (32 consecutive tile-steps meet at most
+// ceil(31 W / T) + 1 ranges).  The apply kernels read exactly the slots that
+// exist (sym_segments), in a fixed order.
+__device__ __forceinline__ int64_t sym_owner(int64_t p, int64_t W, int64_t T)
+{
+    return ((p + 1) * W - 1) / T;
+}
+
+__device__ __forceinline__ void sym_tile_of(int64_t t, int64_t &I, int64_t &J)
+{
+    int64_t j = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((j + 1) * (j + 2) / 2 <= t) ++j;
+    while (j * (j + 1) / 2 > t) --j;
+    J = j;
+    I = t - j * (j + 1) / 2;
+}
+
+__device__ __forceinline__ int sym_segments(int64_t t, int64_t W, int64_t T)
+{
+    return (int)(sym_owner(32 * t + 31, W, T) - sym_owner(32 * t, W, T)) + 1;
+}
+
 // extra arguments of the double-word pair kernel
 struct DwArgs {
     const float *X3;      // [20][n] three-float drifted state, double-word masses
@@ -57,10 +88,11 @@ struct DwArgs {
 
 void launch_prep_df64(const double *state, const double *mass, double *X, float *X3, int64_t n,
                       double drift, unsigned *status, cudaStream_t s);
-void launch_pair_step_df64(const StepArgs &a, const DwArgs &da, int S, int64_t items, int blocks,
+void launch_pair_step_df64(const StepArgs &a, const DwArgs &da, int Smax, int64_t T, int blocks,
                            bool stats, cudaStream_t s);
-void launch_apply_df64(double *state, const double *X, const void *partial, int64_t n,
-                       int64_t nslots, double post_drift, unsigned *status, cudaStream_t s);
+void launch_apply_df64(double *state, const double *X, const void *partial, int64_t n, int Smax,
+                       int64_t W, int64_t T, double post_drift, unsigned *status,
+                       cudaStream_t s);
 int pair_step_df64_blocks_per_sm(bool stats);
 
 // pair kernel: one persistent wave of `blocks` blocks of `warps` warps
@@ -82,10 +114,10 @@ void launch_mlp_eval(const MlpWeights *W, const float *feat, int64_t count, floa
                      cudaStream_t s);
 // symmetric (Newton's third law) pair kernel: items = tiles * S
 int pair_step_sym_blocks_per_sm(bool stats, bool learned);
-void launch_pair_step_sym(const StepArgs &a, int S, int64_t items, int blocks, bool stats,
+void launch_pair_step_sym(const StepArgs &a, int Smax, int64_t T, int blocks, bool stats,
                           cudaStream_t s);
-void launch_apply_sym(double *state, const double *X, const double *partial, int64_t n,
-                      int64_t nslots, double post_drift, unsigned *status, cudaStream_t s);
+void launch_apply_sym(double *state, const double *X, const double *partial, int64_t n, int Smax,
+                      int64_t W, int64_t T, double post_drift, unsigned *status, cudaStream_t s);
 
 // number of partial-sum slots per row for W warps
 int pair_step_slots(int64_t n, int64_t W);

@@ -14,7 +14,8 @@
 //   a per-warp shared-memory queue that is solved 32 at a time by the FP64
 //   batch solver; each result is added to its row owner and to the lane that
 //   holds its column at that moment, in queue order (deterministic).
-//   Partial sums go out as double-words (float2) to the slots of step_sym.cu.
+//   Partial sums go out as double-words (float2) to the slots of step_sym.cu
+//   (contiguous tile-step ranges per warp, step_common.cuh).
 // apply kernel: Eqs. 27b-d with the slots added in double-word arithmetic
 //   and converted to FP64 once per particle.
 #include <cuda_runtime.h>
@@ -27,32 +28,31 @@
 
 namespace sakura {
 
+// one thread per (particle, component): blockIdx.y = 0..5 for x, y, z, vx,
+// vy, vz, 6 for the mass
 __global__ void prep_df64_kernel(const double *state, const double *mass, double *X, float *X3,
                                  int64_t n, double drift, unsigned *status)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
     if (i >= n) return;
-    const double m = mass[i];
-    if (!(m > 0.0)) atomicOr(status, kStatusMass);
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-        double x;
-        if (q < 3) {
-            x = fma(state[(3 + q) * n + i], drift, state[q * n + i]);
-        } else {
-            x = state[q * n + i];
-        }
-        X[q * n + i] = x;
-        float d0, d1, d2;
-        tf_split(x, d0, d1, d2);
-        X3[(3 * q) * n + i] = d0;
-        X3[(3 * q + 1) * n + i] = d1;
-        X3[(3 * q + 2) * n + i] = d2;
+    if (q == 6) {
+        const double m = mass[i];
+        if (!(m > 0.0)) atomicOr(status, kStatusMass);
+        X[6 * n + i] = m;
+        const float mh = __double2float_rn(m);
+        X3[18 * n + i] = mh;
+        X3[19 * n + i] = __double2float_rn(m - (double)mh);
+        return;
     }
-    X[6 * n + i] = m;
-    const float mh = __double2float_rn(m);
-    X3[18 * n + i] = mh;
-    X3[19 * n + i] = __double2float_rn(m - (double)mh);
+    const double x = q < 3 ? fma(state[(3 + q) * n + i], drift, state[q * n + i])
+                           : state[q * n + i];
+    X[q * n + i] = x;
+    float d0, d1, d2;
+    tf_split(x, d0, d1, d2);
+    X3[(3 * q) * n + i] = d0;
+    X3[(3 * q + 1) * n + i] = d1;
+    X3[(3 * q + 2) * n + i] = d2;
 }
 
 __device__ __forceinline__ dw dw_from_double(double x)
@@ -63,7 +63,7 @@ __device__ __forceinline__ dw dw_from_double(double x)
 
 template <bool STATS>
 __global__ void __launch_bounds__(128)
-    pair_step_sym_df64_kernel(StepArgs a, DwArgs da, int S, int64_t items)
+    pair_step_sym_df64_kernel(StepArgs a, DwArgs da, int Smax, int64_t T)
 {
     __shared__ int queue[4][64];
     __shared__ double qres[4][32][12];
@@ -81,19 +81,16 @@ __global__ void __launch_bounds__(128)
     long long it_sum = 0, slots = 0, fallbacks = 0, ndw = 0;
     int it_max = 0;
 
-    for (int64_t item = w * items / W; item < (w + 1) * items / W; ++item) {
-        const int64_t tile = item / S;
-        const int h = (int)(item - tile * S);
+    const int64_t p1 = (w + 1) * T / W;
+    for (int64_t pos = w * T / W; pos < p1;) {
+        const int64_t tile = pos >> 5;
+        const int k0 = (int)(pos & 31);
+        const int k1 = p1 - pos < 32 - k0 ? k0 + (int)(p1 - pos) : 32;
+        const int h = (int)(w - sym_owner(32 * tile, W, T));  // segment of the tile
+        pos += k1 - k0;
         int64_t I, J;
-        {
-            int64_t jj = (int64_t)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
-            while ((jj + 1) * (jj + 2) / 2 <= tile) ++jj;
-            while (jj * (jj + 1) / 2 > tile) --jj;
-            J = jj;
-            I = tile - jj * (jj + 1) / 2;
-        }
+        sym_tile_of(tile, I, J);
         const bool diag = I == J;
-        const int k0 = h * 32 / S, k1 = (h + 1) * 32 / S;
         const int64_t i = 32 * I + lane;
         const bool irow = i < n;
         float xi[18];
@@ -232,14 +229,14 @@ __global__ void __launch_bounds__(128)
         // row sums of rows i to slot (J, h); column sums to slot (I, h)
         float2 *part = reinterpret_cast<float2 *>(a.partial);
         if (irow) {
-            float2 *dst = part + (J * S + h) * 6 * n;
+            float2 *dst = part + (J * Smax + h) * 6 * n;
 #pragma unroll
             for (int q = 0; q < 6; ++q) dst[q * n + i] = make_float2(racc[q].h, racc[q].l);
         }
         if (!diag) {
             const int64_t jc = 32 * J + ((lane + k1 - 1) & 31);
             if (jc < n) {
-                float2 *dst = part + (I * S + h) * 6 * n;
+                float2 *dst = part + (I * Smax + h) * 6 * n;
 #pragma unroll
                 for (int q = 0; q < 6; ++q) dst[q * n + jc] = make_float2(cacc[q].h, cacc[q].l);
             }
@@ -268,41 +265,36 @@ __global__ void __launch_bounds__(128)
 }
 
 // Eqs. 27b-d: block (x, y) takes 32 particles (one per lane) and the
-// component pair (y, 3 + y); its kApplyDwWarps warps add the double-word
-// slots k = w, w + kApplyDwWarps, ... of those particles, warp 0 adds the
-// warps' sums in warp order, converts to FP64 and applies the update.
+// component pair (y, 3 + y); its kApplyDwWarps warps add the existing
+// double-word slots of the other blocks Q = w, w + kApplyDwWarps, ... of
+// those particles, warp 0 adds the warps' sums in warp order, converts to
+// FP64 and applies the update.
 constexpr int kApplyDwWarps = 16;
 
 __global__ void __launch_bounds__(32 * kApplyDwWarps)
-    apply_df64_kernel(double *state, const double *X, const float2 *partial, int64_t n,
-                      int64_t nslots, double post_drift, unsigned *status)
+    apply_df64_kernel(double *state, const double *X, const float2 *partial, int64_t n, int Smax,
+                      int64_t W, int64_t T, double post_drift, unsigned *status)
 {
     __shared__ float2 red[kApplyDwWarps][2][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int q = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t P = blockIdx.x;
+    const int64_t i = P * 32 + lane;
+    const int64_t nb = (n + 31) >> 5;
     dw dr = {0.0f, 0.0f}, dv = {0.0f, 0.0f};
     if (i < n) {
-        dw er1 = {0.0f, 0.0f}, ev1 = {0.0f, 0.0f};
-        int64_t k = wid;
-        for (; k + kApplyDwWarps < nslots; k += 2 * kApplyDwWarps) {
-            const float2 a0 = partial[(k * 6 + q) * n + i];
-            const float2 b0 = partial[(k * 6 + 3 + q) * n + i];
-            const float2 a1 = partial[((k + kApplyDwWarps) * 6 + q) * n + i];
-            const float2 b1 = partial[((k + kApplyDwWarps) * 6 + 3 + q) * n + i];
-            dw_acc(dr, dw{a0.x, a0.y});
-            dw_acc(dv, dw{b0.x, b0.y});
-            dw_acc(er1, dw{a1.x, a1.y});
-            dw_acc(ev1, dw{b1.x, b1.y});
+        // slot k = Q Smax + o holds the segment o of the tile of blocks P, Q
+        for (int64_t Q = wid; Q < nb; Q += kApplyDwWarps) {
+            const int64_t tile = P <= Q ? Q * (Q + 1) / 2 + P : P * (P + 1) / 2 + Q;
+            const int segs = sym_segments(tile, W, T);
+            for (int o = 0; o < segs; ++o) {
+                const int64_t k = Q * Smax + o;
+                const float2 a0 = partial[(k * 6 + q) * n + i];
+                const float2 b0 = partial[(k * 6 + 3 + q) * n + i];
+                dw_acc(dr, dw{a0.x, a0.y});
+                dw_acc(dv, dw{b0.x, b0.y});
+            }
         }
-        for (; k < nslots; k += kApplyDwWarps) {
-            const float2 a0 = partial[(k * 6 + q) * n + i];
-            const float2 b0 = partial[(k * 6 + 3 + q) * n + i];
-            dw_acc(dr, dw{a0.x, a0.y});
-            dw_acc(dv, dw{b0.x, b0.y});
-        }
-        dr = dw_add(dr, er1);
-        dv = dw_add(dv, ev1);
     }
     red[wid][0][lane] = make_float2(dr.h, dr.l);
     red[wid][1][lane] = make_float2(dv.h, dv.l);
@@ -345,25 +337,25 @@ int pair_step_df64_blocks_per_sm(bool stats)
 void launch_prep_df64(const double *state, const double *mass, double *X, float *X3, int64_t n,
                       double drift, unsigned *status, cudaStream_t s)
 {
-    const int threads = 256;
-    prep_df64_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
+    const int threads = 64;
+    prep_df64_kernel<<<dim3((unsigned)((n + threads - 1) / threads), 7), threads, 0, s>>>(
         state, mass, X, X3, n, drift, status);
 }
 
-void launch_pair_step_df64(const StepArgs &a, const DwArgs &da, int S, int64_t items, int blocks,
+void launch_pair_step_df64(const StepArgs &a, const DwArgs &da, int Smax, int64_t T, int blocks,
                            bool stats, cudaStream_t s)
 {
-    int Sv = S;
-    int64_t it = items;
+    int Sv = Smax;
+    int64_t it = T;
     void *args[] = {(void *)&a, (void *)&da, (void *)&Sv, (void *)&it};
     cudaLaunchKernel(df64_kernel(stats), dim3(blocks), dim3(128), args, 0, s);
 }
 
-void launch_apply_df64(double *state, const double *X, const void *partial, int64_t n,
-                       int64_t nslots, double post_drift, unsigned *status, cudaStream_t s)
+void launch_apply_df64(double *state, const double *X, const void *partial, int64_t n, int Smax,
+                       int64_t W, int64_t T, double post_drift, unsigned *status, cudaStream_t s)
 {
     apply_df64_kernel<<<dim3((unsigned)((n + 31) / 32), 3), 32 * kApplyDwWarps, 0, s>>>(
-        state, X, reinterpret_cast<const float2 *>(partial), n, nslots, post_drift, status);
+        state, X, reinterpret_cast<const float2 *>(partial), n, Smax, W, T, post_drift, status);
 }
 
 }  // namespace sakura

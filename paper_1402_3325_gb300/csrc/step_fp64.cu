@@ -193,7 +193,7 @@ int pair_step_slots(int64_t n, int64_t W)
 void launch_prep_step(const double *state, const double *mass, double *X, int64_t n,
                       double drift, unsigned *status, cudaStream_t s)
 {
-    const int threads = 256;
+    const int threads = 64;  // small blocks spread a small n over many SMs
     prep_step_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(state, mass, X,
                                                                                  n, drift, status);
 }

@@ -8,19 +8,19 @@
 // So each pair is solved once and adds  m_j delta/m_ij  to particle i and
 // -m_i delta/m_ij  to particle j (Eq. 23 with 1/m_i folded in).
 //
-// Work: 32 x 32 tiles (row block I, column block J), I <= J, optionally cut
-// into S step ranges.  A warp takes one (tile, range) item.  Lane l owns row
+// Work: 32 x 32 tiles (row block I, column block J), I <= J; each warp takes
+// a contiguous range of tile-steps (step_common.cuh).  Lane l owns row
 // i = 32 I + l; at step k it solves the pair with column c = (l + k) mod 32,
 // so the 32 lanes always hold 32 different columns.  Row sums stay in the
 // lane; column sums travel with their column: after each step every lane
 // takes the column accumulator of lane l + 1 (warp shuffle), so the
 // accumulator of column (l + k) mod 32 is in lane l at step k.  Diagonal tiles
 // (I = J) solve their ordered pairs (i != j) and keep only row sums.
-// Partials go to part[slot][6][n] with slot = other_block * S + range: the
-// row sums of tile (I, J) to slot (J, h) of the rows, the column sums to slot
-// (I, h) of the columns.  Every (slot, particle) is written exactly once and
-// the apply kernel adds a particle's nb * S slots in a fixed order
-// (deterministic, no atomics).
+// Partials go to part[slot][6][n] with slot = other_block * Smax + segment:
+// the row sums of tile (I, J) to slot (J, h) of the rows, the column sums to
+// slot (I, h) of the columns.  Every existing (slot, particle) is written
+// exactly once and the apply kernel adds a particle's existing slots in a
+// fixed order (deterministic, no atomics).
 #include <cuda_runtime.h>
 
 #include "kepler_fp64.cuh"
@@ -30,18 +30,9 @@
 
 namespace sakura {
 
-__device__ __forceinline__ void tile_of(int64_t t, int64_t &I, int64_t &J)
-{
-    int64_t j = (int64_t)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-    while ((j + 1) * (j + 2) / 2 <= t) ++j;
-    while (j * (j + 1) / 2 > t) --j;
-    J = j;
-    I = t - j * (j + 1) / 2;
-}
-
 template <bool STATS, bool LEARNED>
 __global__ void __launch_bounds__(128)
-    pair_step_sym_kernel(StepArgs a, int S, int64_t items)
+    pair_step_sym_kernel(StepArgs a, int Smax, int64_t T)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(dsm);
@@ -58,13 +49,16 @@ __global__ void __launch_bounds__(128)
     long long it_sum = 0, slots = 0, fallbacks = 0;
     int it_max = 0;
 
-    for (int64_t item = w * items / W; item < (w + 1) * items / W; ++item) {
-        const int64_t tile = item / S;
-        const int h = (int)(item - tile * S);
+    const int64_t p1 = (w + 1) * T / W;
+    for (int64_t pos = w * T / W; pos < p1;) {
+        const int64_t tile = pos >> 5;
+        const int k0 = (int)(pos & 31);
+        const int k1 = p1 - pos < 32 - k0 ? k0 + (int)(p1 - pos) : 32;
+        const int h = (int)(w - sym_owner(32 * tile, W, T));  // segment of the tile
+        pos += k1 - k0;
         int64_t I, J;
-        tile_of(tile, I, J);
+        sym_tile_of(tile, I, J);
         const bool diag = I == J;
-        const int k0 = h * 32 / S, k1 = (h + 1) * 32 / S;
         const int64_t i = 32 * I + lane;
         const bool irow = i < n;
         double xi = 0, yi = 0, zi = 0, vxi = 0, vyi = 0, vzi = 0, mi = 1;
@@ -121,14 +115,14 @@ __global__ void __launch_bounds__(128)
         }
         // row sums of rows i to slot (J, h); column sums to slot (I, h)
         if (irow) {
-            double *dst = a.partial + (J * S + h) * 6 * n;
+            double *dst = a.partial + (J * Smax + h) * 6 * n;
 #pragma unroll
             for (int q = 0; q < 6; ++q) dst[q * n + i] = racc[q];
         }
         if (!diag) {
             const int64_t j = 32 * J + ((lane + k1 - 1) & 31);
             if (j < n) {
-                double *dst = a.partial + (I * S + h) * 6 * n;
+                double *dst = a.partial + (I * Smax + h) * 6 * n;
 #pragma unroll
                 for (int q = 0; q < 6; ++q) dst[q * n + j] = cacc[q];
             }
@@ -154,39 +148,41 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-// Eqs. 27b-d with the nslots slots of each particle added in a fixed order.
-// Block (x, y) takes 32 particles (one per lane) and the component pair
-// (y, 3 + y), so that a step's partials are read by 3 n / 32 blocks; its
-// kApplyWarps warps sum the slots k = w, w + kApplyWarps, ... (coalesced
-// loads, four interleaved sums each) and warp 0 adds the warps' sums in
-// warp order and applies the update of x_y and v_y.
+// Eqs. 27b-d with the existing slots of each particle added in a fixed
+// order.  Block (x, y) takes 32 particles (one per lane) and the component
+// pair (y, 3 + y), so that a step's partials are read by 3 n / 32 blocks; its
+// kApplyWarps warps sum the slots of the other blocks Q = w, w + kApplyWarps,
+// ... (coalesced loads, two interleaved sums each) and warp 0 adds the warps'
+// sums in warp order and applies the update of x_y and v_y.
 constexpr int kApplyWarps = 16;
 
 __global__ void __launch_bounds__(32 * kApplyWarps)
-    apply_sym_kernel(double *state, const double *X, const double *partial, int64_t n,
-                     int64_t nslots, double post_drift, unsigned *status)
+    apply_sym_kernel(double *state, const double *X, const double *partial, int64_t n, int Smax,
+                     int64_t W, int64_t T, double post_drift, unsigned *status)
 {
     __shared__ double red[kApplyWarps][2][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int q = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+    const int64_t P = blockIdx.x;
+    const int64_t i = P * 32 + lane;
+    const int64_t nb = (n + 31) >> 5;
     double dr = 0.0, dv = 0.0;
     if (i < n) {
-        double er[4] = {0, 0, 0, 0}, ev[4] = {0, 0, 0, 0};
-        int64_t k = wid;
-        for (; k + 3 * kApplyWarps < nslots; k += 4 * kApplyWarps) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                er[u] += partial[((k + u * kApplyWarps) * 6 + q) * n + i];
-                ev[u] += partial[((k + u * kApplyWarps) * 6 + 3 + q) * n + i];
+        // slot k = Q Smax + o holds the segment o of the tile of blocks P, Q
+        double er[2] = {0, 0}, ev[2] = {0, 0};
+        int u = 0;
+        for (int64_t Q = wid; Q < nb; Q += kApplyWarps) {
+            const int64_t tile = P <= Q ? Q * (Q + 1) / 2 + P : P * (P + 1) / 2 + Q;
+            const int segs = sym_segments(tile, W, T);
+            for (int o = 0; o < segs; ++o) {
+                const int64_t k = Q * Smax + o;
+                er[u] += partial[(k * 6 + q) * n + i];
+                ev[u] += partial[(k * 6 + 3 + q) * n + i];
+                u ^= 1;
             }
         }
-        for (; k < nslots; k += kApplyWarps) {
-            er[0] += partial[(k * 6 + q) * n + i];
-            ev[0] += partial[(k * 6 + 3 + q) * n + i];
-        }
-        dr = (er[0] + er[1]) + (er[2] + er[3]);
-        dv = (ev[0] + ev[1]) + (ev[2] + ev[3]);
+        dr = er[0] + er[1];
+        dv = ev[0] + ev[1];
     }
     red[wid][0][lane] = dr;
     red[wid][1][lane] = dv;
@@ -230,22 +226,22 @@ int pair_step_sym_blocks_per_sm(bool stats, bool learned)
     return b > 0 ? b : 1;
 }
 
-void launch_pair_step_sym(const StepArgs &a, int S, int64_t items, int blocks, bool stats,
+void launch_pair_step_sym(const StepArgs &a, int Smax, int64_t T, int blocks, bool stats,
                           cudaStream_t s)
 {
     const bool learned = a.mlp != nullptr;
-    int Sv = S;
-    int64_t it = items;
+    int Sv = Smax;
+    int64_t it = T;
     void *args[] = {(void *)&a, (void *)&Sv, (void *)&it};
     cudaLaunchKernel(sym_kernel(stats, learned), dim3(blocks), dim3(128), args, sym_smem(learned),
                      s);
 }
 
-void launch_apply_sym(double *state, const double *X, const double *partial, int64_t n,
-                      int64_t nslots, double post_drift, unsigned *status, cudaStream_t s)
+void launch_apply_sym(double *state, const double *X, const double *partial, int64_t n, int Smax,
+                      int64_t W, int64_t T, double post_drift, unsigned *status, cudaStream_t s)
 {
     apply_sym_kernel<<<dim3((unsigned)((n + 31) / 32), 3), 32 * kApplyWarps, 0, s>>>(
-        state, X, partial, n, nslots, post_drift, status);
+        state, X, partial, n, Smax, W, T, post_drift, status);
 }
 
 }  // namespace sakura
