@@ -65,6 +65,10 @@ C_EVAL = 41
 C_STEP = 6
 # the symmetric mode adds the column accumulation (6 FMA) to every solve
 C_SYM = 12
+# a solve finished by the Taylor carry (single-precision seed): one more
+# Laguerre correction (C_STEP) and the carry of G1..G3 and F' with a new
+# 1/F' (29: h2 (2), dF''/ds (4), three G's and F' (17), reciprocal (6))
+C_CARRY = 29
 
 # FP64 ALU peak of one GB300: 152 SMs x 2 FP64 FMA units x 2 flop x 2.07 GHz
 # (the unit count follows from the nominal 1.25 TFLOP/s at 2.07 GHz).
@@ -76,7 +80,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 # the library's double-word code on the host with an operation tally over the
 # pairs of each workload's first step (tests/df64_flop_count.py; a CPU test
 # checks these figures against the current code)
-DF64_FLOPS_PER_SOLVE = {"plummer1024": 2039.0, "bh16384": 2016.1, "binaries16384": 2017.2}
+DF64_FLOPS_PER_SOLVE = {"plummer1024": 1940.0, "bh16384": 1917.1, "binaries16384": 1918.2}
 
 
 def _workload(name: str, seed: int):
@@ -251,7 +255,7 @@ def run_ensemble(args, rank, world, device, stream, dist):
     from paper_1402_3325_gb300 import sakura as sk
     ens, _, desc = _workload(args.workload, seed=rank)
     guess = {"taylor": sk.GUESS_TAYLOR, "standard": sk.GUESS_STANDARD,
-             "learned": sk.GUESS_LEARNED}[args.guess]
+             "learned": sk.GUESS_LEARNED, "fp32": sk.GUESS_FP32}[args.guess]
     sizes = ens.offsets[1:] - ens.offsets[:-1]
     n2 = int((sizes * sizes).sum())
     st = torch.tensor(ens.state, device=device)
@@ -307,7 +311,8 @@ def run_ensemble(args, rank, world, device, stream, dist):
             "data": "synthetic",
             "config": {"workload": desc, "nsys": ens.nsys, "particles": int(ens.offsets[-1]),
                        "n2_per_step": n2, "pairs_solved_per_step": pairs, "order": 2,
-                       "form": "batched", "kepler_guess": args.guess,
+                       "form": "batched",
+                       "kepler_guess": "taylor" if args.guess == "fp32" else args.guess,
                        "block_warps": warps, "blocks": blocks, "autotune_ms": tune,
                        "l2": "state (7.7 MB) stays in shared memory for the whole call"},
             "gpu_launches": 1,
@@ -381,9 +386,11 @@ def main():
     ap.add_argument("--workload", default="plummer1024",
                     choices=["plummer1024", "bh16384", "binaries16384", "planetary9",
                              "ensemble4096"])
-    ap.add_argument("--guess", default="taylor", choices=["standard", "taylor", "learned"],
-                    help="Kepler initial guess: t/r0, the second-order expansion, or the"
-                         " expansion refined by the trained network")
+    ap.add_argument("--guess", default="fp32",
+                    choices=["standard", "taylor", "learned", "fp32"],
+                    help="Kepler initial guess: t/r0, the second-order expansion, the"
+                         " expansion refined by the trained network, or the root of a"
+                         " single-precision solve of the pair (symmetric FP64 step)")
     ap.add_argument("--pairs", default="symmetric", choices=["symmetric", "ordered"],
                     help="symmetric: each unordered pair solved once (Newton's third law);"
                          " ordered: every ordered pair solved")
@@ -434,7 +441,7 @@ def main():
     s, _, desc = _workload(args.workload, seed=rank)
     n = s.n
     guess = {"taylor": sk.GUESS_TAYLOR, "standard": sk.GUESS_STANDARD,
-             "learned": sk.GUESS_LEARNED}[args.guess]
+             "learned": sk.GUESS_LEARNED, "fp32": sk.GUESS_FP32}[args.guess]
     form_opts = {"pair_mode": sk.PAIRS_SYMMETRIC if args.pairs == "symmetric"
                  else sk.PAIRS_ORDERED}
     if args.form == "df64":
@@ -460,6 +467,7 @@ def main():
     sk.check()
     st = sk.get_stats(reset=True)
     kbar = st["iters"] / max(1, st["solves"])
+    carried = st.get("carries", 0) / max(1, st["solves"])
     solves_per_pair = st["solves"] / max(1, st["pairs"])
     fp32_share = st["fp32_pairs"] / max(1, st["pairs"])
     sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_TIMING, guess=guess,
@@ -531,7 +539,8 @@ def main():
         peak_source = ("152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; flops per solve counted"
                        " by running the double-word code on the host with an operation tally")
     else:
-        flops_solve = C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP + (C_SYM if symmetric else 0)
+        flops_solve = (C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP +
+                       carried * (C_STEP + C_CARRY) + (C_SYM if symmetric else 0))
         peak = FP64_PEAK_GFLOPS / 1e3
         kname = "pair_step_sym" if symmetric else (
             "pair_step_mixed" if args.form == "mixed" else "pair_step_fp64")
@@ -544,6 +553,7 @@ def main():
             "frac": achieved / peak if achieved else None, "traffic": traffic,
             "kernel": kname + "_kernel", "pipe": pipe, "peak_source": peak_source,
             "flops_per_solve": flops_solve, "kepler_evals_per_solve": kbar,
+            "carried_share": carried,
             "solves_per_step": solves,
             "pair_kernel_ms": pair_ms, "pair_kernel_share": pair_ms / ms_step}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

@@ -71,6 +71,12 @@ extern "C" {
 #define SAKURA_GUESS_STANDARD 0 /* s0 = t / r0                               */
 #define SAKURA_GUESS_LEARNED 1  /* s0 from the loaded MLP (sakura_load_mlp)   */
 #define SAKURA_GUESS_TAYLOR 2   /* s0 = (t/r0)(1 - eta0 t / (2 r0^2)): second order in t */
+#define SAKURA_GUESS_FP32 3     /* s0 = the root of a single-precision Laguerre solve of
+                                   the same pair (from a float copy of the drifted
+                                   state, second-order start); the FP64 iteration and
+                                   its convergence test follow as for every guess.
+                                   Symmetric FP64 step only; elsewhere, and for a pair
+                                   whose float solve fails, the second-order guess */
 
 #define SAKURA_FLAG_SYNC_CHECK 1u /* synchronise and report faults on every call */
 #define SAKURA_FLAG_STATS 2u      /* collect iteration statistics (small cost)   */
@@ -115,6 +121,9 @@ typedef struct sakura_stats {
     int64_t timed_launches; /* pair-kernel launches timed (SAKURA_FLAG_TIMING)    */
     double pair_kernel_ms;  /* their summed device time, from CUDA events on the
                                library stream                                    */
+    int64_t carries;      /* FP64 solves finished by a Laguerre step below 2^-20 of
+                             the scale with G1..G3 and r carried to the root by
+                             their Taylor series (symmetric FP64 step)          */
 } sakura_stats;
 
 /* Fill *cfg with the defaults listed above. */

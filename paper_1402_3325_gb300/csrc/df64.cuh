@@ -14,6 +14,8 @@
 //                 for basic building blocks of double-word arithmetic", ACM
 //                 TOMS 44 (2017), Alg. 6 (relative error <= 3u^2, u = 2^-24);
 //   dw_add_f      ibid. Alg. 4 (double-word plus float, <= 2u^2);
+//   dw_add_nc     ibid. Alg. 5 (no cancellation: like signs or a much
+//                 smaller term, <= 3u^2);
 //   dw_mul        ibid. Alg. 12 (<= 4u^2 with FMA; here the l*l term kept);
 //   dw_mul_f      ibid. Alg. 9 (double-word times float, <= 2u^2);
 // and Newton corrections for 1/y and 1/sqrt(x) from a float approximation
@@ -148,6 +150,15 @@ DW_HD dw dw_add(dw x, dw y)
 }
 
 DW_HD dw dw_sub(dw x, dw y) { return dw_add(x, dw_neg(y)); }
+
+// ibid. Alg. 5 (sloppy sum): relative error <= 3u^2 when x and y have the
+// same sign; used only for sums of like-signed terms and for a term much
+// smaller than the other (no cancellation)
+DW_HD dw dw_add_nc(dw x, dw y)
+{
+    const dw s = two_sum(x.h, y.h);
+    return fast_two_sum(s.h, fadd(s.l, fadd(x.l, y.l)));
+}
 
 DW_HD dw dw_add_f(dw x, float y)
 {

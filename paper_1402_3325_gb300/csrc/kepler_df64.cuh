@@ -147,11 +147,11 @@ DW_HD void dw_setup(PairDW &p, const dw rr[3], const dw vv[3], dw m, dw ptau)
     p.y0 = dw_sub(rr[1], dw_mul(ptau, vv[1]));
     p.z0 = dw_sub(rr[2], dw_mul(ptau, vv[2]));
     p.m = m;
-    const dw r2 = dw_add(dw_add(dw_sqr(p.x0), dw_sqr(p.y0)), dw_sqr(p.z0));
+    const dw r2 = dw_add_nc(dw_add_nc(dw_sqr(p.x0), dw_sqr(p.y0)), dw_sqr(p.z0));
     p.ir0 = dw_rsqrt(r2);
     p.r0 = dw_mul(r2, p.ir0);
     p.eta0 = dw_add(dw_add(dw_mul(p.x0, p.vx), dw_mul(p.y0, p.vy)), dw_mul(p.z0, p.vz));
-    const dw v2 = dw_add(dw_add(dw_sqr(p.vx), dw_sqr(p.vy)), dw_sqr(p.vz));
+    const dw v2 = dw_add_nc(dw_add_nc(dw_sqr(p.vx), dw_sqr(p.vy)), dw_sqr(p.vz));
     p.beta = dw_sub(dw_scale(dw_mul(m, p.ir0), 2.0f), v2);
     p.zeta0 = dw_sub(m, dw_mul(p.beta, p.r0));
 }
@@ -174,24 +174,27 @@ DW_HD StumpffDW stumpff_dw(dw x, bool big)
     const dw y = dw_neg(x);
     const float yf = y.h;
     // c2 = 1/2 + y (1/24 + y (1/720 + y (1/40320 + ...))), c3 likewise from
-    // 1/6: the inner terms in float, the outer two or three in double-word
+    // 1/6: the inner terms in float, the outer two or three in double-word;
+    // |y| <= 0.1, so each constant outweighs the term added to it (no
+    // cancellation)
     dw c2, c3;
     if (big) {
         const float t2 = ffma(ffma(1.0f / 479001600.0f, yf, 1.0f / 3628800.0f), yf,
                               1.0f / 40320.0f);
         const float t3 = ffma(ffma(1.0f / 6227020800.0f, yf, 1.0f / 39916800.0f), yf,
                               1.0f / 362880.0f);
-        c2 = dw_add(dw_mul(y, dw_add(SAKURA_DW_INV720, dw_mul_f(y, t2))), SAKURA_DW_INV24);
-        c3 = dw_add(dw_mul(y, dw_add(SAKURA_DW_INV5040, dw_mul_f(y, t3))), SAKURA_DW_INV120);
+        c2 = dw_add_nc(dw_mul(y, dw_add_nc(SAKURA_DW_INV720, dw_mul_f(y, t2))), SAKURA_DW_INV24);
+        c3 = dw_add_nc(dw_mul(y, dw_add_nc(SAKURA_DW_INV5040, dw_mul_f(y, t3))),
+                       SAKURA_DW_INV120);
     } else {
         const float t2 = ffma(ffma(1.0f / 3628800.0f, yf, 1.0f / 40320.0f), yf, 1.0f / 720.0f);
         const float t3 = ffma(ffma(1.0f / 39916800.0f, yf, 1.0f / 362880.0f), yf,
                               1.0f / 5040.0f);
-        c2 = dw_add(dw_mul_f(y, t2), SAKURA_DW_INV24);
-        c3 = dw_add(dw_mul_f(y, t3), SAKURA_DW_INV120);
+        c2 = dw_add_nc(dw_mul_f(y, t2), SAKURA_DW_INV24);
+        c3 = dw_add_nc(dw_mul_f(y, t3), SAKURA_DW_INV120);
     }
     c2 = dw_add_f(dw_mul(y, c2), 0.5f);
-    c3 = dw_add(dw_mul(y, c3), SAKURA_DW_INV6);
+    c3 = dw_add_nc(dw_mul(y, c3), SAKURA_DW_INV6);
     dw c0 = dw_add_f(dw_mul(y, c2), 1.0f);
     dw c1 = dw_add_f(dw_mul(y, c3), 1.0f);
     for (; k > 0; --k) {
@@ -242,7 +245,9 @@ DW_HD EvalDW dw_eval(const PairDW &p, dw s, dw t, bool big)
 }
 
 // Carry G1..G3 and F' = r from s to s - ds (|ds| <= 2^-20 |s|): first-order
-// terms in double-word form, second-order terms in float.
+// terms in double-word form, second-order terms in float.  (The first-order
+// terms are small next to the values, which keeps the sums free of
+// cancellation.)
 DW_HD void dw_carry(EvalDW &e, const PairDW &p)
 {
     const dw d = e.ds;
@@ -250,10 +255,13 @@ DW_HD void dw_carry(EvalDW &e, const PairDW &p)
     const dw G0 = e.c0;
     const float Gm1 = fmul(-p.beta.h, e.G1.h);  // dG0/ds
     const float F3 = ffma(fmul(-p.eta0.h, p.beta.h), e.G1.h, fmul(p.zeta0.h, G0.h));  // dF''/ds
-    e.G3 = dw_add_f(dw_sub(e.G3, dw_mul(d, e.G2)), fmul(h2, e.G1.h));
-    e.G2 = dw_add_f(dw_sub(e.G2, dw_mul(d, e.G1)), fmul(h2, G0.h));
-    e.G1 = dw_add_f(dw_sub(e.G1, dw_mul(d, G0)), fmul(h2, Gm1));
-    e.Fp = dw_add_f(dw_sub(e.Fp, dw_mul(d, e.Fpp)), fmul(h2, F3));
+    // each first-order term is at most about 2^-18 of the value it corrects
+    // (|ds| <= 2^-20 |s|), so an unnormalised product suffices and the
+    // subtraction cannot cancel
+    e.G3 = dw_add_f(dw_add_nc(e.G3, dw_neg(dw_mul(d, e.G2))), fmul(h2, e.G1.h));
+    e.G2 = dw_add_f(dw_add_nc(e.G2, dw_neg(dw_mul(d, e.G1))), fmul(h2, G0.h));
+    e.G1 = dw_add_f(dw_add_nc(e.G1, dw_neg(dw_mul(d, G0))), fmul(h2, Gm1));
+    e.Fp = dw_add_f(dw_add_nc(e.Fp, dw_neg(dw_mul(d, e.Fpp))), fmul(h2, F3));
 }
 
 // Increments of the pair map (Eq. 26, increment form) divided by m, from
@@ -276,20 +284,19 @@ DW_HD void dw_increment_over_m(const PairDW &p, const EvalDW &e, dw qtau,
     out[2] = dw_add(dw_mul(A, p.z0), dw_mul(B, p.vz));
 }
 
-// Phase 1 with the class test: the float Kepler input from the leading
-// parts of the exact differences rr, vv (ptau32 = (float)(pre tau),
-// t32 = (float)tau), the range and period conditions, and the FP32 solve.
-DW_HD K32 dw_phase1(const dw rr[3], const dw vv[3], dw m, float ptau32, float t32, int guess)
+// Phase 1 with the class test from float relative coordinates dr, dv (after
+// the one-subscript drift), float m = m_i + m_j, ptau32 = (float)(pre tau),
+// t32 = (float)tau: the backward drift, the range and period conditions and
+// the FP32 solve.  Also the single-precision seed of the FP64 solver.
+DW_HD K32 k32_phase1(const float dr[3], const float dv[3], float m, float ptau32, float t32,
+                     int guess)
 {
-    float x[3], u[3];
-    for (int q = 0; q < 3; ++q) {
-        u[q] = vv[q].h;
-        x[q] = ffma(-ptau32, u[q], rr[q].h);
-    }
+    float x[3];
+    for (int q = 0; q < 3; ++q) x[q] = ffma(-ptau32, dv[q], dr[q]);
     const float r2 = ffma(x[0], x[0], ffma(x[1], x[1], fmul(x[2], x[2])));
-    const float v2 = ffma(u[0], u[0], ffma(u[1], u[1], fmul(u[2], u[2])));
-    const float eta = ffma(x[0], u[0], ffma(x[1], u[1], fmul(x[2], u[2])));
-    const bool range = r2 > 1e-30f && r2 < 1e30f && v2 < 1e30f && m.h > 1e-30f && m.h < 1e30f;
+    const float v2 = ffma(dv[0], dv[0], ffma(dv[1], dv[1], fmul(dv[2], dv[2])));
+    const float eta = ffma(x[0], dv[0], ffma(x[1], dv[1], fmul(x[2], dv[2])));
+    const bool range = r2 > 1e-30f && r2 < 1e30f && v2 < 1e30f && m > 1e-30f && m < 1e30f;
     K32 o;
     o.ok = false;
     o.iters = 0;
@@ -299,16 +306,25 @@ DW_HD K32 dw_phase1(const dw rr[3], const dw vv[3], dw m, float ptau32, float t3
     if (!range) return o;
     const float ir0 = rsqrt_approx(r2);
     const float r0 = fmul(r2, ir0);
-    const float beta = ffma(fmul(2.0f, m.h), ir0, -v2);
-    const float zeta = ffma(-beta, r0, m.h);
+    const float beta = ffma(fmul(2.0f, m), ir0, -v2);
+    const float zeta = ffma(-beta, r0, m);
     // a bound orbit whose step exceeds 0.9 of its period needs t reduced
     // modulo the period: FP64 solver
     if (beta > 0.0f) {
         const float b3 = fmul(fmul(beta, beta), beta);
-        const float tm = fmul(6.2831853f * 0.9f, m.h);
+        const float tm = fmul(6.2831853f * 0.9f, m);
         if (fmul(fmul(t32, t32), b3) >= fmul(tm, tm)) return o;
     }
     return k32_solve(r0, ir0, eta, beta, zeta, t32, guess);
+}
+
+// Phase 1 for the double-word form: the leading floats of the exact
+// double-word differences rr, vv and of m.
+DW_HD K32 dw_phase1(const dw rr[3], const dw vv[3], dw m, float ptau32, float t32, int guess)
+{
+    const float dr[3] = {rr[0].h, rr[1].h, rr[2].h};
+    const float dv[3] = {vv[0].h, vv[1].h, vv[2].h};
+    return k32_phase1(dr, dv, m.h, ptau32, t32, guess);
 }
 
 // Phase 2 for an admitted pair: setup, evaluations from s32, Taylor carry

@@ -212,6 +212,7 @@ struct PairSolve {
     double G1, G2, G3, Fp, ir;      // at the accepted s (ir = 1 / Fp)
     int iters;
     bool done;
+    bool carried;                   // finished by a Taylor carry to the root
     unsigned status;
 };
 
@@ -228,6 +229,7 @@ __device__ __forceinline__ void pair_setup(PairSolve &p, double tau, double m, d
     const double ptau = pre * tau;
     p.status = 0;
     p.iters = 0;
+    p.carried = false;
     p.m = m;
     p.vx = vx;
     p.vy = vy;
@@ -283,7 +285,11 @@ __device__ __forceinline__ void pair_setup(PairSolve &p, double tau, double m, d
 
 // One Laguerre iteration of a lane that is not done, at x = beta s^2; nt is
 // warp-uniform.  Returns true when the new iterate would leave the bracket
-// (the caller then applies pair_safeguard in a warp-uniform branch).
+// (the caller then applies pair_safeguard in a warp-uniform branch).  CARRY:
+// finish with a Taylor carry when the step is small (used where the initial
+// guess is already close for every lane, so that whole warps finish after
+// one evaluation).
+template <bool CARRY>
 __device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, int nt,
                                              const KeplerParams &kp)
 {
@@ -330,7 +336,27 @@ __device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, int nt,
     const float cf = __fdividef(0.8f * u, 1.0f + r);
     const float k = fabsf(u) < 0.5f ? __fdividef(cf, 1.0f - cf)
                                     : __fdividef(5.0f, fmaf(4.0f, r, 1.0f)) - 1.0f;
-    const double sn = s - fma(q, (double)k, q);
+    const double step = fma(q, (double)k, q);
+    const double sn = s - step;
+    // a step below 2^-20 of the scale: the cubically convergent Laguerre step
+    // has reached the root to about 2^-60, so take it and carry G1..G3 and
+    // F' = r there by their Taylor series (dG_k/ds = G_{k-1}, G_0 = c0,
+    // dG_0/ds = -beta G1; third-order terms below 2^-60) instead of
+    // evaluating at the new point
+    const long long sc20 = sc > (20LL << 52) ? sc - (20LL << 52) : 0;
+    if (CARRY && magbits(step) <= sc20) {
+        const double h2 = 0.5 * step * step;
+        const double F3 = fma(-p.eta0 * p.beta, G1, p.zeta0 * c.c0);  // dF''/ds
+        p.G3 = fma(h2, G1, fma(-step, G2, G3));
+        p.G2 = fma(h2, c.c0, fma(-step, G1, G2));
+        p.G1 = fma(h2, -p.beta * G1, fma(-step, c.c0, G1));
+        p.Fp = fma(h2, F3, fma(-step, Fpp, Fp));
+        p.ir = rcp_nr(p.Fp);
+        p.s = sn;
+        p.done = true;
+        p.carried = true;
+        return false;
+    }
     const long long ks = okey(sn);
     if (ks > okey(p.lo) && ks < okey(p.hi)) {
         p.s = sn;

@@ -128,7 +128,7 @@ extern "C" int sakura_step_noalloc(double *state, const double *masses, int64_t 
     }
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
-    sakura::launch_prep_step(state, masses, X, n, drift, d->status, s);
+    sakura::launch_prep_step(state, masses, X, nullptr, n, drift, d->status, s);
     sakura::StepArgs a;
     a.X = X;
     a.partial = partial;

@@ -12,6 +12,7 @@ namespace sakura {
 // call this.  tau, post: this lane's step and post-drift fraction.  Writes
 // the increments divided by m_ij to d (only meaningful when valid), returns
 // the lane's evaluation count and whether it needed bisection.
+template <bool CARRY = false>
 __device__ __forceinline__ void fp64_solve_warp(PairSolve &p, bool valid, double tau,
                                                 double post, const KeplerParams &kp,
                                                 double d[6], int &iters, int &fb)
@@ -22,7 +23,7 @@ __device__ __forceinline__ void fp64_solve_warp(PairSolve &p, bool valid, double
         const unsigned hx = p.done ? 0u : abs_hiword(x);
         const int nt = stumpff_terms(__reduce_max_sync(0xffffffffu, hx));
         bool oob = false;
-        if (!p.done) oob = pair_iterate(p, x, nt, kp);
+        if (!p.done) oob = pair_iterate<CARRY>(p, x, nt, kp);
         if (__any_sync(0xffffffffu, oob)) {
             if (oob) pair_safeguard(p);
         }

@@ -185,10 +185,11 @@ int step_device_sym(double *state, const double *masses, int64_t n, double dt, i
 {
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
     const bool learned = !df64 && g.cfg.guess == SAKURA_GUESS_LEARNED;
+    const bool seed = !df64 && g.cfg.guess == SAKURA_GUESS_FP32;
     const int64_t nb = (n + 31) / 32;
     const int64_t tiles = nb * (nb + 1) / 2;
     const int bps = df64 ? sakura::pair_step_df64_blocks_per_sm(stats)
-                         : sakura::pair_step_sym_blocks_per_sm(stats, learned);
+                         : sakura::pair_step_sym_blocks_per_sm(stats, learned, seed);
     // contiguous tile-step ranges for W <= T warps (step_common.cuh)
     const int64_t T = tiles * 32;
     int64_t blocks = g.cfg.grid_blocks > 0 ? g.cfg.grid_blocks : (int64_t)g.sm_count * bps;
@@ -197,31 +198,36 @@ int step_device_sym(double *state, const double *masses, int64_t n, double dt, i
     const int Smax = (int)((32 * W + T - 1) / T + 1);
     const int64_t nslots = nb * Smax;
     // scratch: X[7][n] doubles, tile partials [nslots][6][n] (doubles, or
-    // double-words of two floats), then (df64) X3[20][n] floats
-    int rc = grow(g.partial, (size_t)(7 * n + nslots * 6 * n + (df64 ? 10 * n : 0)) *
+    // double-words of two floats), then (df64) X3[20][n] or (seed) X32[10][n]
+    // floats
+    int rc = grow(g.partial, (size_t)(7 * n + nslots * 6 * n + (df64 ? 10 * n : 5 * n)) *
                                  sizeof(double));
     if (rc) return rc;
     double *X = (double *)g.partial.ptr;
     double *partial = X + 7 * n;
     float *X3 = (float *)(partial + nslots * 6 * n);
+    float *X32 = seed ? X3 : nullptr;
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
     if (df64)
         sakura::launch_prep_df64(state, masses, X, X3, n, drift, g.d_status, g.stream);
     else
-        sakura::launch_prep_step(state, masses, X, n, drift, g.d_status, g.stream);
+        sakura::launch_prep_step(state, masses, X, X32, n, drift, g.d_status, g.stream);
     sakura::StepArgs a;
     std::memset(&a, 0, sizeof(a));
     a.X = X;
+    a.X32 = X32;
     a.partial = partial;
     a.n = n;
     a.tau = dt;
     a.pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
     a.post = 1.0 - a.pre;
+    a.ptau32 = (float)(a.pre * dt);
+    a.t32 = (float)dt;
     a.tol = g.cfg.kepler_tol * DBL_EPSILON;
     a.max_iter = g.cfg.kepler_max_iter;
     a.bisection = g.cfg.kepler_bisection;
-    a.guess = g.cfg.guess == SAKURA_GUESS_TAYLOR ? 2 : 0;
+    a.guess = (g.cfg.guess == SAKURA_GUESS_TAYLOR || g.cfg.guess == SAKURA_GUESS_FP32) ? 2 : 0;
     a.mlp = learned ? (const sakura::MlpWeights *)g.mlp.ptr : nullptr;
     a.status = g.d_status;
     a.stats = g.d_stats;
@@ -292,7 +298,7 @@ int step_device(double *state, const double *masses, int64_t n, double dt, int o
     if (mixed)
         sakura::launch_prep_mixed(state, masses, X, X32, n, drift, g.d_status, g.stream);
     else
-        sakura::launch_prep_step(state, masses, X, n, drift, g.d_status, g.stream);
+        sakura::launch_prep_step(state, masses, X, nullptr, n, drift, g.d_status, g.stream);
     sakura::StepArgs a;
     a.X = X;
     a.partial = partial;
@@ -300,10 +306,12 @@ int step_device(double *state, const double *masses, int64_t n, double dt, int o
     a.tau = dt;
     a.pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
     a.post = 1.0 - a.pre;
+    a.ptau32 = (float)(a.pre * dt);
+    a.t32 = (float)dt;
     a.tol = g.cfg.kepler_tol * DBL_EPSILON;
     a.max_iter = g.cfg.kepler_max_iter;
     a.bisection = g.cfg.kepler_bisection;
-    a.guess = g.cfg.guess == SAKURA_GUESS_TAYLOR ? 2 : 0;
+    a.guess = (g.cfg.guess == SAKURA_GUESS_TAYLOR || g.cfg.guess == SAKURA_GUESS_FP32) ? 2 : 0;
     a.mlp = (g.cfg.guess == SAKURA_GUESS_LEARNED && !mixed)
                 ? (const sakura::MlpWeights *)g.mlp.ptr
                 : nullptr;
@@ -436,7 +444,7 @@ int sakura_init(const sakura_config *cfg)
     if (c.pair_mode != SAKURA_PAIRS_ORDERED && c.pair_mode != SAKURA_PAIRS_SYMMETRIC)
         return SAKURA_E_ARG;
     if (c.guess != SAKURA_GUESS_STANDARD && c.guess != SAKURA_GUESS_LEARNED &&
-        c.guess != SAKURA_GUESS_TAYLOR)
+        c.guess != SAKURA_GUESS_TAYLOR && c.guess != SAKURA_GUESS_FP32)
         return SAKURA_E_ARG;
     if (cudaSetDevice(c.device) != cudaSuccess) {
         cudaGetLastError();
@@ -623,7 +631,7 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
     a.tol = g.cfg.kepler_tol * DBL_EPSILON;
     a.max_iter = g.cfg.kepler_max_iter;
     a.bisection = g.cfg.kepler_bisection;
-    a.guess = g.cfg.guess == SAKURA_GUESS_TAYLOR ? 2 : 0;
+    a.guess = (g.cfg.guess == SAKURA_GUESS_TAYLOR || g.cfg.guess == SAKURA_GUESS_FP32) ? 2 : 0;
     a.mlp = g.cfg.guess == SAKURA_GUESS_LEARNED ? (const sakura::MlpWeights *)g.mlp.ptr : nullptr;
     a.status = g.d_status;
     a.stats = g.d_stats;
@@ -770,7 +778,7 @@ int sakura_sample_pairs(const double *state, const double *masses, int64_t n, do
     double *X = (double *)g.partial.ptr;
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
-    sakura::launch_prep_step(state, masses, X, n, drift, g.d_status, g.stream);
+    sakura::launch_prep_step(state, masses, X, nullptr, n, drift, g.d_status, g.stream);
     sakura::launch_sample_pairs(X, n, dt, pre, pair_ids, count, features, targets, iters,
                                 g.cfg.kepler_tol * DBL_EPSILON, g.d_status, g.stream);
     if (launch_error()) return SAKURA_E_CUDA;
@@ -855,6 +863,7 @@ int sakura_get_stats(sakura_stats *out, int reset)
     out->warp_slots = (int64_t)h[sakura::kStatSlots];
     out->fallbacks = (int64_t)h[sakura::kStatFallbacks];
     out->fp32_pairs = (int64_t)h[sakura::kStatFp32Pairs];
+    out->carries = (int64_t)h[sakura::kStatCarries];
     collect_timers();
     out->timed_launches = g.timed_launches;
     out->pair_kernel_ms = g.timed_ms;

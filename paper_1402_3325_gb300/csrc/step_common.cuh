@@ -18,6 +18,7 @@ constexpr int kStatMaxIters = 1;
 constexpr int kStatSlots = 2;
 constexpr int kStatFallbacks = 3;
 constexpr int kStatFp32Pairs = 4;
+constexpr int kStatCarries = 5;
 constexpr int kStatCount = 8;
 
 struct StepArgs {
@@ -31,6 +32,9 @@ struct StepArgs {
     int bisection;
     int guess;            // 0 standard, 2 second-order analytic
     const MlpWeights *mlp; // learned guess network (device), or nullptr
+    const float *X32;      // [10][n] float copy for the single-precision seed
+                           // (hi xyz, lo xyz, v xyz, m), or nullptr
+    float ptau32, t32;     // (float)(pre tau), (float)tau for the seed
     unsigned *status;
     unsigned long long *stats;
 };
@@ -113,7 +117,7 @@ void launch_mlp_pack(const float *blob, MlpWeights *W, cudaStream_t s);
 void launch_mlp_eval(const MlpWeights *W, const float *feat, int64_t count, float *out,
                      cudaStream_t s);
 // symmetric (Newton's third law) pair kernel: items = tiles * S
-int pair_step_sym_blocks_per_sm(bool stats, bool learned);
+int pair_step_sym_blocks_per_sm(bool stats, bool learned, bool seed = false);
 void launch_pair_step_sym(const StepArgs &a, int Smax, int64_t T, int blocks, bool stats,
                           cudaStream_t s);
 void launch_apply_sym(double *state, const double *X, const double *partial, int64_t n, int Smax,
@@ -121,7 +125,8 @@ void launch_apply_sym(double *state, const double *X, const double *partial, int
 
 // number of partial-sum slots per row for W warps
 int pair_step_slots(int64_t n, int64_t W);
-void launch_prep_step(const double *state, const double *mass, double *X, int64_t n,
+// X32 (optional): float copy for the single-precision seed, [10][n]
+void launch_prep_step(const double *state, const double *mass, double *X, float *X32, int64_t n,
                       double drift, unsigned *status, cudaStream_t s);
 // W = 0: no pair sums (n = 1)
 void launch_apply_step(double *state, const double *X, const double *partial, int64_t n,

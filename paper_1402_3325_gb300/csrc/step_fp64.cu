@@ -36,8 +36,11 @@ __device__ __host__ __forceinline__ int64_t batch_owner(int64_t b, int64_t B, in
 }
 
 // X[7][n]: drifted positions, velocities, masses.
-__global__ void prep_step_kernel(const double *state, const double *mass, double *X, int64_t n,
-                                 double drift, unsigned *status)
+// X32 (optional): float copy of the drifted state for the single-precision
+// seed, positions split x = hi + lo (hi = fl32(x), lo = fl32(x - hi)) so that
+// float differences keep the accuracy of the separation
+__global__ void prep_step_kernel(const double *state, const double *mass, double *X, float *X32,
+                                 int64_t n, double drift, unsigned *status)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -46,10 +49,18 @@ __global__ void prep_step_kernel(const double *state, const double *mass, double
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const double v = state[(3 + q) * n + i];
-        X[q * n + i] = fma(v, drift, state[q * n + i]);
+        const double x = fma(v, drift, state[q * n + i]);
+        X[q * n + i] = x;
         X[(3 + q) * n + i] = v;
+        if (X32) {
+            const float hi = __double2float_rn(x);
+            X32[q * n + i] = hi;
+            X32[(3 + q) * n + i] = __double2float_rn(x - (double)hi);
+            X32[(6 + q) * n + i] = __double2float_rn(v);
+        }
     }
     X[6 * n + i] = m;
+    if (X32) X32[9 * n + i] = __double2float_rn(m);
 }
 
 template <int WARPS, bool STATS, bool LEARNED>
@@ -190,12 +201,12 @@ int pair_step_slots(int64_t n, int64_t W)
     return (int)((W + n - 1) / n + 1);
 }
 
-void launch_prep_step(const double *state, const double *mass, double *X, int64_t n,
+void launch_prep_step(const double *state, const double *mass, double *X, float *X32, int64_t n,
                       double drift, unsigned *status, cudaStream_t s)
 {
     const int threads = 64;  // small blocks spread a small n over many SMs
-    prep_step_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(state, mass, X,
-                                                                                 n, drift, status);
+    prep_step_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
+        state, mass, X, X32, n, drift, status);
 }
 
 namespace {

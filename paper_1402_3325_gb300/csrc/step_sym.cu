@@ -23,6 +23,7 @@
 // fixed order (deterministic, no atomics).
 #include <cuda_runtime.h>
 
+#include "kepler_df64.cuh"
 #include "kepler_fp64.cuh"
 #include "mlp_infer.cuh"
 #include "pair_batch_fp64.cuh"
@@ -30,8 +31,8 @@
 
 namespace sakura {
 
-template <bool STATS, bool LEARNED>
-__global__ void __launch_bounds__(128)
+template <bool STATS, bool LEARNED, bool SEED>
+__global__ void __launch_bounds__(128, LEARNED ? 2 : 4)
     pair_step_sym_kernel(StepArgs a, int Smax, int64_t T)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -46,8 +47,9 @@ __global__ void __launch_bounds__(128)
     const double *X = a.X;
     const KeplerParams kp{a.tol, a.max_iter, a.bisection};
     unsigned status = 0;
-    long long it_sum = 0, slots = 0, fallbacks = 0;
+    long long it_sum = 0, slots = 0, fallbacks = 0, carries = 0;
     int it_max = 0;
+    const float *X32 = a.X32;
 
     const int64_t p1 = (w + 1) * T / W;
     for (int64_t pos = w * T / W; pos < p1;) {
@@ -71,6 +73,16 @@ __global__ void __launch_bounds__(128)
             vzi = X[5 * n + i];
             mi = X[6 * n + i];
         }
+        float hi_i[3] = {0, 0, 0}, lo_i[3] = {0, 0, 0}, v_i[3] = {0, 0, 0}, m32i = 0.0f;
+        if (SEED && irow) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                hi_i[q] = X32[q * n + i];
+                lo_i[q] = X32[(3 + q) * n + i];
+                v_i[q] = X32[(6 + q) * n + i];
+            }
+            m32i = X32[9 * n + i];
+        }
         double racc[6] = {0, 0, 0, 0, 0, 0}, cacc[6] = {0, 0, 0, 0, 0, 0};
         for (int k = k0; k < k1; ++k) {
             const int c = (lane + k) & 31;
@@ -83,6 +95,21 @@ __global__ void __launch_bounds__(128)
                 pair_setup(p, a.tau, mi + mj, xi - X[j], yi - X[n + j], zi - X[2 * n + j],
                            vxi - X[3 * n + j], vyi - X[4 * n + j], vzi - X[5 * n + j], a.pre,
                            LEARNED ? 2 : a.guess);
+                if (SEED) {
+                    // single-precision seed: the root of the FP32 solve of the
+                    // same pair (unless t was reduced modulo the period)
+                    float dr[3], dv[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        dr[q] = __fadd_rn(__fsub_rn(hi_i[q], X32[q * n + j]),
+                                          __fsub_rn(lo_i[q], X32[(3 + q) * n + j]));
+                        dv[q] = __fsub_rn(v_i[q], X32[(6 + q) * n + j]);
+                    }
+                    const K32 o = k32_phase1(dr, dv, m32i + X32[9 * n + j], a.ptau32, a.t32, 2);
+                    if (o.ok && __double_as_longlong(p.t) == __double_as_longlong(a.tau) &&
+                        !p.done)
+                        p.s = (double)o.s;
+                }
             } else {
                 p.done = true;
                 p.beta = p.s = 0.0;
@@ -92,7 +119,7 @@ __global__ void __launch_bounds__(128)
             if (LEARNED) learned_guess_warp(p, valid, *mlpW, mlpStage + wib * 32 * 16);
             double d[6];
             int iters = 0, fb = 0;
-            fp64_solve_warp(p, valid, a.tau, a.post, kp, d, iters, fb);
+            fp64_solve_warp<SEED>(p, valid, a.tau, a.post, kp, d, iters, fb);
             if (valid) {
 #pragma unroll
                 for (int q = 0; q < 6; ++q) {
@@ -102,6 +129,7 @@ __global__ void __launch_bounds__(128)
                 status |= p.status;
             }
             if (STATS) {
+                carries += (valid && p.carried) ? 1 : 0;
                 it_sum += iters;
                 fallbacks += fb;
                 it_max = max(it_max, iters);
@@ -131,18 +159,20 @@ __global__ void __launch_bounds__(128)
     status = __reduce_or_sync(0xffffffffu, status);
     if (lane == 0 && status) atomicOr(a.status, status);
     if (STATS) {
-        long long s1 = it_sum, s2 = slots, s3 = fallbacks;
+        long long s1 = it_sum, s2 = slots, s3 = fallbacks, s4 = carries;
         int mx = it_max;
         for (int o = 16; o > 0; o >>= 1) {
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
             s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+            s4 += __shfl_xor_sync(0xffffffffu, s4, o);
             mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         }
         if (lane == 0) {
             atomicAdd(&a.stats[kStatIters], (unsigned long long)s1);
             atomicAdd(&a.stats[kStatSlots], (unsigned long long)s2);
             atomicAdd(&a.stats[kStatFallbacks], (unsigned long long)s3);
+            atomicAdd(&a.stats[kStatCarries], (unsigned long long)s4);
             atomicMax(&a.stats[kStatMaxIters], (unsigned long long)mx);
         }
     }
@@ -202,23 +232,26 @@ __global__ void __launch_bounds__(32 * kApplyWarps)
 
 namespace {
 
-const void *sym_kernel(bool stats, bool learned)
+const void *sym_kernel(bool stats, bool learned, bool seed)
 {
     if (learned)
-        return stats ? (const void *)pair_step_sym_kernel<true, true>
-                     : (const void *)pair_step_sym_kernel<false, true>;
-    return stats ? (const void *)pair_step_sym_kernel<true, false>
-                 : (const void *)pair_step_sym_kernel<false, false>;
+        return stats ? (const void *)pair_step_sym_kernel<true, true, false>
+                     : (const void *)pair_step_sym_kernel<false, true, false>;
+    if (seed)
+        return stats ? (const void *)pair_step_sym_kernel<true, false, true>
+                     : (const void *)pair_step_sym_kernel<false, false, true>;
+    return stats ? (const void *)pair_step_sym_kernel<true, false, false>
+                 : (const void *)pair_step_sym_kernel<false, false, false>;
 }
 
 size_t sym_smem(bool learned) { return learned ? sizeof(MlpWeights) + 4 * 32 * 16 * 2 : 0; }
 
 }  // namespace
 
-int pair_step_sym_blocks_per_sm(bool stats, bool learned)
+int pair_step_sym_blocks_per_sm(bool stats, bool learned, bool seed)
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sym_kernel(stats, learned), 128,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sym_kernel(stats, learned, seed), 128,
                                                       sym_smem(learned)) != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -230,11 +263,12 @@ void launch_pair_step_sym(const StepArgs &a, int Smax, int64_t T, int blocks, bo
                           cudaStream_t s)
 {
     const bool learned = a.mlp != nullptr;
+    const bool seed = !learned && a.X32 != nullptr;
     int Sv = Smax;
     int64_t it = T;
     void *args[] = {(void *)&a, (void *)&Sv, (void *)&it};
-    cudaLaunchKernel(sym_kernel(stats, learned), dim3(blocks), dim3(128), args, sym_smem(learned),
-                     s);
+    cudaLaunchKernel(sym_kernel(stats, learned, seed), dim3(blocks), dim3(128), args,
+                     sym_smem(learned), s);
 }
 
 void launch_apply_sym(double *state, const double *X, const double *partial, int64_t n, int Smax,

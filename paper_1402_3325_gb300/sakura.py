@@ -39,6 +39,7 @@ MIXED_RULE_HYP = 1
 GUESS_STANDARD = 0
 GUESS_LEARNED = 1
 GUESS_TAYLOR = 2
+GUESS_FP32 = 3
 FLAG_SYNC_CHECK = 1
 FLAG_STATS = 2
 FLAG_TIMING = 4
@@ -71,10 +72,11 @@ class Config(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in
                 ("steps", "pairs", "iters", "max_iters", "warp_slots", "fp32_pairs",
-                 "fallbacks", "solves", "timed_launches")] + [("pair_kernel_ms", ctypes.c_double)]
+                 "fallbacks", "solves", "timed_launches")] + [
+                     ("pair_kernel_ms", ctypes.c_double), ("carries", ctypes.c_int64)]
 
     def as_dict(self):
-        d = {k: int(getattr(self, k)) for k, _ in self._fields_[:-1]}
+        d = {k: int(getattr(self, k)) for k, t in self._fields_ if t is ctypes.c_int64}
         d["pair_kernel_ms"] = float(self.pair_kernel_ms)
         return d
 

@@ -16,7 +16,8 @@ using sakura::sakura_dw_mufu;
 
 extern "C" {
 
-// op: 0 add, 1 sub, 2 add_f, 3 mul, 4 mul_f, 5 sqr, 6 rcp, 7 rsqrt
+// op: 0 add, 1 sub, 2 add_f, 3 mul, 4 mul_f, 5 sqr, 6 rcp, 7 rsqrt,
+// 8 add without cancellation
 void dw_batch(int op, long n, const float *xh, const float *xl, const float *yh,
               const float *yl, float *zh, float *zl)
 {
@@ -32,6 +33,7 @@ void dw_batch(int op, long n, const float *xh, const float *xl, const float *yh,
             case 5: z = sakura::dw_sqr(x); break;
             case 6: z = sakura::dw_rcp(x); break;
             case 7: z = sakura::dw_rsqrt(x); break;
+            case 8: z = sakura::dw_add_nc(x, y); break;
         }
         zh[k] = z.h;
         zl[k] = z.l;

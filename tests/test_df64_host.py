@@ -2,6 +2,7 @@
 (csrc/df64.cuh), built as host C++: every result is compared with the exact
 value of the operation on the same float inputs (Python fractions), against
 the published relative error bounds (u = 2^-24): add <= 3u^2, add_f <= 2u^2,
+add without cancellation (like signs) <= 3u^2,
 mul <= 5u^2, mul_f <= 2u^2, and <= 4u^2 for the Newton-corrected reciprocal
 and reciprocal square root (exact value rounded to 60 bits).  The difference
 of two doubles through their exact three-float form must be within 4u^2 of
@@ -83,6 +84,20 @@ def test_double_word_arithmetic_error_bounds(lib, op, bound):
         # normalised: |l| <= ulp(h) / 2
         assert abs(float(zl[k])) <= abs(float(zh[k])) * 2.0 ** -24 * 1.0000001
     assert worst <= bound * U2, worst / U2
+
+
+def test_double_word_sum_without_cancellation(lib):
+    # like-signed operands of any relative size
+    rng = np.random.default_rng(8)
+    n = 4000
+    xh, xl = _rand_dw(rng, n, positive=True)
+    yh, yl = _rand_dw(rng, n, -40, 40, positive=True)
+    sign = rng.choice([-1.0, 1.0], n).astype(np.float32)
+    xh, xl, yh, yl = xh * sign, xl * sign, yh * sign, yl * sign
+    zh, zl = _run(lib, 8, xh, xl, yh, yl)
+    worst = max(_rel(_val(zh[k], zl[k]), _val(xh[k], xl[k]) + _val(yh[k], yl[k]))
+                for k in range(n))
+    assert worst <= 3 * U2, worst / U2
 
 
 @pytest.mark.parametrize("op", [6, 7])

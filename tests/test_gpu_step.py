@@ -270,7 +270,7 @@ def _fast_swarm(n=64, seed=0):
 
 
 @pytest.mark.parametrize("pairs", [sk.PAIRS_ORDERED, sk.PAIRS_SYMMETRIC])
-@pytest.mark.parametrize("guess", [sk.GUESS_STANDARD, sk.GUESS_TAYLOR])
+@pytest.mark.parametrize("guess", [sk.GUESS_STANDARD, sk.GUESS_TAYLOR, sk.GUESS_FP32])
 def test_fast_hyperbolic_pairs_with_overflowing_guess(guess, pairs):
     s = _fast_swarm()
     with configured(guess=guess, pair_mode=pairs):
@@ -283,10 +283,11 @@ def test_fast_hyperbolic_pairs_with_overflowing_guess(guess, pairs):
 
 # --- symmetric mode: every unordered pair solved once (Newton's third law) ---
 
+@pytest.mark.parametrize("guess", [sk.GUESS_TAYLOR, sk.GUESS_FP32])
 @pytest.mark.parametrize("order", [2, 1, -1])
 @pytest.mark.parametrize("name,s", SMALL, ids=[n for n, _ in SMALL])
-def test_symmetric_step_matches_oracle(name, s, order):
-    with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=sk.GUESS_TAYLOR):
+def test_symmetric_step_matches_oracle(name, s, order, guess):
+    with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=guess):
         r, v = gpu_step(s, s.dt, order)
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, order, nthreads=NCPU)
     er, ev = rel_err(r, v, rr, vr)
@@ -303,11 +304,53 @@ def test_symmetric_plummer_1024_and_grid_shapes(blocks):
     assert er <= TOL and ev <= TOL, (er, ev)
 
 
-def test_symmetric_full_size_binaries_sampled():
+@pytest.mark.parametrize("guess", [sk.GUESS_TAYLOR, sk.GUESS_FP32])
+def test_symmetric_full_size_binaries_sampled(guess):
     s = ics.plummer_binaries(16384, seed=0)
-    with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=sk.GUESS_TAYLOR):
+    with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=guess):
         er, ev = _full_size_sample(s, seed=2)
     assert er <= TOL and ev <= TOL, (er, ev)
+
+
+def test_symmetric_fp32_guess_full_size_bh_cluster_sampled():
+    with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=sk.GUESS_FP32):
+        er, ev = _full_size_sample(ics.bh_cluster(16384, seed=1), seed=4)
+    assert er <= TOL and ev <= TOL, (er, ev)
+
+
+@pytest.mark.parametrize("blocks", [0, 1, 300])
+def test_fp32_guess_plummer_1024_one_evaluation(blocks):
+    # the single-precision root is within ~1e-7 of the FP64 root, so one
+    # FP64 evaluation and the Taylor carry finish every pair
+    s = ics.plummer(1024, seed=0)
+    with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=sk.GUESS_FP32, grid_blocks=blocks):
+        sk.get_stats(reset=True)
+        r, v = gpu_step(s, s.dt, 2)
+        st = sk.get_stats(reset=True)
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
+    er, ev = rel_err(r, v, rr, vr)
+    assert er <= TOL and ev <= TOL, (er, ev)
+    assert st["iters"] == st["solves"] and st["carries"] == st["solves"]
+
+
+def test_fp32_guess_falls_back_for_reduced_periods():
+    # tight binaries whose period is below the step: t is reduced modulo the
+    # period in FP64, so those pairs use the second-order guess
+    s = ics.plummer_binaries(2048, seed=5)
+    s = ics.System(s.m, s.r, s.v, 2.0 ** -6, "binaries-long-step")
+    with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=sk.GUESS_FP32):
+        sk.get_stats(reset=True)
+        r, v = gpu_step(s, s.dt, 2)
+        st = sk.get_stats(reset=True)
+    assert st["carries"] < st["solves"]
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([[0, 1, 2, 3], rng.choice(s.n, 40, replace=False)]))
+    rc, rs, vs = oracle.step_sample(s.m, s.r, s.v, s.dt, idx, 2, nthreads=NCPU)
+    R = np.sqrt((r ** 2).sum(1).mean())
+    V = np.sqrt((v ** 2).sum(1).mean())
+    er = np.linalg.norm(r[idx] - rs, axis=1) / np.maximum(np.linalg.norm(rs, axis=1), R)
+    ev = np.linalg.norm(v[idx] - vs, axis=1) / np.maximum(np.linalg.norm(vs, axis=1), V)
+    assert er.max() <= TOL and ev.max() <= TOL, (er.max(), ev.max())
 
 
 def test_symmetric_counts_solves():
