@@ -169,7 +169,8 @@ class ClockSampler:
 def _kernel_sources_hash(kernel: str = "pair_step_sym") -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1402_3325_gb300", "csrc")
-    files = {"pair_step_sym": ["step_sym.cu"], "pair_step_fp64": ["step_fp64.cu"],
+    files = {"pair_step_sym": ["df64.cuh", "kepler_df64.cuh", "step_sym.cu"],
+             "pair_step_fp64": ["step_fp64.cu"],
              "pair_step_sym_df64": ["df64.cuh", "kepler_df64.cuh", "step_df64.cu"]}.get(
                  kernel, ["step_fp64.cu"])
     for f in ["kepler_fp64.cuh", "pair_batch_fp64.cuh"] + files:
@@ -339,6 +340,7 @@ def _variant_df64(args, sk, s, device, stream, flush, guess):
     mass = torch.tensor(s.m, device=device)
     state = torch.tensor(s.soa(), device=device)
     sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_STATS, guess=guess, **opts)
+    sk.get_stats(reset=True)
     for _ in range(args.warmup):
         sk.step(state, mass, s.dt, 2)
     sk.check()
