@@ -349,6 +349,7 @@ def _variant_df64(args, sk, s, device, stream, flush, guess):
     share = st["fp32_pairs"] / max(1, st["solves"])
     sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_TIMING, guess=guess, **opts)
     state.copy_(torch.tensor(s.soa(), device=device))
+    E0 = sk.energy(state, mass)
     sk.get_stats(reset=True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -362,6 +363,7 @@ def _variant_df64(args, sk, s, device, stream, flush, guess):
     sk.check()
     ms_total = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     st = sk.get_stats(reset=True)
+    dE = abs(sk.energy(state, mass) / E0 - 1.0)
     pair_ms = st["pair_kernel_ms"] / max(1, st["timed_launches"])
     flops = DF64_FLOPS_PER_SOLVE.get(args.workload)
     solves = n * (n - 1) * spp
@@ -372,6 +374,7 @@ def _variant_df64(args, sk, s, device, stream, flush, guess):
             "dtype": "f32 double-word (pair solves) + f64 (drift, sums, fallback pairs)",
             "parity": "same 1e-12 per-step bound against the FP64 oracle as the FP64 form",
             "double_word_solve_share": share,
+            "energy_error": dE,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak if achieved else None,
                          "traffic": _profiled_traffic(args.workload, "pair_step_sym_df64"),
@@ -469,12 +472,14 @@ def main():
     sk.check()
     st = sk.get_stats(reset=True)
     kbar = st["iters"] / max(1, st["solves"])
+    st_iters_fp64 = float(st["iters"]) / max(1, args.warmup)
     carried = st.get("carries", 0) / max(1, st["solves"])
     solves_per_pair = st["solves"] / max(1, st["pairs"])
     fp32_share = st["fp32_pairs"] / max(1, st["pairs"])
     sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_TIMING, guess=guess,
             **form_opts)
     state.copy_(torch.tensor(s.soa(), device=device))
+    E0 = sk.energy(state, mass)
     sk.get_stats(reset=True)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -494,6 +499,7 @@ def main():
     sk.check()
     ms_total = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     st = sk.get_stats(reset=True)
+    energy_error = abs(sk.energy(state, mass) / E0 - 1.0)  # outside the timed region
     pair_ms = st["pair_kernel_ms"] / max(1, st["timed_launches"])
     if dist is not None:
         t = torch.tensor([ms_total], device=device, dtype=torch.float64)
@@ -540,6 +546,17 @@ def main():
         kname, pipe = "pair_step_sym_df64", "fp32"
         peak_source = ("152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; flops per solve counted"
                        " by running the double-word code on the host with an operation tally")
+    elif args.form == "mixed":
+        # FP64 flops per ordered pair: the FP64 accumulation (6 FMA) of an
+        # FP32-class pair, the full FP64 solve of the others (the FP32 solves
+        # run on the FP32 pipe and are not counted here)
+        k64 = st_iters_fp64 / max(1.0, solves_per_pair * n * (n - 1) * (1.0 - fp32_share))
+        flops_solve = (fp32_share * 12.0 + (1.0 - fp32_share) *
+                       (C_FIX + k64 * C_EVAL + max(0.0, k64 - 1.0) * C_STEP))
+        peak = FP64_PEAK_GFLOPS / 1e3
+        kname, pipe = "pair_step_mixed", "fp64 (FP32-class pairs: accumulation only)"
+        peak_source = ("152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz; flops per pair counted"
+                       " for the FP64 work only")
     else:
         flops_solve = (C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP +
                        carried * (C_STEP + C_CARRY) + (C_SYM if symmetric else 0))
@@ -569,6 +586,7 @@ def main():
                        "kepler_guess": args.guess,
                        "fp32_pair_share": fp32_share,
                        "pairs_solved_per_step": n * (n - 1),
+                       "energy_error_over_timed_steps": energy_error,
                        "l2": "256 MB buffer written between timed steps (state fits in L2)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "gpu_launches": 3 * args.steps,
