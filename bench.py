@@ -69,6 +69,9 @@ C_SYM = 12
 # Laguerre correction (C_STEP) and the carry of G1..G3 and F' with a new
 # 1/F' (29: h2 (2), dF''/ds (4), three G's and F' (17), reciprocal (6))
 C_CARRY = 29
+# FP32-class pair of the symmetric mixed form (see the roofline code below)
+C_MIX32_FIX = 46 + 34 + 156
+C_MIX32_ITER = 53
 
 # FP64 ALU peak of one GB300: 152 SMs x 2 FP64 FMA units x 2 flop x 2.07 GHz
 # (the unit count follows from the nominal 1.25 TFLOP/s at 2.07 GHz).
@@ -546,6 +549,23 @@ def main():
         kname, pipe = "pair_step_sym_df64", "fp32"
         peak_source = ("152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; flops per solve counted"
                        " by running the double-word code on the host with an operation tally")
+    elif args.form == "mixed" and args.pairs == "symmetric" and fp32_share >= 0.5:
+        # FP32 flops of an FP32-class unordered pair (hand count from
+        # csrc/kepler_fp32.cuh and csrc/step_mixed.cu, FMA = 2): class test
+        # 46, solve setup and epilogue 34, per Laguerre iteration 53 (the last
+        # one stops at the test, -11), double-word sums of m_j d and -m_i d
+        # 156; kbar = single-precision iterations per solve
+        flops_solve = fp32_share * (C_MIX32_FIX + kbar * C_MIX32_ITER - 11.0)
+        peak = FP32_PEAK_GFLOPS / 1e3
+        kname, pipe = "pair_step_sym_mixed", "fp32"
+        peak_source = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; flops counted by hand"
+    elif args.form == "mixed" and args.pairs == "symmetric":
+        # mostly FP64-class pairs (through the FP64 queue): their FP64 solves
+        flops_solve = (1.0 - fp32_share) * (C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP +
+                                            C_SYM)
+        peak = FP64_PEAK_GFLOPS / 1e3
+        kname, pipe = "pair_step_sym_mixed", "fp64"
+        peak_source = "152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"
     elif args.form == "mixed":
         # FP64 flops per ordered pair: the FP64 accumulation (6 FMA) of an
         # FP32-class pair, the full FP64 solve of the others (the FP32 solves
@@ -582,7 +602,7 @@ def main():
                       if args.form == "df64" else "f64"),
             "data": "synthetic",
             "config": {"workload": desc, "n": n, "dt": s.dt, "order": 2, "form": args.form,
-                       "pairs": args.pairs if args.form in ("fp64", "df64") else "ordered",
+                       "pairs": args.pairs,
                        "kepler_guess": args.guess,
                        "fp32_pair_share": fp32_share,
                        "pairs_solved_per_step": n * (n - 1),

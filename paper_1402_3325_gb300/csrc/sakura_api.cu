@@ -181,15 +181,16 @@ sakura::dw split_dw(double d)
 // Unordered pairs once (Newton's third law): systolic 32 x 32 tiles; df64:
 // the pair solves in double-word arithmetic (step_df64.cu).
 int step_device_sym(double *state, const double *masses, int64_t n, double dt, int order,
-                    bool df64)
+                    bool df64, bool mixed)
 {
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
-    const bool learned = !df64 && g.cfg.guess == SAKURA_GUESS_LEARNED;
-    const bool seed = !df64 && g.cfg.guess == SAKURA_GUESS_FP32;
+    const bool learned = !df64 && !mixed && g.cfg.guess == SAKURA_GUESS_LEARNED;
+    const bool seed = !df64 && !mixed && g.cfg.guess == SAKURA_GUESS_FP32;
     const int64_t nb = (n + 31) / 32;
     const int64_t tiles = nb * (nb + 1) / 2;
-    const int bps = df64 ? sakura::pair_step_df64_blocks_per_sm(stats)
-                         : sakura::pair_step_sym_blocks_per_sm(stats, learned, seed);
+    const int bps = df64    ? sakura::pair_step_df64_blocks_per_sm(stats)
+                    : mixed ? sakura::pair_step_sym_mixed_blocks_per_sm(stats)
+                            : sakura::pair_step_sym_blocks_per_sm(stats, learned, seed);
     // contiguous tile-step ranges for W <= T warps (step_common.cuh)
     const int64_t T = tiles * 32;
     int64_t blocks = g.cfg.grid_blocks > 0 ? g.cfg.grid_blocks : (int64_t)g.sm_count * bps;
@@ -206,17 +207,19 @@ int step_device_sym(double *state, const double *masses, int64_t n, double dt, i
     double *X = (double *)g.partial.ptr;
     double *partial = X + 7 * n;
     float *X3 = (float *)(partial + nslots * 6 * n);
-    float *X32 = seed ? X3 : nullptr;
+    float *X32 = (seed || mixed) ? X3 : nullptr;
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
     if (df64)
         sakura::launch_prep_df64(state, masses, X, X3, n, drift, g.d_status, g.stream);
+    else if (mixed)
+        sakura::launch_prep_mixed(state, masses, X, X32, n, drift, g.d_status, g.stream);
     else
         sakura::launch_prep_step(state, masses, X, X32, n, drift, g.d_status, g.stream);
     sakura::StepArgs a;
     std::memset(&a, 0, sizeof(a));
     a.X = X;
-    a.X32 = X32;
+    a.X32 = mixed ? nullptr : X32;
     a.partial = partial;
     a.n = n;
     a.tau = dt;
@@ -246,6 +249,17 @@ int step_device_sym(double *state, const double *masses, int64_t n, double dt, i
         da.t = split_dw(dt);
         da.qtau = split_dw(a.post * dt);
         sakura::launch_pair_step_df64(a, da, Smax, T, (int)blocks, stats, g.stream);
+    } else if (mixed) {
+        sakura::MixedArgs ma;
+        ma.X32 = X32;
+        ma.rule.ptau = (float)(a.pre * dt);
+        ma.rule.rmin2 = (float)(g.cfg.mixed_r_min * g.cfg.mixed_r_min);
+        ma.rule.emax2 = (float)(g.cfg.mixed_e_max * g.cfg.mixed_e_max);
+        ma.rule.ehyp2 = (float)(g.cfg.mixed_e_hyp * g.cfg.mixed_e_hyp);
+        ma.rule.rule = g.cfg.mixed_rule;
+        ma.tau32 = (float)dt;
+        ma.post32 = (float)a.post;
+        sakura::launch_pair_step_sym_mixed(a, ma, Smax, T, (int)blocks, stats, g.stream);
     } else {
         sakura::launch_pair_step_sym(a, Smax, T, (int)blocks, stats, g.stream);
     }
@@ -278,10 +292,10 @@ constexpr double kSymMaxBytes = 16.0 * 1024 * 1024 * 1024;
 
 int step_device(double *state, const double *masses, int64_t n, double dt, int order)
 {
-    if (g.cfg.pair_mode == SAKURA_PAIRS_SYMMETRIC && g.cfg.precision != SAKURA_PREC_MIXED &&
-        n > 1 && 8.0 * 6.0 * 8.0 * (double)((n + 31) / 32) * (double)n <= kSymMaxBytes)
-        return step_device_sym(state, masses, n, dt, order,
-                               g.cfg.precision == SAKURA_PREC_DF64);
+    if (g.cfg.pair_mode == SAKURA_PAIRS_SYMMETRIC && n > 1 &&
+        8.0 * 6.0 * 8.0 * (double)((n + 31) / 32) * (double)n <= kSymMaxBytes)
+        return step_device_sym(state, masses, n, dt, order, g.cfg.precision == SAKURA_PREC_DF64,
+                               g.cfg.precision == SAKURA_PREC_MIXED);
     const Plan p = plan_step(n);
     const int64_t slots = sakura::pair_step_slots(n, p.W);
     const bool mixed = g.cfg.precision == SAKURA_PREC_MIXED;

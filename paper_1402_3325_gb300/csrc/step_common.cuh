@@ -51,6 +51,10 @@ void launch_prep_mixed(const double *state, const double *mass, double *X, float
 void launch_pair_step_mixed(const StepArgs &a, const MixedArgs &ma, int blocks, bool stats,
                             cudaStream_t s);
 int pair_step_mixed_blocks_per_sm(bool stats);
+// symmetric form (unordered pairs once, step_common.cuh tiling, FP64 partials)
+void launch_pair_step_sym_mixed(const StepArgs &a, const MixedArgs &ma, int Smax, int64_t T,
+                                int blocks, bool stats, cudaStream_t s);
+int pair_step_sym_mixed_blocks_per_sm(bool stats);
 
 // Tiling of the symmetric (Newton's third law) kernels, step_sym.cu and
 // step_df64.cu.  Tile t = J (J + 1) / 2 + I covers row block I and column

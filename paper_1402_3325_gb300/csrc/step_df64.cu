@@ -55,18 +55,12 @@ __global__ void prep_df64_kernel(const double *state, const double *mass, double
     X3[(3 * q + 2) * n + i] = d2;
 }
 
-__device__ __forceinline__ dw dw_from_double(double x)
-{
-    const float h = __double2float_rn(x);
-    return {h, __double2float_rn(x - (double)h)};
-}
-
 template <bool STATS>
 __global__ void __launch_bounds__(128)
     pair_step_sym_df64_kernel(StepArgs a, DwArgs da, int Smax, int64_t T)
 {
     __shared__ int queue[4][64];
-    __shared__ double qres[4][32][12];
+    __shared__ float2 qres[4][32][12];  // queued results as double-words
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     int *qw = queue[wib];
@@ -129,10 +123,14 @@ __global__ void __launch_bounds__(128)
             int iters = 0, fb = 0;
             fp64_solve_warp(p, vq, a.tau, a.post, kp, d, iters, fb);
             if (vq) {
+                // converted to double-words here, with every lane active (the
+                // owners below add them one lane at a time)
 #pragma unroll
                 for (int q = 0; q < 6; ++q) {
-                    qres[wib][lane][q] = mjq * d[q];
-                    qres[wib][lane][6 + q] = -miq * d[q];
+                    const double xr = mjq * d[q], xc = -miq * d[q];
+                    const float rh = __double2float_rn(xr), ch = __double2float_rn(xc);
+                    qres[wib][lane][q] = make_float2(rh, __double2float_rn(xr - (double)rh));
+                    qres[wib][lane][6 + q] = make_float2(ch, __double2float_rn(xc - (double)ch));
                 }
                 status |= p.status;
             }
@@ -149,12 +147,17 @@ __global__ void __launch_bounds__(128)
                 const int eq = qw[q];
                 if ((eq & 31) == lane) {
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) dw_acc(racc[c], dw_from_double(qres[wib][q][c]));
+                    for (int c = 0; c < 6; ++c) {
+                        const float2 x = qres[wib][q][c];
+                        dw_acc(racc[c], dw{x.x, x.y});
+                    }
                 }
                 if (!diag && (eq >> 5) == mycol) {
 #pragma unroll
-                    for (int c = 0; c < 6; ++c)
-                        dw_acc(cacc[c], dw_from_double(qres[wib][q][6 + c]));
+                    for (int c = 0; c < 6; ++c) {
+                        const float2 x = qres[wib][q][6 + c];
+                        dw_acc(cacc[c], dw{x.x, x.y});
+                    }
                 }
             }
             __syncwarp();

@@ -15,6 +15,8 @@
 //   the FP64 path half-empty.  The queue is drained at every row end.
 #include <cuda_runtime.h>
 
+#include "df64.cuh"
+#include "kepler_df64.cuh"
 #include "kepler_fp32.cuh"
 #include "kepler_fp64.cuh"
 #include "pair_batch_fp64.cuh"
@@ -196,6 +198,243 @@ __global__ void __launch_bounds__(WARPS * 32)
             atomicMax(&a.stats[kStatMaxIters], (unsigned long long)mx);
         }
     }
+}
+
+// Symmetric form: every unordered pair once, on the systolic tiles and
+// contiguous tile-step ranges of step_sym.cu (step_common.cuh).  The class
+// rule is symmetric in (i, j) (float negation and round-to-nearest are), so
+// one decision serves both ordered pairs.  An FP32-class pair's increments
+// m_j d and -m_i d (float products, formed exactly by two_prod) are summed in
+// double-word form within the tile segment (at most 32 terms, exact to
+// 2^-48) and the segment sums go out in FP64, where the apply kernel adds
+// them; every other pair joins the per-warp FP64 queue of step_df64.cu.
+template <bool STATS>
+__global__ void __launch_bounds__(128)
+    pair_step_sym_mixed_kernel(StepArgs a, MixedArgs ma, int Smax, int64_t T)
+{
+    __shared__ int queue[4][64];
+    __shared__ float2 qres[4][32][12];  // queued results as double-words
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int *qw = queue[wib];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t n = a.n;
+    const int64_t W = (int64_t)gridDim.x * 4;
+    const int64_t w = (int64_t)blockIdx.x * 4 + wib;
+    const float *X32 = ma.X32;
+    const KeplerParams kp{a.tol, a.max_iter, a.bisection};
+    unsigned status = 0;
+    long long it_sum = 0, slots = 0, fallbacks = 0, n32 = 0;
+    int it_max = 0;
+
+    const int64_t p1 = (w + 1) * T / W;
+    for (int64_t pos = w * T / W; pos < p1;) {
+        const int64_t tile = pos >> 5;
+        const int k0 = (int)(pos & 31);
+        const int k1 = p1 - pos < 32 - k0 ? k0 + (int)(p1 - pos) : 32;
+        const int h = (int)(w - sym_owner(32 * tile, W, T));  // segment of the tile
+        pos += k1 - k0;
+        int64_t I, J;
+        sym_tile_of(tile, I, J);
+        const bool diag = I == J;
+        const int64_t i = 32 * I + lane;
+        const bool irow = i < n;
+        float hi_i[3] = {0, 0, 0}, lo_i[3] = {0, 0, 0}, v_i[3] = {0, 0, 0}, mfi = 1.0f;
+        if (irow) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                hi_i[q] = X32[q * n + i];
+                lo_i[q] = X32[(3 + q) * n + i];
+                v_i[q] = X32[(6 + q) * n + i];
+            }
+            mfi = X32[9 * n + i];
+        }
+        dw racc[6], cacc[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) racc[q] = cacc[q] = dw{0.0f, 0.0f};
+        int tail = 0;
+
+        // FP64 solve of queue entries 0..cnt-1 at step kc, results added to
+        // the row owners and the lanes holding the columns, in queue order
+        auto flush = [&](int kc, int cnt) {
+            const bool vq = lane < cnt;
+            const int e = vq ? qw[lane] : 0;
+            const int64_t iq = 32 * I + (e & 31), jq = 32 * J + (e >> 5);
+            PairSolve p;
+            double miq = 0.0, mjq = 0.0;
+            if (vq) {
+                const double *X = a.X;
+                miq = X[6 * n + iq];
+                mjq = X[6 * n + jq];
+                pair_setup(p, a.tau, miq + mjq, X[iq] - X[jq], X[n + iq] - X[n + jq],
+                           X[2 * n + iq] - X[2 * n + jq], X[3 * n + iq] - X[3 * n + jq],
+                           X[4 * n + iq] - X[4 * n + jq], X[5 * n + iq] - X[5 * n + jq], a.pre,
+                           a.guess);
+            } else {
+                p.done = true;
+                p.beta = p.s = 0.0;
+                p.iters = 0;
+                p.status = 0;
+            }
+            double d[6];
+            int iters = 0, fb = 0;
+            fp64_solve_warp(p, vq, a.tau, a.post, kp, d, iters, fb);
+            if (vq) {
+                // converted to double-words here, with every lane active (the
+                // owners below add them one lane at a time)
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const double xr = mjq * d[q], xc = -miq * d[q];
+                    const float rh = __double2float_rn(xr), ch = __double2float_rn(xc);
+                    qres[wib][lane][q] = make_float2(rh, __double2float_rn(xr - (double)rh));
+                    qres[wib][lane][6 + q] = make_float2(ch, __double2float_rn(xc - (double)ch));
+                }
+                status |= p.status;
+            }
+            if (STATS) {
+                it_sum += iters;
+                fallbacks += fb;
+                it_max = max(it_max, iters);
+                const int wmax = __reduce_max_sync(0xffffffffu, iters);
+                if (lane == 0) slots += 32LL * wmax;
+            }
+            __syncwarp();
+            const int mycol = (lane + kc) & 31;
+            for (int q = 0; q < cnt; ++q) {
+                const int eq = qw[q];
+                if ((eq & 31) == lane) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        const float2 x = qres[wib][q][c];
+                        dw_acc(racc[c], dw{x.x, x.y});
+                    }
+                }
+                if (!diag && (eq >> 5) == mycol) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        const float2 x = qres[wib][q][6 + c];
+                        dw_acc(cacc[c], dw{x.x, x.y});
+                    }
+                }
+            }
+            __syncwarp();
+        };
+
+        for (int k = k0; k < k1; ++k) {
+            const int c = (lane + k) & 31;
+            const int64_t j = 32 * J + c;
+            const bool valid = irow && j < n && (!diag || c != lane);
+            bool solved32 = false;
+            int it32 = 0;
+            if (valid) {
+                float hi_j[3], lo_j[3], v_j[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    hi_j[q] = X32[q * n + j];
+                    lo_j[q] = X32[(3 + q) * n + j];
+                    v_j[q] = X32[(6 + q) * n + j];
+                }
+                const float mfj = X32[9 * n + j];
+                Pair32 p;
+                pair32_setup(p, hi_i, lo_i, v_i, mfi, hi_j, lo_j, v_j, mfj, ma.rule);
+                if (p.fp32) {
+                    float d[6];
+                    solved32 = pair32_solve(p, ma.tau32, ma.post32, a.guess, d, it32);
+                    if (solved32) {
+#pragma unroll
+                        for (int q = 0; q < 6; ++q) {
+                            dw_acc(racc[q], two_prod(mfj, d[q]));
+                            dw_acc(cacc[q], two_prod(-mfi, d[q]));
+                        }
+                    }
+                }
+            }
+            if (STATS) {
+                n32 += solved32 ? (diag ? 1 : 2) : 0;  // in ordered pairs
+                // single-precision iterations of the FP32-class solves
+                it_sum += solved32 ? it32 : 0;
+                it_max = max(it_max, solved32 ? it32 : 0);
+            }
+            const bool need64 = valid && !solved32;
+            const unsigned mask = __ballot_sync(0xffffffffu, need64);
+            if (need64) qw[tail + __popc(mask & lt_mask)] = lane | (c << 5);
+            tail += __popc(mask);
+            __syncwarp();
+            while (tail >= 32 || (k + 1 == k1 && tail > 0)) {
+                const int cnt = min(tail, 32);
+                flush(k, cnt);
+                if (lane < tail - cnt) qw[lane] = qw[cnt + lane];
+                __syncwarp();
+                tail -= cnt;
+            }
+            if (!diag && k + 1 < k1) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    cacc[q].h = __shfl_sync(0xffffffffu, cacc[q].h, (lane + 1) & 31);
+                    cacc[q].l = __shfl_sync(0xffffffffu, cacc[q].l, (lane + 1) & 31);
+                }
+            }
+        }
+        // segment sums in FP64: rows of i to slot (J, h), columns to slot (I, h)
+        if (irow) {
+            double *dst = a.partial + (J * Smax + h) * 6 * n;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) dst[q * n + i] = (double)racc[q].h + (double)racc[q].l;
+        }
+        if (!diag) {
+            const int64_t jc = 32 * J + ((lane + k1 - 1) & 31);
+            if (jc < n) {
+                double *dst = a.partial + (I * Smax + h) * 6 * n;
+#pragma unroll
+                for (int q = 0; q < 6; ++q)
+                    dst[q * n + jc] = (double)cacc[q].h + (double)cacc[q].l;
+            }
+        }
+    }
+    status = __reduce_or_sync(0xffffffffu, status);
+    if (lane == 0 && status) atomicOr(a.status, status);
+    if (STATS) {
+        long long s1 = it_sum, s2 = slots, s3 = fallbacks, s4 = n32;
+        int mx = it_max;
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+            s4 += __shfl_xor_sync(0xffffffffu, s4, o);
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) {
+            atomicAdd(&a.stats[kStatIters], (unsigned long long)s1);
+            atomicAdd(&a.stats[kStatSlots], (unsigned long long)s2);
+            atomicAdd(&a.stats[kStatFallbacks], (unsigned long long)s3);
+            atomicAdd(&a.stats[kStatFp32Pairs], (unsigned long long)s4);
+            atomicMax(&a.stats[kStatMaxIters], (unsigned long long)mx);
+        }
+    }
+}
+
+void launch_pair_step_sym_mixed(const StepArgs &a, const MixedArgs &ma, int Smax, int64_t T,
+                                int blocks, bool stats, cudaStream_t s)
+{
+    if (stats)
+        pair_step_sym_mixed_kernel<true><<<blocks, 128, 0, s>>>(a, ma, Smax, T);
+    else
+        pair_step_sym_mixed_kernel<false><<<blocks, 128, 0, s>>>(a, ma, Smax, T);
+}
+
+int pair_step_sym_mixed_blocks_per_sm(bool stats)
+{
+    int b = 0;
+    const cudaError_t e =
+        stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &b, pair_step_sym_mixed_kernel<true>, 128, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &b, pair_step_sym_mixed_kernel<false>, 128, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return b > 0 ? b : 1;
 }
 
 void launch_prep_mixed(const double *state, const double *mass, double *X, float *X32,

@@ -2,7 +2,9 @@
 perturbing pairs; FP64 for the rest and for all accumulation).
 
 * The number of pairs solved in FP32 equals the oracle's single-precision
-  class count exactly (same decision, same precision, same operation order).
+  class count exactly (same decision, same precision, same operation order),
+  in both pair modes (the symmetric kernel decides once per unordered pair;
+  the rule is symmetric in (i, j)).
 * With a class rule that admits no pair, every pair goes through the per-warp
   FP64 queue and the step matches the FP64 oracle to 1e-12.
 * Otherwise one step stays within the stated bound of the FP64 oracle
@@ -77,11 +79,15 @@ CASES = [
 ]
 
 
+PAIRS = [sk.PAIRS_SYMMETRIC, sk.PAIRS_ORDERED]
+
+
+@pytest.mark.parametrize("pairs", PAIRS, ids=["symmetric", "ordered"])
 @pytest.mark.parametrize("name,make,rule", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("order", [2, -1])
-def test_mixed_class_count_and_accuracy(name, make, rule, order):
+def test_mixed_class_count_and_accuracy(name, make, rule, order, pairs):
     s = make()
-    with mixed(mixed_rule=rule, guess=sk.GUESS_TAYLOR):
+    with mixed(mixed_rule=rule, guess=sk.GUESS_TAYLOR, pair_mode=pairs):
         r, v, st = step_gpu(s, order)
     cnt, _ = oracle.pair_classes(s.m, s.r, s.v, s.dt, rule=rule, order=order)
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, order, nthreads=NCPU)
@@ -92,10 +98,11 @@ def test_mixed_class_count_and_accuracy(name, make, rule, order):
     assert er <= STEP_BOUND and ev <= STEP_BOUND
 
 
-def test_mixed_without_fp32_pairs_is_fp64_exact():
+@pytest.mark.parametrize("pairs", PAIRS, ids=["symmetric", "ordered"])
+def test_mixed_without_fp32_pairs_is_fp64_exact(pairs):
     # r_min larger than the system: every pair takes the FP64 queue
     s = ics.random_cluster(700, seed=11, mass_spread=2.0)
-    with mixed(mixed_r_min=1e6):
+    with mixed(mixed_r_min=1e6, pair_mode=pairs):
         r, v, st = step_gpu(s, 2)
     assert st["fp32_pairs"] == 0
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
@@ -103,12 +110,13 @@ def test_mixed_without_fp32_pairs_is_fp64_exact():
     assert er <= 1e-12 and ev <= 1e-12, (er, ev)
 
 
-def test_mixed_energy_drift_bh_cluster():
+@pytest.mark.parametrize("pairs", PAIRS, ids=["symmetric", "ordered"])
+def test_mixed_energy_drift_bh_cluster(pairs):
     # BH cluster, hyperbolic rule: 16 steps of the mixed and the FP64 form
     # from the same start; energies from the oracle's compensated sum
     s = ics.bh_cluster(2048, seed=2)
     E0 = oracle.energy(s.m, s.r, s.v)[0]
-    with mixed(mixed_rule=1, guess=sk.GUESS_TAYLOR):
+    with mixed(mixed_rule=1, guess=sk.GUESS_TAYLOR, pair_mode=pairs):
         rm, vm, stm = step_gpu(s, 2, nsteps=16)
     rf, vf, _ = step_gpu(s, 2, nsteps=16)
     Em = oracle.energy(s.m, rm, vm)[0]
