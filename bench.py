@@ -274,6 +274,7 @@ def run_ensemble(args, rank, world, device, stream, dist):
     sk.check()
     stt = sk.get_stats(reset=True)
     kbar = stt["iters"] / max(1, stt["pairs"])
+    carried = stt.get("carries", 0) / max(1, stt["pairs"])
     warps, blocks, tune = sk.batched_tuning()
     sk.init(device.index, stream=stream.cuda_stream, guess=guess)
     st.copy_(torch.tensor(ens.state, device=device))
@@ -306,7 +307,7 @@ def run_ensemble(args, rank, world, device, stream, dist):
     if rank != 0:
         return 0
     pairs = int((sizes * (sizes - 1)).sum())
-    flops_pair = C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP
+    flops_pair = C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP + carried * (C_STEP + C_CARRY)
     achieved = pairs * args.steps * flops_pair / (ms * 1e-3) / 1e12
     peak = FP64_PEAK_GFLOPS / 1e3
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -316,7 +317,7 @@ def run_ensemble(args, rank, world, device, stream, dist):
             "config": {"workload": desc, "nsys": ens.nsys, "particles": int(ens.offsets[-1]),
                        "n2_per_step": n2, "pairs_solved_per_step": pairs, "order": 2,
                        "form": "batched",
-                       "kepler_guess": "taylor" if args.guess == "fp32" else args.guess,
+                       "kepler_guess": args.guess,
                        "block_warps": warps, "blocks": blocks, "autotune_ms": tune,
                        "l2": "state (7.7 MB) stays in shared memory for the whole call"},
             "gpu_launches": 1,
@@ -329,8 +330,37 @@ def run_ensemble(args, rank, world, device, stream, dist):
                     "h2d_bytes_per_step": int(st.numel() * 8) // args.steps,
                     "d2h_bytes_per_step": int(st.numel() * 8) // args.steps,
                     "note": "state copied in and out once around the K-step call"}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline_ensemble(ens)
     print(json.dumps(line))
     return 0
+
+
+def _cpu_baseline_ensemble(ens, budget_s=10.0):
+    """The oracle on the host cores over a bounded sample of the ensemble:
+    whole systems in order, each for as many of its steps as the budget
+    allows (at most 2000), N^2 * steps / s over the sample."""
+    import oracle
+    cores = os.cpu_count() or 1
+    oracle.build()
+    t0 = time.perf_counter()
+    work = 0
+    nsys = 0
+    for k in range(ens.nsys):
+        s = ens.system(k)
+        r, v = s.r.copy(), s.v.copy()
+        for _ in range(2000):
+            rc, r, v = oracle.step(s.m, r, v, s.dt, 2, nthreads=cores)
+            work += s.n * s.n
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        nsys += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": work / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the first {nsys} system(s) of the same ensemble, consecutive steps from"
+                      f" their initial states, OpenMP over i on {cores} threads, {el:.1f} s"}
 
 
 def _variant_df64(args, sk, s, device, stream, flush, guess):

@@ -32,7 +32,7 @@ struct BatchCache {
     int warps = 4;
     int blocks = 0;
     bool tuned = false;
-    bool tuned_learned = false;
+    int tuned_variant = 0;  // 1: learned guess, 2: single-precision seed
     cudaGraphExec_t exec = nullptr;
     sakura::BatchArgs graph_args{};
     int graph_warps = 0, graph_blocks = 0;
@@ -618,7 +618,7 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
         bc.host_offsets.assign(host_offsets, host_offsets + nsys + 1);
         bc.ntasks = (int)tb.size() - 1;
         bc.tuned = false;
-        bc.tuned_learned = false;
+        bc.tuned_variant = 0;
         if (bc.exec) cudaGraphExecDestroy(bc.exec);
         bc.exec = nullptr;
     }
@@ -647,9 +647,11 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
     a.bisection = g.cfg.kepler_bisection;
     a.guess = (g.cfg.guess == SAKURA_GUESS_TAYLOR || g.cfg.guess == SAKURA_GUESS_FP32) ? 2 : 0;
     a.mlp = g.cfg.guess == SAKURA_GUESS_LEARNED ? (const sakura::MlpWeights *)g.mlp.ptr : nullptr;
+    a.seed = g.cfg.guess == SAKURA_GUESS_FP32 ? 1 : 0;
     a.status = g.d_status;
     a.stats = g.d_stats;
     const bool learned = a.mlp != nullptr;
+    const bool seed = a.seed != 0;
 
     // autotune the block shape once per schedule, on a scratch copy
     static const int kCand[4] = {1, 2, 4, 8};
@@ -658,7 +660,7 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
         if (bc.warps != 1 && bc.warps != 2 && bc.warps != 4 && bc.warps != 8) bc.warps = 4;
         bc.blocks = g.cfg.grid_blocks > 0
                         ? g.cfg.grid_blocks
-                        : g.sm_count * sakura::batched_blocks_per_sm(bc.warps, stats, learned);
+                        : g.sm_count * sakura::batched_blocks_per_sm(bc.warps, stats, learned, seed);
         if (!(g.cfg.flags & SAKURA_FLAG_NO_AUTOTUNE) && g.cfg.block_warps <= 0 &&
             g.cfg.grid_blocks <= 0) {
             if ((rc = grow(bc.tune_state, 6 * (size_t)total * sizeof(double)))) return rc;
@@ -672,7 +674,7 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
             double best = 1e300;
             for (int c = 0; c < 4; ++c) {
                 const int w = kCand[c];
-                const int blocks = g.sm_count * sakura::batched_blocks_per_sm(w, false, learned);
+                const int blocks = g.sm_count * sakura::batched_blocks_per_sm(w, false, learned, seed);
                 float ms = 0.f;
                 for (int rep = 0; rep < 2; ++rep) {  // first launch warms up
                     cudaMemcpyAsync(t.state, state, 6 * (size_t)total * sizeof(double),
@@ -701,16 +703,17 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
                             g.stream);
         }
         if (stats)
-            bc.blocks = g.sm_count * sakura::batched_blocks_per_sm(bc.warps, true, learned);
+            bc.blocks = g.sm_count * sakura::batched_blocks_per_sm(bc.warps, true, learned, seed);
         bc.tuned = true;
     }
     // (re)build the graph when anything it captured changed
-    if (bc.tuned_learned != learned) {
-        // occupancy differs with the network in shared memory
+    const int variant = (learned ? 1 : 0) | (seed ? 2 : 0);
+    if (bc.tuned_variant != variant) {
+        // occupancy differs with the network or the float copies in shared memory
         bc.blocks = g.cfg.grid_blocks > 0
                         ? g.cfg.grid_blocks
-                        : g.sm_count * sakura::batched_blocks_per_sm(bc.warps, stats, learned);
-        bc.tuned_learned = learned;
+                        : g.sm_count * sakura::batched_blocks_per_sm(bc.warps, stats, learned, seed);
+        bc.tuned_variant = variant;
     }
     const bool same = bc.exec && bc.graph_warps == bc.warps && bc.graph_blocks == bc.blocks &&
                       bc.graph_stats == stats &&

@@ -30,6 +30,7 @@
 #include <numeric>
 #include <vector>
 
+#include "kepler_df64.cuh"
 #include "kepler_fp64.cuh"
 #include "mlp_infer.cuh"
 #include "pair_batch_fp64.cuh"
@@ -40,11 +41,15 @@ namespace sakura {
 
 constexpr int kBatchMaxN = 64;
 
-template <int WARPS, bool STATS, bool LEARNED>
+// SEED: the single-precision seed and the Taylor carry of the symmetric
+// FP64 kernel (float copies of the drifted state in shared memory, hi + lo
+// positions, refreshed after every drift)
+template <int WARPS, bool STATS, bool LEARNED, bool SEED>
 __global__ void __launch_bounds__(WARPS * 32)
     batched_kernel(BatchArgs a)
 {
     __shared__ double sh[WARPS][7][kBatchMaxN];
+    __shared__ float sh32[WARPS][SEED ? 10 : 1][kBatchMaxN];
     extern __shared__ __align__(16) unsigned char dsm[];
     MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(dsm);
     __nv_bfloat16 *mlpStage = reinterpret_cast<__nv_bfloat16 *>(dsm + sizeof(MlpWeights));
@@ -52,10 +57,11 @@ __global__ void __launch_bounds__(WARPS * 32)
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     double(*S)[kBatchMaxN] = sh[wib];
+    float(*S32)[kBatchMaxN] = sh32[wib];
     const int64_t tot = a.total;
     const KeplerParams kp{a.tol, a.max_iter, a.bisection};
     unsigned status = 0;
-    long long it_sum = 0, slots = 0, fallbacks = 0;
+    long long it_sum = 0, slots = 0, fallbacks = 0, carries = 0;
     int it_max = 0;
 
     while (true) {
@@ -105,8 +111,19 @@ __global__ void __launch_bounds__(WARPS * 32)
                 const int i = my_base + my_row + 32 * r;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) S[c][i] = fma(S[3 + c][i], drift, S[c][i]);
+                if (SEED) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float hi = __double2float_rn(S[c][i]);
+                        S32[c][i] = hi;
+                        S32[3 + c][i] = __double2float_rn(S[c][i] - (double)hi);
+                        S32[6 + c][i] = __double2float_rn(S[3 + c][i]);
+                    }
+                    S32[9][i] = __double2float_rn(S[6][i]);
+                }
             }
             __syncwarp();
+            const float ptau32 = (float)(a.pre * tau), t32 = (float)tau;
             double acc0[6] = {0, 0, 0, 0, 0, 0}, acc1[6] = {0, 0, 0, 0, 0, 0};
             int r = 0, jp = 0;
             for (int jj = 0; jj < maxlen; ++jj) {
@@ -121,6 +138,19 @@ __global__ void __launch_bounds__(WARPS * 32)
                     pair_setup(p, tau, S[6][i] + mj, S[0][i] - S[0][j], S[1][i] - S[1][j],
                                S[2][i] - S[2][j], S[3][i] - S[3][j], S[4][i] - S[4][j],
                                S[5][i] - S[5][j], a.pre, LEARNED ? 2 : a.guess);
+                    if (SEED) {
+                        float dr[3], dv[3];
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            dr[c] = __fadd_rn(__fsub_rn(S32[c][i], S32[c][j]),
+                                              __fsub_rn(S32[3 + c][i], S32[3 + c][j]));
+                            dv[c] = __fsub_rn(S32[6 + c][i], S32[6 + c][j]);
+                        }
+                        const K32 o = k32_phase1(dr, dv, S32[9][i] + S32[9][j], ptau32, t32, 2);
+                        if (o.ok && __double_as_longlong(p.t) == __double_as_longlong(tau) &&
+                            !p.done)
+                            p.s = (double)o.s;
+                    }
                 } else {
                     p.done = true;
                     p.beta = p.s = 0.0;
@@ -130,7 +160,8 @@ __global__ void __launch_bounds__(WARPS * 32)
                 if (LEARNED) learned_guess_warp(p, valid, *mlpW, mlpStage + wib * 32 * 16);
                 double d[6];
                 int iters = 0, fb = 0;
-                fp64_solve_warp(p, valid, tau, a.post, kp, d, iters, fb);
+                fp64_solve_warp<SEED>(p, valid, tau, a.post, kp, d, iters, fb);
+                if (STATS) carries += (valid && p.carried) ? 1 : 0;
                 if (valid) {
                     if (r == 0) {
 #pragma unroll
@@ -187,18 +218,20 @@ __global__ void __launch_bounds__(WARPS * 32)
     status = __reduce_or_sync(0xffffffffu, status);
     if (lane == 0 && status) atomicOr(a.status, status);
     if (STATS) {
-        long long s1 = it_sum, s2 = slots, s3 = fallbacks;
+        long long s1 = it_sum, s2 = slots, s3 = fallbacks, s4 = carries;
         int mx = it_max;
         for (int o = 16; o > 0; o >>= 1) {
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
             s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+            s4 += __shfl_xor_sync(0xffffffffu, s4, o);
             mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         }
         if (lane == 0) {
             atomicAdd(&a.stats[kStatIters], (unsigned long long)s1);
             atomicAdd(&a.stats[kStatSlots], (unsigned long long)s2);
             atomicAdd(&a.stats[kStatFallbacks], (unsigned long long)s3);
+            atomicAdd(&a.stats[kStatCarries], (unsigned long long)s4);
             atomicMax(&a.stats[kStatMaxIters], (unsigned long long)mx);
         }
     }
@@ -207,22 +240,25 @@ __global__ void __launch_bounds__(WARPS * 32)
 namespace {
 
 template <int W>
-const void *kernel_ptr(bool stats, bool learned)
+const void *kernel_ptr(bool stats, bool learned, bool seed)
 {
     if (learned)
-        return stats ? (const void *)batched_kernel<W, true, true>
-                     : (const void *)batched_kernel<W, false, true>;
-    return stats ? (const void *)batched_kernel<W, true, false>
-                 : (const void *)batched_kernel<W, false, false>;
+        return stats ? (const void *)batched_kernel<W, true, true, false>
+                     : (const void *)batched_kernel<W, false, true, false>;
+    if (seed)
+        return stats ? (const void *)batched_kernel<W, true, false, true>
+                     : (const void *)batched_kernel<W, false, false, true>;
+    return stats ? (const void *)batched_kernel<W, true, false, false>
+                 : (const void *)batched_kernel<W, false, false, false>;
 }
 
-const void *batched_kernel_ptr(int warps, bool stats, bool learned)
+const void *batched_kernel_ptr(int warps, bool stats, bool learned, bool seed)
 {
     switch (warps) {
-    case 1: return kernel_ptr<1>(stats, learned);
-    case 2: return kernel_ptr<2>(stats, learned);
-    case 8: return kernel_ptr<8>(stats, learned);
-    default: return kernel_ptr<4>(stats, learned);
+    case 1: return kernel_ptr<1>(stats, learned, seed);
+    case 2: return kernel_ptr<2>(stats, learned, seed);
+    case 8: return kernel_ptr<8>(stats, learned, seed);
+    default: return kernel_ptr<4>(stats, learned, seed);
     }
 }
 
@@ -233,10 +269,12 @@ size_t batched_dyn_smem(int warps, bool learned)
 
 }  // namespace
 
-int batched_blocks_per_sm(int warps, bool stats, bool learned)
+int batched_blocks_per_sm(int warps, bool stats, bool learned, bool seed)
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_kernel_ptr(warps, stats, learned),
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b,
+                                                      batched_kernel_ptr(warps, stats, learned,
+                                                                         seed),
                                                       warps * 32,
                                                       batched_dyn_smem(warps, learned)) !=
         cudaSuccess) {
@@ -297,8 +335,8 @@ void launch_batched(const BatchArgs &a, int warps, int blocks, bool stats, cudaS
 {
     const bool learned = a.mlp != nullptr;
     void *args[] = {(void *)&a};
-    cudaLaunchKernel(batched_kernel_ptr(warps, stats, learned), dim3(blocks), dim3(warps * 32),
-                     args, batched_dyn_smem(warps, learned), s);
+    cudaLaunchKernel(batched_kernel_ptr(warps, stats, learned, a.seed != 0), dim3(blocks),
+                     dim3(warps * 32), args, batched_dyn_smem(warps, learned), s);
 }
 
 cudaError_t build_batched_graph(const BatchArgs &a, int warps, int blocks, bool stats,
@@ -322,7 +360,7 @@ cudaError_t build_batched_graph(const BatchArgs &a, int warps, int blocks, bool 
         void *args[] = {(void *)&copy};
         cudaKernelNodeParams kpar;
         std::memset(&kpar, 0, sizeof(kpar));
-        kpar.func = (void *)batched_kernel_ptr(warps, stats, a.mlp != nullptr);
+        kpar.func = (void *)batched_kernel_ptr(warps, stats, a.mlp != nullptr, a.seed != 0);
         kpar.gridDim = dim3(blocks);
         kpar.blockDim = dim3(warps * 32);
         kpar.sharedMemBytes = (unsigned)batched_dyn_smem(warps, a.mlp != nullptr);

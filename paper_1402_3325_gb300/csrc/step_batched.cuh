@@ -32,12 +32,13 @@ struct BatchArgs {
     int max_iter;
     int bisection;
     int guess;
+    int seed;                 // 1: single-precision seed and Taylor carry
     const MlpWeights *mlp;    // learned guess network, or nullptr
     unsigned *status;
     unsigned long long *stats;
 };
 
-int batched_blocks_per_sm(int warps, bool stats, bool learned = false);
+int batched_blocks_per_sm(int warps, bool stats, bool learned = false, bool seed = false);
 void build_batch_schedule(const int64_t *offsets, int nsys, std::vector<int> &task_begin,
                           std::vector<int> &task_sys);
 void launch_batched(const BatchArgs &a, int warps, int blocks, bool stats, cudaStream_t s);

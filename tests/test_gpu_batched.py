@@ -86,6 +86,19 @@ def test_batched_one_step_matches_oracle(order):
     check_against_oracle(ens, got, order, 1, TOL)
 
 
+@pytest.mark.parametrize("order", [2, 1, -1])
+def test_batched_fp32_seed_matches_oracle(order):
+    # the single-precision seed and the Taylor carry in the batched kernel
+    ens = small_ensemble(seed=5)
+    with configured(guess=sk.GUESS_FP32):
+        sk.get_stats(reset=True)
+        got = run_batched(ens, order, 3)
+        st = sk.get_stats(reset=True)
+    check_against_oracle(ens, got, order, 3, 1e-11)
+    assert st["carries"] > 0.5 * st["pairs"]
+    assert st["iters"] < 1.5 * st["pairs"]
+
+
 def test_batched_many_steps_matches_oracle():
     ens = small_ensemble(nsys=24, seed=8)
     got = run_batched(ens, 2, 20)
