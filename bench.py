@@ -86,6 +86,24 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 DF64_FLOPS_PER_SOLVE = {"plummer1024": 1940.0, "bh16384": 1917.1, "binaries16384": 1918.2}
 
 
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The largest of every rank's x (the timing rule: the slowest rank sets
+    the job's time); x itself without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64,
+                     device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world: int, work_per_rank: float, ms_total: float) -> float:
+    """Whole-job throughput of `world` replicas, each doing work_per_rank
+    units (N^2 * steps), over the slowest rank's time in milliseconds."""
+    return world * work_per_rank / (ms_total * 1e-3)
+
+
 def _workload(name: str, seed: int):
     from paper_1402_3325_gb300 import ics
     if name == "plummer1024":
@@ -289,12 +307,8 @@ def run_ensemble(args, rank, world, device, stream, dist):
         e1.record(stream)
         torch.cuda.synchronize(device)
     sk.check()
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n2 * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, device)
+    value = whole_job_value(world, n2 * args.steps, ms)
     # end to end: host buffers copied in and out around the same call
     host = torch.empty(tuple(st.shape), dtype=torch.float64).pin_memory()
     host.copy_(torch.tensor(ens.state))
@@ -534,12 +548,9 @@ def main():
     st = sk.get_stats(reset=True)
     energy_error = abs(sk.energy(state, mass) / E0 - 1.0)  # outside the timed region
     pair_ms = st["pair_kernel_ms"] / max(1, st["timed_launches"])
-    if dist is not None:
-        t = torch.tensor([ms_total], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, dist, device)
     ms_step = ms_total / args.steps
-    value = world * n * n * args.steps / (ms_total * 1e-3)
+    value = whole_job_value(world, n * n * args.steps, ms_total)
 
     # end to end through the host-buffer entry point, copies in the timed region
     e2e = None
@@ -557,12 +568,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             sk.evolve_host(host_state, host_mass, s.dt, 2, 1)
-        el = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([el], device=device, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
-        e2e = {"value": world * n * n * args.steps / el, "unit": UNIT,
+        el = max_over_ranks(time.perf_counter() - t0, dist, device)
+        e2e = {"value": whole_job_value(world, n * n * args.steps, el * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(host_state.nbytes + host_mass.nbytes),
                "d2h_bytes_per_step": int(host_state.nbytes)}
 
