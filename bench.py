@@ -69,6 +69,9 @@ C_SYM = 12
 # Laguerre correction (C_STEP) and the carry of G1..G3 and F' with a new
 # 1/F' (29: h2 (2), dF''/ds (4), three G's and F' (17), reciprocal (6))
 C_CARRY = 29
+# the seeded solve skips the second-order guess (4) and the tolerance test's
+# product (1), and takes its near-root step in Halley form (the same count)
+C_SEED_SAVED = 5
 # FP32-class pair of the symmetric mixed form (see the roofline code below)
 C_MIX32_FIX = 46 + 34 + 156
 C_MIX32_ITER = 53
@@ -616,7 +619,8 @@ def main():
                        " for the FP64 work only")
     else:
         flops_solve = (C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP +
-                       carried * (C_STEP + C_CARRY) + (C_SYM if symmetric else 0))
+                       carried * (C_STEP + C_CARRY) + (C_SYM if symmetric else 0) -
+                       (C_SEED_SAVED if (args.guess == "fp32" and symmetric) else 0))
         peak = FP64_PEAK_GFLOPS / 1e3
         kname = "pair_step_sym" if symmetric else (
             "pair_step_mixed" if args.form == "mixed" else "pair_step_fp64")

@@ -321,9 +321,10 @@ __device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, int nt,
             p.hi = s;
         return true;
     }
-    // |q| <= tol * max(|s|, |t| / r)
+    // |q| <= tol * max(|s|, |t| / r) (with the carry, a small step is taken
+    // and carried instead)
     const long long sc = max(magbits(s), magbits(p.t * ip));
-    if (magbits(q) <= magbits(kp.tol * __longlong_as_double(sc))) {
+    if (!CARRY && magbits(q) <= magbits(kp.tol * __longlong_as_double(sc))) {
         p.done = true;
         return false;
     }
@@ -331,12 +332,21 @@ __device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, int nt,
         p.lo = s;
     else
         p.hi = s;
-    const float u = (float)(1.25 * q * (Fpp * ip));
-    const float r = sqrt_approx(fabsf(1.0f - u));
-    const float cf = __fdividef(0.8f * u, 1.0f + r);
-    const float k = fabsf(u) < 0.5f ? __fdividef(cf, 1.0f - cf)
-                                    : __fdividef(5.0f, fmaf(4.0f, r, 1.0f)) - 1.0f;
-    const double step = fma(q, (double)k, q);
+    const double qh = q * (Fpp * ip);  // = u / 1.25
+    double step;
+    if (CARRY && magbits(qh) < 0x3f50000000000000LL) {
+        // |u| < 2^-10 (a root next to the seed): the Laguerre step
+        // q (1 + k) with k = u / 2.5 + O(u^2), Halley's correction, whose
+        // cubic error is far below round-off here
+        step = fma(0.5 * q, qh, q);
+    } else {
+        const float u = (float)(1.25 * qh);
+        const float r = sqrt_approx(fabsf(1.0f - u));
+        const float cf = __fdividef(0.8f * u, 1.0f + r);
+        const float k = fabsf(u) < 0.5f ? __fdividef(cf, 1.0f - cf)
+                                        : __fdividef(5.0f, fmaf(4.0f, r, 1.0f)) - 1.0f;
+        step = fma(q, (double)k, q);
+    }
     const double sn = s - step;
     // a step below 2^-20 of the scale: the cubically convergent Laguerre step
     // has reached the root to about 2^-60, so take it and carry G1..G3 and

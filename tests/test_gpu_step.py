@@ -342,7 +342,9 @@ def test_fp32_guess_falls_back_for_reduced_periods():
         sk.get_stats(reset=True)
         r, v = gpu_step(s, s.dt, 2)
         st = sk.get_stats(reset=True)
-    assert st["carries"] < st["solves"]
+    # the fallback lanes start from the second-order guess and need a second
+    # FP64 evaluation before their carry
+    assert st["iters"] > st["solves"]
     rng = np.random.default_rng(1)
     idx = np.unique(np.concatenate([[0, 1, 2, 3], rng.choice(s.n, 40, replace=False)]))
     rc, rs, vs = oracle.step_sample(s.m, s.r, s.v, s.dt, idx, 2, nthreads=NCPU)
