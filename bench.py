@@ -296,6 +296,7 @@ def run_ensemble(args, rank, world, device, stream, dist):
     stt = sk.get_stats(reset=True)
     kbar = stt["iters"] / max(1, stt["pairs"])
     carried = stt.get("carries", 0) / max(1, stt["pairs"])
+    lane_eff = stt["iters"] / max(1, stt["warp_slots"])
     warps, blocks, tune = sk.batched_tuning()
     sk.init(device.index, stream=stream.cuda_stream, guess=guess)
     st.copy_(torch.tensor(ens.state, device=device))
@@ -341,7 +342,8 @@ def run_ensemble(args, rank, world, device, stream, dist):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "batched_kernel", "pipe": "fp64",
-                         "flops_per_pair": flops_pair, "kepler_iters_mean": kbar},
+                         "flops_per_pair": flops_pair, "kepler_iters_mean": kbar,
+                         "iteration_lane_efficiency": lane_eff},
             "clocks": clocks.summary(),
             "e2e": {"value": world * n2 * args.steps / el, "unit": UNIT,
                     "h2d_bytes_per_step": int(st.numel() * 8) // args.steps,
@@ -522,6 +524,9 @@ def main():
     sk.check()
     st = sk.get_stats(reset=True)
     kbar = st["iters"] / max(1, st["solves"])
+    # share of warp iteration slots doing useful work: divergent iteration
+    # counts leave lanes idle while the warp's slowest lane finishes
+    lane_eff = st["iters"] / max(1, st["warp_slots"])
     st_iters_fp64 = float(st["iters"]) / max(1, args.warmup)
     carried = st.get("carries", 0) / max(1, st["solves"])
     solves_per_pair = st["solves"] / max(1, st["pairs"])
@@ -634,6 +639,7 @@ def main():
             "kernel": kname + "_kernel", "pipe": pipe, "peak_source": peak_source,
             "flops_per_solve": flops_solve, "kepler_evals_per_solve": kbar,
             "carried_share": carried,
+            "iteration_lane_efficiency": lane_eff,
             "solves_per_step": solves,
             "pair_kernel_ms": pair_ms, "pair_kernel_share": pair_ms / ms_step}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
