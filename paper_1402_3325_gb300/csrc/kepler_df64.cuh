@@ -88,7 +88,9 @@ DW_HD float stumpff32_terms(float x, float &c0, float &c1, float &c2)
 
 // Laguerre iterations in FP32 from the standard (guess 0) or second-order
 // (guess 2) initial value (approximate reciprocals: this phase only needs
-// the root to about 1e-7).
+// the root to about 1e-7).  It stops at the Newton-step test or after a
+// Laguerre step below 2^-8 of the scale, so a lane close to its root takes
+// one evaluation and the warp seldom waits for a second.
 DW_HD K32 k32_solve(float r0, float ir0, float eta, float beta, float zeta, float t, int guess)
 {
     K32 o;
@@ -119,7 +121,15 @@ DW_HD K32 k32_solve(float r0, float ir0, float eta, float beta, float zeta, floa
         }
         const float u = fmul(fmul(1.25f, q), fmul(Fpp, ir));
         const float den = ffma(4.0f, fsqrt_approx(fabsf(fsub(1.0f, u))), 1.0f);
-        s = fsub(s, fmul(fmul(5.0f, q), rcp_approx(den)));
+        const float step = fmul(fmul(5.0f, q), rcp_approx(den));
+        s = fsub(s, step);
+        // a step below 2^-8 of the scale leaves the cubically convergent
+        // iteration at single-precision round-off: accept without evaluating
+        // again (only s is needed from this phase)
+        if (fabsf(step) <= fmul(0x1p-8f, fmaxf(fabsf(s), fabsf(fmul(t, ir))))) {
+            o.ok = true;
+            break;
+        }
     }
     o.s = s;
     o.x = fmul(fmul(beta, s), s);

@@ -4,11 +4,15 @@
 // quartering and doubling, Laguerre n = 5 with the Newton-step convergence
 // test, increment form of the Eq. 26 pair map divided by m = m_i + m_j), in
 // FP32 throughout.  The test stops a lane when |F/F'| <= 4 eps32 max(|s|,
-// |t| |1/F'|), eps32 = 2^-23; a lane that has not converged after
-// kFp32MaxIter steps is handed to the FP64 solver.  Only pairs that the FP32
-// class rule admits (distant, low- or very-high-eccentricity pairs, whose
-// increments are small next to the state) come here; their increments are
-// accumulated in FP64 by the caller.
+// |t| |1/F'|), eps32 = 2^-23, or after a Laguerre step below 2^-11 of that
+// scale (then carried to by a Taylor series); a lane that has not converged
+// after kFp32MaxIter steps is handed to the FP64 solver.  The solve's
+// reciprocals and square root are the hardware approximations (about 1 ulp):
+// only the class decision must be reproducible, and it keeps correctly
+// rounded operations.  Only pairs that the FP32 class rule admits (distant,
+// low- or very-high-eccentricity pairs, whose increments are small next to
+// the state) come here; the caller accumulates their increments (in FP64, or
+// as exact double-word sums of the float products, step_mixed.cu).
 //
 // The class rule is evaluated on the hi/lo float split of the drifted
 // positions with correctly rounded single-precision operations in a fixed
@@ -16,6 +20,8 @@
 #pragma once
 
 #include <cstdint>
+
+#include "df64.cuh"
 
 namespace sakura {
 
@@ -137,7 +143,7 @@ __device__ __forceinline__ bool pair32_solve(const Pair32 &p, float tau, float p
         const float F = fmaf(r0, s, fmaf(p.eta, G2, fmaf(zeta0, G3, -t)));
         const float Fp = fmaf(p.eta, G1, fmaf(zeta0, G2, r0));
         const float Fpp = fmaf(p.eta, c.c0, zeta0 * G1);
-        ir = __frcp_rn(Fp);
+        ir = rcp_approx(Fp);
         const float q = F * ir;
         ++iters;
         if (fabsf(q) <= tol * fmaxf(fabsf(s), fabsf(t * ir))) {
@@ -145,8 +151,27 @@ __device__ __forceinline__ bool pair32_solve(const Pair32 &p, float tau, float p
             break;
         }
         const float u = 1.25f * q * Fpp * ir;
-        const float den = 1.0f + 4.0f * sqrtf(fabsf(1.0f - u));
-        s = s - 5.0f * q * __frcp_rn(den);
+        const float den = 1.0f + 4.0f * fsqrt_approx(fabsf(1.0f - u));
+        const float step = 5.0f * q * rcp_approx(den);
+        s = s - step;
+        // a Laguerre step below 2^-11 of the scale: the root is reached to
+        // single-precision round-off, so carry G1..G3 and F' = r to it by
+        // their Taylor series (dG_k/ds = G_{k-1}, G_0 = c0, dG_0/ds = -beta
+        // G1) instead of evaluating again; lanes near their root then finish
+        // together
+        if (fabsf(step) <= 0x1p-11f * fmaxf(fabsf(s), fabsf(t * ir))) {
+            const float h2 = 0.5f * step * step;
+            const float F3 = fmaf(-p.eta * beta, G1, zeta0 * c.c0);  // dF''/ds
+            const float nG3 = fmaf(h2, G1, fmaf(-step, G2, G3));
+            const float nG2 = fmaf(h2, c.c0, fmaf(-step, G1, G2));
+            const float nG1 = fmaf(h2, -beta * G1, fmaf(-step, c.c0, G1));
+            ir = rcp_approx(fmaf(h2, F3, fmaf(-step, Fpp, Fp)));
+            G1 = nG1;
+            G2 = nG2;
+            G3 = nG3;
+            done = true;
+            break;
+        }
     }
     if (!done) return false;
     const float fm1 = -G2 * ir0;

@@ -352,8 +352,11 @@ __global__ void __launch_bounds__(128)
             if (STATS) {
                 n32 += solved32 ? (diag ? 1 : 2) : 0;  // in ordered pairs
                 // single-precision iterations of the FP32-class solves
-                it_sum += solved32 ? it32 : 0;
-                it_max = max(it_max, solved32 ? it32 : 0);
+                const int its = solved32 ? it32 : 0;
+                it_sum += its;
+                it_max = max(it_max, its);
+                const int wmax = __reduce_max_sync(0xffffffffu, its);
+                if (lane == 0) slots += 32LL * wmax;
             }
             const bool need64 = valid && !solved32;
             const unsigned mask = __ballot_sync(0xffffffffu, need64);
