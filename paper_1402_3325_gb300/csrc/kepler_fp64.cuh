@@ -92,6 +92,13 @@ __device__ __forceinline__ double rcp_nr(double x)
     return fma(y, fma(e, e, e), y);
 }
 
+// 1/x to a relative error of about 2^-38: one quadratic step y (1 + e).
+__device__ __forceinline__ double rcp_nr2(double x)
+{
+    const double y = rcp_seed(x);
+    return fma(y, fma(-x, y, 1.0), y);
+}
+
 // 1/sqrt(x) to about one ulp (x > 0 normal and finite): one cubic step
 // y (1 + e/2 + 3 e^2 / 8), e = 1 - x y^2, from a seed with error <= 2^-19.
 __device__ __forceinline__ double rsqrt_nr(double x)
@@ -283,26 +290,27 @@ __device__ __forceinline__ void pair_setup(PairSolve &p, double tau, double m, d
     p.done = (magbits(p.t) == 0);
 }
 
-// One Laguerre iteration of a lane that is not done, at x = beta s^2; nt is
-// warp-uniform.  Returns true when the new iterate would leave the bracket
-// (the caller then applies pair_safeguard in a warp-uniform branch).  CARRY:
-// finish with a Taylor carry when the step is small (used where the initial
-// guess is already close for every lane, so that whole warps finish after
-// one evaluation).
+// One Laguerre iteration of a lane that is not done, at s2 = s^2 and x =
+// beta s^2; nt is warp-uniform.  Returns true when the new iterate would
+// leave the bracket (the caller then applies pair_safeguard in a warp-uniform
+// branch).  CARRY: finish with a Taylor carry when the step is small (used
+// where the initial guess is already close for every lane, so that whole
+// warps finish after one evaluation).  With the carry, 1/F' at the iterate
+// only forms the step (to 2^-38, a relative error that vanishes with the
+// step) and is recomputed in full at the accepted root.
 template <bool CARRY>
-__device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, int nt,
+__device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, double s2, int nt,
                                              const KeplerParams &kp)
 {
     const double s = p.s;
     const Stumpff c = stumpff_fp64(x, nt);
-    const double s2 = s * s;
     const double G1 = s * c.c1;
     const double G2 = s2 * c.c2;
     const double G3 = s2 * s * c.c3;
     const double F = fma(p.r0, s, fma(p.eta0, G2, fma(p.zeta0, G3, -p.t)));
     const double Fp = fma(p.eta0, G1, fma(p.zeta0, G2, p.r0));
     const double Fpp = fma(p.eta0, c.c0, p.zeta0 * G1);
-    const double ip = rcp_nr(Fp);
+    const double ip = CARRY ? rcp_nr2(Fp) : rcp_nr(Fp);
     const double q = F * ip;
     p.G1 = G1;
     p.G2 = G2;
@@ -322,8 +330,8 @@ __device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, int nt,
         return true;
     }
     // |q| <= tol * max(|s|, |t| / r) (with the carry, a small step is taken
-    // and carried instead)
-    const long long sc = max(magbits(s), magbits(p.t * ip));
+    // and carried instead, on the scale |s|)
+    const long long sc = CARRY ? magbits(s) : max(magbits(s), magbits(p.t * ip));
     if (!CARRY && magbits(q) <= magbits(kp.tol * __longlong_as_double(sc))) {
         p.done = true;
         return false;
@@ -432,8 +440,8 @@ __device__ __forceinline__ void pair_bisect(PairSolve &p)
 }
 
 // Increments divided by m = m_i + m_j: out[0..2] = delta_r / m,
-// out[3..5] = delta_v / m.
-__device__ __forceinline__ void pair_increment_over_m(const PairSolve &p, double tau, double post,
+// out[3..5] = delta_v / m; qtau = post * tau.
+__device__ __forceinline__ void pair_increment_over_m(const PairSolve &p, double tau, double qtau,
                                                       double out[6])
 {
     const double ir = p.ir;
@@ -442,7 +450,6 @@ __device__ __forceinline__ void pair_increment_over_m(const PairSolve &p, double
     if (__double_as_longlong(p.t) != __double_as_longlong(tau)) gmt += (p.t - tau) * rcp_nr(p.m);
     const double fd = -p.G1 * p.ir0 * ir;
     const double gdm1 = -p.G2 * ir;
-    const double qtau = post * tau;
     const double A = fma(-qtau, fd, fm1);
     const double B = fma(-qtau, gdm1, gmt);
     out[3] = fma(fd, p.x0, gdm1 * p.vx);

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(128)
     const KeplerParams kp{tol, 50, 1};
     double d[6];
     int it = 0, fb = 0;
-    fp64_solve_warp(p, valid, tau, 1.0 - pre, kp, d, it, fb);
+    fp64_solve_warp(p, valid, tau, (1.0 - pre) * tau, kp, d, it, fb);
     if (!valid_id) return;
     float f[6] = {0, 0, 0, 0, 0, 0}, w = 0.0f, tg = 0.0f;
     if (valid && guess_features(p.t, p.m, p.r0, p.ir0, p.eta0, p.beta, f, w) && w > 0.0f) {

@@ -9,21 +9,22 @@ namespace sakura {
 
 // Warp-synchronous FP64 solve of 32 pairs, one per lane, whose setup is
 // done (lanes with p.done == true at entry idle).  Every lane of the warp must
-// call this.  tau, post: this lane's step and post-drift fraction.  Writes
+// call this.  tau, qtau: this lane's step and post-drift time (post * tau).  Writes
 // the increments divided by m_ij to d (only meaningful when valid), returns
 // the lane's evaluation count and whether it needed bisection.
 template <bool CARRY = false>
 __device__ __forceinline__ void fp64_solve_warp(PairSolve &p, bool valid, double tau,
-                                                double post, const KeplerParams &kp,
+                                                double qtau, const KeplerParams &kp,
                                                 double d[6], int &iters, int &fb)
 {
     for (int it = 0; it < kp.max_iter; ++it) {
         if (__all_sync(0xffffffffu, p.done)) break;
-        const double x = p.beta * p.s * p.s;
+        const double s2 = p.s * p.s;
+        const double x = p.beta * s2;
         const unsigned hx = p.done ? 0u : abs_hiword(x);
         const int nt = stumpff_terms(__reduce_max_sync(0xffffffffu, hx));
         bool oob = false;
-        if (!p.done) oob = pair_iterate<CARRY>(p, x, nt, kp);
+        if (!p.done) oob = pair_iterate<CARRY>(p, x, s2, nt, kp);
         if (__any_sync(0xffffffffu, oob)) {
             if (oob) pair_safeguard(p);
         }
@@ -38,7 +39,7 @@ __device__ __forceinline__ void fp64_solve_warp(PairSolve &p, bool valid, double
         }
     }
     iters = valid ? p.iters : 0;
-    if (valid) pair_increment_over_m(p, tau, post, d);
+    if (valid) pair_increment_over_m(p, tau, qtau, d);
 }
 
 // Learned initial guess for the 32 lanes (every lane calls): replaces the
@@ -94,7 +95,7 @@ __device__ __forceinline__ void fp64_pair_batch(const double *X, int64_t n, int6
     }
     if (LEARNED) learned_guess_warp(p, valid, *W, stage);
     double d[6];
-    fp64_solve_warp(p, valid, a.tau, a.post, kp, d, iters, fb);
+    fp64_solve_warp(p, valid, a.tau, a.post * a.tau, kp, d, iters, fb);
     if (valid) {
 #pragma unroll
         for (int q = 0; q < 6; ++q) acc[q] = fma(mj, d[q], acc[q]);

@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(WARPS * 32)
             const double tau = dt * a.sub[(int)(sub % a.nsub)];
             const double drift = a.drift_frac * tau;
             const double post_drift = a.post_drift_frac * tau;
+            const double qtau = a.post * tau;
             for (int r = 0; r < nrows; ++r) {
                 const int i = my_base + my_row + 32 * r;
 #pragma unroll
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(WARPS * 32)
                 if (LEARNED) learned_guess_warp(p, valid, *mlpW, mlpStage + wib * 32 * 16);
                 double d[6];
                 int iters = 0, fb = 0;
-                fp64_solve_warp<SEED>(p, valid, tau, a.post, kp, d, iters, fb);
+                fp64_solve_warp<SEED>(p, valid, tau, qtau, kp, d, iters, fb);
                 if (STATS) carries += (valid && p.carried) ? 1 : 0;
                 if (valid) {
                     if (r == 0) {

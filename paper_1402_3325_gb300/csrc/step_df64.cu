@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(128)
             }
             double d[6];
             int iters = 0, fb = 0;
-            fp64_solve_warp(p, vq, a.tau, a.post, kp, d, iters, fb);
+            fp64_solve_warp(p, vq, a.tau, a.post * a.tau, kp, d, iters, fb);
             if (vq) {
                 // converted to double-words here, with every lane active (the
                 // owners below add them one lane at a time)

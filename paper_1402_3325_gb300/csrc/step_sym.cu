@@ -32,7 +32,7 @@
 namespace sakura {
 
 template <bool STATS, bool LEARNED, bool SEED>
-__global__ void __launch_bounds__(128, LEARNED ? 2 : 4)
+__global__ void __launch_bounds__(128, LEARNED ? 2 : (SEED ? 3 : 4))
     pair_step_sym_kernel(StepArgs a, int Smax, int64_t T)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(128, LEARNED ? 2 : 4)
             if (LEARNED) learned_guess_warp(p, valid, *mlpW, mlpStage + wib * 32 * 16);
             double d[6];
             int iters = 0, fb = 0;
-            fp64_solve_warp<SEED>(p, valid, a.tau, a.post, kp, d, iters, fb);
+            fp64_solve_warp<SEED>(p, valid, a.tau, a.post * a.tau, kp, d, iters, fb);
             if (valid) {
 #pragma unroll
                 for (int q = 0; q < 6; ++q) {
