@@ -12,6 +12,34 @@ namespace sakura {
 
 struct MlpWeights;
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched by
+// launch_pdl may begin while the kernel before it in the stream is still
+// running: griddep_wait() returns once that kernel has completed and its
+// writes are visible (a hardware dependency, not a polling loop), so every
+// such kernel calls it before it reads what its predecessor wrote.
+// griddep_launch() lets the next kernel in the stream begin its launch.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+inline cudaError_t launch_pdl(const void *fn, dim3 grid, dim3 block, void **args, size_t smem,
+                              cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 // indices into the device statistics counters
 constexpr int kStatIters = 0;
 constexpr int kStatMaxIters = 1;

@@ -33,6 +33,7 @@ namespace sakura {
 __global__ void prep_df64_kernel(const double *state, const double *mass, double *X, float *X3,
                                  int64_t n, double drift, unsigned *status)
 {
+    griddep_launch();  // the pair kernel may begin launching
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int q = blockIdx.y;
     if (i >= n) return;
@@ -61,6 +62,8 @@ __global__ void __launch_bounds__(128)
 {
     __shared__ int queue[4][64];
     __shared__ float2 qres[4][32][12];  // queued results as double-words
+    griddep_wait();    // X and X3 from the prep kernel
+    griddep_launch();  // the apply kernel may begin launching
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     int *qw = queue[wib];
@@ -279,6 +282,7 @@ __global__ void __launch_bounds__(32 * kApplyDwWarps)
                       int64_t W, int64_t T, double post_drift, unsigned *status)
 {
     __shared__ float2 red[kApplyDwWarps][2][32];
+    griddep_wait();  // the pair kernel's partials
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int q = blockIdx.y;
     const int64_t P = blockIdx.x;
@@ -351,14 +355,18 @@ void launch_pair_step_df64(const StepArgs &a, const DwArgs &da, int Smax, int64_
     int Sv = Smax;
     int64_t it = T;
     void *args[] = {(void *)&a, (void *)&da, (void *)&Sv, (void *)&it};
-    cudaLaunchKernel(df64_kernel(stats), dim3(blocks), dim3(128), args, 0, s);
+    launch_pdl(df64_kernel(stats), dim3(blocks), dim3(128), args, 0, s);
 }
 
 void launch_apply_df64(double *state, const double *X, const void *partial, int64_t n, int Smax,
                        int64_t W, int64_t T, double post_drift, unsigned *status, cudaStream_t s)
 {
-    apply_df64_kernel<<<dim3((unsigned)((n + 31) / 32), 3), 32 * kApplyDwWarps, 0, s>>>(
-        state, X, reinterpret_cast<const float2 *>(partial), n, Smax, W, T, post_drift, status);
+    const float2 *part = reinterpret_cast<const float2 *>(partial);
+    void *args[] = {(void *)&state, (void *)&X,    (void *)&part,       (void *)&n,
+                    (void *)&Smax,  (void *)&W,    (void *)&T,          (void *)&post_drift,
+                    (void *)&status};
+    launch_pdl((const void *)apply_df64_kernel, dim3((unsigned)((n + 31) / 32), 3),
+               dim3(32 * kApplyDwWarps), args, 0, s);
 }
 
 }  // namespace sakura

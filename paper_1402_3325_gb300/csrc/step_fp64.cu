@@ -42,6 +42,7 @@ __device__ __host__ __forceinline__ int64_t batch_owner(int64_t b, int64_t B, in
 __global__ void prep_step_kernel(const double *state, const double *mass, double *X, float *X32,
                                  int64_t n, double drift, unsigned *status)
 {
+    griddep_launch();  // the pair kernel may begin launching
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double m = mass[i];

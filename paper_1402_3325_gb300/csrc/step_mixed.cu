@@ -32,6 +32,7 @@ __device__ __host__ __forceinline__ int64_t mixed_owner(int64_t b, int64_t B, in
 __global__ void prep_mixed_kernel(const double *state, const double *mass, double *X, float *X32,
                                   int64_t n, double drift, unsigned *status)
 {
+    griddep_launch();  // the pair kernel may begin launching
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double m = mass[i];
@@ -214,6 +215,8 @@ __global__ void __launch_bounds__(128)
 {
     __shared__ int queue[4][64];
     __shared__ float2 qres[4][32][12];  // queued results as double-words
+    griddep_wait();    // X and X32 from the prep kernel
+    griddep_launch();  // the apply kernel may begin launching
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     int *qw = queue[wib];
@@ -419,10 +422,12 @@ __global__ void __launch_bounds__(128)
 void launch_pair_step_sym_mixed(const StepArgs &a, const MixedArgs &ma, int Smax, int64_t T,
                                 int blocks, bool stats, cudaStream_t s)
 {
-    if (stats)
-        pair_step_sym_mixed_kernel<true><<<blocks, 128, 0, s>>>(a, ma, Smax, T);
-    else
-        pair_step_sym_mixed_kernel<false><<<blocks, 128, 0, s>>>(a, ma, Smax, T);
+    int Sv = Smax;
+    int64_t it = T;
+    void *args[] = {(void *)&a, (void *)&ma, (void *)&Sv, (void *)&it};
+    launch_pdl(stats ? (const void *)pair_step_sym_mixed_kernel<true>
+                     : (const void *)pair_step_sym_mixed_kernel<false>,
+               dim3(blocks), dim3(128), args, 0, s);
 }
 
 int pair_step_sym_mixed_blocks_per_sm(bool stats)

@@ -38,6 +38,8 @@ __global__ void __launch_bounds__(128, LEARNED ? 2 : (SEED ? 3 : 4))
     extern __shared__ __align__(16) unsigned char dsm[];
     MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(dsm);
     __nv_bfloat16 *mlpStage = reinterpret_cast<__nv_bfloat16 *>(dsm + sizeof(MlpWeights));
+    griddep_wait();    // X from the prep kernel
+    griddep_launch();  // the apply kernel may begin launching
     if (LEARNED) mlp_load_shared(*mlpW, a.mlp);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -197,6 +199,7 @@ __global__ void __launch_bounds__(32 * kApplyWarps)
                      int64_t W, int64_t T, double post_drift, unsigned *status)
 {
     __shared__ double red[kApplyWarps][2][32];
+    griddep_wait();  // the pair kernel's partials
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int q = blockIdx.y;
     const int64_t P = blockIdx.x;
@@ -273,15 +276,18 @@ void launch_pair_step_sym(const StepArgs &a, int Smax, int64_t T, int blocks, bo
     int Sv = Smax;
     int64_t it = T;
     void *args[] = {(void *)&a, (void *)&Sv, (void *)&it};
-    cudaLaunchKernel(sym_kernel(stats, learned, seed), dim3(blocks), dim3(128), args,
-                     sym_smem(learned), s);
+    launch_pdl(sym_kernel(stats, learned, seed), dim3(blocks), dim3(128), args, sym_smem(learned),
+               s);
 }
 
 void launch_apply_sym(double *state, const double *X, const double *partial, int64_t n, int Smax,
                       int64_t W, int64_t T, double post_drift, unsigned *status, cudaStream_t s)
 {
-    apply_sym_kernel<<<dim3((unsigned)((n + 31) / 32), 3), 32 * kApplyWarps, 0, s>>>(
-        state, X, partial, n, Smax, W, T, post_drift, status);
+    void *args[] = {(void *)&state, (void *)&X,    (void *)&partial,    (void *)&n,
+                    (void *)&Smax,  (void *)&W,    (void *)&T,          (void *)&post_drift,
+                    (void *)&status};
+    launch_pdl((const void *)apply_sym_kernel, dim3((unsigned)((n + 31) / 32), 3),
+               dim3(32 * kApplyWarps), args, 0, s);
 }
 
 }  // namespace sakura
