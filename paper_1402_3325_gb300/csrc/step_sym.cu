@@ -32,7 +32,7 @@
 namespace sakura {
 
 template <bool STATS, bool LEARNED, bool SEED>
-__global__ void __launch_bounds__(128, LEARNED ? 2 : (SEED ? 3 : 4))
+__global__ void __launch_bounds__(128, (LEARNED || SEED) ? 2 : 4)
     pair_step_sym_kernel(StepArgs a, int Smax, int64_t T)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -265,6 +265,10 @@ int pair_step_sym_blocks_per_sm(bool stats, bool learned, bool seed)
         cudaGetLastError();
         return 1;
     }
+    // the seeded kernel runs fastest with 8 warps per SM (measured on GB300:
+    // 120.8 us at 2 blocks per SM against 123.1 at 3 and 139 at 1, Plummer
+    // N = 1024); the others with as many as fit
+    if (seed && b > 2) b = 2;
     return b > 0 ? b : 1;
 }
 
