@@ -740,8 +740,9 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
         const int64_t nk = host_offsets[k + 1] - host_offsets[k];
         pairs += nk * (nk - 1);
     }
+    // every unordered pair is solved once
     g.pairs += pairs * nsteps * a.nsub;
-    g.solves += pairs * nsteps * a.nsub;
+    g.solves += pairs / 2 * nsteps * a.nsub;
     if (g.cfg.flags & SAKURA_FLAG_SYNC_CHECK) return drain_status();
     return SAKURA_OK;
 }

@@ -5,18 +5,34 @@
 // synchronisation beyond its own lanes: the state lives in shared memory for
 // the whole launch.
 //
-// Schedule (built on the host when the offsets change): systems with N > 32
-// get a warp each (lane l owns rows l and l + 32); systems with N <= 32 are
-// packed first-fit-decreasing into warps with at most 32 particles in total
-// (one row per lane).  Tasks are sorted by cost and handed out through an
-// atomic counter (dynamic longest-first).
+// Each unordered pair is solved once (Newton's third law, as in the symmetric
+// single-system kernel): the increments of (i, j) and (j, i) are exact
+// negatives, so the solving lane adds m_j delta / m_ij to i and
+// -m_i delta / m_ij to j (Eq. 23).  A system of N >= 2 particles takes
+// h = floor(N / 2) lanes and walks its pairs in the round-robin ("circle")
+// order, so that its lanes x rounds equal its N (N - 1) / 2 pairs:
+//   N even, M = N - 1: round r = 0 .. M-1 pairs particle M with particle r
+//     (lane 0 of the system) and (r + k) mod M with (r - k) mod M (lane k =
+//     1 .. h-1);
+//   N odd: round r = 0 .. N-1 pairs (r + k) mod N with (r - k) mod N (lane
+//     k - 1 for k = 1 .. h); particle r sits the round out.
+// No particle is in two pairs of a round, so the lanes add to disjoint
+// accumulators (shared memory, in round order: deterministic); over the
+// rounds every unordered pair comes up exactly once.  A single particle
+// takes one lane and no rounds.
 //
-// Per step, per warp: each lane drifts its rows (Eq. 27a), then the lanes walk
-// their rows' j in ascending order in lockstep; every position of that walk is
-// one warp-synchronous FP64 Kepler solve of 32 pairs (same solver as the
-// single-system kernel); each lane accumulates m_j delta / m_ij for its rows
-// in registers (Eq. 23), and after a __syncwarp applies Eqs. 27b-d to its
-// rows in shared memory.  Each system keeps its own dt.
+// Schedule (built on the host when the offsets change): systems are packed
+// first-fit-decreasing into warps of at most 32 lanes and kBatchMaxN = 64
+// particles; a warp's lockstep length is the largest round count among its
+// systems.
+// Tasks are sorted by that length and handed out through an atomic counter
+// (dynamic longest-first).
+//
+// Per step, per warp: lane k of a system drifts its particles 2k and 2k + 1
+// (and the last particle of an odd system, on its last lane) (Eq. 27a),
+// the rounds run as warp-synchronous FP64 Kepler solves (same solver as the
+// single-system kernel), and after a __syncwarp each lane applies Eqs.
+// 27b-d to its particles.  Each system keeps its own dt.
 //
 // The counter reset and the launch form a CUDA graph that is built once per
 // (buffers, schedule, nsteps, order, launch shape) and replayed.  A small
@@ -41,9 +57,18 @@ namespace sakura {
 
 constexpr int kBatchMaxN = 64;
 
+// lanes and rounds of a system of N particles (see above)
+__host__ __device__ __forceinline__ int batch_lanes(int N) { return N < 2 ? 1 : N / 2; }
+__host__ __device__ __forceinline__ int batch_rounds(int N)
+{
+    return N < 2 ? 0 : ((N & 1) ? N : N - 1);
+}
+
 // SEED: the single-precision seed and the Taylor carry of the symmetric
 // FP64 kernel (float copies of the drifted state in shared memory, hi + lo
-// positions, refreshed after every drift)
+// positions, refreshed after every drift).
+// Dynamic shared memory: the accumulators [WARPS][6][kBatchMaxN] doubles,
+// then (LEARNED) the network and its per-warp staging.
 template <int WARPS, bool STATS, bool LEARNED, bool SEED>
 __global__ void __launch_bounds__(WARPS * 32)
     batched_kernel(BatchArgs a)
@@ -51,13 +76,16 @@ __global__ void __launch_bounds__(WARPS * 32)
     __shared__ double sh[WARPS][7][kBatchMaxN];
     __shared__ float sh32[WARPS][SEED ? 10 : 1][kBatchMaxN];
     extern __shared__ __align__(16) unsigned char dsm[];
-    MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(dsm);
-    __nv_bfloat16 *mlpStage = reinterpret_cast<__nv_bfloat16 *>(dsm + sizeof(MlpWeights));
+    double(*shacc)[6][kBatchMaxN] = reinterpret_cast<double(*)[6][kBatchMaxN]>(dsm);
+    unsigned char *dnet = dsm + (size_t)WARPS * 6 * kBatchMaxN * sizeof(double);
+    MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(dnet);
+    __nv_bfloat16 *mlpStage = reinterpret_cast<__nv_bfloat16 *>(dnet + sizeof(MlpWeights));
     if (LEARNED) mlp_load_shared(*mlpW, a.mlp);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     double(*S)[kBatchMaxN] = sh[wib];
     float(*S32)[kBatchMaxN] = sh32[wib];
+    double(*A)[kBatchMaxN] = shacc[wib];
     const int64_t tot = a.total;
     const KeplerParams kp{a.tol, a.max_iter, a.bisection};
     unsigned status = 0;
@@ -70,8 +98,11 @@ __global__ void __launch_bounds__(WARPS * 32)
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= a.ntasks) break;
         const int sb = a.task_begin[t], se = a.task_begin[t + 1];
-        int my_sys = -1, my_base = 0, my_N = 0, my_row = 0;
-        int base = 0;
+        // the lane's system: its particles at my_base .. my_base + my_N - 1,
+        // the lane's index my_k in the system (-1: no system)
+        int my_k = -1, my_base = 0, my_N = 0;
+        double dt = 0.0;
+        int base = 0, lbase = 0;
         for (int q = sb; q < se; ++q) {
             const int k = a.task_sys[q];
             const int64_t o0 = a.offsets[k];
@@ -83,24 +114,26 @@ __global__ void __launch_bounds__(WARPS * 32)
                 if (!(m > 0.0)) status |= kStatusMass;
                 S[6][base + pi] = m;
             }
-            if (Nk > 32) {
-                my_sys = k;
-                my_row = lane;
-                my_base = 0;
-                my_N = Nk;
-            } else if (lane >= base && lane < base + Nk) {
-                my_sys = k;
-                my_row = lane - base;
+            const int hk = batch_lanes(Nk);
+            if (lane >= lbase && lane < lbase + hk) {
+                my_k = lane - lbase;
                 my_base = base;
                 my_N = Nk;
+                dt = a.dt[k];
             }
             base += Nk;
+            lbase += hk;
         }
         __syncwarp();
-        const int nrows = my_sys < 0 ? 0 : (my_N > 32 ? (lane + 32 < my_N ? 2 : 1) : 1);
-        const double dt = my_sys >= 0 ? a.dt[my_sys] : 0.0;
-        const int mylen = nrows * (my_N - 1);
-        const int maxlen = __reduce_max_sync(0xffffffffu, mylen > 0 ? mylen : 0);
+        const bool odd = (my_N & 1) != 0;
+        const int rounds = my_k >= 0 ? batch_rounds(my_N) : 0;
+        const int M = odd ? my_N : my_N - 1;  // circle length
+        const int maxr = __reduce_max_sync(0xffffffffu, rounds);
+        // the lane's particles 2k, 2k + 1 (and, on the last lane of an odd
+        // system, 2k + 2 = N - 1): drift, accumulators, apply
+        const int np = my_k < 0 ? 0
+                                : (my_N < 2 ? 1
+                                            : 2 + ((odd && my_k == batch_lanes(my_N) - 1) ? 1 : 0));
 
         for (int64_t sub = 0; sub < (int64_t)a.nsteps * a.nsub; ++sub) {
             // sub-step sub % nsub of the composition (one sub-step for orders 2, 1, -1)
@@ -108,8 +141,8 @@ __global__ void __launch_bounds__(WARPS * 32)
             const double drift = a.drift_frac * tau;
             const double post_drift = a.post_drift_frac * tau;
             const double qtau = a.post * tau;
-            for (int r = 0; r < nrows; ++r) {
-                const int i = my_base + my_row + 32 * r;
+            for (int e = 0; e < np; ++e) {
+                const int i = my_base + 2 * my_k + e;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) S[c][i] = fma(S[3 + c][i], drift, S[c][i]);
                 if (SEED) {
@@ -122,24 +155,37 @@ __global__ void __launch_bounds__(WARPS * 32)
                     }
                     S32[9][i] = __double2float_rn(S[6][i]);
                 }
+#pragma unroll
+                for (int c = 0; c < 6; ++c) A[c][i] = 0.0;
             }
             __syncwarp();
             const float ptau32 = (float)(a.pre * tau), t32 = (float)tau;
-            double acc0[6] = {0, 0, 0, 0, 0, 0}, acc1[6] = {0, 0, 0, 0, 0, 0};
-            int r = 0, jp = 0;
-            for (int jj = 0; jj < maxlen; ++jj) {
-                const bool valid = jj < mylen;
+            for (int r = 0; r < maxr; ++r) {
+                // the lane's pair of round r (local indices)
+                int il = my_N, jl = 0;
+                if (r < rounds) {
+                    if (!odd && my_k == 0) {
+                        il = M;
+                        jl = r;
+                    } else {
+                        const int k = odd ? my_k + 1 : my_k;
+                        il = r + k;
+                        if (il >= M) il -= M;
+                        jl = r - k;
+                        if (jl < 0) jl += M;
+                    }
+                }
+                const bool valid = il < my_N;
+                const int i = my_base + il, j = my_base + jl;
                 PairSolve p;
-                double mj = 0.0;
+                double mi = 0.0, mj = 0.0;
                 if (valid) {
-                    const int il = my_row + 32 * r;
-                    const int jl = jp + (jp >= il ? 1 : 0);
-                    const int i = my_base + il, j = my_base + jl;
+                    mi = S[6][i];
                     mj = S[6][j];
-                    pair_setup(p, tau, S[6][i] + mj, S[0][i] - S[0][j], S[1][i] - S[1][j],
-                               S[2][i] - S[2][j], S[3][i] - S[3][j], S[4][i] - S[4][j],
-                               S[5][i] - S[5][j], a.pre, LEARNED ? 2 : a.guess);
+                    K32 o;
                     if (SEED) {
+                        // single-precision seed: the root of the FP32 solve of
+                        // the same pair (unless t is reduced modulo the period)
                         float dr[3], dv[3];
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
@@ -147,10 +193,21 @@ __global__ void __launch_bounds__(WARPS * 32)
                                               __fsub_rn(S32[3 + c][i], S32[3 + c][j]));
                             dv[c] = __fsub_rn(S32[6 + c][i], S32[6 + c][j]);
                         }
-                        const K32 o = k32_phase1(dr, dv, S32[9][i] + S32[9][j], ptau32, t32, 2);
+                        o = k32_phase1(dr, dv, S32[9][i] + S32[9][j], ptau32, t32, 2);
+                    }
+                    pair_setup(p, tau, mi + mj, S[0][i] - S[0][j], S[1][i] - S[1][j],
+                               S[2][i] - S[2][j], S[3][i] - S[3][j], S[4][i] - S[4][j],
+                               S[5][i] - S[5][j], a.pre, LEARNED ? 2 : (SEED ? 0 : a.guess));
+                    if (SEED) {
                         if (o.ok && __double_as_longlong(p.t) == __double_as_longlong(tau) &&
-                            !p.done)
+                            !p.done) {
                             p.s = (double)o.s;
+                        } else if (!p.done) {
+                            // no usable seed: the second-order guess, as
+                            // pair_setup computes it
+                            const double cq = 0.5 * p.s * (p.eta0 * p.ir0);
+                            if (magbits(cq) < 0x3fe0000000000000LL) p.s = fma(-cq, p.s, p.s);
+                        }
                     }
                 } else {
                     p.done = true;
@@ -164,18 +221,13 @@ __global__ void __launch_bounds__(WARPS * 32)
                 fp64_solve_warp<SEED>(p, valid, tau, qtau, kp, d, iters, fb);
                 if (STATS) carries += (valid && p.carried) ? 1 : 0;
                 if (valid) {
-                    if (r == 0) {
+                    // i and j are in no other lane's pair of this round
 #pragma unroll
-                        for (int q = 0; q < 6; ++q) acc0[q] = fma(mj, d[q], acc0[q]);
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 6; ++q) acc1[q] = fma(mj, d[q], acc1[q]);
+                    for (int q = 0; q < 6; ++q) {
+                        A[q][i] = fma(mj, d[q], A[q][i]);
+                        A[q][j] = fma(-mi, d[q], A[q][j]);
                     }
                     status |= p.status;
-                    if (++jp == my_N - 1) {
-                        jp = 0;
-                        ++r;
-                    }
                 }
                 if (STATS) {
                     it_sum += iters;
@@ -184,15 +236,14 @@ __global__ void __launch_bounds__(WARPS * 32)
                     const int wmax = __reduce_max_sync(0xffffffffu, iters);
                     if (lane == 0) slots += 32LL * wmax;
                 }
+                __syncwarp();  // the next round's lanes read these sums
             }
-            __syncwarp();
-            for (int rr = 0; rr < nrows; ++rr) {
-                const int i = my_base + my_row + 32 * rr;
-                const double *dd = rr == 0 ? acc0 : acc1;
+            for (int e = 0; e < np; ++e) {
+                const int i = my_base + 2 * my_k + e;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const double v1 = S[3 + c][i] + dd[3 + c];
-                    S[c][i] = fma(v1, post_drift, S[c][i] + dd[c]);
+                    const double v1 = S[3 + c][i] + A[3 + c][i];
+                    S[c][i] = fma(v1, post_drift, S[c][i] + A[c][i]);
                     S[3 + c][i] = v1;
                 }
             }
@@ -265,7 +316,18 @@ const void *batched_kernel_ptr(int warps, bool stats, bool learned, bool seed)
 
 size_t batched_dyn_smem(int warps, bool learned)
 {
-    return learned ? sizeof(MlpWeights) + (size_t)warps * 32 * 16 * 2 : 0;
+    return (size_t)warps * 6 * kBatchMaxN * sizeof(double) +
+           (learned ? sizeof(MlpWeights) + (size_t)warps * 32 * 16 * 2 : 0);
+}
+
+// kernel pointer, with its dynamic shared memory allowed (above 48 KB per
+// block with the static arrays for 8 warps)
+const void *batched_kernel_ready(int warps, bool stats, bool learned, bool seed)
+{
+    const void *fn = batched_kernel_ptr(warps, stats, learned, seed);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)batched_dyn_smem(warps, learned));
+    return fn;
 }
 
 }  // namespace
@@ -274,8 +336,8 @@ int batched_blocks_per_sm(int warps, bool stats, bool learned, bool seed)
 {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b,
-                                                      batched_kernel_ptr(warps, stats, learned,
-                                                                         seed),
+                                                      batched_kernel_ready(warps, stats, learned,
+                                                                           seed),
                                                       warps * 32,
                                                       batched_dyn_smem(warps, learned)) !=
         cudaSuccess) {
@@ -285,9 +347,10 @@ int batched_blocks_per_sm(int warps, bool stats, bool learned, bool seed)
     return b > 0 ? b : 1;
 }
 
-// Schedule: systems with N > 32 alone, the others packed first-fit-decreasing
-// into warps of at most 32 particles; tasks sorted by cost (lockstep length
-// (N-1) x rows per lane) so the atomic counter hands out the longest first.
+// Schedule: systems packed first-fit-decreasing into warps of at most 32
+// lanes (batch_lanes) and kBatchMaxN particles (the shared-memory state);
+// tasks sorted by cost (the lockstep length, the task's largest round count)
+// so the atomic counter hands out the longest first.
 void build_batch_schedule(const int64_t *offsets, int nsys, std::vector<int> &task_begin,
                           std::vector<int> &task_sys)
 {
@@ -296,31 +359,30 @@ void build_batch_schedule(const int64_t *offsets, int nsys, std::vector<int> &ta
     auto size = [&](int k) { return (int)(offsets[k + 1] - offsets[k]); };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return size(a) > size(b); });
     struct Bin {
-        int cap;
+        int lanes;  // free lanes
+        int room;   // free particle slots
         int cost;
         std::vector<int> sys;
     };
     std::vector<Bin> bins;
     for (int k : order) {
         const int N = size(k);
-        if (N > 32) {
-            bins.push_back({0, (N - 1) * 2, {k}});
-            continue;
-        }
+        const int h = batch_lanes(N), rounds = batch_rounds(N);
         bool placed = false;
         // first fit over the most recent bins (sizes are sorted, so earlier
         // bins are nearly full)
         const int from = std::max(0, (int)bins.size() - 64);
         for (int b = from; b < (int)bins.size(); ++b) {
-            if (bins[b].cap >= N && !bins[b].sys.empty() && size(bins[b].sys[0]) <= 32) {
-                bins[b].cap -= N;
+            if (bins[b].lanes >= h && bins[b].room >= N) {
+                bins[b].lanes -= h;
+                bins[b].room -= N;
                 bins[b].sys.push_back(k);
-                bins[b].cost = std::max(bins[b].cost, N - 1);
+                bins[b].cost = std::max(bins[b].cost, rounds);
                 placed = true;
                 break;
             }
         }
-        if (!placed) bins.push_back({32 - N, N - 1, {k}});
+        if (!placed) bins.push_back({32 - h, kBatchMaxN - N, rounds, {k}});
     }
     std::stable_sort(bins.begin(), bins.end(),
                      [](const Bin &a, const Bin &b) { return a.cost > b.cost; });
@@ -336,7 +398,7 @@ void launch_batched(const BatchArgs &a, int warps, int blocks, bool stats, cudaS
 {
     const bool learned = a.mlp != nullptr;
     void *args[] = {(void *)&a};
-    cudaLaunchKernel(batched_kernel_ptr(warps, stats, learned, a.seed != 0), dim3(blocks),
+    cudaLaunchKernel(batched_kernel_ready(warps, stats, learned, a.seed != 0), dim3(blocks),
                      dim3(warps * 32), args, batched_dyn_smem(warps, learned), s);
 }
 
@@ -361,7 +423,7 @@ cudaError_t build_batched_graph(const BatchArgs &a, int warps, int blocks, bool 
         void *args[] = {(void *)&copy};
         cudaKernelNodeParams kpar;
         std::memset(&kpar, 0, sizeof(kpar));
-        kpar.func = (void *)batched_kernel_ptr(warps, stats, a.mlp != nullptr, a.seed != 0);
+        kpar.func = (void *)batched_kernel_ready(warps, stats, a.mlp != nullptr, a.seed != 0);
         kpar.gridDim = dim3(blocks);
         kpar.blockDim = dim3(warps * 32);
         kpar.sharedMemBytes = (unsigned)batched_dyn_smem(warps, a.mlp != nullptr);

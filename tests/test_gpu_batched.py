@@ -95,8 +95,10 @@ def test_batched_fp32_seed_matches_oracle(order):
         got = run_batched(ens, order, 3)
         st = sk.get_stats(reset=True)
     check_against_oracle(ens, got, order, 3, 1e-11)
-    assert st["carries"] > 0.5 * st["pairs"]
-    assert st["iters"] < 1.5 * st["pairs"]
+    # each unordered pair is solved once
+    assert 2 * st["solves"] == st["pairs"]
+    assert st["carries"] > 0.5 * st["solves"]
+    assert st["iters"] < 1.5 * st["solves"]
 
 
 def test_batched_many_steps_matches_oracle():
