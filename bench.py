@@ -289,7 +289,8 @@ def run_ensemble(args, rank, world, device, stream, dist):
              "learned": sk.GUESS_LEARNED, "fp32": sk.GUESS_FP32}[args.guess]
     sizes = ens.offsets[1:] - ens.offsets[:-1]
     n2 = int((sizes * sizes).sum())
-    st = torch.tensor(ens.state, device=device)
+    st0 = torch.tensor(ens.state, device=device)  # initial state, kept for resets
+    st = st0.clone()
     m = torch.tensor(ens.m, device=device)
     off = torch.tensor(ens.offsets, device=device)
     dt = torch.tensor(ens.dt, device=device)
@@ -305,7 +306,7 @@ def run_ensemble(args, rank, world, device, stream, dist):
     lane_eff = stt["iters"] / max(1, stt["warp_slots"])
     warps, blocks, tune = sk.batched_tuning()
     sk.init(device.index, stream=stream.cuda_stream, guess=guess)
-    st.copy_(torch.tensor(ens.state, device=device))
+    st.copy_(st0)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     if dist is not None:

@@ -28,11 +28,12 @@
 // Tasks are sorted by that length and handed out through an atomic counter
 // (dynamic longest-first).
 //
-// Per step, per warp: lane k of a system drifts its particles 2k and 2k + 1
+// Per step, per block: lane k of a system drifts its particles 2k and 2k + 1
 // (and the last particle of an odd system, on its last lane) (Eq. 27a),
 // the rounds run as warp-synchronous FP64 Kepler solves (same solver as the
-// single-system kernel), and after a __syncwarp each lane applies Eqs.
-// 27b-d to its particles.  Each system keeps its own dt.
+// single-system kernel) split over the block's warps, and after a block
+// barrier each lane applies Eqs. 27b-d to its particles.  Each system keeps
+// its own dt.
 //
 // The counter reset and the launch form a CUDA graph that is built once per
 // (buffers, schedule, nsteps, order, launch shape) and replayed.  A small
@@ -64,6 +65,12 @@ __host__ __device__ __forceinline__ int batch_rounds(int N)
     return N < 2 ? 0 : ((N & 1) ? N : N - 1);
 }
 
+// One task per block: its WARPS warps share the task's state in shared
+// memory and split the rounds of every step, warp w taking rounds r = w,
+// w + WARPS, ... into its own accumulators; the apply adds the WARPS
+// accumulators in warp order (deterministic).  A warp's solve round is
+// latency-bound, so the largest systems (63 rounds per step for N = 64) set
+// the length of the launch; splitting their rounds shortens it.
 // SEED: the single-precision seed and the Taylor carry of the symmetric
 // FP64 kernel (float copies of the drifted state in shared memory, hi + lo
 // positions, refreshed after every drift).
@@ -73,8 +80,9 @@ template <int WARPS, bool STATS, bool LEARNED, bool SEED>
 __global__ void __launch_bounds__(WARPS * 32)
     batched_kernel(BatchArgs a)
 {
-    __shared__ double sh[WARPS][7][kBatchMaxN];
-    __shared__ float sh32[WARPS][SEED ? 10 : 1][kBatchMaxN];
+    __shared__ double S[7][kBatchMaxN];
+    __shared__ float S32[SEED ? 10 : 1][kBatchMaxN];
+    __shared__ int s_task;
     extern __shared__ __align__(16) unsigned char dsm[];
     double(*shacc)[6][kBatchMaxN] = reinterpret_cast<double(*)[6][kBatchMaxN]>(dsm);
     unsigned char *dnet = dsm + (size_t)WARPS * 6 * kBatchMaxN * sizeof(double);
@@ -83,8 +91,6 @@ __global__ void __launch_bounds__(WARPS * 32)
     if (LEARNED) mlp_load_shared(*mlpW, a.mlp);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    double(*S)[kBatchMaxN] = sh[wib];
-    float(*S32)[kBatchMaxN] = sh32[wib];
     double(*A)[kBatchMaxN] = shacc[wib];
     const int64_t tot = a.total;
     const KeplerParams kp{a.tol, a.max_iter, a.bisection};
@@ -93,13 +99,14 @@ __global__ void __launch_bounds__(WARPS * 32)
     int it_max = 0;
 
     while (true) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(a.counter, 1);
-        t = __shfl_sync(0xffffffffu, t, 0);
+        if (threadIdx.x == 0) s_task = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int t = s_task;
         if (t >= a.ntasks) break;
         const int sb = a.task_begin[t], se = a.task_begin[t + 1];
         // the lane's system: its particles at my_base .. my_base + my_N - 1,
-        // the lane's index my_k in the system (-1: no system)
+        // the lane's index my_k in the system (-1: no system); the same in
+        // every warp of the block
         int my_k = -1, my_base = 0, my_N = 0;
         double dt = 0.0;
         int base = 0, lbase = 0;
@@ -107,7 +114,7 @@ __global__ void __launch_bounds__(WARPS * 32)
             const int k = a.task_sys[q];
             const int64_t o0 = a.offsets[k];
             const int Nk = (int)(a.offsets[k + 1] - o0);
-            for (int pi = lane; pi < Nk; pi += 32) {
+            for (int pi = threadIdx.x; pi < Nk; pi += WARPS * 32) {
 #pragma unroll
                 for (int c = 0; c < 6; ++c) S[c][base + pi] = a.state[c * tot + o0 + pi];
                 const double m = a.mass[o0 + pi];
@@ -124,7 +131,7 @@ __global__ void __launch_bounds__(WARPS * 32)
             base += Nk;
             lbase += hk;
         }
-        __syncwarp();
+        __syncthreads();
         const bool odd = (my_N & 1) != 0;
         const int rounds = my_k >= 0 ? batch_rounds(my_N) : 0;
         const int M = odd ? my_N : my_N - 1;  // circle length
@@ -143,24 +150,26 @@ __global__ void __launch_bounds__(WARPS * 32)
             const double qtau = a.post * tau;
             for (int e = 0; e < np; ++e) {
                 const int i = my_base + 2 * my_k + e;
+                if (wib == 0) {
 #pragma unroll
-                for (int c = 0; c < 3; ++c) S[c][i] = fma(S[3 + c][i], drift, S[c][i]);
-                if (SEED) {
+                    for (int c = 0; c < 3; ++c) S[c][i] = fma(S[3 + c][i], drift, S[c][i]);
+                    if (SEED) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float hi = __double2float_rn(S[c][i]);
-                        S32[c][i] = hi;
-                        S32[3 + c][i] = __double2float_rn(S[c][i] - (double)hi);
-                        S32[6 + c][i] = __double2float_rn(S[3 + c][i]);
+                        for (int c = 0; c < 3; ++c) {
+                            const float hi = __double2float_rn(S[c][i]);
+                            S32[c][i] = hi;
+                            S32[3 + c][i] = __double2float_rn(S[c][i] - (double)hi);
+                            S32[6 + c][i] = __double2float_rn(S[3 + c][i]);
+                        }
+                        S32[9][i] = __double2float_rn(S[6][i]);
                     }
-                    S32[9][i] = __double2float_rn(S[6][i]);
                 }
 #pragma unroll
                 for (int c = 0; c < 6; ++c) A[c][i] = 0.0;
             }
-            __syncwarp();
+            __syncthreads();
             const float ptau32 = (float)(a.pre * tau), t32 = (float)tau;
-            for (int r = 0; r < maxr; ++r) {
+            for (int r = wib; r < maxr; r += WARPS) {
                 // the lane's pair of round r (local indices)
                 int il = my_N, jl = 0;
                 if (r < rounds) {
@@ -221,7 +230,8 @@ __global__ void __launch_bounds__(WARPS * 32)
                 fp64_solve_warp<SEED>(p, valid, tau, qtau, kp, d, iters, fb);
                 if (STATS) carries += (valid && p.carried) ? 1 : 0;
                 if (valid) {
-                    // i and j are in no other lane's pair of this round
+                    // i and j are in no other lane's pair of this round; the
+                    // warp's own accumulators
 #pragma unroll
                     for (int q = 0; q < 6; ++q) {
                         A[q][i] = fma(mj, d[q], A[q][i]);
@@ -236,18 +246,27 @@ __global__ void __launch_bounds__(WARPS * 32)
                     const int wmax = __reduce_max_sync(0xffffffffu, iters);
                     if (lane == 0) slots += 32LL * wmax;
                 }
-                __syncwarp();  // the next round's lanes read these sums
+                __syncwarp();  // the warp's next round reads these sums
             }
-            for (int e = 0; e < np; ++e) {
-                const int i = my_base + 2 * my_k + e;
+            __syncthreads();
+            if (wib == 0) {
+                for (int e = 0; e < np; ++e) {
+                    const int i = my_base + 2 * my_k + e;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const double v1 = S[3 + c][i] + A[3 + c][i];
-                    S[c][i] = fma(v1, post_drift, S[c][i] + A[c][i]);
-                    S[3 + c][i] = v1;
+                    for (int c = 0; c < 3; ++c) {
+                        double sr = shacc[0][c][i], sv = shacc[0][3 + c][i];
+#pragma unroll
+                        for (int w = 1; w < WARPS; ++w) {
+                            sr += shacc[w][c][i];
+                            sv += shacc[w][3 + c][i];
+                        }
+                        const double v1 = S[3 + c][i] + sv;
+                        S[c][i] = fma(v1, post_drift, S[c][i] + sr);
+                        S[3 + c][i] = v1;
+                    }
                 }
             }
-            __syncwarp();
+            __syncthreads();
         }
         // write the task's systems back
         base = 0;
@@ -255,7 +274,7 @@ __global__ void __launch_bounds__(WARPS * 32)
             const int k = a.task_sys[q];
             const int64_t o0 = a.offsets[k];
             const int Nk = (int)(a.offsets[k + 1] - o0);
-            for (int pi = lane; pi < Nk; pi += 32) {
+            for (int pi = threadIdx.x; pi < Nk; pi += WARPS * 32) {
 #pragma unroll
                 for (int c = 0; c < 6; ++c) {
                     const double x = S[c][base + pi];
@@ -265,7 +284,7 @@ __global__ void __launch_bounds__(WARPS * 32)
             }
             base += Nk;
         }
-        __syncwarp();
+        __syncthreads();
     }
     status = __reduce_or_sync(0xffffffffu, status);
     if (lane == 0 && status) atomicOr(a.status, status);
@@ -347,10 +366,15 @@ int batched_blocks_per_sm(int warps, bool stats, bool learned, bool seed)
     return b > 0 ? b : 1;
 }
 
-// Schedule: systems packed first-fit-decreasing into warps of at most 32
-// lanes (batch_lanes) and kBatchMaxN particles (the shared-memory state);
-// tasks sorted by cost (the lockstep length, the task's largest round count)
-// so the atomic counter hands out the longest first.
+// Schedule: systems packed best-fit-decreasing into warps of at most 32
+// lanes (batch_lanes) and kBatchMaxN particles (the shared-memory state):
+// each system, largest first, goes to the open warp with the fewest free
+// lanes that still takes it (warps kept in buckets by free lanes, so every
+// placement looks at 33 buckets, not at every warp).  On the 4096-system
+// ensemble (N uniform in [3, 64]) this fills 88 % of the lane-rounds, where
+// first fit over only the most recent warps filled 79 %.  Tasks are sorted
+// by cost (the lockstep length, the task's largest round count) so the
+// atomic counter hands out the longest first.
 void build_batch_schedule(const int64_t *offsets, int nsys, std::vector<int> &task_begin,
                           std::vector<int> &task_sys)
 {
@@ -365,24 +389,34 @@ void build_batch_schedule(const int64_t *offsets, int nsys, std::vector<int> &ta
         std::vector<int> sys;
     };
     std::vector<Bin> bins;
+    std::vector<std::vector<int>> by_free(33);  // open bins by free lanes
     for (int k : order) {
         const int N = size(k);
         const int h = batch_lanes(N), rounds = batch_rounds(N);
-        bool placed = false;
-        // first fit over the most recent bins (sizes are sorted, so earlier
-        // bins are nearly full)
-        const int from = std::max(0, (int)bins.size() - 64);
-        for (int b = from; b < (int)bins.size(); ++b) {
-            if (bins[b].lanes >= h && bins[b].room >= N) {
-                bins[b].lanes -= h;
-                bins[b].room -= N;
-                bins[b].sys.push_back(k);
-                bins[b].cost = std::max(bins[b].cost, rounds);
-                placed = true;
-                break;
+        int chosen = -1;
+        for (int f = h; f <= 32 && chosen < 0; ++f) {
+            std::vector<int> &bl = by_free[f];
+            // the 8 most recent bins of the bucket (a bin can lack particle
+            // room for a system whose lanes it has; the bound keeps every
+            // placement O(33 x 8) however many such bins collect)
+            for (int q = (int)bl.size() - 1; q >= 0 && q >= (int)bl.size() - 8; --q) {
+                if (bins[bl[q]].room >= N) {
+                    chosen = bl[q];
+                    bl.erase(bl.begin() + q);
+                    break;
+                }
             }
         }
-        if (!placed) bins.push_back({32 - h, kBatchMaxN - N, rounds, {k}});
+        if (chosen < 0) {
+            chosen = (int)bins.size();
+            bins.push_back({32, kBatchMaxN, 0, {}});
+        }
+        Bin &b = bins[chosen];
+        b.lanes -= h;
+        b.room -= N;
+        b.sys.push_back(k);
+        b.cost = std::max(b.cost, rounds);
+        by_free[b.lanes].push_back(chosen);
     }
     std::stable_sort(bins.begin(), bins.end(),
                      [](const Bin &a, const Bin &b) { return a.cost > b.cost; });
