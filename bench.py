@@ -54,9 +54,9 @@ UNIT = "pair-solves/s"
 # from paper_1402_3325_gb300/csrc/{step_fp64.cu,kepler_fp64.cuh}: FMA = 2,
 # add/sub/mul = 1 (comparisons run on the integer pipe and are not counted).
 #   C_FIX  = relative state and m_ij (7) + setup: backward drift, r0 and 1/r0
-#            by seeded third-order refinement, eta0, v0^2, beta, zeta0 and the
-#            second-order guess (49) + Lagrange epilogue (26) + m_j-weighted
-#            accumulation (12)
+#            by seeded third-order refinement, eta0, v0^2, beta (2 m_ij by an
+#            exponent add), zeta0 and the second-order guess (48) + Lagrange
+#            epilogue (26) + m_j-weighted accumulation (12)
 #   C_EVAL = one evaluation: beta s^2 (1), 3-term Stumpff series (12),
 #            G-functions (5), F, F', F'' (13), 1/F' (6), Newton step and
 #            convergence test (3)
@@ -64,20 +64,22 @@ UNIT = "pair-solves/s"
 # per pair: C_FIX + kbar * C_EVAL + (kbar - 1) * C_STEP, kbar = measured mean
 # evaluations.  ncu cross-check (profiles/pair_step_fp64_plummer1024.md):
 # 191 FP64 flops per pair executed, 4 % above this count.
-C_FIX = 94
+C_FIX = 93
 C_EVAL = 40
 C_STEP = 6
 # the symmetric mode adds the column accumulation (6 FMA) to every solve
 C_SYM = 12
 # a solve finished by the Taylor carry (single-precision seed): one more
 # Laguerre correction (C_STEP) and the carry of G1..G3 and F' with a new
-# 1/F' (29: h2 (2), dF''/ds (4), three G's and F' (17), reciprocal (6))
-C_CARRY = 29
-# the seeded solve skips the second-order guess (4) and the tolerance test's
-# product (1), takes its near-root step in Halley form (the same count),
-# scales the carry test by |s| (1) and forms the step's 1/F' by one
-# quadratic refinement (2)
-C_SEED_SAVED = 8
+# 1/F' (28: h2 (1; the half by an exponent add), dF''/ds (4), three G's and
+# F' (17), reciprocal (6))
+C_CARRY = 28
+# the seeded solve skips the standard (1) and second-order (4) guesses and
+# the tolerance test's product (1), takes its near-root step in Halley form
+# (the same count, less the half of q done by an exponent add: 1), scales
+# the carry test by |s| (1) and forms the step's 1/F' by one quadratic
+# refinement (2)
+C_SEED_SAVED = 10
 # FP32-class pair of the symmetric mixed form (see the roofline code below)
 C_MIX32_FIX = 46 + 34 + 156
 C_MIX32_ITER = 53

@@ -58,6 +58,8 @@
 
 #include <cstdint>
 
+#include "fp_bits.cuh"
+
 namespace sakura {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -225,7 +227,8 @@ struct PairSolve {
 
 // Setup of one pair: backward drift, invariants, period reduction, guess.
 // rr0, vv0: relative state after the one-subscript drift; m: m_i + m_j.
-// guess: 0 = standard s0 = t/r0; 2 = second order in t, s0 = (t/r0)(1 -
+// guess: -1 = none (the caller sets s; s = 0 here); 0 = standard s0 = t/r0;
+// 2 = second order in t, s0 = (t/r0)(1 -
 // eta0 t / (2 r0^2)), from ds/dt = 1/r and d2s/dt2 = -eta0/r0^3 at t = 0;
 // when the correction exceeds 1/2 in size (fast radial motion over the
 // step) the expansion is not trusted and the standard guess is used.
@@ -263,7 +266,7 @@ __device__ __forceinline__ void pair_setup(PairSolve &p, double tau, double m, d
     p.ir = p.ir0;
     p.eta0 = fma(p.x0, vx, fma(p.y0, vy, p.z0 * vz));
     const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
-    p.beta = fma(2.0 * m, p.ir0, -v2);
+    p.beta = fma(scale2(m, 1), p.ir0, -v2);
     p.zeta0 = fma(-p.beta, p.r0, m);
     p.t = tau;
     // bound orbit with |t| > P = 2 pi m / beta^1.5  <=>  t^2 beta^3 > (2 pi m)^2
@@ -275,7 +278,7 @@ __device__ __forceinline__ void pair_setup(PairSolve &p, double tau, double m, d
             p.t = fmod(tau, P);
         }
     }
-    p.s = p.t * p.ir0;  // standard initial guess
+    p.s = guess < 0 ? 0.0 : p.t * p.ir0;  // standard initial guess
     if (guess == 2) {
         const double c = 0.5 * p.s * (p.eta0 * p.ir0);  // eta0 t / (2 r0^2)
         if (magbits(c) < 0x3fe0000000000000LL) p.s = fma(-c, p.s, p.s);  // |c| < 1/2
@@ -346,7 +349,7 @@ __device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, double s2, 
         // |u| < 2^-10 (a root next to the seed): the Laguerre step
         // q (1 + k) with k = u / 2.5 + O(u^2), Halley's correction, whose
         // cubic error is far below round-off here
-        step = fma(0.5 * q, qh, q);
+        step = fma(scale2(q, -1), qh, q);
     } else {
         const float u = (float)(1.25 * qh);
         const float r = sqrt_approx(fabsf(1.0f - u));
@@ -363,7 +366,7 @@ __device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, double s2, 
     // evaluating at the new point
     const long long sc20 = sc > (20LL << 52) ? sc - (20LL << 52) : 0;
     if (CARRY && magbits(step) <= sc20) {
-        const double h2 = 0.5 * step * step;
+        const double h2 = scale2(step * step, -1);
         const double F3 = fma(-p.eta0 * p.beta, G1, p.zeta0 * c.c0);  // dF''/ds
         p.G3 = fma(h2, G1, fma(-step, G2, G3));
         p.G2 = fma(h2, c.c0, fma(-step, G1, G2));

@@ -206,14 +206,15 @@ __global__ void __launch_bounds__(WARPS * 32)
                     }
                     pair_setup(p, tau, mi + mj, S[0][i] - S[0][j], S[1][i] - S[1][j],
                                S[2][i] - S[2][j], S[3][i] - S[3][j], S[4][i] - S[4][j],
-                               S[5][i] - S[5][j], a.pre, LEARNED ? 2 : (SEED ? 0 : a.guess));
+                               S[5][i] - S[5][j], a.pre, LEARNED ? 2 : (SEED ? -1 : a.guess));
                     if (SEED) {
                         if (o.ok && __double_as_longlong(p.t) == __double_as_longlong(tau) &&
                             !p.done) {
-                            p.s = (double)o.s;
+                            p.s = f2d(o.s);
                         } else if (!p.done) {
                             // no usable seed: the second-order guess, as
                             // pair_setup computes it
+                            p.s = p.t * p.ir0;
                             const double cq = 0.5 * p.s * (p.eta0 * p.ir0);
                             if (magbits(cq) < 0x3fe0000000000000LL) p.s = fma(-cq, p.s, p.s);
                         }

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED) ? 2 : 4)
                 mj = X[6 * n + j];
                 pair_setup(p, a.tau, mi + mj, xi - X[j], yi - X[n + j], zi - X[2 * n + j],
                            vxi - X[3 * n + j], vyi - X[4 * n + j], vzi - X[5 * n + j], a.pre,
-                           LEARNED ? 2 : (SEED ? 0 : a.guess));
+                           LEARNED ? 2 : (SEED ? -1 : a.guess));
                 if (SEED) {
                     // single-precision seed: the root of the FP32 solve of the
                     // same pair (unless t was reduced modulo the period)
@@ -110,10 +110,11 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED) ? 2 : 4)
                     const K32 o = k32_phase1(dr, dv, m32i + X32[9 * n + j], a.ptau32, a.t32, 2);
                     if (o.ok && __double_as_longlong(p.t) == __double_as_longlong(a.tau) &&
                         !p.done) {
-                        p.s = (double)o.s;
+                        p.s = f2d(o.s);
                     } else if (!p.done) {
                         // no usable seed: the second-order guess, as pair_setup
                         // computes it
+                        p.s = p.t * p.ir0;
                         const double cq = 0.5 * p.s * (p.eta0 * p.ir0);
                         if (magbits(cq) < 0x3fe0000000000000LL) p.s = fma(-cq, p.s, p.s);
                     }
