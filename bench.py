@@ -94,7 +94,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 # the library's double-word code on the host with an operation tally over the
 # pairs of each workload's first step (tests/df64_flop_count.py; a CPU test
 # checks these figures against the current code)
-DF64_FLOPS_PER_SOLVE = {"plummer1024": 1919.3, "bh16384": 1914.0, "binaries16384": 1914.2}
+DF64_FLOPS_PER_SOLVE = {"plummer1024": 1922.0, "bh16384": 1922.0, "binaries16384": 1922.0}
 
 
 def max_over_ranks(x: float, dist=None, device=None) -> float:

@@ -8,8 +8,8 @@
 //
 //   1. FP32: the Kepler input from the leading float of each exact
 //      double-word difference, then Laguerre iterations in single precision
-//      until |F/F'| <= 4 eps32 max(|s|, |t/F'|) (k32_solve).  This finds the
-//      root to about 1e-7.
+//      until a step falls below 2^-8 of max(|s|, |t/F'|) (k32_solve).  This
+//      finds the root to about 1e-7.
 //   2. Double-word (df64.cuh): the Kepler input (backward drift, r0, 1/r0,
 //      eta0, beta, zeta0), F, F' and F'' at s in double-word arithmetic and
 //      one Laguerre correction ds = q (1 + k), q = F / F' in double-word form
@@ -88,9 +88,9 @@ DW_HD float stumpff32_terms(float x, float &c0, float &c1, float &c2)
 
 // Laguerre iterations in FP32 from the standard (guess 0) or second-order
 // (guess 2) initial value (approximate reciprocals: this phase only needs
-// the root to about 1e-7).  It stops at the Newton-step test or after a
-// Laguerre step below 2^-8 of the scale, so a lane close to its root takes
-// one evaluation and the warp seldom waits for a second.
+// the root to about 1e-7).  It stops after a Laguerre step below 2^-8 of
+// the scale (the step taken), so a lane close to its root takes one
+// evaluation and the warp seldom waits for a second.
 DW_HD K32 k32_solve(float r0, float ir0, float eta, float beta, float zeta, float t, int guess)
 {
     K32 o;
@@ -100,7 +100,6 @@ DW_HD K32 k32_solve(float r0, float ir0, float eta, float beta, float zeta, floa
         const float c = fmul(fmul(0.5f, s), fmul(eta, ir0));
         if (fabsf(c) < 0.5f) s = ffma(-c, s, s);
     }
-    const float tol = 4.0f * 1.1920929e-7f;
     o.ok = false;
     o.iters = 0;
     for (int it = 0; it < kDwFp32MaxIter; ++it) {
@@ -115,10 +114,8 @@ DW_HD K32 k32_solve(float r0, float ir0, float eta, float beta, float zeta, floa
         const float q = fmul(F, ir);
         ++o.iters;
         if (!(fabsf(q) <= 1e30f)) break;  // overflow or NaN
-        if (fabsf(q) <= fmul(tol, fmaxf(fabsf(s), fabsf(fmul(t, ir))))) {
-            o.ok = true;
-            break;
-        }
+        // (no separate |q| test: a lane at its root takes a step of a few
+        // ulps and stops below, so every lane follows one path)
         const float u = fmul(fmul(1.25f, q), fmul(Fpp, ir));
         const float den = ffma(4.0f, fsqrt_approx(fabsf(fsub(1.0f, u))), 1.0f);
         const float step = fmul(fmul(5.0f, q), rcp_approx(den));

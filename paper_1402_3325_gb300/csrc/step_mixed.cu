@@ -213,13 +213,18 @@ template <bool STATS>
 __global__ void __launch_bounds__(128)
     pair_step_sym_mixed_kernel(StepArgs a, MixedArgs ma, int Smax, int64_t T)
 {
-    __shared__ int queue[4][64];
+    // FP64-class pairs wait in a per-warp queue (global i, j) until 32 have
+    // collected or the warp's range ends, so that the FP64 solves run with
+    // every lane busy: a queue flushed at every segment end ran mostly
+    // single-lane solves (13 % of the kernel on GB300).  (Flushing queues of
+    // 8 or more at segment ends was slower under both class rules.)
+    __shared__ int queue_i[4][64], queue_j[4][64];
     __shared__ float2 qres[4][32][12];  // queued results as double-words
     griddep_wait();    // X and X32 from the prep kernel
     griddep_launch();  // the apply kernel may begin launching
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    int *qw = queue[wib];
+    int *qi = queue_i[wib], *qj = queue_j[wib];
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n = a.n;
     const int64_t W = (int64_t)gridDim.x * 4;
@@ -229,6 +234,112 @@ __global__ void __launch_bounds__(128)
     unsigned status = 0;
     long long it_sum = 0, slots = 0, fallbacks = 0, n32 = 0;
     int it_max = 0;
+    int tail = 0;  // queued pairs
+
+    // FP64 solve of queue entries 0..cnt-1.  Entries of the current tile
+    // (I, J) at step kc are added to the row owners' and column holders'
+    // double-word sums, in queue order; entries of the warp's earlier
+    // segments are added to those segments' FP64 partials, which this warp
+    // wrote and no other warp touches, in queue order where two entries meet
+    // the same element (passes by rank among equal targets).
+    auto flush = [&](int64_t I, int64_t J, bool diag, int kc, int cnt, dw racc[6], dw cacc[6]) {
+        const bool vq = lane < cnt;
+        const int64_t iq = vq ? qi[lane] : 0, jq = vq ? qj[lane] : 0;
+        const bool cur = vq && (iq >> 5) == I && (jq >> 5) == J;
+        PairSolve p;
+        double miq = 0.0, mjq = 0.0;
+        if (vq) {
+            const double *X = a.X;
+            miq = X[6 * n + iq];
+            mjq = X[6 * n + jq];
+            pair_setup(p, a.tau, miq + mjq, X[iq] - X[jq], X[n + iq] - X[n + jq],
+                       X[2 * n + iq] - X[2 * n + jq], X[3 * n + iq] - X[3 * n + jq],
+                       X[4 * n + iq] - X[4 * n + jq], X[5 * n + iq] - X[5 * n + jq], a.pre,
+                       a.guess);
+        } else {
+            p.done = true;
+            p.beta = p.s = 0.0;
+            p.iters = 0;
+            p.status = 0;
+        }
+        double d[6];
+        int iters = 0, fb = 0;
+        fp64_solve_warp(p, vq, a.tau, a.post * a.tau, kp, d, iters, fb);
+        double xr[6], xc[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            xr[q] = mjq * d[q];
+            xc[q] = -miq * d[q];
+        }
+        if (vq) status |= p.status;
+        if (cur) {
+            // converted to double-words here, with every lane active (the
+            // owners below add them one lane at a time)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const float rh = __double2float_rn(xr[q]), ch = __double2float_rn(xc[q]);
+                qres[wib][lane][q] = make_float2(rh, __double2float_rn(xr[q] - (double)rh));
+                qres[wib][lane][6 + q] = make_float2(ch, __double2float_rn(xc[q] - (double)ch));
+            }
+        }
+        if (STATS) {
+            it_sum += iters;
+            fallbacks += fb;
+            it_max = max(it_max, iters);
+            const int wmax = __reduce_max_sync(0xffffffffu, iters);
+            if (lane == 0) slots += 32LL * wmax;
+        }
+        __syncwarp();
+        if (__any_sync(0xffffffffu, cur)) {
+            const int mycol = (lane + kc) & 31;
+            for (int q = 0; q < cnt; ++q) {
+                const int ie = qi[q], je = qj[q];
+                if ((ie >> 5) != I || (je >> 5) != J) continue;
+                if ((ie & 31) == lane) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        const float2 x = qres[wib][q][c];
+                        dw_acc(racc[c], dw{x.x, x.y});
+                    }
+                }
+                if (!diag && (je & 31) == mycol) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) {
+                        const float2 x = qres[wib][q][6 + c];
+                        dw_acc(cacc[c], dw{x.x, x.y});
+                    }
+                }
+            }
+        }
+        const bool old = vq && !cur;
+        if (__any_sync(0xffffffffu, old)) {
+            // the entry's tile and this warp's segment of it
+            const int64_t Iq = iq >> 5, Jq = jq >> 5;
+            const int64_t tq = Jq * (Jq + 1) / 2 + Iq;
+            const int64_t hq = old ? w - sym_owner(32 * tq, W, T) : 0;
+            const bool dq = Iq == Jq;
+            for (int side = 0; side < 2; ++side) {
+                const bool act = old && (side == 0 || !dq);
+                // target element: slot (other block, segment) of particle
+                const int64_t slot = side == 0 ? Jq * Smax + hq : Iq * Smax + hq;
+                const int64_t part = side == 0 ? iq : jq;
+                const long long key = act ? (long long)(slot * n + part) : -1 - (long long)lane;
+                const unsigned same = __match_any_sync(0xffffffffu, key);
+                const int rank = __popc(same & lt_mask);
+                const int passes = __reduce_max_sync(0xffffffffu, act ? rank : 0);
+                for (int pass = 0; pass <= passes; ++pass) {
+                    if (act && rank == pass) {
+                        double *dst = a.partial + slot * 6 * n + part;
+#pragma unroll
+                        for (int c = 0; c < 6; ++c)
+                            dst[c * n] += side == 0 ? xr[c] : xc[c];
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+        __syncwarp();
+    };
 
     const int64_t p1 = (w + 1) * T / W;
     for (int64_t pos = w * T / W; pos < p1;) {
@@ -255,73 +366,6 @@ __global__ void __launch_bounds__(128)
         dw racc[6], cacc[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) racc[q] = cacc[q] = dw{0.0f, 0.0f};
-        int tail = 0;
-
-        // FP64 solve of queue entries 0..cnt-1 at step kc, results added to
-        // the row owners and the lanes holding the columns, in queue order
-        auto flush = [&](int kc, int cnt) {
-            const bool vq = lane < cnt;
-            const int e = vq ? qw[lane] : 0;
-            const int64_t iq = 32 * I + (e & 31), jq = 32 * J + (e >> 5);
-            PairSolve p;
-            double miq = 0.0, mjq = 0.0;
-            if (vq) {
-                const double *X = a.X;
-                miq = X[6 * n + iq];
-                mjq = X[6 * n + jq];
-                pair_setup(p, a.tau, miq + mjq, X[iq] - X[jq], X[n + iq] - X[n + jq],
-                           X[2 * n + iq] - X[2 * n + jq], X[3 * n + iq] - X[3 * n + jq],
-                           X[4 * n + iq] - X[4 * n + jq], X[5 * n + iq] - X[5 * n + jq], a.pre,
-                           a.guess);
-            } else {
-                p.done = true;
-                p.beta = p.s = 0.0;
-                p.iters = 0;
-                p.status = 0;
-            }
-            double d[6];
-            int iters = 0, fb = 0;
-            fp64_solve_warp(p, vq, a.tau, a.post * a.tau, kp, d, iters, fb);
-            if (vq) {
-                // converted to double-words here, with every lane active (the
-                // owners below add them one lane at a time)
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const double xr = mjq * d[q], xc = -miq * d[q];
-                    const float rh = __double2float_rn(xr), ch = __double2float_rn(xc);
-                    qres[wib][lane][q] = make_float2(rh, __double2float_rn(xr - (double)rh));
-                    qres[wib][lane][6 + q] = make_float2(ch, __double2float_rn(xc - (double)ch));
-                }
-                status |= p.status;
-            }
-            if (STATS) {
-                it_sum += iters;
-                fallbacks += fb;
-                it_max = max(it_max, iters);
-                const int wmax = __reduce_max_sync(0xffffffffu, iters);
-                if (lane == 0) slots += 32LL * wmax;
-            }
-            __syncwarp();
-            const int mycol = (lane + kc) & 31;
-            for (int q = 0; q < cnt; ++q) {
-                const int eq = qw[q];
-                if ((eq & 31) == lane) {
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        const float2 x = qres[wib][q][c];
-                        dw_acc(racc[c], dw{x.x, x.y});
-                    }
-                }
-                if (!diag && (eq >> 5) == mycol) {
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        const float2 x = qres[wib][q][6 + c];
-                        dw_acc(cacc[c], dw{x.x, x.y});
-                    }
-                }
-            }
-            __syncwarp();
-        };
 
         for (int k = k0; k < k1; ++k) {
             const int c = (lane + k) & 31;
@@ -363,15 +407,20 @@ __global__ void __launch_bounds__(128)
             }
             const bool need64 = valid && !solved32;
             const unsigned mask = __ballot_sync(0xffffffffu, need64);
-            if (need64) qw[tail + __popc(mask & lt_mask)] = lane | (c << 5);
+            if (need64) {
+                qi[tail + __popc(mask & lt_mask)] = (int)i;
+                qj[tail + __popc(mask & lt_mask)] = (int)j;
+            }
             tail += __popc(mask);
             __syncwarp();
-            while (tail >= 32 || (k + 1 == k1 && tail > 0)) {
-                const int cnt = min(tail, 32);
-                flush(k, cnt);
-                if (lane < tail - cnt) qw[lane] = qw[cnt + lane];
+            if (tail >= 32) {
+                flush(I, J, diag, k, 32, racc, cacc);
+                if (lane < tail - 32) {
+                    qi[lane] = qi[32 + lane];
+                    qj[lane] = qj[32 + lane];
+                }
                 __syncwarp();
-                tail -= cnt;
+                tail -= 32;
             }
             if (!diag && k + 1 < k1) {
 #pragma unroll
@@ -396,6 +445,12 @@ __global__ void __launch_bounds__(128)
                     dst[q * n + jc] = (double)cacc[q].h + (double)cacc[q].l;
             }
         }
+        __syncwarp();
+    }
+    // the pairs still queued belong to written segments
+    if (tail > 0) {
+        dw none[6];
+        flush(-1, -1, false, 0, tail, none, none);
     }
     status = __reduce_or_sync(0xffffffffu, status);
     if (lane == 0 && status) atomicOr(a.status, status);
