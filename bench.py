@@ -81,8 +81,8 @@ C_CARRY = 28
 # refinement (2)
 C_SEED_SAVED = 10
 # FP32-class pair of the symmetric mixed form (see the roofline code below)
-C_MIX32_FIX = 46 + 34 + 156
-C_MIX32_ITER = 53
+C_MIX32_FIX = 46 + 44 + 168
+C_MIX32_ITER = 71
 
 # FP64 ALU peak of one GB300: 152 SMs x 2 FP64 FMA units x 2 flop x 2.07 GHz
 # (the unit count follows from the nominal 1.25 TFLOP/s at 2.07 GHz).
@@ -621,10 +621,14 @@ def main():
     elif args.form == "mixed" and args.pairs == "symmetric" and fp32_share >= 0.5:
         # FP32 flops of an FP32-class unordered pair (hand count from
         # csrc/kepler_fp32.cuh and csrc/step_mixed.cu, FMA = 2): class test
-        # 46, solve setup and epilogue 34, per Laguerre iteration 53 (the last
-        # one stops at the test, -11), double-word sums of m_j d and -m_i d
-        # 156; kbar = single-precision iterations per solve
-        flops_solve = fp32_share * (C_MIX32_FIX + kbar * C_MIX32_ITER - 11.0)
+        # 46, solve setup 12, epilogue with increments and finiteness test 32,
+        # per Laguerre iteration 71 (evaluation 37, step 9, stopping test 2,
+        # carry of G1..G3 and F' 23), double-word sums of m_j d and -m_i d
+        # 168 (12 x (two_prod 3 + renormalised sum 11)); kbar =
+        # single-precision iterations per solve.  ncu counts 354 for kbar = 1
+        # (profiles/pair_step_sym_mixed_bh16384.md): the correctly rounded
+        # divisions and square root of the class test take more than counted.
+        flops_solve = fp32_share * (C_MIX32_FIX + kbar * C_MIX32_ITER)
         peak = FP32_PEAK_GFLOPS / 1e3
         kname, pipe = "pair_step_sym_mixed", "fp32"
         peak_source = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; flops counted by hand"
