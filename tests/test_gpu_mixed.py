@@ -125,3 +125,35 @@ def test_mixed_energy_drift_bh_cluster(pairs):
           f" |Em-Ef|/|E| {abs(Em - Ef) / abs(E0):.3e} fp32 share"
           f" {stm['fp32_pairs'] / stm['pairs']:.3f}")
     assert abs(Em - Ef) <= 1e-9 * abs(E0)
+
+
+@pytest.mark.parametrize("blocks", [1, 7])
+@pytest.mark.parametrize("rule", [0, 1], ids=["literal", "hyp"])
+def test_mixed_queue_across_segments(rule, blocks):
+    # few warps, each over many tiles: FP64-class pairs queued in one
+    # segment are solved in a later one and added to the earlier segment's
+    # partials (in queue order where two meet the same element)
+    s = ics.bh_cluster(2048, seed=11)
+    with mixed(mixed_rule=rule, guess=sk.GUESS_TAYLOR, pair_mode=sk.PAIRS_SYMMETRIC,
+               grid_blocks=blocks):
+        r, v, st = step_gpu(s, 2)
+        r2, v2, _ = step_gpu(s, 2)
+    cnt, _ = oracle.pair_classes(s.m, s.r, s.v, s.dt, rule=rule, order=2)
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
+    er, ev = rel_err(r, v, rr, vr)
+    assert st["fp32_pairs"] == cnt
+    assert er <= STEP_BOUND and ev <= STEP_BOUND, (er, ev)
+    np.testing.assert_array_equal(r, r2)
+    np.testing.assert_array_equal(v, v2)
+
+
+@pytest.mark.parametrize("blocks", [1, 5])
+def test_mixed_all_fp64_queue_across_segments_is_fp64_exact(blocks):
+    # every pair through the FP64 queue, whose entries cross segment ends
+    s = ics.random_cluster(700, seed=12, mass_spread=2.0)
+    with mixed(mixed_r_min=1e6, pair_mode=sk.PAIRS_SYMMETRIC, grid_blocks=blocks):
+        r, v, st = step_gpu(s, 2)
+    assert st["fp32_pairs"] == 0
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
+    er, ev = rel_err(r, v, rr, vr)
+    assert er <= 1e-12 and ev <= 1e-12, (er, ev)
