@@ -56,6 +56,53 @@ __global__ void prep_df64_kernel(const double *state, const double *mass, double
     X3[(3 * q + 2) * n + i] = d2;
 }
 
+// FP64 solve of queue entries 0..cnt-1 of tile (I, J): the results are
+// converted to double-words here, with every lane active, into qres[lane]
+// (the owners then add them one lane at a time).  Kept out of line so that
+// the double-word hot loop's code stays small: 1.6-2.7 % faster on GB300.
+__device__ __noinline__ void df64_queue_solve(const StepArgs &a, const int *qw, int cnt,
+                                              int64_t I, int64_t J, int guess,
+                                              float2 (*qres)[12], unsigned *status,
+                                              int *iters_out, int *fb_out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t n = a.n;
+    const KeplerParams kp{a.tol, a.max_iter, a.bisection};
+    const bool vq = lane < cnt;
+    const int e = vq ? qw[lane] : 0;
+    const int64_t iq = 32 * I + (e & 31), jq = 32 * J + (e >> 5);
+    PairSolve p;
+    double miq = 0.0, mjq = 0.0;
+    if (vq) {
+        const double *X = a.X;
+        miq = X[6 * n + iq];
+        mjq = X[6 * n + jq];
+        pair_setup(p, a.tau, miq + mjq, X[iq] - X[jq], X[n + iq] - X[n + jq],
+                   X[2 * n + iq] - X[2 * n + jq], X[3 * n + iq] - X[3 * n + jq],
+                   X[4 * n + iq] - X[4 * n + jq], X[5 * n + iq] - X[5 * n + jq], a.pre, guess);
+    } else {
+        p.done = true;
+        p.beta = p.s = 0.0;
+        p.iters = 0;
+        p.status = 0;
+    }
+    double d[6];
+    int iters = 0, fb = 0;
+    fp64_solve_warp(p, vq, a.tau, a.post * a.tau, kp, d, iters, fb);
+    if (vq) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const double xr = mjq * d[q], xc = -miq * d[q];
+            const float rh = __double2float_rn(xr), ch = __double2float_rn(xc);
+            qres[lane][q] = make_float2(rh, __double2float_rn(xr - (double)rh));
+            qres[lane][6 + q] = make_float2(ch, __double2float_rn(xc - (double)ch));
+        }
+        *status |= p.status;
+    }
+    *iters_out = iters;
+    *fb_out = fb;
+}
+
 template <bool STATS>
 __global__ void __launch_bounds__(128)
     pair_step_sym_df64_kernel(StepArgs a, DwArgs da, int Smax, int64_t T)
@@ -72,7 +119,6 @@ __global__ void __launch_bounds__(128)
     const int64_t W = (int64_t)gridDim.x * 4;
     const int64_t w = (int64_t)blockIdx.x * 4 + wib;
     const float *X3 = da.X3;
-    const KeplerParams kp{a.tol, a.max_iter, a.bisection};
     const int guess = a.guess == 1 ? 2 : a.guess;
     unsigned status = 0;
     long long it_sum = 0, slots = 0, fallbacks = 0, ndw = 0;
@@ -103,40 +149,8 @@ __global__ void __launch_bounds__(128)
         // FP64 solve of queue entries 0..cnt-1 at step kc, results added to
         // the row owners and the lanes holding the columns, in queue order
         auto flush = [&](int kc, int cnt) {
-            const bool vq = lane < cnt;
-            const int e = vq ? qw[lane] : 0;
-            const int64_t iq = 32 * I + (e & 31), jq = 32 * J + (e >> 5);
-            PairSolve p;
-            double miq = 0.0, mjq = 0.0;
-            if (vq) {
-                const double *X = a.X;
-                miq = X[6 * n + iq];
-                mjq = X[6 * n + jq];
-                pair_setup(p, a.tau, miq + mjq, X[iq] - X[jq], X[n + iq] - X[n + jq],
-                           X[2 * n + iq] - X[2 * n + jq], X[3 * n + iq] - X[3 * n + jq],
-                           X[4 * n + iq] - X[4 * n + jq], X[5 * n + iq] - X[5 * n + jq], a.pre,
-                           guess);
-            } else {
-                p.done = true;
-                p.beta = p.s = 0.0;
-                p.iters = 0;
-                p.status = 0;
-            }
-            double d[6];
             int iters = 0, fb = 0;
-            fp64_solve_warp(p, vq, a.tau, a.post * a.tau, kp, d, iters, fb);
-            if (vq) {
-                // converted to double-words here, with every lane active (the
-                // owners below add them one lane at a time)
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const double xr = mjq * d[q], xc = -miq * d[q];
-                    const float rh = __double2float_rn(xr), ch = __double2float_rn(xc);
-                    qres[wib][lane][q] = make_float2(rh, __double2float_rn(xr - (double)rh));
-                    qres[wib][lane][6 + q] = make_float2(ch, __double2float_rn(xc - (double)ch));
-                }
-                status |= p.status;
-            }
+            df64_queue_solve(a, qw, cnt, I, J, guess, qres[wib], &status, &iters, &fb);
             if (STATS) {
                 it_sum += iters;
                 fallbacks += fb;
