@@ -14,7 +14,9 @@ timed with CUDA events on the library stream.  The pair kernel's own
 duration (the roofline's denominator) is taken with CUDA events around each
 pair-kernel launch in a second pass of the same K steps, so that those
 events, which hold each launch until the previous kernel has finished, do
-not add to the timed steps.
+not add to the timed steps.  The 9-body planetary workload (72 pairs per
+step, launch-latency bound) is timed as replays of a CUDA graph of 100
+captured ``sakura_step`` calls (``--graph-steps``).
 
 Printed JSON line (rank 0): value (device-resident throughput of the plain
 FP64 form), e2e (the same through the host-buffer entry point
@@ -487,6 +489,10 @@ def main():
                     help="literal: FP32 iff r > 0.1 and e < 0.9; hyp: ... or e > 10")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the double-word form reported beside the FP64 headline")
+    ap.add_argument("--graph-steps", type=int, default=None,
+                    help="time the steps as replays of a CUDA graph of this many captured"
+                         " steps (default: 100 for planetary9, whose 72 pairs per step make it"
+                         " launch-latency bound; 0 for the others)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -558,20 +564,40 @@ def main():
     carried = st.get("carries", 0) / max(1, st["solves"])
     solves_per_pair = st["solves"] / max(1, st["pairs"])
     fp32_share = st["fp32_pairs"] / max(1, st["pairs"])
+    graph_steps = args.graph_steps if args.graph_steps is not None else (
+        100 if args.workload == "planetary9" else 0)
+    if graph_steps > 0 and args.steps % graph_steps != 0:
+        raise SystemExit("--steps must be a multiple of --graph-steps")
     sk.init(device.index, stream=stream.cuda_stream, guess=guess, **form_opts)
     state.copy_(torch.tensor(s.soa(), device=device))
     E0 = sk.energy(state, mass)
 
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    graph = None
+    if graph_steps > 0:
+        # the library's steps captured on a side stream (their scratch is
+        # already sized, so a step allocates nothing and can be captured)
+        gstream = torch.cuda.Stream(device)
+        sk.init(device.index, stream=gstream.cuda_stream, guess=guess, **form_opts)
+        torch.cuda.synchronize(device)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=gstream):
+            for _ in range(graph_steps):
+                sk.step(state, mass, s.dt, 2)
+        torch.cuda.synchronize(device)
+    nt = args.steps // graph_steps if graph is not None else args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(nt)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(nt)]
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize(device)
     with ClockSampler(device.index) as clocks:
-        for k in range(args.steps):
+        for k in range(nt):
             flush.fill_(float(k))
             starts[k].record(stream)
-            sk.step(state, mass, s.dt, 2)
+            if graph is not None:
+                graph.replay()
+            else:
+                sk.step(state, mass, s.dt, 2)
             ends[k].record(stream)
         torch.cuda.synchronize(device)
     if dist is not None:
@@ -685,7 +711,14 @@ def main():
                        "fp32_pair_share": fp32_share,
                        "pairs_solved_per_step": n * (n - 1),
                        "energy_error_over_timed_steps": energy_error,
-                       "l2": "256 MB buffer written between timed steps (state fits in L2)",
+                       "l2": ("256 MB buffer written between timed replays of the graph"
+                              " (state fits in L2)" if graph is not None else
+                              "256 MB buffer written between timed steps (state fits in L2)"),
+                       "graph_steps": graph_steps,
+                       "timing": (f"{nt} replays of a CUDA graph of {graph_steps} captured"
+                                  " sakura_step calls, each timed with CUDA events"
+                                  if graph is not None else
+                                  "each sakura_step call timed with CUDA events"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "gpu_launches": 3 * args.steps,
             "solves_per_pair": solves_per_pair,
