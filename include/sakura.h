@@ -166,7 +166,12 @@ int sakura_set_stream(void *stream);
  *   masses: device double[n], all > 0.
  *   n >= 1; dt any finite value (negative integrates backwards).
  * Errors: E_NOINIT, E_ARG (n < 1, order not in {2,1,-1,4,6,8}, NULL
- * pointer, non-finite dt); device faults as described above. */
+ * pointer, non-finite dt); device faults as described above.
+ * Stream capture: once a call with the same n, order and configuration has
+ * sized the library scratch, a call enqueues kernels on the library stream
+ * only (no allocation, no synchronisation unless SAKURA_FLAG_SYNC_CHECK or
+ * SAKURA_FLAG_TIMING is set), so runs of steps can be captured into a CUDA
+ * graph and replayed. */
 int sakura_step(double *state, const double *masses, int64_t n, double dt, int order);
 
 /* nsteps consecutive steps on HOST buffers: copies state and masses to
