@@ -194,12 +194,14 @@ int sakura_energy(const double *state, const double *masses, int64_t n, double *
  *   (used to build the work schedule, rebuilt when they change);
  *   dt: device double[nsys], one step size per system.
  * Runs nsteps steps of the given order (2, 1, -1, 4, 6, 8) on every system, state
- * updated in place.  A warp runs all steps of its systems with the state in
- * shared memory; the launch is a CUDA graph (counter reset + kernel), built
- * once per (buffers, schedule, nsteps, order, block shape) and replayed.  The
- * first call with a new schedule times the candidate block shapes (1, 2, 4, 8
- * warps) on a scratch copy and keeps the fastest unless
- * SAKURA_FLAG_NO_AUTOTUNE is set or cfg.block_warps / cfg.grid_blocks fix it.
+ * updated in place.  Each unordered pair of a system is solved once per
+ * step.  A block runs all steps of its systems with the state in shared
+ * memory, its warps splitting every step's pair rounds; the launch is a CUDA
+ * graph (counter reset + kernel), built once per (buffers, schedule, nsteps,
+ * order, block shape) and replayed.  The first call with a new schedule
+ * times the candidate block shapes (1, 2, 4, 8 warps) on a scratch copy and
+ * keeps the fastest unless SAKURA_FLAG_NO_AUTOTUNE is set or
+ * cfg.block_warps / cfg.grid_blocks fix it.
  * Systems need 1 <= N <= SAKURA_BATCH_MAX_N particles (else SAKURA_E_ARG). */
 int sakura_step_batched(double *state, const double *masses, const int64_t *offsets,
                         const int64_t *host_offsets, int nsys, const double *dt, int order,

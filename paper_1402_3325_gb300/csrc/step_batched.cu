@@ -22,11 +22,11 @@
 // takes one lane and no rounds.
 //
 // Schedule (built on the host when the offsets change): systems are packed
-// first-fit-decreasing into warps of at most 32 lanes and kBatchMaxN = 64
-// particles; a warp's lockstep length is the largest round count among its
-// systems.
-// Tasks are sorted by that length and handed out through an atomic counter
-// (dynamic longest-first).
+// best-fit-decreasing into tasks of at most 32 lanes and kBatchMaxN = 64
+// particles (build_batch_schedule); a task's lockstep length is the largest
+// round count among its systems.  Tasks are sorted by that length and
+// handed out through an atomic counter (dynamic longest-first), one task to
+// a block at a time.
 //
 // Per step, per block: lane k of a system drifts its particles 2k and 2k + 1
 // (and the last particle of an odd system, on its last lane) (Eq. 27a),
