@@ -207,7 +207,8 @@ def _kernel_sources_hash(kernel: str = "pair_step_sym") -> str:
              "pair_step_fp64": ["step_fp64.cu"],
              "pair_step_sym_df64": ["df64.cuh", "kepler_df64.cuh", "step_df64.cu"]}.get(
                  kernel, ["step_fp64.cu"])
-    for f in ["kepler_fp64.cuh", "pair_batch_fp64.cuh"] + files:
+    for f in ["kepler_fp64.cuh", "pair_batch_fp64.cuh", "fp_bits.cuh", "step_common.cuh",
+              "kepler_fp32.cuh"] + files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
