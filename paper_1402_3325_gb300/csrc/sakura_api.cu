@@ -32,7 +32,6 @@ struct BatchCache {
     int warps = 4;
     int blocks = 0;
     bool tuned = false;
-    int tuned_variant = 0;  // 1: learned guess, 2: single-precision seed
     cudaGraphExec_t exec = nullptr;
     sakura::BatchArgs graph_args{};
     int graph_warps = 0, graph_blocks = 0;
@@ -618,7 +617,6 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
         bc.host_offsets.assign(host_offsets, host_offsets + nsys + 1);
         bc.ntasks = (int)tb.size() - 1;
         bc.tuned = false;
-        bc.tuned_variant = 0;
         if (bc.exec) cudaGraphExecDestroy(bc.exec);
         bc.exec = nullptr;
     }
@@ -702,19 +700,15 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
             cudaMemsetAsync(g.d_stats, 0, sakura::kStatCount * sizeof(unsigned long long),
                             g.stream);
         }
-        if (stats)
-            bc.blocks = g.sm_count * sakura::batched_blocks_per_sm(bc.warps, true, learned, seed);
         bc.tuned = true;
     }
+    // one wave of the kernel variant this call runs (statistics, the network
+    // and the float copies change its occupancy), not of the variant that
+    // happened to be running when the shape was tuned
+    bc.blocks = g.cfg.grid_blocks > 0
+                    ? g.cfg.grid_blocks
+                    : g.sm_count * sakura::batched_blocks_per_sm(bc.warps, stats, learned, seed);
     // (re)build the graph when anything it captured changed
-    const int variant = (learned ? 1 : 0) | (seed ? 2 : 0);
-    if (bc.tuned_variant != variant) {
-        // occupancy differs with the network or the float copies in shared memory
-        bc.blocks = g.cfg.grid_blocks > 0
-                        ? g.cfg.grid_blocks
-                        : g.sm_count * sakura::batched_blocks_per_sm(bc.warps, stats, learned, seed);
-        bc.tuned_variant = variant;
-    }
     const bool same = bc.exec && bc.graph_warps == bc.warps && bc.graph_blocks == bc.blocks &&
                       bc.graph_stats == stats &&
                       std::memcmp(&bc.graph_args, &a, sizeof(a)) == 0;
