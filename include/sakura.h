@@ -177,7 +177,16 @@ int sakura_step(double *state, const double *masses, int64_t n, double dt, int o
 /* nsteps consecutive steps on HOST buffers: copies state and masses to
  * library-owned device memory, runs the steps, copies the state back and
  * synchronises.  state: host double[6][n]; masses: host double[n].  order
- * as for sakura_step. */
+ * as for sakura_step.  Errors as for sakura_step; the call returns (and
+ * clears) every device fault pending on the library stream.
+ * Page-locked buffers mapped into the device's address space (cudaHostAlloc,
+ * cudaMallocHost, or cudaHostRegister, under the unified addressing of
+ * 64-bit Linux), with nsteps >= 1: no copy-engine transfers.  The first
+ * sub-step's drift kernel reads state and masses in place and the last
+ * sub-step's apply kernel writes state in place; sub-steps in between run in
+ * library memory.  Both buffers are checked at their first and last byte,
+ * and each must be one allocation of at least the stated size.  Pageable
+ * buffers are staged through library memory with cudaMemcpyAsync. */
 int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt,
                        int order, int nsteps);
 

@@ -46,6 +46,8 @@ struct Context {
     unsigned *d_status = nullptr;
     unsigned long long *d_stats = nullptr;
     double *d_energy = nullptr;  // [3] E, T, U
+    unsigned *h_status = nullptr;      // page-locked host copy of the status word
+    unsigned *h_status_dev = nullptr;  // its address on the device
     Buffer partial;              // pair-kernel segment sums
     Buffer energy_work;
     Buffer host_state, host_mass;  // device copies for sakura_evolve_host
@@ -123,18 +125,29 @@ int launch_error()
 }
 
 // Synchronise, read and clear the status word.
+// Copies the status word into page-locked host memory and clears it (one
+// thread, after every earlier kernel on the stream): one launch instead of a
+// copy-engine transfer, whose fixed latency is several times larger.  It is
+// launched as a programmatic dependent; griddep_wait returns once the kernel
+// before it has completed and its writes are visible.
+__global__ void publish_status_kernel(unsigned *status, unsigned *host_status)
+{
+    sakura::griddep_wait();
+    const unsigned st = *status;
+    *host_status = st;
+    if (st) *status = 0u;
+}
+
 int drain_status()
 {
-    unsigned st = 0;
-    if (cudaMemcpyAsync(&st, g.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, g.stream) !=
-        cudaSuccess)
+    void *args[] = {(void *)&g.d_status, (void *)&g.h_status_dev};
+    if (sakura::launch_pdl((const void *)publish_status_kernel, dim3(1), dim3(1), args, 0,
+                           g.stream) != cudaSuccess) {
+        cudaGetLastError();
         return SAKURA_E_CUDA;
-    if (cudaStreamSynchronize(g.stream) != cudaSuccess) return SAKURA_E_CUDA;
-    if (st) {
-        if (cudaMemsetAsync(g.d_status, 0, sizeof(unsigned), g.stream) != cudaSuccess)
-            return SAKURA_E_CUDA;
     }
-    return status_to_code(st);
+    if (cudaStreamSynchronize(g.stream) != cudaSuccess) return SAKURA_E_CUDA;
+    return status_to_code(*(volatile unsigned *)g.h_status);
 }
 
 struct Plan {
@@ -179,8 +192,8 @@ sakura::dw split_dw(double d)
 
 // Unordered pairs once (Newton's third law): systolic 32 x 32 tiles; df64:
 // the pair solves in double-word arithmetic (step_df64.cu).
-int step_device_sym(double *state, const double *masses, int64_t n, double dt, int order,
-                    bool df64, bool mixed)
+int step_device_sym(const double *src, double *dst, const double *masses, int64_t n, double dt,
+                    int order, bool df64, bool mixed)
 {
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
     const bool learned = !df64 && !mixed && g.cfg.guess == SAKURA_GUESS_LEARNED;
@@ -210,11 +223,11 @@ int step_device_sym(double *state, const double *masses, int64_t n, double dt, i
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
     if (df64)
-        sakura::launch_prep_df64(state, masses, X, X3, n, drift, g.d_status, g.stream);
+        sakura::launch_prep_df64(src, masses, X, X3, n, drift, g.d_status, g.stream);
     else if (mixed)
-        sakura::launch_prep_mixed(state, masses, X, X32, n, drift, g.d_status, g.stream);
+        sakura::launch_prep_mixed(src, masses, X, X32, n, drift, g.d_status, g.stream);
     else
-        sakura::launch_prep_step(state, masses, X, X32, n, drift, g.d_status, g.stream);
+        sakura::launch_prep_step(src, masses, X, X32, n, drift, g.d_status, g.stream);
     sakura::StepArgs a;
     std::memset(&a, 0, sizeof(a));
     a.X = X;
@@ -267,10 +280,10 @@ int step_device_sym(double *state, const double *masses, int64_t n, double dt, i
         g.timers.push_back(tm);
     }
     if (df64)
-        sakura::launch_apply_df64(state, X, partial, n, Smax, W, T, post_drift, g.d_status,
+        sakura::launch_apply_df64(dst, X, partial, n, Smax, W, T, post_drift, g.d_status,
                                   g.stream);
     else
-        sakura::launch_apply_sym(state, X, partial, n, Smax, W, T, post_drift, g.d_status,
+        sakura::launch_apply_sym(dst, X, partial, n, Smax, W, T, post_drift, g.d_status,
                                  g.stream);
     rc = launch_error();
     if (rc) return rc;
@@ -289,11 +302,17 @@ int step_device_sym(double *state, const double *masses, int64_t n, double dt, i
 // kSymMaxBytes the ordered-pair kernel (O(n) scratch) is used instead.
 constexpr double kSymMaxBytes = 16.0 * 1024 * 1024 * 1024;
 
-int step_device(double *state, const double *masses, int64_t n, double dt, int order)
+// One step of the given order from src to dst (the same buffer, or two
+// buffers that do not overlap): the drift kernel reads src and masses, the
+// apply kernel writes dst.  Either kernel copies the masses into row 6 of the
+// drifted state X[7][n] at the start of the scratch buffer (step_masses).
+int step_device(const double *src, double *dst, const double *masses, int64_t n, double dt,
+                int order)
 {
     if (g.cfg.pair_mode == SAKURA_PAIRS_SYMMETRIC && n > 1 &&
         8.0 * 6.0 * 8.0 * (double)((n + 31) / 32) * (double)n <= kSymMaxBytes)
-        return step_device_sym(state, masses, n, dt, order, g.cfg.precision == SAKURA_PREC_DF64,
+        return step_device_sym(src, dst, masses, n, dt, order,
+                               g.cfg.precision == SAKURA_PREC_DF64,
                                g.cfg.precision == SAKURA_PREC_MIXED);
     const Plan p = plan_step(n);
     const int64_t slots = sakura::pair_step_slots(n, p.W);
@@ -309,9 +328,9 @@ int step_device(double *state, const double *masses, int64_t n, double dt, int o
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
     if (mixed)
-        sakura::launch_prep_mixed(state, masses, X, X32, n, drift, g.d_status, g.stream);
+        sakura::launch_prep_mixed(src, masses, X, X32, n, drift, g.d_status, g.stream);
     else
-        sakura::launch_prep_step(state, masses, X, nullptr, n, drift, g.d_status, g.stream);
+        sakura::launch_prep_step(src, masses, X, nullptr, n, drift, g.d_status, g.stream);
     sakura::StepArgs a;
     a.X = X;
     a.partial = partial;
@@ -360,7 +379,7 @@ int step_device(double *state, const double *masses, int64_t n, double dt, int o
     } else {
         W = 0;  // a single particle only drifts
     }
-    sakura::launch_apply_step(state, X, partial, n, W, post_drift, g.d_status, g.stream);
+    sakura::launch_apply_step(dst, X, partial, n, W, post_drift, g.d_status, g.stream);
     rc = launch_error();
     if (rc) return rc;
     g.steps += 1;
@@ -403,16 +422,38 @@ int substeps(int order, double *w, int *sub_order)
     return cnt;
 }
 
+// The device copy of the masses that the last step's drift kernel wrote.
+const double *step_masses(int64_t n) { return (const double *)g.partial.ptr + 6 * n; }
+
 int step_composed(double *state, const double *masses, int64_t n, double dt, int order)
 {
     double w[sakura::kMaxSubsteps];
     int so;
     const int cnt = substeps(order, w, &so);
     for (int u = 0; u < cnt; ++u) {
-        const int rc = step_device(state, masses, n, w[u] * dt, so);
+        const int rc = step_device(state, state, masses, n, w[u] * dt, so);
         if (rc) return rc;
     }
     return SAKURA_OK;
+}
+
+// Device address of a host buffer of `bytes` bytes that is page-locked and
+// mapped into the device's address space (cudaHostAlloc, cudaMallocHost or
+// cudaHostRegister under unified addressing), checked at its first and last
+// byte; null otherwise.
+const void *mapped_host(const void *p, size_t bytes)
+{
+    cudaPointerAttributes a, b;
+    const char *last = (const char *)p + bytes - 1;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
+        cudaPointerGetAttributes(&b, last) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer ||
+        (const char *)b.devicePointer != (const char *)a.devicePointer + bytes - 1)
+        return nullptr;
+    return a.devicePointer;
 }
 
 }  // namespace
@@ -471,6 +512,10 @@ int sakura_init(const sakura_config *cfg)
             return SAKURA_E_NOMEM;
         if (cudaMalloc(&g.d_energy, 3 * sizeof(double)) != cudaSuccess) return SAKURA_E_NOMEM;
         if (cudaMemset(g.d_status, 0, sizeof(unsigned)) != cudaSuccess) return SAKURA_E_CUDA;
+        if (cudaHostAlloc(&g.h_status, sizeof(unsigned), cudaHostAllocMapped) != cudaSuccess ||
+            cudaHostGetDevicePointer(&g.h_status_dev, g.h_status, 0) != cudaSuccess)
+            return SAKURA_E_NOMEM;
+        *g.h_status = 0u;
         if (cudaMemset(g.d_stats, 0, sakura::kStatCount * sizeof(unsigned long long)) !=
             cudaSuccess)
             return SAKURA_E_CUDA;
@@ -504,6 +549,7 @@ int sakura_finalize(void)
     cudaFree(g.d_status);
     cudaFree(g.d_stats);
     cudaFree(g.d_energy);
+    if (g.h_status) cudaFreeHost(g.h_status);
     for (auto &p : g.timers) g.spare.push_back(p);
     for (auto &p : g.spare) {
         cudaEventDestroy(p.first);
@@ -541,23 +587,47 @@ int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt
     if (!state || !masses || n < 1 || !valid_step_order(order) || !std::isfinite(dt) ||
         nsteps < 0)
         return SAKURA_E_ARG;
-    int rc = grow(g.host_state, 6 * (size_t)n * sizeof(double));
+    const size_t sbytes = 6 * (size_t)n * sizeof(double), mbytes = (size_t)n * sizeof(double);
+    int rc;
+    // page-locked, mapped buffers: the first drift kernel reads the host
+    // state and masses and the last apply kernel writes the host state
+    // (NVLink-C2C loads and stores), in place of copy-engine transfers
+    double *hs = nsteps > 0 ? (double *)mapped_host(state, sbytes) : nullptr;
+    const double *hm = hs ? (const double *)mapped_host(masses, mbytes) : nullptr;
+    if (hs && hm) {
+        double w[sakura::kMaxSubsteps];
+        int so;
+        const int cnt = substeps(order, w, &so);
+        const int64_t total = (int64_t)cnt * nsteps;
+        double *ds = nullptr;
+        if (total > 1) {
+            rc = grow(g.host_state, sbytes);
+            if (rc) return rc;
+            ds = (double *)g.host_state.ptr;
+        }
+        for (int64_t k = 0; k < total; ++k) {
+            // after the first sub-step the masses come from the copy the last
+            // drift kernel left in the scratch (same n: it is not reallocated)
+            rc = step_device(k == 0 ? hs : ds, k == total - 1 ? hs : ds,
+                             k == 0 ? hm : step_masses(n), n, w[k % cnt] * dt, so);
+            if (rc) return rc;
+        }
+        return drain_status();
+    }
+    rc = grow(g.host_state, sbytes);
     if (rc) return rc;
-    rc = grow(g.host_mass, (size_t)n * sizeof(double));
+    rc = grow(g.host_mass, mbytes);
     if (rc) return rc;
     double *ds = (double *)g.host_state.ptr;
     double *dm = (double *)g.host_mass.ptr;
-    if (cudaMemcpyAsync(ds, state, 6 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
-                        g.stream) != cudaSuccess ||
-        cudaMemcpyAsync(dm, masses, (size_t)n * sizeof(double), cudaMemcpyHostToDevice,
-                        g.stream) != cudaSuccess)
+    if (cudaMemcpyAsync(ds, state, sbytes, cudaMemcpyHostToDevice, g.stream) != cudaSuccess ||
+        cudaMemcpyAsync(dm, masses, mbytes, cudaMemcpyHostToDevice, g.stream) != cudaSuccess)
         return SAKURA_E_CUDA;
     for (int k = 0; k < nsteps; ++k) {
         rc = step_composed(ds, dm, n, dt, order);
         if (rc) return rc;
     }
-    if (cudaMemcpyAsync(state, ds, 6 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost,
-                        g.stream) != cudaSuccess)
+    if (cudaMemcpyAsync(state, ds, sbytes, cudaMemcpyDeviceToHost, g.stream) != cudaSuccess)
         return SAKURA_E_CUDA;
     return drain_status();
 }

@@ -192,6 +192,79 @@ def test_evolve_host_equals_device_steps():
     np.testing.assert_array_equal(host, ics.to_soa(r, v))
 
 
+def _pinned(a):
+    t = torch.empty(a.shape, dtype=torch.float64).pin_memory()
+    t.numpy()[...] = a
+    return t
+
+
+@pytest.mark.parametrize("order,nsteps", [(2, 1), (2, 3), (1, 2), (4, 1), (4, 2)])
+def test_evolve_host_pinned_equals_device_steps(order, nsteps):
+    # page-locked buffers: the kernels read and write the host state in
+    # place (one sub-step, or the first and last of several)
+    s = ics.random_cluster(300, seed=3)
+    r, v = gpu_step(s, s.dt, order, nsteps=nsteps)
+    hs, hm = _pinned(s.soa()), _pinned(s.m)
+    sk.get_stats(reset=True)
+    sk.evolve_host(hs.numpy(), hm.numpy(), s.dt, order, nsteps)
+    sub = 3 if order == 4 else 1
+    assert sk.get_stats(reset=True)["steps"] == sub * nsteps
+    np.testing.assert_array_equal(hs.numpy(), ics.to_soa(r, v))
+    np.testing.assert_array_equal(hm.numpy(), s.m)
+
+
+@pytest.mark.parametrize("form", ["df64", "mixed", "ordered"])
+def test_evolve_host_pinned_other_forms(form):
+    opts = {"df64": dict(precision=sk.PREC_DF64), "mixed": dict(precision=sk.PREC_MIXED),
+            "ordered": dict(pair_mode=sk.PAIRS_ORDERED)}[form]
+    s = ics.random_cluster(200, seed=5)
+    with configured(**opts):
+        r, v = gpu_step(s, s.dt, 2, nsteps=2)
+        hs, hm = _pinned(s.soa()), _pinned(s.m)
+        sk.evolve_host(hs.numpy(), hm.numpy(), s.dt, 2, 2)
+        np.testing.assert_array_equal(hs.numpy(), ics.to_soa(r, v))
+
+
+def test_evolve_host_pinned_state_pageable_masses():
+    # one page-locked buffer and one pageable one: the copy-engine path
+    s = ics.random_cluster(100, seed=4)
+    r, v = gpu_step(s, s.dt, 2, nsteps=2)
+    hs = _pinned(s.soa())
+    sk.evolve_host(hs.numpy(), s.m.copy(), s.dt, 2, 2)
+    np.testing.assert_array_equal(hs.numpy(), ics.to_soa(r, v))
+
+
+def test_evolve_host_pinned_zero_steps_and_single_particle():
+    s = ics.random_cluster(50, seed=6)
+    hs, hm = _pinned(s.soa()), _pinned(s.m)
+    sk.evolve_host(hs.numpy(), hm.numpy(), s.dt, 2, 0)
+    np.testing.assert_array_equal(hs.numpy(), s.soa())
+    one = _pinned(s.soa()[:, :1].copy())
+    m1 = _pinned(s.m[:1].copy())
+    sk.evolve_host(one.numpy(), m1.numpy(), 0.25, 2, 2)
+    x0 = s.soa()[:, 0]
+    np.testing.assert_allclose(one.numpy()[:3, 0], x0[:3] + 0.5 * x0[3:], rtol=1e-14, atol=1e-14)
+    np.testing.assert_array_equal(one.numpy()[3:, 0], x0[3:])
+
+
+def test_evolve_host_pinned_reports_faults_once():
+    bad = ics.random_cluster(40, seed=2)
+    bad.r[5] = bad.r[6]
+    bad.v[5] = bad.v[6]
+    good = ics.random_cluster(40, seed=2)
+    hs, hm = _pinned(bad.soa()), _pinned(bad.m)
+    for _ in range(2):
+        hs.numpy()[...] = bad.soa()
+        with pytest.raises(sk.SakuraError) as e:
+            sk.evolve_host(hs.numpy(), hm.numpy(), 0.01, 2, 1)
+        assert e.value.code == sk.E_COINCIDENT
+    hs.numpy()[...] = good.soa()
+    sk.evolve_host(hs.numpy(), hm.numpy(), 0.01, 2, 1)
+    assert sk.check_code() == sk.OK
+    r, v = gpu_step(good, 0.01, 2)
+    np.testing.assert_array_equal(hs.numpy(), ics.to_soa(r, v))
+
+
 def test_stats_count_pairs_and_iterations():
     s = ics.random_cluster(200, seed=9)
     with configured(pair_mode=sk.PAIRS_ORDERED):
