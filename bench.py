@@ -15,8 +15,9 @@ duration (the roofline's denominator) is taken with CUDA events around each
 pair-kernel launch in a second pass of the same K steps, so that those
 events, which hold each launch until the previous kernel has finished, do
 not add to the timed steps.  The 9-body planetary workload (72 pairs per
-step, launch-latency bound) is timed as replays of a CUDA graph of 100
-captured ``sakura_step`` calls (``--graph-steps``).
+step) runs in the single-block kernel for small systems and is timed as
+calls of ``sakura_evolve`` of 100 steps each (``--steps-per-call``), one
+launch per call.
 
 Printed JSON line (rank 0): value (device-resident throughput of the plain
 FP64 form), e2e (the same through the host-buffer entry point
@@ -396,22 +397,26 @@ def _cpu_baseline_ensemble(ens, budget_s=10.0):
                       f" their initial states, OpenMP over i on {cores} threads, {el:.1f} s"}
 
 
-def _pair_kernel_ms(args, sk, s, state, mass, device, stream, flush, guess, opts):
-    """Mean duration of the pair kernel over a second pass of args.steps
-    steps, timed the same way as the timed steps (L2 flushed before each),
-    with CUDA events recorded by the library around each pair-kernel launch
-    on its stream."""
+def _pair_kernel_ms(args, sk, s, state, mass, device, stream, flush, guess, opts, per_call=1):
+    """Mean duration of the pair kernel per step over a second pass of
+    args.steps steps in calls of per_call steps, timed the same way as the
+    timed steps (L2 flushed before each call), with CUDA events recorded by
+    the library around each pair-kernel launch on its stream (for the
+    single-block kernel of small systems: the launch that runs the call)."""
     import torch
     sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_TIMING, guess=guess, **opts)
     sk.get_stats(reset=True)
     torch.cuda.synchronize(device)
-    for k in range(args.steps):
+    for k in range(args.steps // per_call):
         flush.fill_(float(k))
-        sk.step(state, mass, s.dt, 2)
+        if per_call > 1:
+            sk.evolve(state, mass, s.dt, 2, per_call)
+        else:
+            sk.step(state, mass, s.dt, 2)
     torch.cuda.synchronize(device)
     sk.check()
     st = sk.get_stats(reset=True)
-    return st["pair_kernel_ms"] / max(1, st["timed_launches"])
+    return st["pair_kernel_ms"] / max(1, args.steps)
 
 
 def _variant_df64(args, sk, s, device, stream, flush, guess):
@@ -490,10 +495,10 @@ def main():
                     help="literal: FP32 iff r > 0.1 and e < 0.9; hyp: ... or e > 10")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the double-word form reported beside the FP64 headline")
-    ap.add_argument("--graph-steps", type=int, default=None,
-                    help="time the steps as replays of a CUDA graph of this many captured"
-                         " steps (default: 100 for planetary9, whose 72 pairs per step make it"
-                         " launch-latency bound; 0 for the others)")
+    ap.add_argument("--steps-per-call", type=int, default=None,
+                    help="time the steps as calls of sakura_evolve of this many steps"
+                         " (default: 100 for planetary9, whose 72 pairs per step run in one"
+                         " block for the whole call; 1, i.e. sakura_step, for the others)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -565,27 +570,18 @@ def main():
     carried = st.get("carries", 0) / max(1, st["solves"])
     solves_per_pair = st["solves"] / max(1, st["pairs"])
     fp32_share = st["fp32_pairs"] / max(1, st["pairs"])
-    graph_steps = args.graph_steps if args.graph_steps is not None else (
-        100 if args.workload == "planetary9" else 0)
-    if graph_steps > 0 and args.steps % graph_steps != 0:
-        raise SystemExit("--steps must be a multiple of --graph-steps")
+    per_call = args.steps_per_call if args.steps_per_call is not None else (
+        100 if args.workload == "planetary9" else 1)
+    if per_call < 1 or args.steps % per_call != 0:
+        raise SystemExit("--steps must be a multiple of --steps-per-call")
+    # the single-block kernel (csrc/step_small.cu) takes the FP64 form of
+    # small systems, each unordered pair once, non-learned guesses
+    small = (n <= sk.SMALL_MAX_N and args.form == "fp64" and args.pairs == "symmetric" and
+             args.guess != "learned")
     sk.init(device.index, stream=stream.cuda_stream, guess=guess, **form_opts)
     state.copy_(torch.tensor(s.soa(), device=device))
     E0 = sk.energy(state, mass)
-
-    graph = None
-    if graph_steps > 0:
-        # the library's steps captured on a side stream (their scratch is
-        # already sized, so a step allocates nothing and can be captured)
-        gstream = torch.cuda.Stream(device)
-        sk.init(device.index, stream=gstream.cuda_stream, guess=guess, **form_opts)
-        torch.cuda.synchronize(device)
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=gstream):
-            for _ in range(graph_steps):
-                sk.step(state, mass, s.dt, 2)
-        torch.cuda.synchronize(device)
-    nt = args.steps // graph_steps if graph is not None else args.steps
+    nt = args.steps // per_call
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(nt)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(nt)]
     if dist is not None:
@@ -595,8 +591,8 @@ def main():
         for k in range(nt):
             flush.fill_(float(k))
             starts[k].record(stream)
-            if graph is not None:
-                graph.replay()
+            if per_call > 1:
+                sk.evolve(state, mass, s.dt, 2, per_call)
             else:
                 sk.step(state, mass, s.dt, 2)
             ends[k].record(stream)
@@ -606,7 +602,8 @@ def main():
     sk.check()
     ms_total = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     energy_error = abs(sk.energy(state, mass) / E0 - 1.0)  # outside the timed region
-    pair_ms = _pair_kernel_ms(args, sk, s, state, mass, device, stream, flush, guess, form_opts)
+    pair_ms = _pair_kernel_ms(args, sk, s, state, mass, device, stream, flush, guess, form_opts,
+                              per_call)
     ms_total = max_over_ranks(ms_total, dist, device)
     ms_step = ms_total / args.steps
     value = whole_job_value(world, n * n * args.steps, ms_total)
@@ -682,8 +679,8 @@ def main():
                        carried * (C_STEP + C_CARRY) + (C_SYM if symmetric else 0) -
                        (C_SEED_SAVED if (args.guess == "fp32" and symmetric) else 0))
         peak = FP64_PEAK_GFLOPS / 1e3
-        kname = "pair_step_sym" if symmetric else (
-            "pair_step_mixed" if args.form == "mixed" else "pair_step_fp64")
+        kname = "small" if small else ("pair_step_sym" if symmetric else (
+            "pair_step_mixed" if args.form == "mixed" else "pair_step_fp64"))
         pipe = "fp64"
         peak_source = ("152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (derived from the nominal"
                        " 1.25 TFLOP/s; FMA probe measured 1.19)")
@@ -712,16 +709,18 @@ def main():
                        "fp32_pair_share": fp32_share,
                        "pairs_solved_per_step": n * (n - 1),
                        "energy_error_over_timed_steps": energy_error,
-                       "l2": ("256 MB buffer written between timed replays of the graph"
-                              " (state fits in L2)" if graph is not None else
+                       "l2": ("256 MB buffer written between timed calls (state fits in L2)"
+                              if per_call > 1 else
                               "256 MB buffer written between timed steps (state fits in L2)"),
-                       "graph_steps": graph_steps,
-                       "timing": (f"{nt} replays of a CUDA graph of {graph_steps} captured"
-                                  " sakura_step calls, each timed with CUDA events"
-                                  if graph is not None else
+                       "steps_per_call": per_call,
+                       "timing": (f"{nt} calls of sakura_evolve of {per_call} steps, each"
+                                  " timed with CUDA events" if per_call > 1 else
                                   "each sakura_step call timed with CUDA events"),
+                       "kernels": ("single-block kernel for small systems, every step of a"
+                                   " call in one launch" if small else
+                                   "drift, pair and apply kernels per step"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": nt if small else 3 * args.steps,
             "solves_per_pair": solves_per_pair,
             "roofline": roof, "clocks": clocks.summary()}
     if e2e is not None:

@@ -82,6 +82,8 @@ extern "C" {
 #define SAKURA_FLAG_STATS 2u      /* collect iteration statistics (small cost)   */
 #define SAKURA_FLAG_TIMING 4u     /* time every pair-kernel launch with CUDA events */
 #define SAKURA_FLAG_NO_AUTOTUNE 8u /* batched path: skip the block-shape autotuner  */
+#define SAKURA_FLAG_NO_SMALL 16u   /* n <= 20: use the multi-kernel step instead of  */
+                                   /* the single-block kernel (for comparisons)      */
 
 #define SAKURA_BATCH_MAX_N 64     /* largest system of sakura_step_batched       */
 
@@ -161,7 +163,11 @@ int sakura_set_stream(void *stream);
  * default) each unordered pair is solved once, its two ordered increments
  * being exact negatives; the library scratch then grows to at most
  * 8 x 6 x 8 ceil(n/32) n bytes (12 MB at n = 1024, 400 MB at 16384), and
- * above 16 GB the ordered kernel is used.
+ * above 16 GB the ordered kernel is used.  Systems of 2 <= n <= 20 in the
+ * FP64 form with symmetric pairs and a non-learned guess run in one launch
+ * of a single-block kernel that keeps the system in shared memory and packs
+ * the pairs densely over its lanes (no scratch; SAKURA_FLAG_NO_SMALL turns
+ * it off).
  *   state:  device double[6][n], updated in place.
  *   masses: device double[n], all > 0.
  *   n >= 1; dt any finite value (negative integrates backwards).
@@ -173,6 +179,14 @@ int sakura_set_stream(void *stream);
  * SAKURA_FLAG_TIMING is set), so runs of steps can be captured into a CUDA
  * graph and replayed. */
 int sakura_step(double *state, const double *masses, int64_t n, double dt, int order);
+
+/* nsteps consecutive steps of sakura_step on a device state, in place,
+ * asynchronous.  Systems that sakura_step runs in the single-block kernel
+ * take all nsteps steps in one launch (the state stays in shared memory
+ * between steps); other systems take nsteps sakura_step calls.  nsteps >= 0
+ * (0: nothing).  Arguments, errors and stream capture as for sakura_step. */
+int sakura_evolve(double *state, const double *masses, int64_t n, double dt, int order,
+                  int nsteps);
 
 /* nsteps consecutive steps on HOST buffers: copies state and masses to
  * library-owned device memory, runs the steps, copies the state back and
@@ -186,7 +200,9 @@ int sakura_step(double *state, const double *masses, int64_t n, double dt, int o
  * sub-step's apply kernel writes state in place; sub-steps in between run in
  * library memory.  Both buffers are checked at their first and last byte,
  * and each must be one allocation of at least the stated size.  Pageable
- * buffers are staged through library memory with cudaMemcpyAsync. */
+ * buffers are staged through library memory with cudaMemcpyAsync.  Systems
+ * of the single-block kernel (see sakura_step) take all nsteps steps in one
+ * launch, which reads and writes the mapped buffers directly. */
 int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt,
                        int order, int nsteps);
 

@@ -16,6 +16,7 @@
 #include "mlp_infer.cuh"
 #include "step_batched.cuh"
 #include "step_common.cuh"
+#include "step_small.cuh"
 
 namespace {
 
@@ -437,6 +438,61 @@ int step_composed(double *state, const double *masses, int64_t n, double dt, int
     return SAKURA_OK;
 }
 
+// Systems small enough for the single-block kernel (step_small.cu): the FP64
+// form with each unordered pair once and a non-learned guess.
+bool small_path(int64_t n)
+{
+    return n >= 2 && n <= sakura::kSmallMaxN && g.cfg.precision == SAKURA_PREC_FP64 &&
+           g.cfg.pair_mode == SAKURA_PAIRS_SYMMETRIC && g.cfg.guess != SAKURA_GUESS_LEARNED &&
+           !(g.cfg.flags & SAKURA_FLAG_NO_SMALL);
+}
+
+// nsteps steps of the given order from src to dst in one launch of the
+// single-block kernel (src and dst device or mapped host memory).
+int step_small(const double *src, double *dst, const double *masses, int64_t n, double dt,
+               int order, int nsteps)
+{
+    sakura::SmallArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.src = src;
+    a.dst = dst;
+    a.mass = masses;
+    a.n = (int)n;
+    a.nsteps = nsteps;
+    int so;
+    a.nsub = substeps(order, a.sub, &so);
+    a.dt = dt;
+    a.drift_frac = so == 2 ? 0.5 : (so == 1 ? 0.0 : 1.0);
+    a.post_drift_frac = so == 2 ? 0.5 : (so == 1 ? 1.0 : 0.0);
+    a.pre = a.drift_frac;
+    a.post = 1.0 - a.pre;
+    a.tol = g.cfg.kepler_tol * DBL_EPSILON;
+    a.max_iter = g.cfg.kepler_max_iter;
+    a.bisection = g.cfg.kepler_bisection;
+    a.guess = g.cfg.guess == SAKURA_GUESS_TAYLOR ? 2 : 0;
+    a.status = g.d_status;
+    a.stats = g.d_stats;
+    const bool timing = (g.cfg.flags & SAKURA_FLAG_TIMING) != 0;
+    std::pair<cudaEvent_t, cudaEvent_t> tm{nullptr, nullptr};
+    if (timing) {
+        tm = take_timer();
+        cudaEventRecord(tm.first, g.stream);
+    }
+    sakura::launch_small(a, (g.cfg.flags & SAKURA_FLAG_STATS) != 0,
+                         g.cfg.guess == SAKURA_GUESS_FP32, g.stream);
+    if (timing) {
+        cudaEventRecord(tm.second, g.stream);
+        g.timers.push_back(tm);
+    }
+    const int rc = launch_error();
+    if (rc) return rc;
+    const int64_t subs = (int64_t)nsteps * a.nsub;
+    g.steps += subs;
+    g.pairs += n * (n - 1) * subs;
+    g.solves += n * (n - 1) / 2 * subs;
+    return SAKURA_OK;
+}
+
 // Device address of a host buffer of `bytes` bytes that is page-locked and
 // mapped into the device's address space (cudaHostAlloc, cudaMallocHost or
 // cudaHostRegister under unified addressing), checked at its first and last
@@ -573,7 +629,28 @@ int sakura_step(double *state, const double *masses, int64_t n, double dt, int o
     if (!state || !masses || n < 1 || !valid_step_order(order) || !std::isfinite(dt))
         return SAKURA_E_ARG;
     if (g.cfg.guess == SAKURA_GUESS_LEARNED && !g.mlp_loaded) return SAKURA_E_ARG;
-    int rc = step_composed(state, masses, n, dt, order);
+    int rc = small_path(n) ? step_small(state, state, masses, n, dt, order, 1)
+                           : step_composed(state, masses, n, dt, order);
+    if (rc) return rc;
+    if (g.cfg.flags & SAKURA_FLAG_SYNC_CHECK) return drain_status();
+    return SAKURA_OK;
+}
+
+int sakura_evolve(double *state, const double *masses, int64_t n, double dt, int order,
+                  int nsteps)
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    if (!state || !masses || n < 1 || !valid_step_order(order) || !std::isfinite(dt) ||
+        nsteps < 0)
+        return SAKURA_E_ARG;
+    if (g.cfg.guess == SAKURA_GUESS_LEARNED && !g.mlp_loaded) return SAKURA_E_ARG;
+    int rc = SAKURA_OK;
+    if (nsteps > 0 && small_path(n)) {
+        rc = step_small(state, state, masses, n, dt, order, nsteps);
+    } else {
+        for (int k = 0; k < nsteps && rc == SAKURA_OK; ++k)
+            rc = step_composed(state, masses, n, dt, order);
+    }
     if (rc) return rc;
     if (g.cfg.flags & SAKURA_FLAG_SYNC_CHECK) return drain_status();
     return SAKURA_OK;
@@ -594,6 +671,11 @@ int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt
     // (NVLink-C2C loads and stores), in place of copy-engine transfers
     double *hs = nsteps > 0 ? (double *)mapped_host(state, sbytes) : nullptr;
     const double *hm = hs ? (const double *)mapped_host(masses, mbytes) : nullptr;
+    if (hs && hm && small_path(n)) {
+        rc = step_small(hs, hs, hm, n, dt, order, nsteps);
+        if (rc) return rc;
+        return drain_status();
+    }
     if (hs && hm) {
         double w[sakura::kMaxSubsteps];
         int so;
@@ -623,9 +705,14 @@ int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt
     if (cudaMemcpyAsync(ds, state, sbytes, cudaMemcpyHostToDevice, g.stream) != cudaSuccess ||
         cudaMemcpyAsync(dm, masses, mbytes, cudaMemcpyHostToDevice, g.stream) != cudaSuccess)
         return SAKURA_E_CUDA;
-    for (int k = 0; k < nsteps; ++k) {
-        rc = step_composed(ds, dm, n, dt, order);
+    if (nsteps > 0 && small_path(n)) {
+        rc = step_small(ds, ds, dm, n, dt, order, nsteps);
         if (rc) return rc;
+    } else {
+        for (int k = 0; k < nsteps; ++k) {
+            rc = step_composed(ds, dm, n, dt, order);
+            if (rc) return rc;
+        }
     }
     if (cudaMemcpyAsync(state, ds, sbytes, cudaMemcpyDeviceToHost, g.stream) != cudaSuccess)
         return SAKURA_E_CUDA;

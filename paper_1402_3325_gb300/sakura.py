@@ -44,6 +44,9 @@ FLAG_SYNC_CHECK = 1
 FLAG_STATS = 2
 FLAG_TIMING = 4
 FLAG_NO_AUTOTUNE = 8
+FLAG_NO_SMALL = 16
+# largest system of the single-block kernel (csrc/step_small.cuh)
+SMALL_MAX_N = 20
 BATCH_MAX_N = 64
 
 MLP_FLOATS = 6 * 64 + 64 + 64 * 64 + 64 + 64 + 1 + 6 + 6 + 2
@@ -109,6 +112,7 @@ def load(path: str = LIB_PATH):
     lib.sakura_finalize.argtypes = []
     lib.sakura_set_stream.argtypes = [P]
     lib.sakura_step.argtypes = [P, P, I64, D, I]
+    lib.sakura_evolve.argtypes = [P, P, I64, D, I, I]
     lib.sakura_evolve_host.argtypes = [P, P, I64, D, I, I]
     lib.sakura_energy.argtypes = [P, P, I64, ctypes.POINTER(D)]
     lib.sakura_step_batched.argtypes = [P, P, P, P, I, P, I, I]
@@ -125,7 +129,7 @@ def load(path: str = LIB_PATH):
     lib.sakura_strerror.argtypes = [I]
     lib.sakura_strerror.restype = ctypes.c_char_p
     for name in ("sakura_init", "sakura_finalize", "sakura_set_stream", "sakura_step",
-                 "sakura_evolve_host", "sakura_energy", "sakura_step_batched",
+                 "sakura_evolve", "sakura_evolve_host", "sakura_energy", "sakura_step_batched",
                  "sakura_load_mlp", "sakura_get_stats", "sakura_check",
                  "sakura_step_noalloc", "sakura_batched_tuning", "sakura_sample_pairs",
                  "sakura_mlp_grad", "sakura_mlp_train", "sakura_mlp_eval"):
@@ -195,6 +199,16 @@ def step(state, masses, dt: float, order: int = 2):
         raise ValueError("state must have shape (6, n)")
     _check(load().sakura_step(_ptr(state), _ptr(masses), n, float(dt), int(order)),
            "sakura_step")
+
+
+def evolve(state, masses, dt: float, order: int = 2, nsteps: int = 1):
+    """nsteps steps in place on a CUDA float64 state [6, n] with masses [n]
+    (one launch for the systems of the single-block kernel)."""
+    n = masses.shape[0]
+    if tuple(state.shape) != (6, n):
+        raise ValueError("state must have shape (6, n)")
+    _check(load().sakura_evolve(_ptr(state), _ptr(masses), n, float(dt), int(order),
+                                int(nsteps)), "sakura_evolve")
 
 
 NOALLOC_MAX_N = 65536

@@ -48,3 +48,21 @@ def test_mlp_size_constant_matches_header():
     with open(sk.HEADER) as fh:
         assert "4687" in fh.read()
     assert sk.MLP_FLOATS == 4687
+
+
+def test_flag_and_small_limit_constants_match_the_sources():
+    import os
+    import re
+    with open(sk.HEADER) as fh:
+        hdr = fh.read()
+    for name in ("SYNC_CHECK", "STATS", "TIMING", "NO_AUTOTUNE", "NO_SMALL"):
+        m = re.search(r"#define SAKURA_FLAG_%s (\d+)u" % name, hdr)
+        assert m and int(m.group(1)) == getattr(sk, "FLAG_" + name), name
+    src = os.path.join(os.path.dirname(sk.LIB_PATH), "csrc", "step_small.cuh")
+    with open(src) as fh:
+        m = re.search(r"constexpr int kSmallMaxN = (\d+);", fh.read())
+    assert m and int(m.group(1)) == sk.SMALL_MAX_N
+
+
+def test_evolve_entry_points_without_gpu(lib):
+    assert lib.sakura_evolve(None, None, 4, 0.1, 2, 3) == sk.E_NOINIT
