@@ -206,7 +206,8 @@ def _kernel_sources_hash(kernel: str = "pair_step_sym") -> str:
     csrc = os.path.join(ROOT, "paper_1402_3325_gb300", "csrc")
     files = {"pair_step_sym": ["df64.cuh", "kepler_df64.cuh", "step_sym.cu"],
              "pair_step_fp64": ["step_fp64.cu"],
-             "pair_step_sym_df64": ["df64.cuh", "kepler_df64.cuh", "step_df64.cu"]}.get(
+             "pair_step_sym_df64": ["df64.cuh", "kepler_df64.cuh", "step_df64.cu"],
+             "small": ["df64.cuh", "kepler_df64.cuh", "step_small.cu", "step_small.cuh"]}.get(
                  kernel, ["step_fp64.cu"])
     for f in ["kepler_fp64.cuh", "pair_batch_fp64.cuh", "fp_bits.cuh", "step_common.cuh",
               "kepler_fp32.cuh"] + files:
