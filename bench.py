@@ -236,22 +236,32 @@ def _profiled_traffic(workload: str, kernel: str):
         return None
 
 
-def _cpu_baseline(s, dt, budget_s=10.0, max_steps=256):
+def _cpu_baseline(s, dt, budget_s=10.0, max_steps=256, min_s=2.0):
+    """The oracle on the host cores: up to max_steps consecutive steps of the
+    workload from its initial state, stopped after budget_s; a workload that
+    takes less than min_s is run again from its initial state until min_s
+    has passed (a few milliseconds cannot be timed reliably)."""
     import oracle
     cores = os.cpu_count() or 1
     oracle.build()
-    r, v = s.r.copy(), s.v.copy()
     t0 = time.perf_counter()
-    steps = 0
-    while steps < max_steps:
-        rc, r, v = oracle.step(s.m, r, v, dt, 2, nthreads=cores)
-        steps += 1
-        if time.perf_counter() - t0 >= budget_s:
+    steps = passes = 0
+    while True:
+        r, v = s.r.copy(), s.v.copy()
+        for _ in range(max_steps):
+            rc, r, v = oracle.step(s.m, r, v, dt, 2, nthreads=cores)
+            steps += 1
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        passes += 1
+        el = time.perf_counter() - t0
+        if el >= min_s or el >= budget_s:
             break
-    el = time.perf_counter() - t0
+    what = (f"{steps} consecutive steps" if passes == 1 else
+            f"{passes} passes of {max_steps} consecutive steps")
     return {"value": s.n ** 2 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{steps} consecutive steps of the same workload (N={s.n}) from its"
-                      f" initial state, OpenMP over i on {cores} threads, {el:.1f} s"}
+            "sample": f"{what} of the same workload (N={s.n}) from its initial state,"
+                      f" OpenMP over i on {cores} threads, {el:.1f} s"}
 
 
 def run_reference(args, rank):
@@ -420,10 +430,10 @@ def _pair_kernel_ms(args, sk, s, state, mass, device, stream, flush, guess, opts
     return st["pair_kernel_ms"] / max(1, args.steps)
 
 
-def _variant_df64(args, sk, s, device, stream, flush, guess):
+def _variant_df64(args, sk, s, device, stream, flush, guess, per_call=1, small=False):
     """The same workload and step count in the double-word form (FP64-accurate
-    pair solves on the FP32 pipe), timed the same way; reported beside the
-    plain FP64 headline."""
+    pair solves on the FP32 pipe), timed the same way (calls of per_call
+    steps); reported beside the plain FP64 headline."""
     import torch
     n = s.n
     opts = dict(pair_mode=sk.PAIRS_SYMMETRIC, precision=sk.PREC_DF64)
@@ -440,19 +450,24 @@ def _variant_df64(args, sk, s, device, stream, flush, guess):
     sk.init(device.index, stream=stream.cuda_stream, guess=guess, **opts)
     state.copy_(torch.tensor(s.soa(), device=device))
     E0 = sk.energy(state, mass)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    nt = args.steps // per_call
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(nt)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(nt)]
     torch.cuda.synchronize(device)
-    for k in range(args.steps):
+    for k in range(nt):
         flush.fill_(float(k))
         starts[k].record(stream)
-        sk.step(state, mass, s.dt, 2)
+        if per_call > 1:
+            sk.evolve(state, mass, s.dt, 2, per_call)
+        else:
+            sk.step(state, mass, s.dt, 2)
         ends[k].record(stream)
     torch.cuda.synchronize(device)
     sk.check()
     ms_total = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
     dE = abs(sk.energy(state, mass) / E0 - 1.0)
-    pair_ms = _pair_kernel_ms(args, sk, s, state, mass, device, stream, flush, guess, opts)
+    pair_ms = _pair_kernel_ms(args, sk, s, state, mass, device, stream, flush, guess, opts,
+                              per_call)
     flops = DF64_FLOPS_PER_SOLVE.get(args.workload)
     solves = n * (n - 1) * spp
     achieved = solves * flops / (pair_ms * 1e-3) / 1e12 if flops else None
@@ -465,8 +480,10 @@ def _variant_df64(args, sk, s, device, stream, flush, guess):
             "energy_error": dE,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak if achieved else None,
-                         "traffic": _profiled_traffic(args.workload, "pair_step_sym_df64"),
-                         "kernel": "pair_step_sym_df64_kernel", "pipe": "fp32",
+                         "traffic": _profiled_traffic(
+                             args.workload, "small" if small else "pair_step_sym_df64"),
+                         "kernel": "small_kernel" if small else "pair_step_sym_df64_kernel",
+                         "pipe": "fp32",
                          "flops_per_solve": flops, "pair_kernel_ms": pair_ms}}
 
 
@@ -575,10 +592,11 @@ def main():
         100 if args.workload == "planetary9" else 1)
     if per_call < 1 or args.steps % per_call != 0:
         raise SystemExit("--steps must be a multiple of --steps-per-call")
-    # the single-block kernel (csrc/step_small.cu) takes the FP64 form of
-    # small systems, each unordered pair once, non-learned guesses
-    small = (n <= sk.SMALL_MAX_N and args.form == "fp64" and args.pairs == "symmetric" and
-             args.guess != "learned")
+    # the single-block kernel (csrc/step_small.cu) takes the FP64 and
+    # double-word forms of small systems, each unordered pair once,
+    # non-learned guesses
+    small = (n <= sk.SMALL_MAX_N and args.form in ("fp64", "df64") and
+             args.pairs == "symmetric" and args.guess != "learned")
     sk.init(device.index, stream=stream.cuda_stream, guess=guess, **form_opts)
     state.copy_(torch.tensor(s.soa(), device=device))
     E0 = sk.energy(state, mass)
@@ -640,7 +658,7 @@ def main():
     if args.form == "df64":
         flops_solve = DF64_FLOPS_PER_SOLVE.get(args.workload)
         peak = FP32_PEAK_GFLOPS / 1e3
-        kname, pipe = "pair_step_sym_df64", "fp32"
+        kname, pipe = ("small" if small else "pair_step_sym_df64"), "fp32"
         peak_source = ("152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz; flops per solve counted"
                        " by running the double-word code on the host with an operation tally")
     elif args.form == "mixed" and args.pairs == "symmetric" and fp32_share >= 0.5:
@@ -728,9 +746,11 @@ def main():
         line["e2e"] = e2e
     if (args.form == "fp64" and args.pairs == "symmetric" and not args.no_variants and
             args.workload in DF64_FLOPS_PER_SOLVE):
-        line["variants"] = {"df64": _variant_df64(args, sk, s, device, stream, flush, guess)}
+        line["variants"] = {"df64": _variant_df64(args, sk, s, device, stream, flush, guess,
+                                                  per_call, n <= sk.SMALL_MAX_N)}
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline(s, s.dt)
+        line["cpu_baseline"] = _cpu_baseline(s, s.dt,
+                                             max_steps=min(256, _workload(args.workload, 0)[1]))
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

@@ -439,10 +439,11 @@ int step_composed(double *state, const double *masses, int64_t n, double dt, int
 }
 
 // Systems small enough for the single-block kernel (step_small.cu): the FP64
-// form with each unordered pair once and a non-learned guess.
+// or double-word form with each unordered pair once and a non-learned guess.
 bool small_path(int64_t n)
 {
-    return n >= 2 && n <= sakura::kSmallMaxN && g.cfg.precision == SAKURA_PREC_FP64 &&
+    return n >= 2 && n <= sakura::kSmallMaxN &&
+           (g.cfg.precision == SAKURA_PREC_FP64 || g.cfg.precision == SAKURA_PREC_DF64) &&
            g.cfg.pair_mode == SAKURA_PAIRS_SYMMETRIC && g.cfg.guess != SAKURA_GUESS_LEARNED &&
            !(g.cfg.flags & SAKURA_FLAG_NO_SMALL);
 }
@@ -469,7 +470,12 @@ int step_small(const double *src, double *dst, const double *masses, int64_t n, 
     a.tol = g.cfg.kepler_tol * DBL_EPSILON;
     a.max_iter = g.cfg.kepler_max_iter;
     a.bisection = g.cfg.kepler_bisection;
-    a.guess = g.cfg.guess == SAKURA_GUESS_TAYLOR ? 2 : 0;
+    const bool dw = g.cfg.precision == SAKURA_PREC_DF64;
+    // the double-word form's FP32 phase seeds its own evaluations; its FP64
+    // solves (pairs it does not admit) start from the second-order guess
+    a.guess = (g.cfg.guess == SAKURA_GUESS_TAYLOR || (dw && g.cfg.guess == SAKURA_GUESS_FP32))
+                  ? 2
+                  : 0;
     a.status = g.d_status;
     a.stats = g.d_stats;
     const bool timing = (g.cfg.flags & SAKURA_FLAG_TIMING) != 0;
@@ -479,7 +485,7 @@ int step_small(const double *src, double *dst, const double *masses, int64_t n, 
         cudaEventRecord(tm.first, g.stream);
     }
     sakura::launch_small(a, (g.cfg.flags & SAKURA_FLAG_STATS) != 0,
-                         g.cfg.guess == SAKURA_GUESS_FP32, g.stream);
+                         !dw && g.cfg.guess == SAKURA_GUESS_FP32, dw, g.stream);
     if (timing) {
         cudaEventRecord(tm.second, g.stream);
         g.timers.push_back(tm);

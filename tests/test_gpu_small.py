@@ -91,6 +91,43 @@ def test_small_step_matches_oracle(name, s, order, guess):
     assert er <= TOL and ev <= TOL, (er, ev)
 
 
+@pytest.mark.parametrize("guess", ["fp32", "standard"])
+@pytest.mark.parametrize("order", [2, 1, -1])
+@pytest.mark.parametrize("name,s", SYSTEMS, ids=[n for n, _ in SYSTEMS])
+def test_small_double_word_step_matches_oracle(name, s, order, guess):
+    # the double-word form: pair solves on the FP32 pipe, FP64 solves for the
+    # pairs it does not admit, sums in FP64; the same 1e-12 bound
+    with configured(guess=GUESSES[guess], precision=sk.PREC_DF64):
+        sk.get_stats(reset=True)
+        r, v = run(s, s.dt, order)
+        st = sk.get_stats(reset=True)
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, order, nthreads=NCPU)
+    assert rc == oracle.OK
+    er, ev = rel_err(r, v, rr, vr)
+    assert er <= TOL and ev <= TOL, (er, ev)
+    assert 0 <= st["fp32_pairs"] <= st["solves"] == s.n * (s.n - 1) // 2
+
+
+def test_small_double_word_solves_most_pairs_and_repeats_bit_for_bit():
+    s = ics.planetary(0)
+    with configured(guess=sk.GUESS_FP32, precision=sk.PREC_DF64):
+        sk.get_stats(reset=True)
+        a = dev(s.soa())
+        m = dev(s.m)
+        sk.evolve(a, m, s.dt, 2, 40)
+        st = sk.get_stats(reset=True)
+        b = dev(s.soa())
+        for _ in range(40):
+            sk.step(b, m, s.dt, 2)
+        sk.check()
+    assert st["fp32_pairs"] >= 0.9 * st["solves"], st
+    np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+    rc, rr, vr = oracle.evolve(s.m, s.r, s.v, s.dt, 40)
+    r, v = ics.from_soa(a.cpu().numpy())
+    er, ev = rel_err(r, v, rr, vr)
+    assert er <= 1e-11 and ev <= 1e-11, (er, ev)
+
+
 @pytest.mark.parametrize("order", [4, 6])
 @pytest.mark.parametrize("name,s", SYSTEMS[:4], ids=[n for n, _ in SYSTEMS[:4]])
 def test_small_composed_step_matches_oracle(name, s, order):
@@ -137,15 +174,18 @@ def test_small_evolve_equals_repeated_steps(order):
         np.testing.assert_array_equal(ps.numpy(), a.cpu().numpy())
 
 
+@pytest.mark.parametrize("form", ["fp64", "df64"])
 @pytest.mark.parametrize("name,s", SYSTEMS, ids=[n for n, _ in SYSTEMS])
-def test_small_agrees_with_multi_kernel_step(name, s):
+def test_small_agrees_with_multi_kernel_step(name, s, form):
     # one step from the same input: the same solves, a different summation
     # order, so rounding only, well inside the 1e-12 per-step bound that each
     # meets against the oracle.  (Over several steps the tight binaries, many
     # periods per step, amplify such differences: 7.6e-11 in v after three.)
-    with configured(guess=sk.GUESS_FP32):
+    prec = sk.PREC_DF64 if form == "df64" else sk.PREC_FP64
+    with configured(guess=sk.GUESS_FP32, precision=prec):
         r1, v1 = run(s, s.dt, 2)
-    with configured(guess=sk.GUESS_FP32, flags=sk.FLAG_STATS | sk.FLAG_NO_SMALL):
+    with configured(guess=sk.GUESS_FP32, precision=prec,
+                    flags=sk.FLAG_STATS | sk.FLAG_NO_SMALL):
         r2, v2 = run(s, s.dt, 2)
     er, ev = rel_err(r1, v1, r2, v2)
     assert er <= 1e-13 and ev <= 1e-13, (er, ev)
@@ -170,13 +210,15 @@ def test_small_limits_route_elsewhere():
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
     er, ev = rel_err(r, v, rr, vr)
     assert er <= TOL and ev <= TOL, (er, ev)
+    # (the mixed form's own parity bound is 1e-8, tests/test_gpu_mixed.py)
     s = ics.random_cluster(12, seed=9)
-    for opts in (dict(pair_mode=sk.PAIRS_ORDERED), dict(precision=sk.PREC_DF64)):
+    for opts, tol in ((dict(pair_mode=sk.PAIRS_ORDERED), TOL),
+                      (dict(precision=sk.PREC_MIXED), 1e-8)):
         with configured(**opts):
             r, v = run(s, s.dt, 2)
         rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
         er, ev = rel_err(r, v, rr, vr)
-        assert er <= TOL and ev <= TOL, (opts, er, ev)
+        assert er <= tol and ev <= tol, (opts, er, ev)
 
 
 def test_small_zero_steps_is_a_no_op():
