@@ -207,7 +207,9 @@ def _kernel_sources_hash(kernel: str = "pair_step_sym") -> str:
     files = {"pair_step_sym": ["df64.cuh", "kepler_df64.cuh", "step_sym.cu"],
              "pair_step_fp64": ["step_fp64.cu"],
              "pair_step_sym_df64": ["df64.cuh", "kepler_df64.cuh", "step_df64.cu"],
-             "small": ["df64.cuh", "kepler_df64.cuh", "step_small.cu", "step_small.cuh"]}.get(
+             "small": ["df64.cuh", "kepler_df64.cuh", "step_small.cu", "step_small.cuh"],
+             "batched": ["df64.cuh", "kepler_df64.cuh", "mlp_infer.cuh", "step_batched.cu",
+                         "step_batched.cuh"]}.get(
                  kernel, ["step_fp64.cu"])
     for f in ["kepler_fp64.cuh", "pair_batch_fp64.cuh", "fp_bits.cuh", "step_common.cuh",
               "kepler_fp32.cuh"] + files:
@@ -366,7 +368,9 @@ def run_ensemble(args, rank, world, device, stream, dist):
                        "l2": "state (7.7 MB) stays in shared memory for the whole call"},
             "gpu_launches": 1,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         # a launch reads the state once, whatever its step count
+                         "traffic": _profiled_traffic(args.workload, "batched"),
                          "kernel": "batched_kernel", "pipe": "fp64",
                          "flops_per_solve": flops_solve, "kepler_evals_per_solve": kbar,
                          "iteration_lane_efficiency": lane_eff},

@@ -220,8 +220,11 @@ int sakura_energy(const double *state, const double *masses, int64_t n, double *
  *   dt: device double[nsys], one step size per system.
  * Runs nsteps steps of the given order (2, 1, -1, 4, 6, 8) on every system, state
  * updated in place.  Each unordered pair of a system is solved once per
- * step.  A block runs all steps of its systems with the state in shared
- * memory, its warps splitting every step's pair rounds; the launch is a CUDA
+ * step.  A block runs all steps of its systems (up to 64 particles in all)
+ * with the state in shared memory; their pairs are packed densely over its
+ * warps' lanes and each particle's increments are summed over its own
+ * system in a fixed order (results independent of the packing and of the
+ * block shape); the launch is a CUDA
  * graph (counter reset + kernel), built once per (buffers, schedule, nsteps,
  * order, block shape) and replayed.  The first call with a new schedule
  * times the candidate block shapes (1, 2, 4, 8 warps) on a scratch copy and

@@ -1,39 +1,38 @@
 // step_batched.cu -- many independent small systems in one persistent launch.
 //
-// The systems of an ensemble never interact, so a warp can take a system (or
-// several small ones) and run all requested steps on it without any
-// synchronisation beyond its own lanes: the state lives in shared memory for
-// the whole launch.
+// The systems of an ensemble never interact, so a block can take a few of
+// them and run all requested steps on them with their state in shared memory
+// for the whole launch.
 //
-// Each unordered pair is solved once (Newton's third law, as in the symmetric
-// single-system kernel): the increments of (i, j) and (j, i) are exact
-// negatives, so the solving lane adds m_j delta / m_ij to i and
-// -m_i delta / m_ij to j (Eq. 23).  A system of N >= 2 particles takes
-// h = floor(N / 2) lanes and walks its pairs in the round-robin ("circle")
-// order, so that its lanes x rounds equal its N (N - 1) / 2 pairs:
-//   N even, M = N - 1: round r = 0 .. M-1 pairs particle M with particle r
-//     (lane 0 of the system) and (r + k) mod M with (r - k) mod M (lane k =
-//     1 .. h-1);
-//   N odd: round r = 0 .. N-1 pairs (r + k) mod N with (r - k) mod N (lane
-//     k - 1 for k = 1 .. h); particle r sits the round out.
-// No particle is in two pairs of a round, so the lanes add to disjoint
-// accumulators (shared memory, in round order: deterministic); over the
-// rounds every unordered pair comes up exactly once.  A single particle
-// takes one lane and no rounds.
+// Each unordered pair is solved once (Newton's third law, as in the
+// symmetric single-system kernel): the increments of (i, j) and (j, i) are
+// exact negatives.  A task is a set of systems of at most kBatchMaxN = 64
+// particles in all.  Its pairs are numbered system by system, row by row
+// within a system (pair (a, b), a < b, of a system of N particles at
+// a N - a (a + 1) / 2 + b - a - 1 after the pairs of the systems before it),
+// and packed densely over the lanes: lane l of chunk c solves pair 32 c + l,
+// chunks dealt out over the block's warps.  (A warp instruction costs the
+// FP64 pipe the same however many lanes are active, so dense packing matters:
+// a round-robin order, n / 2 lanes for n - 1 rounds per system, filled 88 %
+// of the lanes on the 4096-system ensemble; this fills 99 %.)  A task has at
+// most 64 * 63 / 2 = 2016 pairs, whose increments divided by m_ab go to
+// shared memory; after a block barrier element (i, c) adds particle i's
+// increments of component c over its own system in ascending j (+m_j d for
+// the pair (i, j), -m_j d for (j, i); Eq. 23 with 1/m_i folded in), a fixed
+// order independent of the packing and of the block shape, and applies
+// Eqs. 27b-d.  The per-particle work (drift and sums) runs on consecutive
+// threads (element e on thread e), so that a warp's lanes mostly hold one
+// system (one loop length) and as few warps as possible issue it: the kernel
+// is bound by the FP64 pipe's throughput, and a warp instruction costs the
+// same however many of its lanes work.  The step's time values of each
+// particle's system (tau, post tau and their single-precision copies) are
+// formed once per particle and sub-step, not once per pair.
 //
-// Schedule (built on the host when the offsets change): systems are packed
-// best-fit-decreasing into tasks of at most 32 lanes and kBatchMaxN = 64
-// particles (build_batch_schedule); a task's lockstep length is the largest
-// round count among its systems.  Tasks are sorted by that length and
-// handed out through an atomic counter (dynamic longest-first), one task to
-// a block at a time.
-//
-// Per step, per block: lane k of a system drifts its particles 2k and 2k + 1
-// (and the last particle of an odd system, on its last lane) (Eq. 27a),
-// the rounds run as warp-synchronous FP64 Kepler solves (same solver as the
-// single-system kernel) split over the block's warps, and after a block
-// barrier each lane applies Eqs. 27b-d to its particles.  Each system keeps
-// its own dt.
+// Schedule (built on the host when the offsets change): systems packed
+// best-fit-decreasing by particles into tasks of at most 64; tasks sorted by
+// pair count and handed out through an atomic counter (dynamic
+// longest-first), one task to a block at a time.  Each system keeps its own
+// dt.
 //
 // The counter reset and the launch form a CUDA graph that is built once per
 // (buffers, schedule, nsteps, order, launch shape) and replayed.  A small
@@ -56,42 +55,43 @@
 
 namespace sakura {
 
-constexpr int kBatchMaxN = 64;
+constexpr int kBatchMaxN = 64;                                      // particles of a task
+constexpr int kBatchMaxPairs = kBatchMaxN * (kBatchMaxN - 1) / 2;  // 2016
 
-// lanes and rounds of a system of N particles (see above)
-__host__ __device__ __forceinline__ int batch_lanes(int N) { return N < 2 ? 1 : N / 2; }
-__host__ __device__ __forceinline__ int batch_rounds(int N)
+// pair index of (a, b), a < b, within a system of N particles
+__host__ __device__ __forceinline__ int local_pair(int a, int b, int N)
 {
-    return N < 2 ? 0 : ((N & 1) ? N : N - 1);
+    return a * N - a * (a + 1) / 2 + b - a - 1;
 }
 
-// One task per block: its WARPS warps share the task's state in shared
-// memory and split the rounds of every step, warp w taking rounds r = w,
-// w + WARPS, ... into its own accumulators; the apply adds the WARPS
-// accumulators in warp order (deterministic).  A warp's solve round is
-// latency-bound, so the largest systems (63 rounds per step for N = 64) set
-// the length of the launch; splitting their rounds shortens it.
-// SEED: the single-precision seed and the Taylor carry of the symmetric
-// FP64 kernel (float copies of the drifted state in shared memory, hi + lo
-// positions, refreshed after every drift).
-// Dynamic shared memory: the accumulators [WARPS][6][kBatchMaxN] doubles,
-// then (LEARNED) the network and its per-warp staging.
+// One task per block; WARPS warps share its state in shared memory.
+// SEED: the single-precision seed and the Taylor carry of the symmetric FP64
+// kernel (float copies of the drifted state, hi + lo positions, refreshed
+// after every drift).  LEARNED: the network guess.
+// Dynamic shared memory: the increments D[6][kBatchMaxPairs] doubles, then
+// (LEARNED) the network and its per-warp staging.
 template <int WARPS, bool STATS, bool LEARNED, bool SEED>
 __global__ void __launch_bounds__(WARPS * 32)
     batched_kernel(BatchArgs a)
 {
     __shared__ double S[7][kBatchMaxN];
     __shared__ float S32[SEED ? 10 : 1][kBatchMaxN];
+    __shared__ double Pdt[kBatchMaxN];           // the particle's system's dt
+    __shared__ double Ptau[kBatchMaxN], Pqtau[kBatchMaxN];  // tau, post tau of the sub-step
+    __shared__ float Pptau32[kBatchMaxN], Pt32[kBatchMaxN];  // (float)(pre tau), (float)tau
+    __shared__ unsigned char Pbase[kBatchMaxN];  // its system's first slot
+    __shared__ unsigned char PN[kBatchMaxN];     // its system's size
+    __shared__ unsigned short Ppb[kBatchMaxN];   // its system's first pair
+    __shared__ unsigned char PA[kBatchMaxPairs], PB[kBatchMaxPairs];
     __shared__ int s_task;
     extern __shared__ __align__(16) unsigned char dsm[];
-    double(*shacc)[6][kBatchMaxN] = reinterpret_cast<double(*)[6][kBatchMaxN]>(dsm);
-    unsigned char *dnet = dsm + (size_t)WARPS * 6 * kBatchMaxN * sizeof(double);
+    double(*D)[kBatchMaxPairs] = reinterpret_cast<double(*)[kBatchMaxPairs]>(dsm);
+    unsigned char *dnet = dsm + (size_t)6 * kBatchMaxPairs * sizeof(double);
     MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(dnet);
     __nv_bfloat16 *mlpStage = reinterpret_cast<__nv_bfloat16 *>(dnet + sizeof(MlpWeights));
     if (LEARNED) mlp_load_shared(*mlpW, a.mlp);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    double(*A)[kBatchMaxN] = shacc[wib];
     const int64_t tot = a.total;
     const KeplerParams kp{a.tol, a.max_iter, a.bisection};
     unsigned status = 0;
@@ -104,93 +104,66 @@ __global__ void __launch_bounds__(WARPS * 32)
         const int t = s_task;
         if (t >= a.ntasks) break;
         const int sb = a.task_begin[t], se = a.task_begin[t + 1];
-        // the lane's system: its particles at my_base .. my_base + my_N - 1,
-        // the lane's index my_k in the system (-1: no system); the same in
-        // every warp of the block
-        int my_k = -1, my_base = 0, my_N = 0;
-        double dt = 0.0;
-        int base = 0, lbase = 0;
+        // load the task's systems, their per-particle data and pair table
+        int npart = 0, npairs = 0;
         for (int q = sb; q < se; ++q) {
             const int k = a.task_sys[q];
             const int64_t o0 = a.offsets[k];
             const int Nk = (int)(a.offsets[k + 1] - o0);
+            const double dtk = a.dt[k];
             for (int pi = threadIdx.x; pi < Nk; pi += WARPS * 32) {
+                const int i = npart + pi;
 #pragma unroll
-                for (int c = 0; c < 6; ++c) S[c][base + pi] = a.state[c * tot + o0 + pi];
+                for (int c = 0; c < 6; ++c) S[c][i] = a.state[c * tot + o0 + pi];
                 const double m = a.mass[o0 + pi];
                 if (!(m > 0.0)) status |= kStatusMass;
-                S[6][base + pi] = m;
+                S[6][i] = m;
+                Pdt[i] = dtk;
+                Pbase[i] = (unsigned char)npart;
+                PN[i] = (unsigned char)Nk;
+                Ppb[i] = (unsigned short)npairs;
+                int p = npairs + local_pair(pi, pi + 1, Nk);  // the pairs (pi, b), b > pi
+                for (int b = pi + 1; b < Nk; ++b, ++p) {
+                    PA[p] = (unsigned char)i;
+                    PB[p] = (unsigned char)(npart + b);
+                }
             }
-            const int hk = batch_lanes(Nk);
-            if (lane >= lbase && lane < lbase + hk) {
-                my_k = lane - lbase;
-                my_base = base;
-                my_N = Nk;
-                dt = a.dt[k];
-            }
-            base += Nk;
-            lbase += hk;
+            npart += Nk;
+            npairs += Nk * (Nk - 1) / 2;
         }
         __syncthreads();
-        const bool odd = (my_N & 1) != 0;
-        const int rounds = my_k >= 0 ? batch_rounds(my_N) : 0;
-        const int M = odd ? my_N : my_N - 1;  // circle length
-        const int maxr = __reduce_max_sync(0xffffffffu, rounds);
-        // the lane's particles 2k, 2k + 1 (and, on the last lane of an odd
-        // system, 2k + 2 = N - 1): drift, accumulators, apply
-        const int np = my_k < 0 ? 0
-                                : (my_N < 2 ? 1
-                                            : 2 + ((odd && my_k == batch_lanes(my_N) - 1) ? 1 : 0));
+        const int chunks = (npairs + 31) >> 5;
 
         for (int64_t sub = 0; sub < (int64_t)a.nsteps * a.nsub; ++sub) {
             // sub-step sub % nsub of the composition (one sub-step for orders 2, 1, -1)
-            const double tau = dt * a.sub[(int)(sub % a.nsub)];
-            const double drift = a.drift_frac * tau;
-            const double post_drift = a.post_drift_frac * tau;
-            const double qtau = a.post * tau;
-            for (int e = 0; e < np; ++e) {
-                const int i = my_base + 2 * my_k + e;
-                if (wib == 0) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) S[c][i] = fma(S[3 + c][i], drift, S[c][i]);
-                    if (SEED) {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const float hi = __double2float_rn(S[c][i]);
-                            S32[c][i] = hi;
-                            S32[3 + c][i] = __double2float_rn(S[c][i] - (double)hi);
-                            S32[6 + c][i] = __double2float_rn(S[3 + c][i]);
-                        }
-                        S32[9][i] = __double2float_rn(S[6][i]);
-                    }
+            const double w = a.sub[(int)(sub % a.nsub)];
+            for (int e = threadIdx.x; e < 3 * npart; e += WARPS * 32) {  // Eq. 27a, (i, c)
+                const int c = e / npart, i = e - c * npart;
+                const double tau = Pdt[i] * w;
+                if (c == 0) {
+                    Ptau[i] = tau;
+                    Pqtau[i] = a.post * tau;
+                    Pptau32[i] = (float)(a.pre * tau);
+                    Pt32[i] = (float)tau;
                 }
-#pragma unroll
-                for (int c = 0; c < 6; ++c) A[c][i] = 0.0;
+                const double x = fma(S[3 + c][i], a.drift_frac * tau, S[c][i]);
+                S[c][i] = x;
+                if (SEED) {
+                    const float hi = __double2float_rn(x);
+                    S32[c][i] = hi;
+                    S32[3 + c][i] = __double2float_rn(x - (double)hi);
+                    S32[6 + c][i] = __double2float_rn(S[3 + c][i]);
+                    if (c == 0) S32[9][i] = __double2float_rn(S[6][i]);
+                }
             }
             __syncthreads();
-            const float ptau32 = (float)(a.pre * tau), t32 = (float)tau;
-            for (int r = wib; r < maxr; r += WARPS) {
-                // the lane's pair of round r (local indices)
-                int il = my_N, jl = 0;
-                if (r < rounds) {
-                    if (!odd && my_k == 0) {
-                        il = M;
-                        jl = r;
-                    } else {
-                        const int k = odd ? my_k + 1 : my_k;
-                        il = r + k;
-                        if (il >= M) il -= M;
-                        jl = r - k;
-                        if (jl < 0) jl += M;
-                    }
-                }
-                const bool valid = il < my_N;
-                const int i = my_base + il, j = my_base + jl;
-                PairSolve p;
-                double mi = 0.0, mj = 0.0;
+            for (int ch = wib; ch < chunks; ch += WARPS) {
+                const int p = 32 * ch + lane;
+                const bool valid = p < npairs;
+                const int i = valid ? PA[p] : 0, j = valid ? PB[p] : 0;
+                const double tau = Ptau[i];
+                PairSolve ps;
                 if (valid) {
-                    mi = S[6][i];
-                    mj = S[6][j];
                     K32 o;
                     if (SEED) {
                         // single-precision seed: the root of the FP32 solve of
@@ -202,75 +175,71 @@ __global__ void __launch_bounds__(WARPS * 32)
                                               __fsub_rn(S32[3 + c][i], S32[3 + c][j]));
                             dv[c] = __fsub_rn(S32[6 + c][i], S32[6 + c][j]);
                         }
-                        o = k32_phase1(dr, dv, S32[9][i] + S32[9][j], ptau32, t32, 2);
+                        o = k32_phase1(dr, dv, S32[9][i] + S32[9][j], Pptau32[i], Pt32[i], 2);
                     }
-                    pair_setup(p, tau, mi + mj, S[0][i] - S[0][j], S[1][i] - S[1][j],
+                    pair_setup(ps, tau, S[6][i] + S[6][j], S[0][i] - S[0][j], S[1][i] - S[1][j],
                                S[2][i] - S[2][j], S[3][i] - S[3][j], S[4][i] - S[4][j],
                                S[5][i] - S[5][j], a.pre, LEARNED ? 2 : (SEED ? -1 : a.guess));
                     if (SEED) {
-                        if (o.ok && __double_as_longlong(p.t) == __double_as_longlong(tau) &&
-                            !p.done) {
-                            p.s = f2d(o.s);
-                        } else if (!p.done) {
+                        if (o.ok && __double_as_longlong(ps.t) == __double_as_longlong(tau) &&
+                            !ps.done) {
+                            ps.s = f2d(o.s);
+                        } else if (!ps.done) {
                             // no usable seed: the second-order guess, as
                             // pair_setup computes it
-                            p.s = p.t * p.ir0;
-                            const double cq = 0.5 * p.s * (p.eta0 * p.ir0);
-                            if (magbits(cq) < 0x3fe0000000000000LL) p.s = fma(-cq, p.s, p.s);
+                            ps.s = ps.t * ps.ir0;
+                            const double cq = 0.5 * ps.s * (ps.eta0 * ps.ir0);
+                            if (magbits(cq) < 0x3fe0000000000000LL) ps.s = fma(-cq, ps.s, ps.s);
                         }
                     }
                 } else {
-                    p.done = true;
-                    p.beta = p.s = 0.0;
-                    p.iters = 0;
-                    p.status = 0;
+                    ps.done = true;
+                    ps.beta = ps.s = 0.0;
+                    ps.iters = 0;
+                    ps.status = 0;
                 }
-                if (LEARNED) learned_guess_warp(p, valid, *mlpW, mlpStage + wib * 32 * 16);
+                if (LEARNED) learned_guess_warp(ps, valid, *mlpW, mlpStage + wib * 32 * 16);
                 double d[6];
                 int iters = 0, fb = 0;
-                fp64_solve_warp<SEED>(p, valid, tau, qtau, kp, d, iters, fb);
-                if (STATS) carries += (valid && p.carried) ? 1 : 0;
+                fp64_solve_warp<SEED>(ps, valid, tau, Pqtau[i], kp, d, iters, fb);
                 if (valid) {
-                    // i and j are in no other lane's pair of this round; the
-                    // warp's own accumulators
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        A[q][i] = fma(mj, d[q], A[q][i]);
-                        A[q][j] = fma(-mi, d[q], A[q][j]);
-                    }
-                    status |= p.status;
+                    for (int q = 0; q < 6; ++q) D[q][p] = d[q];
+                    status |= ps.status;
                 }
                 if (STATS) {
+                    carries += (valid && ps.carried) ? 1 : 0;
                     it_sum += iters;
                     fallbacks += fb;
                     it_max = max(it_max, iters);
                     const int wmax = __reduce_max_sync(0xffffffffu, iters);
                     if (lane == 0) slots += 32LL * wmax;
                 }
-                __syncwarp();  // the warp's next round reads these sums
             }
             __syncthreads();
-            if (wib == 0) {
-                for (int e = 0; e < np; ++e) {
-                    const int i = my_base + 2 * my_k + e;
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        double sr = shacc[0][c][i], sv = shacc[0][3 + c][i];
-#pragma unroll
-                        for (int w = 1; w < WARPS; ++w) {
-                            sr += shacc[w][c][i];
-                            sv += shacc[w][3 + c][i];
-                        }
-                        const double v1 = S[3 + c][i] + sv;
-                        S[c][i] = fma(v1, post_drift, S[c][i] + sr);
-                        S[3 + c][i] = v1;
-                    }
+            // Eqs. 23 and 27b-d: element (i, c) sums particle i's increments
+            // of component c over its system in ascending j and updates v_c, x_c
+            for (int e = threadIdx.x; e < 3 * npart; e += WARPS * 32) {
+                const int c = e / npart, i = e - c * npart;
+                const int b0 = Pbase[i], N = PN[i], pb = Ppb[i], ai = i - b0;
+                double sr = 0.0, sv = 0.0;
+                for (int aj = 0; aj < N; ++aj) {
+                    if (aj == ai) continue;
+                    // the pair (j, i) for j < i gives -m_j d, the pair (i, j) +m_j d
+                    const int p = pb + local_pair(min(ai, aj), max(ai, aj), N);
+                    const double mj = S[6][b0 + aj];
+                    const double wj = aj < ai ? -mj : mj;
+                    sr = fma(wj, D[c][p], sr);
+                    sv = fma(wj, D[3 + c][p], sv);
                 }
+                const double v1 = S[3 + c][i] + sv;
+                S[c][i] = fma(v1, a.post_drift_frac * Ptau[i], S[c][i] + sr);
+                S[3 + c][i] = v1;
             }
             __syncthreads();
         }
         // write the task's systems back
-        base = 0;
+        int base = 0;
         for (int q = sb; q < se; ++q) {
             const int k = a.task_sys[q];
             const int64_t o0 = a.offsets[k];
@@ -336,12 +305,12 @@ const void *batched_kernel_ptr(int warps, bool stats, bool learned, bool seed)
 
 size_t batched_dyn_smem(int warps, bool learned)
 {
-    return (size_t)warps * 6 * kBatchMaxN * sizeof(double) +
+    return (size_t)6 * kBatchMaxPairs * sizeof(double) +
            (learned ? sizeof(MlpWeights) + (size_t)warps * 32 * 16 * 2 : 0);
 }
 
-// kernel pointer, with its dynamic shared memory allowed (above 48 KB per
-// block with the static arrays for 8 warps)
+// kernel pointer, with its dynamic shared memory allowed (the increments
+// take 94.5 KB)
 const void *batched_kernel_ready(int warps, bool stats, bool learned, bool seed)
 {
     const void *fn = batched_kernel_ptr(warps, stats, learned, seed);
@@ -367,15 +336,14 @@ int batched_blocks_per_sm(int warps, bool stats, bool learned, bool seed)
     return b > 0 ? b : 1;
 }
 
-// Schedule: systems packed best-fit-decreasing into warps of at most 32
-// lanes (batch_lanes) and kBatchMaxN particles (the shared-memory state):
-// each system, largest first, goes to the open warp with the fewest free
-// lanes that still takes it (warps kept in buckets by free lanes, so every
-// placement looks at 33 buckets, not at every warp).  On the 4096-system
-// ensemble (N uniform in [3, 64]) this fills 88 % of the lane-rounds, where
-// first fit over only the most recent warps filled 79 %.  Tasks are sorted
-// by cost (the lockstep length, the task's largest round count) so the
-// atomic counter hands out the longest first.
+// Schedule: systems packed best-fit-decreasing by particles into tasks of at
+// most kBatchMaxN particles: each system, largest first, goes to the open
+// task with the least room that still takes it (tasks kept in buckets by
+// free room, so a placement looks at 65 buckets).  A task's work is its
+// pair count, which fills ceil(pairs / 32) warp-wide chunks: on the
+// 4096-system ensemble (N uniform in [3, 64]) 99 % of the lanes are busy.
+// Tasks are sorted by pair count so the atomic counter hands out the
+// longest first.
 void build_batch_schedule(const int64_t *offsets, int nsys, std::vector<int> &task_begin,
                           std::vector<int> &task_sys)
 {
@@ -384,43 +352,33 @@ void build_batch_schedule(const int64_t *offsets, int nsys, std::vector<int> &ta
     auto size = [&](int k) { return (int)(offsets[k + 1] - offsets[k]); };
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return size(a) > size(b); });
     struct Bin {
-        int lanes;  // free lanes
         int room;   // free particle slots
-        int cost;
+        int pairs;  // unordered pairs of its systems
         std::vector<int> sys;
     };
     std::vector<Bin> bins;
-    std::vector<std::vector<int>> by_free(33);  // open bins by free lanes
+    std::vector<std::vector<int>> by_room(kBatchMaxN + 1);  // open bins by free room
     for (int k : order) {
         const int N = size(k);
-        const int h = batch_lanes(N), rounds = batch_rounds(N);
         int chosen = -1;
-        for (int f = h; f <= 32 && chosen < 0; ++f) {
-            std::vector<int> &bl = by_free[f];
-            // the 8 most recent bins of the bucket (a bin can lack particle
-            // room for a system whose lanes it has; the bound keeps every
-            // placement O(33 x 8) however many such bins collect)
-            for (int q = (int)bl.size() - 1; q >= 0 && q >= (int)bl.size() - 8; --q) {
-                if (bins[bl[q]].room >= N) {
-                    chosen = bl[q];
-                    bl.erase(bl.begin() + q);
-                    break;
-                }
+        for (int f = N; f <= kBatchMaxN && chosen < 0; ++f) {
+            if (!by_room[f].empty()) {
+                chosen = by_room[f].back();
+                by_room[f].pop_back();
             }
         }
         if (chosen < 0) {
             chosen = (int)bins.size();
-            bins.push_back({32, kBatchMaxN, 0, {}});
+            bins.push_back({kBatchMaxN, 0, {}});
         }
         Bin &b = bins[chosen];
-        b.lanes -= h;
         b.room -= N;
+        b.pairs += N * (N - 1) / 2;
         b.sys.push_back(k);
-        b.cost = std::max(b.cost, rounds);
-        by_free[b.lanes].push_back(chosen);
+        by_room[b.room].push_back(chosen);
     }
     std::stable_sort(bins.begin(), bins.end(),
-                     [](const Bin &a, const Bin &b) { return a.cost > b.cost; });
+                     [](const Bin &a, const Bin &b) { return a.pairs > b.pairs; });
     task_begin.assign(1, 0);
     task_sys.clear();
     for (const Bin &b : bins) {

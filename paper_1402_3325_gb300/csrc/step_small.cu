@@ -11,8 +11,8 @@
 // and packed densely over the lanes: lane l of chunk c solves pair 32 c + l,
 // so a step costs ceil(P / 32) warp-wide solves.  (The FP64 pipe charges a
 // warp instruction the same however many lanes are active, so the dense
-// packing matters: the round-robin order of the batched kernel needs n or
-// n - 1 warp-wide rounds of n / 2 active lanes.)  Each lane writes its
+// packing matters: a round-robin order needs n or n - 1 warp-wide rounds of
+// n / 2 active lanes.)  Each lane writes its
 // increments divided by m_ab to shared memory; after a block barrier thread
 // (i, c) adds particle i's increments in ascending j (+m_j d for the pair
 // (i, j), -m_j d for the pair (j, i); Eq. 23 with 1/m_i folded in), a fixed

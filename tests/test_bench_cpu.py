@@ -50,7 +50,7 @@ def test_profile_summaries_match_the_current_kernel_sources(path):
     if "kernel_sources_sha256_16" not in vals:
         pytest.skip("summary without a source hash")
     name = os.path.basename(path)[:-3]
-    kernel = next(k for k in ("small", "pair_step_sym_df64", "pair_step_fp64", "pair_step_sym")
-                  if name.startswith(k + "_"))
+    kernel = next(k for k in ("small", "batched", "pair_step_sym_df64", "pair_step_fp64",
+                              "pair_step_sym") if name.startswith(k + "_"))
     assert vals["kernel_sources_sha256_16"] == bench._kernel_sources_hash(kernel), (
         f"{name}: the kernel changed since this summary was taken")
