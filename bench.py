@@ -5,19 +5,21 @@ literal N^2 count; the kernel solves each of the N(N-1)/2 unordered pairs
 once and applies it to both particles).
 
 Default workload: equal-mass Plummer sphere, N = 1024, virial units,
-dt = 2^-8, 256 steps (one N-body time unit), second-order map, FP64.  One
-"step" is one ``sakura_step`` call: the prep kernel (drift, Eq. 27a), the
-pair kernel (every unordered pair's Kepler solve on systolic 32 x 32 tiles)
-and the apply kernel (Eqs. 27b-d).  The state (56 KB) fits in L2, so a
-256 MB buffer is written between timed steps to flush L2; each step is
-timed with CUDA events on the library stream.  The pair kernel's own
-duration (the roofline's denominator) is taken with CUDA events around each
-pair-kernel launch in a second pass of the same K steps, so that those
-events, which hold each launch until the previous kernel has finished, do
-not add to the timed steps.  The 9-body planetary workload (72 pairs per
-step) runs in the single-block kernel for small systems and is timed as
-calls of ``sakura_evolve`` of 100 steps each (``--steps-per-call``), one
-launch per call.
+dt = 2^-8, 256 steps (one N-body time unit), second-order map, FP64.  A
+step is the pair kernel (every unordered pair's Kepler solve on systolic
+32 x 32 tiles) and the apply kernel (Eqs. 27b-d), which also drifts for the
+next step (Eq. 27a); a call's first step has a prep kernel for its drift.
+The 256 steps are timed as 8 calls of ``sakura_evolve`` of 32 steps
+(``--steps-per-call``; 1 times single ``sakura_step`` calls, each with its
+own prep kernel), each call timed with CUDA events on the library stream.
+The state (56 KB) fits in L2, so a 256 MB buffer is written between timed
+calls to flush L2.  The pair kernel's own duration (the roofline's
+denominator) is taken with CUDA events around each pair-kernel launch in a
+second pass of the same calls, so that those events, which hold each launch
+until the previous kernel has finished, do not add to the timed steps.  The
+9-body planetary workload (72 pairs per step) runs in the single-block
+kernel for small systems and is timed as calls of ``sakura_evolve`` of 100
+steps each, one launch per call.
 
 Printed JSON line (rank 0): value (device-resident throughput of the plain
 FP64 form), e2e (the same through the host-buffer entry point
@@ -520,7 +522,9 @@ def main():
     ap.add_argument("--steps-per-call", type=int, default=None,
                     help="time the steps as calls of sakura_evolve of this many steps"
                          " (default: 100 for planetary9, whose 72 pairs per step run in one"
-                         " block for the whole call; 1, i.e. sakura_step, for the others)")
+                         " block for the whole call; 32 for plummer1024, whose steps after the"
+                         " first in a call need no drift kernel; 1, i.e. sakura_step, for the"
+                         " others)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -593,7 +597,7 @@ def main():
     solves_per_pair = st["solves"] / max(1, st["pairs"])
     fp32_share = st["fp32_pairs"] / max(1, st["pairs"])
     per_call = args.steps_per_call if args.steps_per_call is not None else (
-        100 if args.workload == "planetary9" else 1)
+        100 if args.workload == "planetary9" else (32 if args.workload == "plummer1024" else 1))
     if per_call < 1 or args.steps % per_call != 0:
         raise SystemExit("--steps must be a multiple of --steps-per-call")
     # the single-block kernel (csrc/step_small.cu) takes the FP64 and
@@ -743,7 +747,13 @@ def main():
                                    " call in one launch" if small else
                                    "drift, pair and apply kernels per step"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "gpu_launches": nt if small else 3 * args.steps,
+            # small systems: one launch per call; symmetric FP64 tiles: a
+            # prep kernel per call, then a pair and an apply kernel per step
+            # (each apply drifts for the next); otherwise prep, pair, apply
+            "gpu_launches": (nt if small else
+                             nt * (1 + 2 * per_call) if (args.form == "fp64" and
+                                                         args.pairs == "symmetric")
+                             else 3 * args.steps),
             "solves_per_pair": solves_per_pair,
             "roofline": roof, "clocks": clocks.summary()}
     if e2e is not None:

@@ -193,8 +193,12 @@ sakura::dw split_dw(double d)
 
 // Unordered pairs once (Newton's third law): systolic 32 x 32 tiles; df64:
 // the pair solves in double-word arithmetic (step_df64.cu).
+// prepped: X (and X32) already hold this sub-step's drifted state, written
+// by the previous apply kernel (FP64 form only); fuse: the apply kernel also
+// applies the next sub-step's drift next_drift and writes its X (and X32).
 int step_device_sym(const double *src, double *dst, const double *masses, int64_t n, double dt,
-                    int order, bool df64, bool mixed)
+                    int order, bool df64, bool mixed, bool prepped = false, bool fuse = false,
+                    double next_drift = 0.0)
 {
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
     const bool learned = !df64 && !mixed && g.cfg.guess == SAKURA_GUESS_LEARNED;
@@ -227,7 +231,7 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
         sakura::launch_prep_df64(src, masses, X, X3, n, drift, g.d_status, g.stream);
     else if (mixed)
         sakura::launch_prep_mixed(src, masses, X, X32, n, drift, g.d_status, g.stream);
-    else
+    else if (!prepped)
         sakura::launch_prep_step(src, masses, X, X32, n, drift, g.d_status, g.stream);
     sakura::StepArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -284,8 +288,8 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
         sakura::launch_apply_df64(dst, X, partial, n, Smax, W, T, post_drift, g.d_status,
                                   g.stream);
     else
-        sakura::launch_apply_sym(dst, X, partial, n, Smax, W, T, post_drift, g.d_status,
-                                 g.stream);
+        sakura::launch_apply_sym(dst, X, X32, partial, n, Smax, W, T, post_drift,
+                                 fuse && !mixed, next_drift, g.d_status, g.stream);
     rc = launch_error();
     if (rc) return rc;
     g.steps += 1;
@@ -307,14 +311,23 @@ constexpr double kSymMaxBytes = 16.0 * 1024 * 1024 * 1024;
 // buffers that do not overlap): the drift kernel reads src and masses, the
 // apply kernel writes dst.  Either kernel copies the masses into row 6 of the
 // drifted state X[7][n] at the start of the scratch buffer (step_masses).
-int step_device(const double *src, double *dst, const double *masses, int64_t n, double dt,
-                int order)
+bool sym_path(int64_t n)
 {
-    if (g.cfg.pair_mode == SAKURA_PAIRS_SYMMETRIC && n > 1 &&
-        8.0 * 6.0 * 8.0 * (double)((n + 31) / 32) * (double)n <= kSymMaxBytes)
+    return g.cfg.pair_mode == SAKURA_PAIRS_SYMMETRIC && n > 1 &&
+           8.0 * 6.0 * 8.0 * (double)((n + 31) / 32) * (double)n <= kSymMaxBytes;
+}
+
+// Sub-steps whose apply kernel can also drift for the next one: the FP64
+// form on symmetric tiles.
+bool fusable(int64_t n) { return sym_path(n) && g.cfg.precision == SAKURA_PREC_FP64; }
+
+int step_device(const double *src, double *dst, const double *masses, int64_t n, double dt,
+                int order, bool prepped = false, bool fuse = false, double next_drift = 0.0)
+{
+    if (sym_path(n))
         return step_device_sym(src, dst, masses, n, dt, order,
                                g.cfg.precision == SAKURA_PREC_DF64,
-                               g.cfg.precision == SAKURA_PREC_MIXED);
+                               g.cfg.precision == SAKURA_PREC_MIXED, prepped, fuse, next_drift);
     const Plan p = plan_step(n);
     const int64_t slots = sakura::pair_step_slots(n, p.W);
     const bool mixed = g.cfg.precision == SAKURA_PREC_MIXED;
@@ -426,13 +439,28 @@ int substeps(int order, double *w, int *sub_order)
 // The device copy of the masses that the last step's drift kernel wrote.
 const double *step_masses(int64_t n) { return (const double *)g.partial.ptr + 6 * n; }
 
-int step_composed(double *state, const double *masses, int64_t n, double dt, int order)
+// nsteps steps of the given order as one run of sub-steps: the first reads
+// src, the last writes dst, the others read and write mid (src, mid and dst
+// may be the same buffer).  From the second sub-step on, the masses come
+// from the copy that the first drift kernel left in the scratch (same n, so
+// the scratch is not reallocated).  On symmetric FP64 tiles every apply
+// kernel but the last also drifts for the next sub-step, so only the first
+// sub-step runs a prep kernel (the same arithmetic: results are unchanged).
+int run_substeps(const double *src, double *mid, double *dst, const double *masses, int64_t n,
+                 double dt, int order, int nsteps)
 {
     double w[sakura::kMaxSubsteps];
     int so;
     const int cnt = substeps(order, w, &so);
-    for (int u = 0; u < cnt; ++u) {
-        const int rc = step_device(state, state, masses, n, w[u] * dt, so);
+    const int64_t total = (int64_t)cnt * nsteps;
+    const bool fuse = fusable(n);
+    for (int64_t k = 0; k < total; ++k) {
+        const bool last = k == total - 1;
+        const double tn = last ? 0.0 : w[(k + 1) % cnt] * dt;
+        const double next_drift = so == 2 ? 0.5 * tn : (so == 1 ? 0.0 : tn);  // as the prep
+        const int rc = step_device(k == 0 ? src : mid, last ? dst : mid,
+                                   k == 0 ? masses : step_masses(n), n, w[k % cnt] * dt, so,
+                                   fuse && k > 0, fuse && !last, next_drift);
         if (rc) return rc;
     }
     return SAKURA_OK;
@@ -636,7 +664,7 @@ int sakura_step(double *state, const double *masses, int64_t n, double dt, int o
         return SAKURA_E_ARG;
     if (g.cfg.guess == SAKURA_GUESS_LEARNED && !g.mlp_loaded) return SAKURA_E_ARG;
     int rc = small_path(n) ? step_small(state, state, masses, n, dt, order, 1)
-                           : step_composed(state, masses, n, dt, order);
+                           : run_substeps(state, state, state, masses, n, dt, order, 1);
     if (rc) return rc;
     if (g.cfg.flags & SAKURA_FLAG_SYNC_CHECK) return drain_status();
     return SAKURA_OK;
@@ -651,12 +679,9 @@ int sakura_evolve(double *state, const double *masses, int64_t n, double dt, int
         return SAKURA_E_ARG;
     if (g.cfg.guess == SAKURA_GUESS_LEARNED && !g.mlp_loaded) return SAKURA_E_ARG;
     int rc = SAKURA_OK;
-    if (nsteps > 0 && small_path(n)) {
-        rc = step_small(state, state, masses, n, dt, order, nsteps);
-    } else {
-        for (int k = 0; k < nsteps && rc == SAKURA_OK; ++k)
-            rc = step_composed(state, masses, n, dt, order);
-    }
+    if (nsteps > 0)
+        rc = small_path(n) ? step_small(state, state, masses, n, dt, order, nsteps)
+                           : run_substeps(state, state, state, masses, n, dt, order, nsteps);
     if (rc) return rc;
     if (g.cfg.flags & SAKURA_FLAG_SYNC_CHECK) return drain_status();
     return SAKURA_OK;
@@ -683,23 +708,17 @@ int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt
         return drain_status();
     }
     if (hs && hm) {
+        // sub-steps between the first and the last run in library memory
         double w[sakura::kMaxSubsteps];
         int so;
-        const int cnt = substeps(order, w, &so);
-        const int64_t total = (int64_t)cnt * nsteps;
         double *ds = nullptr;
-        if (total > 1) {
+        if ((int64_t)substeps(order, w, &so) * nsteps > 1) {
             rc = grow(g.host_state, sbytes);
             if (rc) return rc;
             ds = (double *)g.host_state.ptr;
         }
-        for (int64_t k = 0; k < total; ++k) {
-            // after the first sub-step the masses come from the copy the last
-            // drift kernel left in the scratch (same n: it is not reallocated)
-            rc = step_device(k == 0 ? hs : ds, k == total - 1 ? hs : ds,
-                             k == 0 ? hm : step_masses(n), n, w[k % cnt] * dt, so);
-            if (rc) return rc;
-        }
+        rc = run_substeps(hs, ds, hs, hm, n, dt, order, nsteps);
+        if (rc) return rc;
         return drain_status();
     }
     rc = grow(g.host_state, sbytes);
@@ -711,14 +730,10 @@ int sakura_evolve_host(double *state, const double *masses, int64_t n, double dt
     if (cudaMemcpyAsync(ds, state, sbytes, cudaMemcpyHostToDevice, g.stream) != cudaSuccess ||
         cudaMemcpyAsync(dm, masses, mbytes, cudaMemcpyHostToDevice, g.stream) != cudaSuccess)
         return SAKURA_E_CUDA;
-    if (nsteps > 0 && small_path(n)) {
-        rc = step_small(ds, ds, dm, n, dt, order, nsteps);
+    if (nsteps > 0) {
+        rc = small_path(n) ? step_small(ds, ds, dm, n, dt, order, nsteps)
+                           : run_substeps(ds, ds, ds, dm, n, dt, order, nsteps);
         if (rc) return rc;
-    } else {
-        for (int k = 0; k < nsteps; ++k) {
-            rc = step_composed(ds, dm, n, dt, order);
-            if (rc) return rc;
-        }
     }
     if (cudaMemcpyAsync(state, ds, sbytes, cudaMemcpyDeviceToHost, g.stream) != cudaSuccess)
         return SAKURA_E_CUDA;

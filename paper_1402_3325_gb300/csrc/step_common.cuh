@@ -152,8 +152,11 @@ void launch_mlp_eval(const MlpWeights *W, const float *feat, int64_t count, floa
 int pair_step_sym_blocks_per_sm(bool stats, bool learned, bool seed = false);
 void launch_pair_step_sym(const StepArgs &a, int Smax, int64_t T, int blocks, bool stats,
                           cudaStream_t s);
-void launch_apply_sym(double *state, const double *X, const double *partial, int64_t n, int Smax,
-                      int64_t W, int64_t T, double post_drift, unsigned *status, cudaStream_t s);
+// fuse: also apply the next sub-step's drift next_drift and write its
+// drifted copy to X (and X32, if not null), replacing the next prep kernel
+void launch_apply_sym(double *state, double *X, float *X32, const double *partial, int64_t n,
+                      int Smax, int64_t W, int64_t T, double post_drift, bool fuse,
+                      double next_drift, unsigned *status, cudaStream_t s);
 
 // number of partial-sum slots per row for W warps
 int pair_step_slots(int64_t n, int64_t W);

@@ -193,14 +193,22 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED) ? 2 : 4)
 // kApplyWarps warps sum the slots of the other blocks Q = w, w + kApplyWarps,
 // ... (coalesced loads, two interleaved sums each) and warp 0 adds the warps'
 // sums in warp order and applies the update of x_y and v_y.
+// fuse: the next sub-step's drift (Eq. 27a, next_drift) is applied too and
+// its drifted copy written to X (and X32), as the prep kernel would write it
+// from the new state, so that a run of steps needs no prep kernel after its
+// first; the next pair kernel may then begin launching at once.
 constexpr int kApplyWarps = 16;
 
 __global__ void __launch_bounds__(32 * kApplyWarps)
-    apply_sym_kernel(double *state, const double *X, const double *partial, int64_t n, int Smax,
-                     int64_t W, int64_t T, double post_drift, unsigned *status)
+    apply_sym_kernel(double *state, double *X, float *X32, const double *partial, int64_t n,
+                     int Smax, int64_t W, int64_t T, double post_drift, int fuse,
+                     double next_drift, unsigned *status)
 {
     __shared__ double red[kApplyWarps][2][32];
     griddep_wait();  // the pair kernel's partials
+    // a kernel that follows reads this one's output only after its own
+    // griddep_wait (the next pair kernel) or is launched plainly
+    griddep_launch();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int q = blockIdx.y;
     const int64_t P = blockIdx.x;
@@ -238,6 +246,17 @@ __global__ void __launch_bounds__(32 * kApplyWarps)
     if (!isfinite(x1) || !isfinite(v1)) atomicOr(status, kStatusNonfinite);
     state[q * n + i] = x1;
     state[(3 + q) * n + i] = v1;
+    if (fuse) {
+        const double x = fma(v1, next_drift, x1);
+        X[q * n + i] = x;
+        X[(3 + q) * n + i] = v1;
+        if (X32) {
+            const float hi = __double2float_rn(x);
+            X32[q * n + i] = hi;
+            X32[(3 + q) * n + i] = __double2float_rn(x - (double)hi);
+            X32[(6 + q) * n + i] = __double2float_rn(v1);
+        }
+    }
 }
 
 namespace {
@@ -285,12 +304,14 @@ void launch_pair_step_sym(const StepArgs &a, int Smax, int64_t T, int blocks, bo
                s);
 }
 
-void launch_apply_sym(double *state, const double *X, const double *partial, int64_t n, int Smax,
-                      int64_t W, int64_t T, double post_drift, unsigned *status, cudaStream_t s)
+void launch_apply_sym(double *state, double *X, float *X32, const double *partial, int64_t n,
+                      int Smax, int64_t W, int64_t T, double post_drift, bool fuse,
+                      double next_drift, unsigned *status, cudaStream_t s)
 {
-    void *args[] = {(void *)&state, (void *)&X,    (void *)&partial,    (void *)&n,
-                    (void *)&Smax,  (void *)&W,    (void *)&T,          (void *)&post_drift,
-                    (void *)&status};
+    int f = fuse ? 1 : 0;
+    void *args[] = {(void *)&state,      (void *)&X, (void *)&X32, (void *)&partial,
+                    (void *)&n,          (void *)&Smax, (void *)&W, (void *)&T,
+                    (void *)&post_drift, (void *)&f, (void *)&next_drift, (void *)&status};
     launch_pdl((const void *)apply_sym_kernel, dim3((unsigned)((n + 31) / 32), 3),
                dim3(32 * kApplyWarps), args, 0, s);
 }
