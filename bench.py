@@ -596,10 +596,15 @@ def main():
     carried = st.get("carries", 0) / max(1, st["solves"])
     solves_per_pair = st["solves"] / max(1, st["pairs"])
     fp32_share = st["fp32_pairs"] / max(1, st["pairs"])
-    per_call = args.steps_per_call if args.steps_per_call is not None else (
-        100 if args.workload == "planetary9" else (32 if args.workload == "plummer1024" else 1))
-    if per_call < 1 or args.steps % per_call != 0:
-        raise SystemExit("--steps must be a multiple of --steps-per-call")
+    if args.steps_per_call is not None:
+        per_call = args.steps_per_call
+        if per_call < 1 or args.steps % per_call != 0:
+            raise SystemExit("--steps must be a multiple of --steps-per-call")
+    else:
+        # the workload's call length, or the largest divisor of --steps below it
+        cap = 100 if args.workload == "planetary9" else (32 if args.workload == "plummer1024"
+                                                         else 1)
+        per_call = max(d for d in range(1, min(cap, args.steps) + 1) if args.steps % d == 0)
     # the single-block kernel (csrc/step_small.cu) takes the FP64 and
     # double-word forms of small systems, each unordered pair once,
     # non-learned guesses
