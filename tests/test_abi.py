@@ -66,3 +66,18 @@ def test_flag_and_small_limit_constants_match_the_sources():
 
 def test_evolve_entry_points_without_gpu(lib):
     assert lib.sakura_evolve(None, None, 4, 0.1, 2, 3) == sk.E_NOINIT
+
+
+def test_no_cpu_fallback(monkeypatch, tmp_path):
+    # the binding takes CUDA tensors only, and a missing library is an error,
+    # not a detour through host code
+    torch = pytest.importorskip("torch")
+    state = torch.zeros((6, 4), dtype=torch.float64)
+    mass = torch.ones(4, dtype=torch.float64)
+    for call in (lambda: sk.step(state, mass, 0.1, 2), lambda: sk.evolve(state, mass, 0.1, 2, 3),
+                 lambda: sk.energy(state, mass)):
+        with pytest.raises(ValueError, match="CUDA tensor"):
+            call()
+    monkeypatch.setattr(sk, "_lib", None)
+    with pytest.raises(ImportError, match="no CPU fallback"):
+        sk.load(str(tmp_path / "libsakura.so"))
