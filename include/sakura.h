@@ -240,6 +240,20 @@ int sakura_step_batched(double *state, const double *masses, const int64_t *offs
  * SAKURA_E_ARG if no batched call has been tuned yet. */
 int sakura_batched_tuning(int *warps, int *blocks, double times_ms[4]);
 
+/* The work schedule sakura_step_batched builds for these systems, on the
+ * host (no device work, no sakura_init needed): tasks of at most 64
+ * particles in all, each run by one block with its pairs packed densely over
+ * the block's lanes, listed longest first.
+ *   host_offsets: int64[nsys+1] as for sakura_step_batched;
+ *   task_begin: caller's int[nsys+1], receives ntasks+1 offsets into task_sys;
+ *   task_sys: caller's int[nsys], receives the systems of task t at
+ *   task_sys[task_begin[t] .. task_begin[t+1]-1], every system exactly once;
+ *   ntasks: receives the number of tasks.
+ * Errors: E_ARG (null pointer, nsys < 1, host_offsets[0] != 0, a system of
+ * N < 1 or N > SAKURA_BATCH_MAX_N). */
+int sakura_batched_schedule(const int64_t *host_offsets, int nsys, int *task_begin,
+                            int *task_sys, int *ntasks);
+
 /* ---- learned initial guess ------------------------------------------
  * The paper leaves the Kepler solver's starting value open (Sec. 2.3 only
  * names a universal-variable solver).  With cfg.guess = SAKURA_GUESS_LEARNED

@@ -930,6 +930,23 @@ int sakura_batched_tuning(int *warps, int *blocks, double times_ms[4])
     return SAKURA_OK;
 }
 
+int sakura_batched_schedule(const int64_t *host_offsets, int nsys, int *task_begin,
+                            int *task_sys, int *ntasks)
+{
+    if (!host_offsets || nsys < 1 || !task_begin || !task_sys || !ntasks) return SAKURA_E_ARG;
+    if (host_offsets[0] != 0) return SAKURA_E_ARG;
+    for (int k = 0; k < nsys; ++k) {
+        const int64_t nk = host_offsets[k + 1] - host_offsets[k];
+        if (nk < 1 || nk > SAKURA_BATCH_MAX_N) return SAKURA_E_ARG;
+    }
+    std::vector<int> tb, ts;
+    sakura::build_batch_schedule(host_offsets, nsys, tb, ts);
+    *ntasks = (int)tb.size() - 1;
+    std::memcpy(task_begin, tb.data(), tb.size() * sizeof(int));
+    std::memcpy(task_sys, ts.data(), ts.size() * sizeof(int));
+    return SAKURA_OK;
+}
+
 int sakura_load_mlp(const void *weights, size_t bytes)
 {
     if (!g.init) return SAKURA_E_NOINIT;

@@ -125,13 +125,15 @@ def load(path: str = LIB_PATH):
     lib.sakura_mlp_eval.argtypes = [P, I64, P]
     lib.sakura_batched_tuning.argtypes = [ctypes.POINTER(I), ctypes.POINTER(I),
                                           ctypes.POINTER(D)]
+    lib.sakura_batched_schedule.argtypes = [P, I, P, P, ctypes.POINTER(I)]
     lib.sakura_check.argtypes = []
     lib.sakura_strerror.argtypes = [I]
     lib.sakura_strerror.restype = ctypes.c_char_p
     for name in ("sakura_init", "sakura_finalize", "sakura_set_stream", "sakura_step",
                  "sakura_evolve", "sakura_evolve_host", "sakura_energy", "sakura_step_batched",
                  "sakura_load_mlp", "sakura_get_stats", "sakura_check",
-                 "sakura_step_noalloc", "sakura_batched_tuning", "sakura_sample_pairs",
+                 "sakura_step_noalloc", "sakura_batched_tuning", "sakura_batched_schedule",
+                 "sakura_sample_pairs",
                  "sakura_mlp_grad", "sakura_mlp_train", "sakura_mlp_eval"):
         getattr(lib, name).restype = I
     _lib = lib
@@ -262,6 +264,20 @@ def batched_tuning():
     _check(load().sakura_batched_tuning(ctypes.byref(w), ctypes.byref(b), t),
            "sakura_batched_tuning")
     return w.value, b.value, {k: t[c] for c, k in enumerate((1, 2, 4, 8))}
+
+
+def batched_schedule(host_offsets):
+    """The batched work schedule for these systems (host only): a list of
+    tasks, each a list of system indices, longest first."""
+    import numpy as np
+    off = np.ascontiguousarray(host_offsets, dtype=np.int64)
+    nsys = off.shape[0] - 1
+    tb = np.zeros(nsys + 1, dtype=np.int32)
+    ts = np.zeros(max(nsys, 1), dtype=np.int32)
+    nt = ctypes.c_int()
+    _check(load().sakura_batched_schedule(off.ctypes.data, nsys, tb.ctypes.data, ts.ctypes.data,
+                                          ctypes.byref(nt)), "sakura_batched_schedule")
+    return [ts[tb[t]:tb[t + 1]].tolist() for t in range(nt.value)]
 
 
 def load_mlp(weights):
