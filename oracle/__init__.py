@@ -84,7 +84,7 @@ def _load():
             lib.oracle_energy.restype = ctypes.c_int
             lib.oracle_pair_classes.argtypes = [I64, P, P, P, D, ctypes.c_int, ctypes.c_int,
                                                 D, D, D,
-                                                ctypes.POINTER(ctypes.c_uint8)]
+                                                ctypes.POINTER(ctypes.c_uint8), P, P]
             lib.oracle_pair_classes.restype = I64
             lib.oracle_version.restype = ctypes.c_char_p
             _lib = lib
@@ -176,18 +176,27 @@ def energy(m, r, v):
 
 def pair_classes(m, r, v, tau: float, rule: int = 0, r_min: float = 0.1,
                  e_max: float = 0.9, e_hyp: float = 10.0, want_matrix: bool = False,
-                 order: int = 2):
+                 order: int = 2, want_values: bool = False):
     """Single-precision eligibility of every ordered pair of the step that
-    starts from (r, v) (mixed-precision form), decided in single precision
-    with a fixed operation order.  Returns (count, matrix or None)."""
+    starts from (r, v) (mixed-precision form): r = |r0| and e of the pair's
+    Kepler input (Eq. 26), in double precision.  Returns (count, matrix or
+    None), or (count, matrix, r2, e2) with the n x n squared separations and
+    squared eccentricities when want_values."""
     m = np.ascontiguousarray(m, dtype=np.float64)
     r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
     n = m.shape[0]
+    want_matrix = want_matrix or want_values
     mat = np.zeros((n, n), dtype=np.uint8) if want_matrix else None
     ptr = mat.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if want_matrix else None
+    r2 = np.zeros((n, n)) if want_values else None
+    e2 = np.zeros((n, n)) if want_values else None
     cnt = _load().oracle_pair_classes(n, _dp(m), _dp(r), _dp(v), float(tau), int(order), int(rule),
-                                      float(r_min), float(e_max), float(e_hyp), ptr)
+                                      float(r_min), float(e_max), float(e_hyp), ptr,
+                                      _dp(r2) if want_values else None,
+                                      _dp(e2) if want_values else None)
+    if want_values:
+        return int(cnt), mat, r2, e2
     return int(cnt), mat
 
 

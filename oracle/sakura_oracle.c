@@ -616,87 +616,60 @@ int oracle_energy(int64_t n, const double *m, const double *r, const double *v,
 
 /* ------------------------------------------------------------------ */
 /* Precision class of each ordered pair for the mixed-precision form.  */
-/* The class is an integer decision taken in single precision; the     */
-/* operations and their order are fixed so that any implementation     */
-/* that follows them (with IEEE rounding and no contraction) takes the */
-/* same decision:                                                      */
-/*   x_d = x + v * drift          (double, the first drift of the step)*/
-/*   hi = (float)x_d, lo = (float)(x_d - (double)hi)                    */
-/*   dx = (hi_i - hi_j) + (lo_i - lo_j), du = (float)v_i - (float)v_j   */
-/*   x0 = dx - ptau * du,  ptau = (float)(pre * tau)                    */
-/*   r2 = (x0^2 + y0^2) + z0^2, v2, eta = r0.v0 likewise               */
-/*   m = (float)m_i + (float)m_j, h2 = r2 v2 - eta^2                    */
-/*   E = 0.5 v2 - m / sqrt(r2), e2 = 1 + ((2 E) h2) / (m m)             */
-/*   rule 0: single iff r2 > rmin2 and e2 < emax2                       */
-/*   rule 1: single iff r2 > rmin2 and (e2 < emax2 or e2 > ehyp2)       */
-/* with rmin2 = (float)(r_min^2) etc.  order selects (drift, pre):      */
-/* 2 -> (tau/2, 1/2), 1 -> (0, 0), -1 -> (tau, 1).                      */
-/* Writes one byte per ordered pair (row i, column j; diagonal 0) when  */
-/* cls != NULL and returns the number of single-precision pairs.        */
+/* The rule is stated on the pair's Kepler input (r0, v0) of Eq. 26,   */
+/* the relative state after the first drift (Eq. 27a) and the backward */
+/* drift over pre * tau (Eq. 17), with m = m_i + m_j:                  */
+/*   r = |r0|,  E = v0^2 / 2 - m / r,  h^2 = |r0 x v0|^2,              */
+/*   e^2 = 1 + 2 E h^2 / m^2           (all in double precision)        */
+/*   rule 0: single iff r > r_min and e < e_max                         */
+/*   rule 1: single iff r > r_min and (e < e_max or e > e_hyp)          */
+/* order selects (drift, pre): 2 -> (tau/2, 1/2), 1 -> (0, 0),          */
+/* -1 -> (tau, 1).  Writes one byte per ordered pair (row i, column j;  */
+/* diagonal 0) when cls != NULL, and the pair's r^2 and e^2 when r2 and */
+/* e2 are not NULL (n x n doubles each, diagonal 0); returns the number */
+/* of single-precision pairs.                                           */
 /* ------------------------------------------------------------------ */
 int64_t oracle_pair_classes(int64_t n, const double *m, const double *r, const double *v,
                             double tau, int order, int rule, double r_min, double e_max,
-                            double e_hyp, uint8_t *cls)
+                            double e_hyp, uint8_t *cls, double *r2out, double *e2out)
 {
     double drift = order == 2 ? 0.5 * tau : (order == 1 ? 0.0 : tau);
     double pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
-    float ptau = (float)(pre * tau);
-    float rmin2 = (float)(r_min * r_min);
-    float emax2 = (float)(e_max * e_max);
-    float ehyp2 = (float)(e_hyp * e_hyp);
-    float *hi = (float *)malloc(sizeof(float) * (size_t)(3 * n));
-    float *lo = (float *)malloc(sizeof(float) * (size_t)(3 * n));
-    float *vf = (float *)malloc(sizeof(float) * (size_t)(3 * n));
-    float *mf = (float *)malloc(sizeof(float) * (size_t)n);
-    if (!hi || !lo || !vf || !mf) {
-        free(hi);
-        free(lo);
-        free(vf);
-        free(mf);
-        return -1;
-    }
-    for (int64_t i = 0; i < n; ++i) {
-        for (int q = 0; q < 3; ++q) {
-            double xd = r[3 * i + q] + v[3 * i + q] * drift;
-            float h = (float)xd;
-            hi[3 * i + q] = h;
-            lo[3 * i + q] = (float)(xd - (double)h);
-            vf[3 * i + q] = (float)v[3 * i + q];
-        }
-        mf[i] = (float)m[i];
-    }
+    double *rd = (double *)malloc(sizeof(double) * (size_t)(3 * n));
+    if (!rd) return -1;
+    for (int64_t i = 0; i < n; ++i)
+        for (int q = 0; q < 3; ++q) rd[3 * i + q] = r[3 * i + q] + v[3 * i + q] * drift;
     int64_t count = 0;
     for (int64_t i = 0; i < n; ++i)
         for (int64_t j = 0; j < n; ++j) {
             uint8_t c = 0;
+            double rsq = 0.0, esq = 0.0;
             if (i != j) {
-                float x[3], u[3];
+                double x0[3], u0[3];
                 for (int q = 0; q < 3; ++q) {
-                    float d = (hi[3 * i + q] - hi[3 * j + q]) + (lo[3 * i + q] - lo[3 * j + q]);
-                    u[q] = vf[3 * i + q] - vf[3 * j + q];
-                    float pu = ptau * u[q];
-                    x[q] = d - pu;
+                    u0[q] = v[3 * i + q] - v[3 * j + q];
+                    x0[q] = (rd[3 * i + q] - rd[3 * j + q]) - u0[q] * tau * pre;
                 }
-                float r2 = (x[0] * x[0] + x[1] * x[1]) + x[2] * x[2];
-                float v2 = (u[0] * u[0] + u[1] * u[1]) + u[2] * u[2];
-                float eta = (x[0] * u[0] + x[1] * u[1]) + x[2] * u[2];
-                float mm = mf[i] + mf[j];
-                float h2 = r2 * v2 - eta * eta;
-                float rr = sqrtf(r2);
-                float E = 0.5f * v2 - mm / rr;
-                float e2 = 1.0f + ((2.0f * E) * h2) / (mm * mm);
-                int far = r2 > rmin2;
-                int lowe = e2 < emax2;
-                int hyp = (rule == 1) && (e2 > ehyp2);
+                double mm = m[i] + m[j];
+                rsq = x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2];
+                double v2 = u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2];
+                double hx = x0[1] * u0[2] - x0[2] * u0[1];
+                double hy = x0[2] * u0[0] - x0[0] * u0[2];
+                double hz = x0[0] * u0[1] - x0[1] * u0[0];
+                double h2 = hx * hx + hy * hy + hz * hz;
+                double E = 0.5 * v2 - mm / sqrt(rsq);
+                esq = 1.0 + 2.0 * E * h2 / (mm * mm);
+                int far = sqrt(rsq) > r_min;
+                int lowe = sqrt(esq > 0.0 ? esq : 0.0) < e_max;
+                int hyp = (rule == 1) && (sqrt(esq > 0.0 ? esq : 0.0) > e_hyp);
                 c = (uint8_t)(far && (lowe || hyp));
             }
             if (cls) cls[i * n + j] = c;
+            if (r2out) r2out[i * n + j] = rsq;
+            if (e2out) e2out[i * n + j] = esq;
             count += c;
         }
-    free(hi);
-    free(lo);
-    free(vf);
-    free(mf);
+    free(rd);
     return count;
 }
 

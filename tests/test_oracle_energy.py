@@ -85,3 +85,31 @@ def test_pair_class_counts_bh_cluster_literal_rule():
     far = int((d[1:] > 0.1).sum())
     assert cnt == 2 * far
     assert mat[1:, 1:].sum() == 0
+
+
+@pytest.mark.parametrize("a,e", [(1.0, 0.05), (1.0, 0.95), (0.5, 30.0), (0.02, 3.0)])
+def test_pair_class_values_are_the_elements(a, e):
+    # the pair's r^2 and e^2 as the rule defines them, for a pair built from
+    # known elements (tau = 0: the Kepler input is the pair's separation)
+    m, r, v = _pair_from_elements(1.0, a, e)
+    cnt, mat, r2, e2 = oracle.pair_classes(m, r, v, 0.0, want_values=True)
+    sep2 = float(((r[0] - r[1]) ** 2).sum())
+    assert r2[0, 1] == pytest.approx(sep2, rel=1e-15) and r2[1, 0] == r2[0, 1]
+    assert e2[0, 1] == pytest.approx(e * e, rel=1e-12)
+    assert r2[0, 0] == 0.0 and e2[1, 1] == 0.0
+
+
+@pytest.mark.parametrize("order", [2, 1, -1])
+def test_pair_class_input_is_the_undrifted_separation(order):
+    # the first drift (Eq. 27a) and the backward drift of Eq. 17 cancel in the
+    # pair's Kepler input for every order: r0 = r_i - r_j, v0 = v_i - v_j of
+    # the state before the step, so r^2 and e^2 do not depend on tau
+    s = ics.random_cluster(40, seed=3, mass_spread=3.0)
+    c0, m0, r20, e20 = oracle.pair_classes(s.m, s.r, s.v, 0.0, rule=1, want_values=True)
+    c1, m1, r21, e21 = oracle.pair_classes(s.m, s.r, s.v, 0.37, rule=1, order=order,
+                                           want_values=True)
+    off = ~np.eye(s.n, dtype=bool)
+    np.testing.assert_allclose(r21[off], r20[off], rtol=1e-13)
+    np.testing.assert_allclose(e21[off], e20[off], rtol=1e-10, atol=1e-12)
+    d = s.r[:, None, :] - s.r[None, :, :]
+    np.testing.assert_allclose(r20[off], (d ** 2).sum(-1)[off], rtol=1e-15)
