@@ -254,6 +254,27 @@ int sakura_batched_tuning(int *warps, int *blocks, double times_ms[4]);
 int sakura_batched_schedule(const int64_t *host_offsets, int nsys, int *task_begin,
                             int *task_sys, int *ntasks);
 
+/* The precision class that the mixed form (SAKURA_PREC_MIXED) gives every
+ * ordered pair of the step of this order (2, 1 or -1) that starts from
+ * state, under the configured rule and thresholds (cfg.mixed_rule,
+ * mixed_r_min, mixed_e_max, mixed_e_hyp).  The rule is stated on the pair's
+ * Kepler input (r0, v0) of Eq. 26 (after the first drift of Eq. 27a and the
+ * backward drift of Eq. 17), with m = m_i + m_j: single precision iff
+ * r = |r0| > r_min and e < e_max (or e > e_hyp under
+ * SAKURA_MIXED_RULE_HYP), e^2 = 1 + 2 (v0^2/2 - m/r) |r0 x v0|^2 / m^2.
+ * The library decides it in single precision, as the mixed pair kernels do
+ * (the same device code), so pairs within rounding of a threshold may be
+ * classed either way.  A pair of class 1 whose single-precision solve fails
+ * is still solved in FP64 by the step.
+ *   state, masses: device arrays as for sakura_step; n <= 2^20.
+ *   classes: device uint8[n][n]; classes[i * n + j] = 1 for the pair (i, j)
+ *   in single precision, 0 in FP64; the diagonal is 0.
+ * Uses the library scratch; synchronises and returns device faults.
+ * Errors: E_NOINIT, E_ARG (null pointer, n < 1 or n > 2^20, order not in
+ * {2, 1, -1}, non-finite dt). */
+int sakura_pair_classes(const double *state, const double *masses, int64_t n, double dt,
+                        int order, unsigned char *classes);
+
 /* ---- learned initial guess ------------------------------------------
  * The paper leaves the Kepler solver's starting value open (Sec. 2.3 only
  * names a universal-variable solver).  With cfg.guess = SAKURA_GUESS_LEARNED
@@ -320,24 +341,29 @@ int sakura_get_stats(sakura_stats *out, int reset);
  * (and clear it), or SAKURA_OK. */
 int sakura_check(void);
 
-/* The FP64 step of sakura_step (default Kepler controls: tolerance 4 eps,
- * 50 Laguerre steps, bisection fallback) for callers that cannot allocate
- * device memory: programs whose GPU memory is owned by another allocator
- * (a framework's caching allocator that has reserved the device would make
- * cudaMalloc fail) and latency-critical loops that must not call
- * cudaMalloc/cudaFree.  The paper has no counterpart; this is an interface
- * convenience.  It needs no sakura_init and allocates nothing: its scratch
- * (drifted state and row sums, 20 x SAKURA_NOALLOC_MAX_N doubles = 10 MiB)
- * and its fault status
- * word are file-scope device arrays that every GPU loading the library holds
- * until the process exits.
+/* An FP64 step for callers that cannot allocate device memory: programs
+ * whose GPU memory is owned by another allocator (a framework's caching
+ * allocator that has reserved the device would make cudaMalloc fail) and
+ * latency-critical loops that must not call cudaMalloc/cudaFree.  The paper
+ * has no counterpart; this is an interface convenience.  It needs no
+ * sakura_init, reads no sakura_config and allocates nothing.  It always runs
+ * the ordered-pair FP64 kernels (SAKURA_PAIRS_ORDERED: every ordered pair
+ * solved) with the standard initial guess t/r0 and the default Kepler
+ * controls (tolerance 4 eps, 50 Laguerre steps, bisection fallback), so its
+ * results equal sakura_step's in that configuration to summation order.
+ * Its scratch (drifted state and row sums, 20 x SAKURA_NOALLOC_MAX_N
+ * doubles = 10 MiB) and its fault status word are file-scope device arrays
+ * that every GPU loading the library holds until the process exits.
  *   state, masses: device arrays as for sakura_step; n <= SAKURA_NOALLOC_MAX_N
- *   (larger n returns SAKURA_E_ARG); stream: cudaStream_t or NULL.
+ *   (larger n returns SAKURA_E_ARG); order 2, 1 or -1; stream: cudaStream_t
+ *   or NULL.
  * Runs on the calling thread's current device and synchronises the stream
  * before returning the first device fault of this call (or SAKURA_OK).
  * The first call on a device looks up the arrays' device addresses; make it
- * before any stream capture.  All calls share the arrays and keep the last
- * call's contents; calls that overlap on the GPU race on them. */
+ * before any stream capture.  Host threads may make first calls
+ * concurrently (the look-up runs once per device).  All calls share the
+ * arrays and keep the last call's contents; calls that overlap on the GPU
+ * (other streams, other threads) race on them. */
 #define SAKURA_NOALLOC_MAX_N 65536
 int sakura_step_noalloc(double *state, const double *masses, int64_t n, double dt, int order,
                         void *stream);

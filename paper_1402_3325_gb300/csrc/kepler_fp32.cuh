@@ -10,16 +10,22 @@
 // path; a separate |F/F'| test for lanes already at the root split the warp
 // and made the symmetric mixed kernel 25 % slower on GB300.  A lane that has
 // not converged after kFp32MaxIter steps is handed to the FP64 solver.  The solve's
-// reciprocals and square root are the hardware approximations (about 1 ulp):
-// only the class decision must be reproducible, and it keeps correctly
-// rounded operations.  Only pairs that the FP32 class rule admits (distant,
-// low- or very-high-eccentricity pairs, whose increments are small next to
-// the state) come here; the caller accumulates their increments (in FP64, or
-// as exact double-word sums of the float products, step_mixed.cu).
+// reciprocals and square root are the hardware approximations (about 1 ulp).
+// Only pairs that the FP32 class rule admits (distant, low- or
+// very-high-eccentricity pairs, whose increments are small next to the state)
+// come here; the caller accumulates their increments (in FP64, or as exact
+// double-word sums of the float products, step_mixed.cu).
 //
-// The class rule is evaluated on the hi/lo float split of the drifted
-// positions with correctly rounded single-precision operations in a fixed
-// order (no contraction), so a CPU reference computes the same decisions.
+// The class rule is stated on the pair's Kepler input (r0, v0) of Eq. 26
+// with m = m_i + m_j: r = |r0|, e^2 = 1 + 2 E h^2 / m^2, E = v0^2/2 - m/r,
+// h^2 = r^2 v0^2 - (r0.v0)^2.  It is decided in single precision on the
+// hi/lo float split of the drifted positions, multiplied through by m^2 > 0
+// so that no division or square root is needed:
+//   e < e_max  <=>  (v0^2 - 2m/r) h^2 < (e_max^2 - 1) m^2,  likewise e > e_hyp,
+// with 1/r from the hardware reciprocal square root.  Pairs next to a
+// threshold may fall either way (a pair of either class is solved
+// correctly); away from the thresholds' rounding band the decision equals the
+// double-precision rule's (tested against the oracle pair by pair).
 #pragma once
 
 #include <cstdint>
@@ -38,16 +44,19 @@ struct Pair32 {
 };
 
 struct ClassRule {
-    float ptau;    // (float)(pre * tau)
-    float rmin2;   // (float)(r_min^2)
-    float emax2;   // (float)(e_max^2)
-    float ehyp2;   // (float)(e_hyp^2)
-    int rule;      // 0: r > r_min and e < e_max; 1: ... or e > e_hyp
+    float ptau;     // (float)(pre * tau)
+    float rmin2;    // (float)(r_min^2)
+    float emax2m1;  // (float)(e_max^2 - 1)
+    float ehyp2m1;  // (float)(e_hyp^2 - 1)
+    int rule;       // 0: r > r_min and e < e_max; 1: ... or e > e_hyp
 };
 
-// dx = (hi_i - hi_j) + (lo_i - lo_j) for each coordinate, dv in float,
-// r0 = dx - ptau dv, then e^2 = 1 + (2 E h^2) / m^2 with E = v^2/2 - m/r and
-// h^2 = r^2 v^2 - (r.v)^2.
+// dx = (hi_i - hi_j) + (lo_i - lo_j) for each coordinate (the separation to
+// the accuracy of the separation), dv in float, r0 = dx - ptau dv, then the
+// class.  The decision is symmetric in (i, j): every quantity it uses is
+// even under (r0, v0) -> (-r0, -v0), and negation commutes with rounding.
+// Pair masses with m^2 below 2^-120 (out of single precision's normal
+// range) stay in FP64.
 __device__ __forceinline__ void pair32_setup(Pair32 &p, const float hi_i[3], const float lo_i[3],
                                              const float v_i[3], float m_i, const float hi_j[3],
                                              const float lo_j[3], const float v_j[3], float m_j,
@@ -56,9 +65,9 @@ __device__ __forceinline__ void pair32_setup(Pair32 &p, const float hi_i[3], con
     float x[3], u[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const float d = __fadd_rn(__fsub_rn(hi_i[q], hi_j[q]), __fsub_rn(lo_i[q], lo_j[q]));
-        u[q] = __fsub_rn(v_i[q], v_j[q]);
-        x[q] = __fsub_rn(d, __fmul_rn(cr.ptau, u[q]));
+        const float d = (hi_i[q] - hi_j[q]) + (lo_i[q] - lo_j[q]);
+        u[q] = v_i[q] - v_j[q];
+        x[q] = fmaf(-cr.ptau, u[q], d);
     }
     p.x0 = x[0];
     p.y0 = x[1];
@@ -66,18 +75,18 @@ __device__ __forceinline__ void pair32_setup(Pair32 &p, const float hi_i[3], con
     p.vx = u[0];
     p.vy = u[1];
     p.vz = u[2];
-    p.r2 = __fadd_rn(__fadd_rn(__fmul_rn(x[0], x[0]), __fmul_rn(x[1], x[1])), __fmul_rn(x[2], x[2]));
-    p.v2 = __fadd_rn(__fadd_rn(__fmul_rn(u[0], u[0]), __fmul_rn(u[1], u[1])), __fmul_rn(u[2], u[2]));
-    p.eta = __fadd_rn(__fadd_rn(__fmul_rn(x[0], u[0]), __fmul_rn(x[1], u[1])), __fmul_rn(x[2], u[2]));
-    p.m = __fadd_rn(m_i, m_j);
-    const float h2 = __fsub_rn(__fmul_rn(p.r2, p.v2), __fmul_rn(p.eta, p.eta));
-    const float r = __fsqrt_rn(p.r2);
-    const float E = __fsub_rn(__fmul_rn(0.5f, p.v2), __fdiv_rn(p.m, r));
-    const float e2 = __fadd_rn(1.0f, __fdiv_rn(__fmul_rn(__fmul_rn(2.0f, E), h2), __fmul_rn(p.m, p.m)));
+    p.r2 = fmaf(x[0], x[0], fmaf(x[1], x[1], x[2] * x[2]));
+    p.v2 = fmaf(u[0], u[0], fmaf(u[1], u[1], u[2] * u[2]));
+    p.eta = fmaf(x[0], u[0], fmaf(x[1], u[1], x[2] * u[2]));
+    p.m = m_i + m_j;
+    const float h2 = fmaf(p.r2, p.v2, -(p.eta * p.eta));
+    const float twoE = fmaf(-2.0f * p.m, rsqrtf(p.r2), p.v2);
+    const float lhs = twoE * h2;
+    const float m2 = p.m * p.m;
     const bool far = p.r2 > cr.rmin2;
-    const bool lowe = e2 < cr.emax2;
-    const bool hyp = (cr.rule == 1) && (e2 > cr.ehyp2);
-    p.fp32 = far && (lowe || hyp);
+    const bool lowe = lhs < cr.emax2m1 * m2;
+    const bool hyp = (cr.rule == 1) && (lhs > cr.ehyp2m1 * m2);
+    p.fp32 = far && m2 >= 0x1p-120f && (lowe || hyp);
 }
 
 struct Stumpff32 {

@@ -1,14 +1,16 @@
-// noalloc.cu -- sakura_step_noalloc: the FP64 step without any device
+// noalloc.cu -- sakura_step_noalloc: an FP64 step without any device
 // allocation.
 //
 // Some callers cannot call cudaMalloc.  A host program whose device memory is
 // entirely held by another allocator (for example a framework's caching
 // allocator that has reserved the GPU) gets out-of-memory from it, and a
 // latency-critical loop cannot afford cudaMalloc/cudaFree, which may
-// synchronise the device.  For them this entry point runs the same pair and
-// apply kernels as sakura_step, but keeps the pair kernel's row-sum scratch
-// and the fault status word in file-scope device arrays that exist for as
-// long as the library is loaded.
+// synchronise the device.  For them this entry point runs the ordered-pair
+// FP64 kernels of sakura_step (every ordered pair solved, standard initial
+// guess t/r0, tolerance 4 eps, 50 Laguerre steps, bisection fallback; it
+// reads no sakura_config), but keeps the pair kernel's row-sum scratch and
+// the fault status word in file-scope device arrays that exist for as long
+// as the library is loaded.
 //
 // Limits and sharing rules:
 //   - n <= SAKURA_NOALLOC_MAX_N (65536); larger n returns SAKURA_E_ARG.
@@ -19,12 +21,15 @@
 //     overlaps on the GPU (other streams, other host threads) race on both.
 //   - The first call on a device looks up the arrays' device addresses with
 //     cudaGetSymbolAddress while that device is current; make that first call
-//     before any stream capture.
+//     before any stream capture.  Host threads may make their first calls
+//     concurrently: each device's look-up runs once (std::call_once) and
+//     later calls see its result.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 #include "kepler_fp64.cuh"
 #include "sakura.h"
@@ -33,9 +38,10 @@
 namespace {
 
 constexpr int64_t kMaxN = SAKURA_NOALLOC_MAX_N;
-// drifted state X[7][n] plus the pair kernel's row partials: for W warps at
-// most (ceil(W/n) + 1) slots of 6 n doubles, i.e. 7n + 6W + 12n doubles;
-// 20 * kMaxN covers W up to 65536 warps.
+// drifted state X[7][n] plus the pair kernel's row partials, ceil(W/n) + 1
+// slots of 6 n doubles for W warps.  While W <= n that is 2 slots, 19 n
+// doubles, within 20 kMaxN for every n <= kMaxN; the launch below halves
+// the grid until the layout fits (smaller n may use W > n).
 constexpr int64_t kScratchDoubles = 20 * kMaxN;
 constexpr int kMaxDevices = 64;
 
@@ -46,37 +52,39 @@ static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 static __device__ __align__(256) unsigned g_noalloc_status[64];
 
 struct DeviceSymbols {
-    bool ready = false;
+    int rc = SAKURA_E_CUDA;  // result of the look-up
     double *scratch = nullptr;
     unsigned *status = nullptr;
     int sm_count = 152;
 };
 
 DeviceSymbols g_dev[kMaxDevices];
+std::once_flag g_dev_once[kMaxDevices];
 
+// Device addresses of the arrays on device dev (the calling thread's current
+// device), looked up once per device; the once_flag orders the look-up
+// before every later read of its result.
 int setup_device(int dev, DeviceSymbols **out)
 {
     if (dev < 0 || dev >= kMaxDevices) return SAKURA_E_ARG;
     DeviceSymbols &d = g_dev[dev];
-    if (!d.ready) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    std::call_once(g_dev_once[dev], [&d, dev]() {
+        void *p = nullptr, *q = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p ||
+            cudaGetSymbolAddress(&q, g_noalloc_status) != cudaSuccess || !q) {
             cudaGetLastError();
-            return SAKURA_E_CUDA;
+            d.rc = SAKURA_E_CUDA;
+            return;
         }
         d.scratch = (double *)p;
-        p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_status) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return SAKURA_E_CUDA;
-        }
-        d.status = (unsigned *)p;
+        d.status = (unsigned *)q;
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
             sms > 0)
             d.sm_count = sms;
-        d.ready = true;
-    }
+        d.rc = SAKURA_OK;
+    });
+    if (d.rc != SAKURA_OK) return d.rc;
     *out = &d;
     return SAKURA_OK;
 }
@@ -87,6 +95,7 @@ int code_from_status(unsigned st)
     if (st & sakura::kStatusNonfinite) return SAKURA_E_NONFINITE;
     if (st & sakura::kStatusCoincident) return SAKURA_E_COINCIDENT;
     if (st & sakura::kStatusKepler) return SAKURA_E_KEPLER;
+    if (st & sakura::kStatusTimeout) return SAKURA_E_TIMEOUT;
     return SAKURA_OK;
 }
 
@@ -118,6 +127,8 @@ extern "C" int sakura_step_noalloc(double *state, const double *masses, int64_t 
     while (blocks > 1 &&
            7 * n + sakura::pair_step_slots(n, blocks * warps) * 6 * n > kScratchDoubles)
         blocks /= 2;
+    if (7 * n + sakura::pair_step_slots(n, blocks * warps) * 6 * n > kScratchDoubles)
+        return SAKURA_E_ARG;  // unreachable for n <= kMaxN (19 n <= 20 kMaxN at W <= n)
     const int64_t W = blocks * warps;
     double *X = d->scratch;
     double *partial = X + 7 * n;
@@ -129,7 +140,7 @@ extern "C" int sakura_step_noalloc(double *state, const double *masses, int64_t 
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
     sakura::launch_prep_step(state, masses, X, nullptr, n, drift, d->status, s);
-    sakura::StepArgs a;
+    sakura::StepArgs a{};
     a.X = X;
     a.partial = partial;
     a.n = n;

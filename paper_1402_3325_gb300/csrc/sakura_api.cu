@@ -185,6 +185,19 @@ Plan plan_step(int64_t n)
     return p;
 }
 
+// The mixed form's class rule with the configured thresholds, for a step
+// whose backward drift is ptau = pre * tau (kepler_fp32.cuh).
+sakura::ClassRule class_rule(double ptau)
+{
+    sakura::ClassRule r;
+    r.ptau = (float)ptau;
+    r.rmin2 = (float)(g.cfg.mixed_r_min * g.cfg.mixed_r_min);
+    r.emax2m1 = (float)(g.cfg.mixed_e_max * g.cfg.mixed_e_max - 1.0);
+    r.ehyp2m1 = (float)(g.cfg.mixed_e_hyp * g.cfg.mixed_e_hyp - 1.0);
+    r.rule = g.cfg.mixed_rule;
+    return r;
+}
+
 sakura::dw split_dw(double d)
 {
     const float h = (float)d;
@@ -269,11 +282,7 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
     } else if (mixed) {
         sakura::MixedArgs ma;
         ma.X32 = X32;
-        ma.rule.ptau = (float)(a.pre * dt);
-        ma.rule.rmin2 = (float)(g.cfg.mixed_r_min * g.cfg.mixed_r_min);
-        ma.rule.emax2 = (float)(g.cfg.mixed_e_max * g.cfg.mixed_e_max);
-        ma.rule.ehyp2 = (float)(g.cfg.mixed_e_hyp * g.cfg.mixed_e_hyp);
-        ma.rule.rule = g.cfg.mixed_rule;
+        ma.rule = class_rule(a.pre * dt);
         ma.tau32 = (float)dt;
         ma.post32 = (float)a.post;
         sakura::launch_pair_step_sym_mixed(a, ma, Smax, T, (int)blocks, stats, g.stream);
@@ -375,11 +384,7 @@ int step_device(const double *src, double *dst, const double *masses, int64_t n,
         if (mixed) {
             sakura::MixedArgs ma;
             ma.X32 = X32;
-            ma.rule.ptau = (float)(a.pre * dt);
-            ma.rule.rmin2 = (float)(g.cfg.mixed_r_min * g.cfg.mixed_r_min);
-            ma.rule.emax2 = (float)(g.cfg.mixed_e_max * g.cfg.mixed_e_max);
-            ma.rule.ehyp2 = (float)(g.cfg.mixed_e_hyp * g.cfg.mixed_e_hyp);
-            ma.rule.rule = g.cfg.mixed_rule;
+            ma.rule = class_rule(a.pre * dt);
             ma.tau32 = (float)dt;
             ma.post32 = (float)a.post;
             sakura::launch_pair_step_mixed(a, ma, p.blocks, stats, g.stream);
@@ -988,6 +993,26 @@ int sakura_sample_pairs(const double *state, const double *masses, int64_t n, do
     sakura::launch_prep_step(state, masses, X, nullptr, n, drift, g.d_status, g.stream);
     sakura::launch_sample_pairs(X, n, dt, pre, pair_ids, count, features, targets, iters,
                                 g.cfg.kepler_tol * DBL_EPSILON, g.d_status, g.stream);
+    if (launch_error()) return SAKURA_E_CUDA;
+    return drain_status();
+}
+
+int sakura_pair_classes(const double *state, const double *masses, int64_t n, double dt,
+                        int order, unsigned char *classes)
+{
+    if (!g.init) return SAKURA_E_NOINIT;
+    if (!state || !masses || !classes || n < 1 || !valid_order(order) || !std::isfinite(dt) ||
+        n > (int64_t)1 << 20)
+        return SAKURA_E_ARG;
+    // X[7][n] doubles and X32[10][n] floats in the head of the step scratch
+    int rc = grow(g.partial, (size_t)12 * n * sizeof(double));
+    if (rc) return rc;
+    double *X = (double *)g.partial.ptr;
+    float *X32 = (float *)(X + 7 * n);
+    const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
+    const double pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
+    sakura::launch_prep_mixed(state, masses, X, X32, n, drift, g.d_status, g.stream);
+    sakura::launch_pair_classes(X32, n, class_rule(pre * dt), classes, g.stream);
     if (launch_error()) return SAKURA_E_CUDA;
     return drain_status();
 }

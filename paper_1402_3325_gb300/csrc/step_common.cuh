@@ -83,6 +83,10 @@ int pair_step_mixed_blocks_per_sm(bool stats);
 void launch_pair_step_sym_mixed(const StepArgs &a, const MixedArgs &ma, int Smax, int64_t T,
                                 int blocks, bool stats, cudaStream_t s);
 int pair_step_sym_mixed_blocks_per_sm(bool stats);
+// the FP32 class of every ordered pair as the mixed kernels decide it
+// (out: n x n bytes), from the float copy that launch_prep_mixed writes
+void launch_pair_classes(const float *X32, int64_t n, const ClassRule &rule, unsigned char *out,
+                         cudaStream_t s);
 
 // Tiling of the symmetric (Newton's third law) kernels, step_sym.cu and
 // step_df64.cu.  Tile t = J (J + 1) / 2 + I covers row block I and column

@@ -476,6 +476,44 @@ __global__ void __launch_bounds__(128, 4)
     }
 }
 
+// The class of every ordered pair (i, j) as the mixed kernels decide it
+// (pair32_setup on the float copy X32 that prep_mixed_kernel writes): one
+// byte per pair, row i, column j, 1 = single precision, diagonal 0.  One
+// thread per pair; consecutive threads take consecutive j.
+__global__ void pair_class_kernel(const float *X32, int64_t n, ClassRule rule,
+                                  unsigned char *out)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n * n) return;
+    const int64_t i = k / n, j = k - i * n;
+    unsigned char c = 0;
+    if (i != j) {
+        float hi_i[3], lo_i[3], v_i[3], hi_j[3], lo_j[3], v_j[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            hi_i[q] = X32[q * n + i];
+            lo_i[q] = X32[(3 + q) * n + i];
+            v_i[q] = X32[(6 + q) * n + i];
+            hi_j[q] = X32[q * n + j];
+            lo_j[q] = X32[(3 + q) * n + j];
+            v_j[q] = X32[(6 + q) * n + j];
+        }
+        Pair32 p;
+        pair32_setup(p, hi_i, lo_i, v_i, X32[9 * n + i], hi_j, lo_j, v_j, X32[9 * n + j], rule);
+        c = p.fp32 ? 1 : 0;
+    }
+    out[k] = c;
+}
+
+void launch_pair_classes(const float *X32, int64_t n, const ClassRule &rule, unsigned char *out,
+                         cudaStream_t s)
+{
+    const int threads = 256;
+    const int64_t total = n * n;
+    pair_class_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, s>>>(
+        X32, n, rule, out);
+}
+
 void launch_pair_step_sym_mixed(const StepArgs &a, const MixedArgs &ma, int Smax, int64_t T,
                                 int blocks, bool stats, cudaStream_t s)
 {

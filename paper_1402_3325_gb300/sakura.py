@@ -120,6 +120,7 @@ def load(path: str = LIB_PATH):
     lib.sakura_get_stats.argtypes = [ctypes.POINTER(Stats), I]
     lib.sakura_step_noalloc.argtypes = [P, P, I64, D, I, P]
     lib.sakura_sample_pairs.argtypes = [P, P, I64, D, I, P, I64, P, P, P]
+    lib.sakura_pair_classes.argtypes = [P, P, I64, D, I, P]
     lib.sakura_mlp_grad.argtypes = [P, P, P, P, I64, P, P]
     lib.sakura_mlp_train.argtypes = [P, P, P, P, I64, I64, I, ctypes.c_float, P]
     lib.sakura_mlp_eval.argtypes = [P, I64, P]
@@ -133,7 +134,7 @@ def load(path: str = LIB_PATH):
                  "sakura_evolve", "sakura_evolve_host", "sakura_energy", "sakura_step_batched",
                  "sakura_load_mlp", "sakura_get_stats", "sakura_check",
                  "sakura_step_noalloc", "sakura_batched_tuning", "sakura_batched_schedule",
-                 "sakura_sample_pairs",
+                 "sakura_sample_pairs", "sakura_pair_classes",
                  "sakura_mlp_grad", "sakura_mlp_train", "sakura_mlp_eval"):
         getattr(lib, name).restype = I
     _lib = lib
@@ -278,6 +279,20 @@ def batched_schedule(host_offsets):
     _check(load().sakura_batched_schedule(off.ctypes.data, nsys, tb.ctypes.data, ts.ctypes.data,
                                           ctypes.byref(nt)), "sakura_batched_schedule")
     return [ts[tb[t]:tb[t + 1]].tolist() for t in range(nt.value)]
+
+
+def pair_classes(state, masses, dt: float, order: int = 2):
+    """The mixed form's precision class of every ordered pair of the step
+    from state (CUDA uint8 [n, n], 1 = single precision), under the
+    configured rule and thresholds."""
+    import torch
+    n = masses.shape[0]
+    if tuple(state.shape) != (6, n):
+        raise ValueError("state must have shape (6, n)")
+    out = torch.empty((n, n), dtype=torch.uint8, device=state.device)
+    _check(load().sakura_pair_classes(_ptr(state), _ptr(masses), n, float(dt), int(order),
+                                      _ptr(out)), "sakura_pair_classes")
+    return out
 
 
 def load_mlp(weights):

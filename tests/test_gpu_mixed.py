@@ -1,10 +1,12 @@
 """GPU tests of the mixed-precision form (FP32 solves for distant, weakly
 perturbing pairs; FP64 for the rest and for all accumulation).
 
-* The number of pairs solved in FP32 equals the oracle's single-precision
-  class count exactly (same decision, same precision, same operation order),
-  in both pair modes (the symmetric kernel decides once per unordered pair;
-  the rule is symmetric in (i, j)).
+* The pair classes the kernels use (exported by sakura_pair_classes) equal
+  the oracle's double-precision rule on every pair except those within the
+  single-precision decision's rounding band of a threshold
+  (tests/mixed_band.py); the number of pairs the step solved in FP32 equals
+  the exported class count, in both pair modes (the symmetric kernel decides
+  once per unordered pair; the rule is symmetric in (i, j)).
 * With a class rule that admits no pair, every pair goes through the per-warp
   FP64 queue and the step matches the FP64 oracle to 1e-12.
 * Otherwise one step stays within the stated bound of the FP64 oracle
@@ -17,6 +19,7 @@ import numpy as np
 import pytest
 
 import oracle
+from mixed_band import check_classes
 from paper_1402_3325_gb300 import ics
 from paper_1402_3325_gb300 import sakura as sk
 
@@ -82,20 +85,46 @@ CASES = [
 PAIRS = [sk.PAIRS_SYMMETRIC, sk.PAIRS_ORDERED]
 
 
+def classes_gpu(s, order):
+    """The exported class matrix of the step from s (current configuration)."""
+    return sk.pair_classes(dev(s.soa()), dev(s.m), s.dt, order).cpu().numpy()
+
+
+def classes_checked(s, rule, order):
+    """GPU class matrix, checked pair by pair against the oracle's rule."""
+    got = classes_gpu(s, order)
+    cnt, orc = oracle.pair_classes(s.m, s.r, s.v, s.dt, rule=rule, order=order,
+                                   want_matrix=True)
+    k = check_classes(got, orc, s.m, s.r, s.v, s.dt, order, rule)
+    print(f"{s.name} rule {rule} order {order}: gpu {int(got.sum())} oracle {cnt} single-"
+          f"precision pairs; {k} boundary pairs differ, all within the rounding band")
+    return got
+
+
 @pytest.mark.parametrize("pairs", PAIRS, ids=["symmetric", "ordered"])
 @pytest.mark.parametrize("name,make,rule", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("order", [2, -1])
 def test_mixed_class_count_and_accuracy(name, make, rule, order, pairs):
     s = make()
     with mixed(mixed_rule=rule, guess=sk.GUESS_TAYLOR, pair_mode=pairs):
+        got = classes_checked(s, rule, order)
         r, v, st = step_gpu(s, order)
-    cnt, _ = oracle.pair_classes(s.m, s.r, s.v, s.dt, rule=rule, order=order)
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, order, nthreads=NCPU)
     er, ev = rel_err(r, v, rr, vr)
     print(f"{name} order {order}: fp32 pairs {st['fp32_pairs']} / {st['pairs']}"
-          f" (oracle {cnt}), err r {er:.2e} v {ev:.2e}")
-    assert st["fp32_pairs"] == cnt
+          f" (classes {int(got.sum())}), err r {er:.2e} v {ev:.2e}")
+    # every pair of the single-precision class converged in FP32 here
+    assert st["fp32_pairs"] == int(got.sum())
     assert er <= STEP_BOUND and ev <= STEP_BOUND
+
+
+@pytest.mark.parametrize("rule", [0, 1], ids=["literal", "hyp"])
+def test_pair_classes_symmetric_and_zero_diagonal(rule):
+    s = ics.random_cluster(500, seed=21, mass_spread=3.0)
+    with mixed(mixed_rule=rule):
+        got = classes_checked(s, rule, 2)
+    assert (np.diag(got) == 0).all()
+    np.testing.assert_array_equal(got, got.T)
 
 
 @pytest.mark.parametrize("pairs", PAIRS, ids=["symmetric", "ordered"])
@@ -138,10 +167,10 @@ def test_mixed_queue_across_segments(rule, blocks):
                grid_blocks=blocks):
         r, v, st = step_gpu(s, 2)
         r2, v2, _ = step_gpu(s, 2)
-    cnt, _ = oracle.pair_classes(s.m, s.r, s.v, s.dt, rule=rule, order=2)
+        got = classes_checked(s, rule, 2)
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
     er, ev = rel_err(r, v, rr, vr)
-    assert st["fp32_pairs"] == cnt
+    assert st["fp32_pairs"] == int(got.sum())
     assert er <= STEP_BOUND and ev <= STEP_BOUND, (er, ev)
     np.testing.assert_array_equal(r, r2)
     np.testing.assert_array_equal(v, v2)

@@ -1,0 +1,152 @@
+"""The mixed-precision form on its own workload, the black-hole cluster at
+full size (black hole of mass 1 plus 16383 stars of total mass 1e-2, Plummer
+scale 1, circular velocities, dt = 2^-10), judged against the FP64 oracle.
+
+* Pair classes: every one of the 16384^2 ordered pairs is classed as the
+  oracle's double-precision rule classes it, except pairs within the
+  single-precision decision's rounding band of a threshold.
+* One step, sampled: 48 particles (the black hole, the stars nearest to it,
+  the rest spread over the cluster) against oracle.step_sample, within the
+  mixed form's per-step bound, under both class rules.
+* The whole run of 256 steps against the oracle's cached run
+  (tests/golden/bh16384_oracle_run.json, written by
+  tests/golden/make_bh16384_oracle_run.py): positions and velocities of the
+  stored sample particles and the total energy, for the mixed form under
+  both rules and for the FP64 form.
+
+Bounds.  One mixed step is held to STEP_BOUND = 1e-8 per particle (relative
+to max(|x_i|, rms), as in the other mixed tests); over 256 steps the
+per-step errors add, so the run is held to 256 x STEP_BOUND.  The FP64 form
+is held to 256 x 1e-12.  Energies: the mixed run's total energy within
+1e-8 |E0| of the oracle's, the FP64 run's within 1e-12 |E0|.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from mixed_band import check_classes
+from paper_1402_3325_gb300 import ics
+from paper_1402_3325_gb300 import sakura as sk
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+NCPU = os.cpu_count() or 1
+N = 16384
+STEP_BOUND = 1e-8
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "bh16384_oracle_run.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1402_3325_gb300 import build
+    build.build()
+    sk.init(0, flags=sk.FLAG_STATS)
+    yield
+    sk.finalize()
+
+
+@pytest.fixture(scope="module")
+def system():
+    return ics.bh_cluster(N, seed=0)
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def rel_err(r, v, rr, vr, R, V):
+    er = np.linalg.norm(r - rr, axis=1) / np.maximum(np.linalg.norm(rr, axis=1), R)
+    ev = np.linalg.norm(v - vr, axis=1) / np.maximum(np.linalg.norm(vr, axis=1), V)
+    return float(er.max()), float(ev.max())
+
+
+def scales(s):
+    return np.sqrt((s.r ** 2).sum(1).mean()), np.sqrt((s.v ** 2).sum(1).mean())
+
+
+def sample48(s):
+    rad = np.linalg.norm(s.r - s.r[0], axis=1)
+    rad[0] = np.inf
+    near = np.argsort(rad)[:15]
+    spread = np.linspace(1, N - 1, 32).astype(np.int64)
+    return np.unique(np.concatenate([[0], near, spread]))[:48]
+
+
+def run_gpu(s, nsteps, **opts):
+    sk.init(0, flags=sk.FLAG_STATS, **opts)
+    st = dev(s.soa())
+    m = dev(s.m)
+    sk.get_stats(reset=True)
+    sk.evolve(st, m, s.dt, 2, nsteps)
+    sk.check()
+    stats = sk.get_stats(reset=True)
+    E = sk.energy(st, m)
+    r, v = ics.from_soa(st.cpu().numpy())
+    sk.init(0, flags=sk.FLAG_STATS)
+    return r, v, E, stats
+
+
+@pytest.mark.parametrize("rule", [0, 1], ids=["literal", "hyp"])
+def test_bh16384_classes_match_oracle(system, rule):
+    s = system
+    sk.init(0, precision=sk.PREC_MIXED, mixed_rule=rule)
+    got = sk.pair_classes(dev(s.soa()), dev(s.m), s.dt, 2).cpu().numpy()
+    sk.init(0, flags=sk.FLAG_STATS)
+    cnt, orc = oracle.pair_classes(s.m, s.r, s.v, s.dt, rule=rule, want_matrix=True)
+    k = check_classes(got, orc, s.m, s.r, s.v, s.dt, 2, rule)
+    print(f"rule {rule}: gpu {int(got.sum())} oracle {cnt} single-precision pairs of"
+          f" {N * (N - 1)}; {k} boundary pairs differ, all within the rounding band")
+    assert k <= 1e-5 * N * N
+
+
+@pytest.mark.parametrize("rule", [0, 1], ids=["literal", "hyp"])
+def test_bh16384_mixed_step_sampled_against_oracle(system, rule):
+    s = system
+    idx = sample48(s)
+    r, v, _, st = run_gpu(s, 1, precision=sk.PREC_MIXED, mixed_rule=rule)
+    rc, rr, vr = oracle.step_sample(s.m, s.r, s.v, s.dt, idx, 2, nthreads=NCPU)
+    assert rc == oracle.OK
+    R, V = scales(s)
+    er, ev = rel_err(r[idx], v[idx], rr, vr, R, V)
+    print(f"rule {rule}: fp32 share {st['fp32_pairs'] / st['pairs']:.4f},"
+          f" one step vs oracle: r {er:.2e} v {ev:.2e}")
+    assert er <= STEP_BOUND and ev <= STEP_BOUND
+
+
+@pytest.fixture(scope="module")
+def golden(system):
+    with open(GOLDEN) as fh:
+        g = json.load(fh)
+    # the same initial state up to the rounding of the generator's libm
+    # calls on this machine: its energy agrees with the stored one
+    E0 = oracle.energy(system.m, system.r, system.v)[0]
+    assert abs(E0 - g["E0"]) <= 1e-14 * abs(g["E0"]), (E0, g["E0"])
+    return g
+
+
+@pytest.mark.parametrize("form,opts,bound,ebound", [
+    ("mixed-literal", dict(precision=sk.PREC_MIXED, mixed_rule=0), 256 * STEP_BOUND, 1e-8),
+    ("mixed-hyp", dict(precision=sk.PREC_MIXED, mixed_rule=1), 256 * STEP_BOUND, 1e-8),
+    ("fp64", dict(guess=sk.GUESS_FP32), 256 * 1e-12, 1e-12),
+], ids=["mixed-literal", "mixed-hyp", "fp64"])
+def test_bh16384_256_steps_against_cached_oracle_run(system, golden, form, opts, bound, ebound):
+    s = system
+    idx = np.array(golden["sample"])
+    R, V = scales(s)
+    r, v, E, st = run_gpu(s, golden["steps"], **opts)
+    cp = golden["checkpoints"][str(golden["steps"])]
+    rr, vr = np.array(cp["r"]), np.array(cp["v"])
+    er, ev = rel_err(r[idx], v[idx], rr, vr, R, V)
+    E0 = golden["E0"]
+    dE_gpu, dE_orc = abs(E / E0 - 1.0), abs(cp["E"] / E0 - 1.0)
+    print(f"{form}: 256 steps, sample of {idx.size}: r {er:.2e} v {ev:.2e};"
+          f" dE/E gpu {dE_gpu:.3e} oracle {dE_orc:.3e}, |E - E_oracle|/|E0|"
+          f" {abs(E - cp['E']) / abs(E0):.3e}; fp32 share {st['fp32_pairs'] / st['pairs']:.4f}")
+    assert er <= bound and ev <= bound
+    assert abs(E - cp["E"]) <= ebound * abs(E0)

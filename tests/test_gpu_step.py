@@ -438,3 +438,29 @@ def test_symmetric_counts_solves():
     diag = 3 * 32 * 31 + 4 * 3
     assert st["pairs"] == n * (n - 1)
     assert st["solves"] == (n * (n - 1) - diag) // 2 + diag
+
+
+def test_headline_evolve_32_steps_matches_oracle_and_single_steps():
+    # the call path the benchmark times: one sakura_evolve call of 32 steps
+    # (symmetric tiles, single-precision seed; each apply kernel drifts for
+    # the next step), against 32 oracle steps (held to 32 x the per-step
+    # bound) and bit for bit against 32 separate sakura_step calls
+    s = ics.plummer(1024, seed=0)
+    with configured(guess=sk.GUESS_FP32, pair_mode=sk.PAIRS_SYMMETRIC):
+        st = dev(s.soa())
+        m = dev(s.m)
+        sk.evolve(st, m, s.dt, 2, 32)
+        sk.check()
+        r, v = ics.from_soa(st.cpu().numpy())
+        st1 = dev(s.soa())
+        for _ in range(32):
+            sk.step(st1, m, s.dt, 2)
+        sk.check()
+        r1, v1 = ics.from_soa(st1.cpu().numpy())
+    rc, rr, vr = oracle.evolve(s.m, s.r, s.v, s.dt, 32, 2, nthreads=NCPU)
+    assert rc == oracle.OK
+    er, ev = rel_err(r, v, rr, vr)
+    print(f"evolve(32) vs oracle: r {er:.2e} v {ev:.2e}")
+    assert er <= 32 * TOL and ev <= 32 * TOL
+    np.testing.assert_array_equal(r, r1)
+    np.testing.assert_array_equal(v, v1)
