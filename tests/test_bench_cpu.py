@@ -33,9 +33,9 @@ def test_reference_arm_prints_the_contract_line():
 def test_cpu_baseline_repeats_a_short_workload():
     from paper_1402_3325_gb300 import ics
     s = ics.planetary(0)
-    cb = bench._cpu_baseline(s, s.dt, budget_s=2.0, max_steps=50, min_s=0.2)
+    cb = bench._cpu_baseline(s, s.dt, budget_s=2.0, max_steps=5, min_s=0.3)
     assert cb["value"] > 0 and cb["kind"] == "oracle"
-    assert "passes of 50 consecutive steps" in cb["sample"]
+    assert "passes of 5 consecutive steps" in cb["sample"]
 
 
 @pytest.mark.parametrize("path", sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))),
@@ -54,3 +54,16 @@ def test_profile_summaries_match_the_current_kernel_sources(path):
                               "pair_step_sym") if name.startswith(k + "_"))
     assert vals["kernel_sources_sha256_16"] == bench._kernel_sources_hash(kernel), (
         f"{name}: the kernel changed since this summary was taken")
+
+
+def test_reference_arm_samples_rows_of_large_workloads(monkeypatch, capsys):
+    # workloads larger than REFERENCE_ROWS particles time that many rows of
+    # each step (oracle.step_sample) and count their ordered pairs
+    import argparse
+    monkeypatch.setattr(bench, "REFERENCE_ROWS", 64)
+    args = argparse.Namespace(workload="plummer1024", steps=3, warmup=1, gpus=1)
+    assert bench.run_reference(args, 0) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["config"]["n"] == 1024
+    assert "64 of the 1024 rows" in line["cpu_baseline"]["sample"]
+    assert line["value"] == pytest.approx(64 * 1024 * 3 / (line["ms_per_step"] * 3e-3))

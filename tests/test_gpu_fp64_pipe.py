@@ -5,10 +5,7 @@ Two facts the FP64 kernels' design and roofline rest on:
   active, so lanes left idle by a schedule are lost throughput (the batched
   kernel's packing is judged by its lane fill);
 * the sustained FMA rate, against which the pair kernel's FP64 instruction
-  count sets its speed of light;
-and, for latency-bound kernels (tests/fp64_latency_probe.cu), how often a
-single warp can issue FP64 instructions at all: a sub-partition's quarter of
-the SM's FP64 rate, several times slower than its FP32 issue.
+  count sets its speed of light.
 Run with -s to see the figures.
 """
 import os
@@ -47,19 +44,3 @@ def test_fp64_pipe_cost_is_per_warp_instruction(tmp_path):
     # a full warp: the sustained FMA rate (two flops each), in TFLOP/s
     print("FP64 FMA peak %.3f TFLOP/s" % (2.0 * rates[32][1] / 1e12))
     assert rates[32][1] > 0
-
-
-def test_single_warp_fp64_issue_is_a_quarter_of_the_sm(tmp_path):
-    exe = tmp_path / "fp64_latency_probe"
-    subprocess.run([_nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
-                    os.path.join(HERE, "fp64_latency_probe.cu"), "-o", str(exe)], check=True)
-    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
-    print(out)
-    f = out.split()
-    c = {f[k]: float(f[k + 1]) for k in range(0, len(f), 2)}
-    # measured on GB300: dependent DFMA ~61 cycles, DADD ~55, FFMA ~25 (the
-    # loop's own counter and branch dominate it), 8 independent DFMA chains
-    # ~64 cycles per instruction: independent work does not raise one
-    # warp's FP64 issue rate
-    assert c["dfma_8chains"] > 0.8 * c["dfma_dep"], c
-    assert c["dfma_dep"] > 2.0 * c["ffma_dep"], c
