@@ -363,6 +363,7 @@ def _measure_batched(args, sk, ens, device, stream, guess, clocks=None, dist=Non
     dt = torch.tensor(ens.dt, device=device)
     gcode = _guess_code(sk, guess)
     sk.init(device.index, stream=stream.cuda_stream, guess=gcode, flags=sk.FLAG_STATS)
+    sk.get_stats(reset=True)  # counters of earlier calls
     sk.step_batched(st, m, off, ens.offsets, dt, 2, args.warmup)   # schedule, autotune
     sk.check()
     stt = sk.get_stats(reset=True)
@@ -660,6 +661,7 @@ def _measure(args, sk, s, device, stream, flush, guess, opts, per_call, clocks=N
     state = state0.clone()
     gcode = _guess_code(sk, guess)
     sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_STATS, guess=gcode, **opts)
+    sk.get_stats(reset=True)  # counters of earlier calls
     for _ in range(args.warmup):
         sk.step(state, mass, s.dt, 2)
     sk.check()

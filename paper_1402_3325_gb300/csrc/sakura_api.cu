@@ -204,6 +204,72 @@ sakura::dw split_dw(double d)
     return {h, (float)(d - (double)h)};
 }
 
+// The mixed form with each unordered pair once, in row-group phases
+// (step_mixed.cu): prep (drift and float copy), pair and apply kernels.
+int step_device_mixed_grp(const double *src, double *dst, const double *masses, int64_t n,
+                          double dt, int order)
+{
+    const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
+    int64_t blocks = g.cfg.grid_blocks > 0
+                         ? g.cfg.grid_blocks
+                         : (int64_t)g.sm_count * sakura::pair_step_grp_mixed_blocks_per_sm(stats);
+    const sakura::GrpLayout L = sakura::make_grp_layout(n, blocks);
+    // scratch: X[7][n] doubles, row partials [Hmax][6][n], column partials
+    // [ng][6][n], then X32[10][n] floats
+    int rc = grow(g.partial, (size_t)(7 * n + (int64_t)(L.Hmax + L.ng) * 6 * n + 5 * n) *
+                                 sizeof(double));
+    if (rc) return rc;
+    double *X = (double *)g.partial.ptr;
+    double *rowpart = X + 7 * n;
+    double *colpart = rowpart + (int64_t)L.Hmax * 6 * n;
+    float *X32 = (float *)(colpart + (int64_t)L.ng * 6 * n);
+    const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
+    const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
+    sakura::launch_prep_mixed(src, masses, X, X32, n, drift, g.d_status, g.stream);
+    sakura::StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.X = X;
+    a.n = n;
+    a.tau = dt;
+    a.pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
+    a.post = 1.0 - a.pre;
+    a.tol = g.cfg.kepler_tol * DBL_EPSILON;
+    a.max_iter = g.cfg.kepler_max_iter;
+    a.bisection = g.cfg.kepler_bisection;
+    a.guess = (g.cfg.guess == SAKURA_GUESS_TAYLOR || g.cfg.guess == SAKURA_GUESS_FP32) ? 2 : 0;
+    a.status = g.d_status;
+    a.stats = g.d_stats;
+    sakura::MixedArgs ma;
+    ma.X32 = X32;
+    ma.rule = class_rule(a.pre * dt);
+    ma.tau32 = (float)dt;
+    ma.post32 = (float)a.post;
+    const bool timing = (g.cfg.flags & SAKURA_FLAG_TIMING) != 0;
+    std::pair<cudaEvent_t, cudaEvent_t> tm{nullptr, nullptr};
+    if (timing) {
+        tm = take_timer();
+        cudaEventRecord(tm.first, g.stream);
+    }
+    sakura::launch_pair_step_grp_mixed(a, ma, L, rowpart, colpart, (int)blocks, stats, g.stream);
+    if (timing) {
+        cudaEventRecord(tm.second, g.stream);
+        g.timers.push_back(tm);
+    }
+    sakura::launch_apply_grp(dst, X, rowpart, colpart, n, L, blocks, post_drift, g.d_status,
+                             g.stream);
+    rc = launch_error();
+    if (rc) return rc;
+    g.steps += 1;
+    g.pairs += n * (n - 1);
+    int64_t diag = 0;  // ordered pairs inside diagonal tiles
+    for (int64_t b = 0; b < L.nb; ++b) {
+        const int64_t nbk = std::min<int64_t>(32, n - 32 * b);
+        diag += nbk * (nbk - 1);
+    }
+    g.solves += (n * (n - 1) - diag) / 2 + diag;
+    return SAKURA_OK;
+}
+
 // Unordered pairs once (Newton's third law): systolic 32 x 32 tiles; df64:
 // the pair solves in double-word arithmetic (step_df64.cu).
 // prepped: X (and X32) already hold this sub-step's drifted state, written
@@ -213,14 +279,14 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
                     int order, bool df64, bool mixed, bool prepped = false, bool fuse = false,
                     double next_drift = 0.0)
 {
+    if (mixed) return step_device_mixed_grp(src, dst, masses, n, dt, order);
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
-    const bool learned = !df64 && !mixed && g.cfg.guess == SAKURA_GUESS_LEARNED;
-    const bool seed = !df64 && !mixed && g.cfg.guess == SAKURA_GUESS_FP32;
+    const bool learned = !df64 && g.cfg.guess == SAKURA_GUESS_LEARNED;
+    const bool seed = !df64 && g.cfg.guess == SAKURA_GUESS_FP32;
     const int64_t nb = (n + 31) / 32;
     const int64_t tiles = nb * (nb + 1) / 2;
-    const int bps = df64    ? sakura::pair_step_df64_blocks_per_sm(stats)
-                    : mixed ? sakura::pair_step_sym_mixed_blocks_per_sm(stats)
-                            : sakura::pair_step_sym_blocks_per_sm(stats, learned, seed);
+    const int bps = df64 ? sakura::pair_step_df64_blocks_per_sm(stats)
+                         : sakura::pair_step_sym_blocks_per_sm(stats, learned, seed);
     // contiguous tile-step ranges for W <= T warps (step_common.cuh)
     const int64_t T = tiles * 32;
     int64_t blocks = g.cfg.grid_blocks > 0 ? g.cfg.grid_blocks : (int64_t)g.sm_count * bps;
@@ -237,19 +303,17 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
     double *X = (double *)g.partial.ptr;
     double *partial = X + 7 * n;
     float *X3 = (float *)(partial + nslots * 6 * n);
-    float *X32 = (seed || mixed) ? X3 : nullptr;
+    float *X32 = seed ? X3 : nullptr;
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
     if (df64)
         sakura::launch_prep_df64(src, masses, X, X3, n, drift, g.d_status, g.stream);
-    else if (mixed)
-        sakura::launch_prep_mixed(src, masses, X, X32, n, drift, g.d_status, g.stream);
     else if (!prepped)
         sakura::launch_prep_step(src, masses, X, X32, n, drift, g.d_status, g.stream);
     sakura::StepArgs a;
     std::memset(&a, 0, sizeof(a));
     a.X = X;
-    a.X32 = mixed ? nullptr : X32;
+    a.X32 = X32;
     a.partial = partial;
     a.n = n;
     a.tau = dt;
@@ -279,13 +343,6 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
         da.t = split_dw(dt);
         da.qtau = split_dw(a.post * dt);
         sakura::launch_pair_step_df64(a, da, Smax, T, (int)blocks, stats, g.stream);
-    } else if (mixed) {
-        sakura::MixedArgs ma;
-        ma.X32 = X32;
-        ma.rule = class_rule(a.pre * dt);
-        ma.tau32 = (float)dt;
-        ma.post32 = (float)a.post;
-        sakura::launch_pair_step_sym_mixed(a, ma, Smax, T, (int)blocks, stats, g.stream);
     } else {
         sakura::launch_pair_step_sym(a, Smax, T, (int)blocks, stats, g.stream);
     }
@@ -298,7 +355,7 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
                                   g.stream);
     else
         sakura::launch_apply_sym(dst, X, X32, partial, n, Smax, W, T, post_drift,
-                                 fuse && !mixed, next_drift, g.d_status, g.stream);
+                                 fuse, next_drift, g.d_status, g.stream);
     rc = launch_error();
     if (rc) return rc;
     g.steps += 1;

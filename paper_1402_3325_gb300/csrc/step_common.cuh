@@ -79,10 +79,25 @@ void launch_prep_mixed(const double *state, const double *mass, double *X, float
 void launch_pair_step_mixed(const StepArgs &a, const MixedArgs &ma, int blocks, bool stats,
                             cudaStream_t s);
 int pair_step_mixed_blocks_per_sm(bool stats);
-// symmetric form (unordered pairs once, step_common.cuh tiling, FP64 partials)
-void launch_pair_step_sym_mixed(const StepArgs &a, const MixedArgs &ma, int Smax, int64_t T,
-                                int blocks, bool stats, cudaStream_t s);
-int pair_step_sym_mixed_blocks_per_sm(bool stats);
+// symmetric form (unordered pairs once) in row-group phases (step_mixed.cu):
+// nb blocks of 32 particles, ng groups of row blocks, P phases in all, at
+// most Hmax row pieces per group for the grid it was made for
+struct GrpLayout {
+    int64_t nb;
+    int64_t P;
+    int ng;
+    int Hmax;
+};
+// the layout for n particles; clamps blocks to the phase count
+GrpLayout make_grp_layout(int64_t n, int64_t &blocks);
+// rowpart: [Hmax][6][n] row partials; colpart: [ng][6][n] column partials
+void launch_pair_step_grp_mixed(const StepArgs &a, const MixedArgs &ma, const GrpLayout &L,
+                                double *rowpart, double *colpart, int blocks, bool stats,
+                                cudaStream_t s);
+int pair_step_grp_mixed_blocks_per_sm(bool stats);
+void launch_apply_grp(double *state, const double *X, const double *rowpart,
+                      const double *colpart, int64_t n, const GrpLayout &L, int64_t blocks,
+                      double post_drift, unsigned *status, cudaStream_t s);
 // the FP32 class of every ordered pair as the mixed kernels decide it
 // (out: n x n bytes), from the float copy that launch_prep_mixed writes
 void launch_pair_classes(const float *X32, int64_t n, const ClassRule &rule, unsigned char *out,

@@ -15,6 +15,8 @@
 //   the FP64 path half-empty.  The queue is drained at every row end.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "df64.cuh"
 #include "kepler_df64.cuh"
 #include "kepler_fp32.cuh"
@@ -201,87 +203,159 @@ __global__ void __launch_bounds__(WARPS * 32)
     }
 }
 
-// Symmetric form: every unordered pair once, on the systolic tiles and
-// contiguous tile-step ranges of step_sym.cu (step_common.cuh).  The class
-// rule is symmetric in (i, j) (float negation and round-to-nearest are), so
-// one decision serves both ordered pairs.  An FP32-class pair's increments
-// m_j d and -m_i d (float products, formed exactly by two_prod) are summed in
-// double-word form within the tile segment (at most 32 terms, exact to
-// 2^-48) and the segment sums go out in FP64, where the apply kernel adds
-// them; every other pair joins the per-warp FP64 queue of step_df64.cu.
-// 4 blocks per SM (120 registers, no spills): 8.5 % faster on GB300 than the
-// 3 that 150 registers allowed
-template <bool STATS>
-__global__ void __launch_bounds__(128, 4)
-    pair_step_sym_mixed_kernel(StepArgs a, MixedArgs ma, int Smax, int64_t T)
+// Symmetric form: every unordered pair once, in row-group phases.
+//
+// A block of kGrpWarps warps owns a group of kGrpWarps consecutive row blocks
+// of 32 particles (warp w: row block I = g kGrpWarps + w).  The block's warps
+// sweep the column blocks J >= g kGrpWarps together, one phase per J: in the
+// phase, warp w solves the 32 x 32 tile (I, J) (nothing when I > J; the
+// ordered pairs of the diagonal tile when I = J) on the systolic schedule of
+// step_sym.cu, lane l owning row i = 32 I + l and solving column
+// (l + k) mod 32 at step k.  Row sums stay in the lane's registers for the
+// whole group; column sums go to the warp's shared-memory accumulators of
+// the phase.  The phases of all groups are numbered group by group (J
+// ascending) and split into contiguous, equal ranges over the persistent
+// grid.  A block takes its phases in windows of up to kGrpWindow phases of
+// one group: after each window a block barrier, then the block adds the
+// warps' column sums of each phase in warp order and writes one column
+// partial per particle of each block J; a block writes one row partial per
+// group it meets.  So the partial sums written per step are one 6-vector per
+// particle per group that covers its column block, plus one per row piece:
+// about 30 MB at n = 16384, which stays in L2, against a 6-vector per
+// particle per tile segment in the earlier contiguous-range kernel (369 MB).
+//
+// The class rule is symmetric in (i, j) (float negation and round-to-nearest
+// are), so one decision serves both ordered pairs.  An FP32-class pair's
+// increments m_j d and -m_i d (float products, formed exactly by two_prod)
+// are summed in double-word form within the window (at most 32 terms per
+// accumulator and phase, exact to 2^-48); the block's column reduction and
+// the row partials go out in FP64, where the apply kernel adds them.  Every
+// other pair joins the warp's FP64 queue, solved 32 at a time and drained at
+// the end of each window, so every queued pair belongs to the current
+// window (drained at every phase, the lone-lane solves before each barrier
+// cost 12 % on GB300).
+constexpr int kGrpWarps = 8;
+// column blocks per window: the block synchronises and reduces its column
+// sums once per window
+constexpr int kGrpWindow = 4;
+
+__host__ __device__ __forceinline__ int64_t grp_start(int64_t g, int64_t nb)
 {
-    // FP64-class pairs wait in a per-warp queue (global i, j) until 32 have
-    // collected or the warp's range ends, so that the FP64 solves run with
-    // every lane busy: a queue flushed at every segment end ran mostly
-    // single-lane solves (13 % of the kernel on GB300).  (Flushing queues of
-    // 8 or more at segment ends was slower under both class rules.)
-    __shared__ int queue_i[4][64], queue_j[4][64];
-    __shared__ float2 qres[4][32][12];  // queued results as double-words
+    return g * nb - (int64_t)kGrpWarps * (g * (g - 1) / 2);
+}
+
+__host__ __device__ __forceinline__ int64_t grp_owner(int64_t p, int64_t B, int64_t P)
+{
+    return ((p + 1) * B - 1) / P;
+}
+
+template <bool STATS>
+__global__ void __launch_bounds__(kGrpWarps * 32, 2)
+    pair_step_grp_mixed_kernel(StepArgs a, MixedArgs ma, GrpLayout L, double *rowpart,
+                               double *colpart)
+{
+    // dynamic shared memory (grp_smem_bytes): the warps' column sums of the
+    // window, float4 q2 of column block slot cb holding components 2 q2 and
+    // 2 q2 + 1 as double-words (h, l, h, l); the window's column blocks
+    // (double buffered): (hi xyz, m), (lo xyz, 0), (v xyz, 0); the FP64
+    // queues and their results
+    extern __shared__ __align__(16) unsigned char gsm[];
+    float4(*cacc)[kGrpWindow][3][32] = reinterpret_cast<float4(*)[kGrpWindow][3][32]>(gsm);
+    float4(*cx)[kGrpWindow][3][32] = reinterpret_cast<float4(*)[kGrpWindow][3][32]>(
+        gsm + sizeof(float4) * kGrpWarps * kGrpWindow * 3 * 32);
+    int(*queue_i)[64] = reinterpret_cast<int(*)[64]>(
+        gsm + sizeof(float4) * (kGrpWarps + 2) * kGrpWindow * 3 * 32);
+    int(*queue_j)[64] = queue_i + kGrpWarps;
+    float2(*qres)[32][12] = reinterpret_cast<float2(*)[32][12]>(queue_j + kGrpWarps);
     griddep_wait();    // X and X32 from the prep kernel
     griddep_launch();  // the apply kernel may begin launching
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    const int tid = threadIdx.x;
     int *qi = queue_i[wib], *qj = queue_j[wib];
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n = a.n;
-    const int64_t W = (int64_t)gridDim.x * 4;
-    const int64_t w = (int64_t)blockIdx.x * 4 + wib;
+    const int64_t nb = L.nb;
+    const int64_t P = L.P;
+    const int64_t B = gridDim.x;
+    const int64_t b = blockIdx.x;
     const float *X32 = ma.X32;
     const KeplerParams kp{a.tol, a.max_iter, a.bisection};
     unsigned status = 0;
     long long it_sum = 0, slots = 0, fallbacks = 0, n32 = 0;
     int it_max = 0;
-    int tail = 0;  // queued pairs
 
-    // FP64 solve of queue entries 0..cnt-1.  Entries of the current tile
-    // (I, J) at step kc are added to the row owners' and column holders'
-    // double-word sums, in queue order; entries of the warp's earlier
-    // segments are added to those segments' FP64 partials, which this warp
-    // wrote and no other warp touches, in queue order where two entries meet
-    // the same element (passes by rank among equal targets).
-    auto flush = [&](int64_t I, int64_t J, bool diag, int kc, int cnt, dw racc[6], dw cacc[6]) {
+    const int64_t p0 = b * P / B, p1 = (b + 1) * P / B;
+    int64_t g = 0;
+    while (g + 1 < L.ng && grp_start(g + 1, nb) <= p0) ++g;
+    int64_t J = g * kGrpWarps + (p0 - grp_start(g, nb));
+    int64_t p = p0;
+    // a window: up to kGrpWindow consecutive phases of one group within the
+    // block's range
+    auto window_len = [&](int64_t pw, int64_t Jw) {
+        const int64_t m = nb - Jw < p1 - pw ? nb - Jw : p1 - pw;
+        return (int)(m < kGrpWindow ? m : kGrpWindow);
+    };
+    // the window's column blocks Jw .. Jw + len - 1 into cx[buf]
+    auto load_cols = [&](int buf, int64_t Jw, int len) {
+        for (int e = tid; e < len * 96; e += kGrpWarps * 32) {
+            const int cb = e / 96, r = (e >> 5) % 3, c = e & 31;
+            const int64_t j = 32 * (Jw + cb) + c;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j < n) {
+                if (r == 0)
+                    v = make_float4(X32[j], X32[n + j], X32[2 * n + j], X32[9 * n + j]);
+                else if (r == 1)
+                    v = make_float4(X32[3 * n + j], X32[4 * n + j], X32[5 * n + j], 0.f);
+                else
+                    v = make_float4(X32[6 * n + j], X32[7 * n + j], X32[8 * n + j], 0.f);
+            }
+            cx[buf][cb][r][c] = v;
+        }
+    };
+    int wl = p < p1 ? window_len(p, J) : 0;
+    if (wl > 0) load_cols(0, J, wl);
+    __syncthreads();
+
+    float hi_i[3] = {0, 0, 0}, lo_i[3] = {0, 0, 0}, v_i[3] = {0, 0, 0}, mfi = 1.0f;
+    dw racc[6];
+    bool new_group = true;
+    int buf = 0;
+
+    // FP64 solve of queue entries 0..cnt-1, all of the current window (column
+    // blocks Jw ..); their increments are added in queue order to the row
+    // owners' sums and to the warp's column accumulators of the window
+    auto flush = [&](int64_t Jw, int cnt) {
         const bool vq = lane < cnt;
         const int64_t iq = vq ? qi[lane] : 0, jq = vq ? qj[lane] : 0;
-        const bool cur = vq && (iq >> 5) == I && (jq >> 5) == J;
-        PairSolve p;
+        PairSolve ps;
         double miq = 0.0, mjq = 0.0;
         if (vq) {
             const double *X = a.X;
             miq = X[6 * n + iq];
             mjq = X[6 * n + jq];
-            pair_setup(p, a.tau, miq + mjq, X[iq] - X[jq], X[n + iq] - X[n + jq],
+            pair_setup(ps, a.tau, miq + mjq, X[iq] - X[jq], X[n + iq] - X[n + jq],
                        X[2 * n + iq] - X[2 * n + jq], X[3 * n + iq] - X[3 * n + jq],
                        X[4 * n + iq] - X[4 * n + jq], X[5 * n + iq] - X[5 * n + jq], a.pre,
                        a.guess);
         } else {
-            p.done = true;
-            p.beta = p.s = 0.0;
-            p.iters = 0;
-            p.status = 0;
+            ps.done = true;
+            ps.beta = ps.s = 0.0;
+            ps.iters = 0;
+            ps.status = 0;
         }
         double d[6];
         int iters = 0, fb = 0;
-        fp64_solve_warp(p, vq, a.tau, a.post * a.tau, kp, d, iters, fb);
-        double xr[6], xc[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            xr[q] = mjq * d[q];
-            xc[q] = -miq * d[q];
-        }
-        if (vq) status |= p.status;
-        if (cur) {
-            // converted to double-words here, with every lane active (the
-            // owners below add them one lane at a time)
+        fp64_solve_warp(ps, vq, a.tau, a.post * a.tau, kp, d, iters, fb);
+        if (vq) {
+            status |= ps.status;
+            // converted to double-words here, with every lane active
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
-                const float rh = __double2float_rn(xr[q]), ch = __double2float_rn(xc[q]);
-                qres[wib][lane][q] = make_float2(rh, __double2float_rn(xr[q] - (double)rh));
-                qres[wib][lane][6 + q] = make_float2(ch, __double2float_rn(xc[q] - (double)ch));
+                const double xr = mjq * d[q], xc = -miq * d[q];
+                const float rh = __double2float_rn(xr), ch = __double2float_rn(xc);
+                qres[wib][lane][q] = make_float2(rh, __double2float_rn(xr - (double)rh));
+                qres[wib][lane][6 + q] = make_float2(ch, __double2float_rn(xc - (double)ch));
             }
         }
         if (STATS) {
@@ -292,167 +366,164 @@ __global__ void __launch_bounds__(128, 4)
             if (lane == 0) slots += 32LL * wmax;
         }
         __syncwarp();
-        if (__any_sync(0xffffffffu, cur)) {
-            const int mycol = (lane + kc) & 31;
-            for (int q = 0; q < cnt; ++q) {
-                const int ie = qi[q], je = qj[q];
-                if ((ie >> 5) != I || (je >> 5) != J) continue;
-                if ((ie & 31) == lane) {
+        for (int e = 0; e < cnt; ++e) {
+            const int ie = qi[e], je = qj[e];
+            if ((ie & 31) == lane) {
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        const float2 x = qres[wib][q][c];
-                        dw_acc(racc[c], dw{x.x, x.y});
-                    }
-                }
-                if (!diag && (je & 31) == mycol) {
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) {
-                        const float2 x = qres[wib][q][6 + c];
-                        dw_acc(cacc[c], dw{x.x, x.y});
-                    }
+                for (int q = 0; q < 6; ++q) {
+                    const float2 x = qres[wib][e][q];
+                    dw_acc(racc[q], dw{x.x, x.y});
                 }
             }
-        }
-        const bool old = vq && !cur;
-        if (__any_sync(0xffffffffu, old)) {
-            // the entry's tile and this warp's segment of it
-            const int64_t Iq = iq >> 5, Jq = jq >> 5;
-            const int64_t tq = Jq * (Jq + 1) / 2 + Iq;
-            const int64_t hq = old ? w - sym_owner(32 * tq, W, T) : 0;
-            const bool dq = Iq == Jq;
-            for (int side = 0; side < 2; ++side) {
-                const bool act = old && (side == 0 || !dq);
-                // target element: slot (other block, segment) of particle
-                const int64_t slot = side == 0 ? Jq * Smax + hq : Iq * Smax + hq;
-                const int64_t part = side == 0 ? iq : jq;
-                const long long key = act ? (long long)(slot * n + part) : -1 - (long long)lane;
-                const unsigned same = __match_any_sync(0xffffffffu, key);
-                const int rank = __popc(same & lt_mask);
-                const int passes = __reduce_max_sync(0xffffffffu, act ? rank : 0);
-                for (int pass = 0; pass <= passes; ++pass) {
-                    if (act && rank == pass) {
-                        double *dst = a.partial + slot * 6 * n + part;
+            // the diagonal tile keeps row sums only
+            const bool dg = (ie >> 5) == (je >> 5);
+            if (!dg && (je & 31) == lane) {
+                const int cb = (int)((je >> 5) - Jw);
 #pragma unroll
-                        for (int c = 0; c < 6; ++c)
-                            dst[c * n] += side == 0 ? xr[c] : xc[c];
-                    }
-                    __syncwarp();
+                for (int q2 = 0; q2 < 3; ++q2) {
+                    const float4 x = cacc[wib][cb][q2][lane];
+                    dw a0{x.x, x.y}, a1{x.z, x.w};
+                    const float2 y0 = qres[wib][e][6 + 2 * q2], y1 = qres[wib][e][7 + 2 * q2];
+                    dw_acc(a0, dw{y0.x, y0.y});
+                    dw_acc(a1, dw{y1.x, y1.y});
+                    cacc[wib][cb][q2][lane] = make_float4(a0.h, a0.l, a1.h, a1.l);
                 }
             }
         }
         __syncwarp();
     };
 
-    const int64_t p1 = (w + 1) * T / W;
-    for (int64_t pos = w * T / W; pos < p1;) {
-        const int64_t tile = pos >> 5;
-        const int k0 = (int)(pos & 31);
-        const int k1 = p1 - pos < 32 - k0 ? k0 + (int)(p1 - pos) : 32;
-        const int h = (int)(w - sym_owner(32 * tile, W, T));  // segment of the tile
-        pos += k1 - k0;
-        int64_t I, J;
-        sym_tile_of(tile, I, J);
-        const bool diag = I == J;
+    while (wl > 0) {
+        const int64_t I = g * kGrpWarps + wib;
         const int64_t i = 32 * I + lane;
-        const bool irow = i < n;
-        float hi_i[3] = {0, 0, 0}, lo_i[3] = {0, 0, 0}, v_i[3] = {0, 0, 0}, mfi = 1.0f;
-        if (irow) {
+        const bool irow = I < nb && i < n;
+        if (new_group) {
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                hi_i[q] = X32[q * n + i];
-                lo_i[q] = X32[(3 + q) * n + i];
-                v_i[q] = X32[(6 + q) * n + i];
-            }
-            mfi = X32[9 * n + i];
-        }
-        dw racc[6], cacc[6];
-#pragma unroll
-        for (int q = 0; q < 6; ++q) racc[q] = cacc[q] = dw{0.0f, 0.0f};
-
-        for (int k = k0; k < k1; ++k) {
-            const int c = (lane + k) & 31;
-            const int64_t j = 32 * J + c;
-            const bool valid = irow && j < n && (!diag || c != lane);
-            bool solved32 = false;
-            int it32 = 0;
-            if (valid) {
-                float hi_j[3], lo_j[3], v_j[3];
+            for (int q = 0; q < 6; ++q) racc[q] = dw{0.0f, 0.0f};
+            if (irow) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    hi_j[q] = X32[q * n + j];
-                    lo_j[q] = X32[(3 + q) * n + j];
-                    v_j[q] = X32[(6 + q) * n + j];
+                    hi_i[q] = X32[q * n + i];
+                    lo_i[q] = X32[(3 + q) * n + i];
+                    v_i[q] = X32[(6 + q) * n + i];
                 }
-                const float mfj = X32[9 * n + j];
-                Pair32 p;
-                pair32_setup(p, hi_i, lo_i, v_i, mfi, hi_j, lo_j, v_j, mfj, ma.rule);
-                if (p.fp32) {
-                    float d[6];
-                    solved32 = pair32_solve(p, ma.tau32, ma.post32, a.guess, d, it32);
-                    if (solved32) {
+                mfi = X32[9 * n + i];
+            }
+            new_group = false;
+        }
+        for (int cb = 0; cb < wl; ++cb) {
 #pragma unroll
-                        for (int q = 0; q < 6; ++q) {
-                            dw_acc(racc[q], two_prod(mfj, d[q]));
-                            dw_acc(cacc[q], two_prod(-mfi, d[q]));
+            for (int q2 = 0; q2 < 3; ++q2)
+                cacc[wib][cb][q2][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+        int tail = 0;
+        for (int cb = 0; cb < wl; ++cb) {
+            const int64_t Jt = J + cb;
+            if (!(I <= Jt && I < nb)) continue;  // warp-uniform: no tile (I, Jt)
+            const bool diag = I == Jt;
+            for (int k = 0; k < 32; ++k) {
+                const int c = (lane + k) & 31;
+                const int64_t j = 32 * Jt + c;
+                const bool valid = irow && j < n && (!diag || c != lane);
+                bool solved32 = false;
+                int it32 = 0;
+                if (valid) {
+                    const float4 c0 = cx[buf][cb][0][c], c1 = cx[buf][cb][1][c],
+                                 c2 = cx[buf][cb][2][c];
+                    const float hi_j[3] = {c0.x, c0.y, c0.z}, lo_j[3] = {c1.x, c1.y, c1.z},
+                                v_j[3] = {c2.x, c2.y, c2.z};
+                    const float mfj = c0.w;
+                    Pair32 pr;
+                    pair32_setup(pr, hi_i, lo_i, v_i, mfi, hi_j, lo_j, v_j, mfj, ma.rule);
+                    if (pr.fp32) {
+                        float d[6];
+                        solved32 = pair32_solve(pr, ma.tau32, ma.post32, a.guess, d, it32);
+                        if (solved32) {
+#pragma unroll
+                            for (int q = 0; q < 6; ++q) dw_acc(racc[q], two_prod(mfj, d[q]));
+                            if (!diag) {
+#pragma unroll
+                                for (int q2 = 0; q2 < 3; ++q2) {
+                                    const float4 x = cacc[wib][cb][q2][c];
+                                    dw a0{x.x, x.y}, a1{x.z, x.w};
+                                    dw_acc(a0, two_prod(-mfi, d[2 * q2]));
+                                    dw_acc(a1, two_prod(-mfi, d[2 * q2 + 1]));
+                                    cacc[wib][cb][q2][c] = make_float4(a0.h, a0.l, a1.h, a1.l);
+                                }
+                            }
                         }
                     }
                 }
-            }
-            if (STATS) {
-                n32 += solved32 ? (diag ? 1 : 2) : 0;  // in ordered pairs
-                // single-precision iterations of the FP32-class solves
-                const int its = solved32 ? it32 : 0;
-                it_sum += its;
-                it_max = max(it_max, its);
-                const int wmax = __reduce_max_sync(0xffffffffu, its);
-                if (lane == 0) slots += 32LL * wmax;
-            }
-            const bool need64 = valid && !solved32;
-            const unsigned mask = __ballot_sync(0xffffffffu, need64);
-            if (need64) {
-                qi[tail + __popc(mask & lt_mask)] = (int)i;
-                qj[tail + __popc(mask & lt_mask)] = (int)j;
-            }
-            tail += __popc(mask);
-            __syncwarp();
-            if (tail >= 32) {
-                flush(I, J, diag, k, 32, racc, cacc);
-                if (lane < tail - 32) {
-                    qi[lane] = qi[32 + lane];
-                    qj[lane] = qj[32 + lane];
+                if (STATS) {
+                    n32 += solved32 ? (diag ? 1 : 2) : 0;  // in ordered pairs
+                    // single-precision iterations of the FP32-class solves
+                    const int its = solved32 ? it32 : 0;
+                    it_sum += its;
+                    it_max = max(it_max, its);
+                    const int wmax = __reduce_max_sync(0xffffffffu, its);
+                    if (lane == 0) slots += 32LL * wmax;
                 }
+                const bool need64 = valid && !solved32;
+                const unsigned mask = __ballot_sync(0xffffffffu, need64);
+                if (need64) {
+                    qi[tail + __popc(mask & lt_mask)] = (int)i;
+                    qj[tail + __popc(mask & lt_mask)] = (int)j;
+                }
+                tail += __popc(mask);
                 __syncwarp();
-                tail -= 32;
-            }
-            if (!diag && k + 1 < k1) {
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    cacc[q].h = __shfl_sync(0xffffffffu, cacc[q].h, (lane + 1) & 31);
-                    cacc[q].l = __shfl_sync(0xffffffffu, cacc[q].l, (lane + 1) & 31);
+                if (tail >= 32) {
+                    flush(J, 32);
+                    if (lane < tail - 32) {
+                        qi[lane] = qi[32 + lane];
+                        qj[lane] = qj[32 + lane];
+                    }
+                    __syncwarp();
+                    tail -= 32;
                 }
             }
         }
-        // segment sums in FP64: rows of i to slot (J, h), columns to slot (I, h)
-        if (irow) {
-            double *dst = a.partial + (J * Smax + h) * 6 * n;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) dst[q * n + i] = (double)racc[q].h + (double)racc[q].l;
+        if (tail > 0) flush(J, tail);
+        __syncthreads();  // every warp's column sums of the window are complete
+        // the next window; its column blocks are loaded now
+        const int64_t pn = p + wl;
+        int64_t gn = g, Jn = J + wl;
+        if (Jn == nb) {
+            gn = g + 1;
+            Jn = gn * kGrpWarps;
         }
-        if (!diag) {
-            const int64_t jc = 32 * J + ((lane + k1 - 1) & 31);
-            if (jc < n) {
-                double *dst = a.partial + (I * Smax + h) * 6 * n;
+        const int wln = pn < p1 ? window_len(pn, Jn) : 0;
+        if (wln > 0) load_cols(buf ^ 1, Jn, wln);
+        // the window's column partials: the warps' sums added in warp order
+        for (int e = tid; e < wl * 192; e += kGrpWarps * 32) {
+            const int cb = e / 192, rem = e - cb * 192, c = rem & 31, q = rem >> 5;
+            const int64_t j = 32 * (J + cb) + c;
+            if (j < n) {
+                double sum = 0.0;
 #pragma unroll
-                for (int q = 0; q < 6; ++q)
-                    dst[q * n + jc] = (double)cacc[q].h + (double)cacc[q].l;
+                for (int w = 0; w < kGrpWarps; ++w) {
+                    const float4 x = cacc[w][cb][q >> 1][c];
+                    sum += (q & 1) ? ((double)x.z + (double)x.w) : ((double)x.x + (double)x.y);
+                }
+                colpart[(g * 6 + q) * n + j] = sum;
             }
         }
-        __syncwarp();
-    }
-    // the pairs still queued belong to written segments
-    if (tail > 0) {
-        dw none[6];
-        flush(-1, -1, false, 0, tail, none, none);
+        // leaving the group (or the block's range): this piece's row partial
+        if (gn != g || pn == p1) {
+            if (irow) {
+                const int64_t h = b - grp_owner(grp_start(g, nb), B, P);
+                double *dst = rowpart + h * 6 * n;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) dst[q * n + i] = (double)racc[q].h + (double)racc[q].l;
+            }
+            new_group = true;
+        }
+        __syncthreads();  // the sums are read and the next column blocks stored
+        p = pn;
+        g = gn;
+        J = Jn;
+        wl = wln;
+        buf ^= 1;
     }
     status = __reduce_or_sync(0xffffffffu, status);
     if (lane == 0 && status) atomicOr(a.status, status);
@@ -474,6 +545,128 @@ __global__ void __launch_bounds__(128, 4)
             atomicMax(&a.stats[kStatMaxIters], (unsigned long long)mx);
         }
     }
+}
+
+// dynamic shared memory of the row-group kernel
+constexpr size_t kGrpSmem = sizeof(float4) * (kGrpWarps + 2) * kGrpWindow * 3 * 32 +
+                            sizeof(int) * 2 * kGrpWarps * 64 + sizeof(float2) * kGrpWarps * 32 * 12;
+
+// Eqs. 27b-d for the row-group layout.  Particle i of row block I (group
+// gi = I / kGrpWarps) adds its group's row pieces h = 0 .. npieces - 1 and the
+// column partials of groups g = 0 .. gi (the phases (g, I)), in that fixed
+// order, spread over the block's warps (slot s to warp s mod
+// kGrpApplyWarps, alternately into two sums) and then added in warp order.  Block (x, y) takes 32 particles and the component pair (y, 3 + y).
+constexpr int kGrpApplyWarps = 8;
+
+__global__ void __launch_bounds__(32 * kGrpApplyWarps)
+    apply_grp_kernel(double *state, const double *X, const double *rowpart,
+                     const double *colpart, int64_t n, GrpLayout L, int64_t B,
+                     double post_drift, unsigned *status)
+{
+    __shared__ double red[kGrpApplyWarps][2][32];
+    griddep_wait();    // the pair kernel's partials
+    griddep_launch();  // what follows waits for this grid or is launched plainly
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int q = blockIdx.y;
+    const int64_t Ib = blockIdx.x;
+    const int64_t i = Ib * 32 + lane;
+    const int64_t gi = Ib / kGrpWarps;
+    const int64_t s0 = grp_start(gi, L.nb), s1 = grp_start(gi + 1, L.nb);
+    const int npieces = (int)(grp_owner(s1 - 1, B, L.P) - grp_owner(s0, B, L.P)) + 1;
+    const int nslots = npieces + (int)gi + 1;
+    double dr = 0.0, dv = 0.0;
+    if (i < n) {
+        auto slot = [&](int sl) {
+            return sl < npieces ? rowpart + (int64_t)sl * 6 * n
+                                : colpart + (int64_t)(sl - npieces) * 6 * n;
+        };
+        double er0 = 0, er1 = 0, ev0 = 0, ev1 = 0;
+        int sl = wid;
+        for (; sl + kGrpApplyWarps < nslots; sl += 2 * kGrpApplyWarps) {
+            const double *b0 = slot(sl), *b1 = slot(sl + kGrpApplyWarps);
+            er0 += b0[q * n + i];
+            ev0 += b0[(3 + q) * n + i];
+            er1 += b1[q * n + i];
+            ev1 += b1[(3 + q) * n + i];
+        }
+        if (sl < nslots) {
+            const double *b0 = slot(sl);
+            er0 += b0[q * n + i];
+            ev0 += b0[(3 + q) * n + i];
+        }
+        dr = er0 + er1;
+        dv = ev0 + ev1;
+    }
+    red[wid][0][lane] = dr;
+    red[wid][1][lane] = dv;
+    __syncthreads();
+    if (wid != 0 || i >= n) return;
+    double tr = red[0][0][lane], tv = red[0][1][lane];
+    for (int w = 1; w < kGrpApplyWarps; ++w) {
+        tr += red[w][0][lane];
+        tv += red[w][1][lane];
+    }
+    const double v1 = X[(3 + q) * n + i] + tv;
+    const double x1 = fma(v1, post_drift, X[q * n + i] + tr);
+    if (!isfinite(x1) || !isfinite(v1)) atomicOr(status, kStatusNonfinite);
+    state[q * n + i] = x1;
+    state[(3 + q) * n + i] = v1;
+}
+
+GrpLayout make_grp_layout(int64_t n, int64_t &blocks)
+{
+    GrpLayout L;
+    L.nb = (n + 31) / 32;
+    L.ng = (int)((L.nb + kGrpWarps - 1) / kGrpWarps);
+    L.P = grp_start(L.ng, L.nb);
+    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, L.P));
+    L.Hmax = 1;
+    for (int64_t g = 0; g < L.ng; ++g) {
+        const int64_t s0 = grp_start(g, L.nb), s1 = grp_start(g + 1, L.nb);
+        const int64_t h = grp_owner(s1 - 1, blocks, L.P) - grp_owner(s0, blocks, L.P) + 1;
+        L.Hmax = std::max<int>(L.Hmax, (int)h);
+    }
+    return L;
+}
+
+void launch_pair_step_grp_mixed(const StepArgs &a, const MixedArgs &ma, const GrpLayout &L,
+                                double *rowpart, double *colpart, int blocks, bool stats,
+                                cudaStream_t s)
+{
+    GrpLayout Lv = L;
+    void *args[] = {(void *)&a, (void *)&ma, (void *)&Lv, (void *)&rowpart, (void *)&colpart};
+    const void *fn = stats ? (const void *)pair_step_grp_mixed_kernel<true>
+                           : (const void *)pair_step_grp_mixed_kernel<false>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGrpSmem);
+    launch_pdl(fn, dim3(blocks), dim3(kGrpWarps * 32), args, kGrpSmem, s);
+}
+
+int pair_step_grp_mixed_blocks_per_sm(bool stats)
+{
+    int b = 0;
+    const void *fn = stats ? (const void *)pair_step_grp_mixed_kernel<true>
+                           : (const void *)pair_step_grp_mixed_kernel<false>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGrpSmem);
+    const cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kGrpWarps * 32, kGrpSmem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return b > 0 ? b : 1;
+}
+
+void launch_apply_grp(double *state, const double *X, const double *rowpart,
+                      const double *colpart, int64_t n, const GrpLayout &L, int64_t blocks,
+                      double post_drift, unsigned *status, cudaStream_t s)
+{
+    GrpLayout Lv = L;
+    int64_t B = blocks;
+    void *args[] = {(void *)&state,   (void *)&X, (void *)&rowpart,    (void *)&colpart,
+                    (void *)&n,       (void *)&Lv, (void *)&B, (void *)&post_drift,
+                    (void *)&status};
+    launch_pdl((const void *)apply_grp_kernel, dim3((unsigned)((n + 31) / 32), 3),
+               dim3(32 * kGrpApplyWarps), args, 0, s);
 }
 
 // The class of every ordered pair (i, j) as the mixed kernels decide it
@@ -512,32 +705,6 @@ void launch_pair_classes(const float *X32, int64_t n, const ClassRule &rule, uns
     const int64_t total = n * n;
     pair_class_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, s>>>(
         X32, n, rule, out);
-}
-
-void launch_pair_step_sym_mixed(const StepArgs &a, const MixedArgs &ma, int Smax, int64_t T,
-                                int blocks, bool stats, cudaStream_t s)
-{
-    int Sv = Smax;
-    int64_t it = T;
-    void *args[] = {(void *)&a, (void *)&ma, (void *)&Sv, (void *)&it};
-    launch_pdl(stats ? (const void *)pair_step_sym_mixed_kernel<true>
-                     : (const void *)pair_step_sym_mixed_kernel<false>,
-               dim3(blocks), dim3(128), args, 0, s);
-}
-
-int pair_step_sym_mixed_blocks_per_sm(bool stats)
-{
-    int b = 0;
-    const cudaError_t e =
-        stats ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &b, pair_step_sym_mixed_kernel<true>, 128, 0)
-              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &b, pair_step_sym_mixed_kernel<false>, 128, 0);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return 1;
-    }
-    return b > 0 ? b : 1;
 }
 
 void launch_prep_mixed(const double *state, const double *mass, double *X, float *X32,

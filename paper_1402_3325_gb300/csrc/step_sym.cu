@@ -206,9 +206,16 @@ __global__ void __launch_bounds__(32 * kApplyWarps)
 {
     __shared__ double red[kApplyWarps][2][32];
     griddep_wait();  // the pair kernel's partials
-    // a kernel that follows reads this one's output only after its own
-    // griddep_wait (the next pair kernel) or is launched plainly
-    griddep_launch();
+    // Without fuse, a kernel that follows reads this one's output only after
+    // its own griddep_wait or is launched plainly, so it may begin launching
+    // now.  With fuse the next kernel is a persistent pair kernel whose
+    // blocks must be spread evenly over the SMs: launched while this grid's
+    // blocks still hold SM resources, some SMs would receive an extra block
+    // (the seeded kernel is sized below its occupancy limit), and its static
+    // work partition would then run those SMs' warps a third slower (a
+    // 16384-body step measured 40.4 ms against 27.4 ms); it waits for this
+    // grid to complete instead.
+    if (!fuse) griddep_launch();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int q = blockIdx.y;
     const int64_t P = blockIdx.x;
