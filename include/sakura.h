@@ -84,6 +84,15 @@ extern "C" {
 #define SAKURA_FLAG_NO_AUTOTUNE 8u /* batched path: skip the block-shape autotuner  */
 #define SAKURA_FLAG_NO_SMALL 16u   /* n <= 20: use the multi-kernel step instead of  */
                                    /* the single-block kernel (for comparisons)      */
+#define SAKURA_FLAG_TILES 32u      /* symmetric FP64 step: always the systolic tile
+                                      kernel (per-warp tile segments, partials per
+                                      segment: 3 n^2 bytes of scratch), the default
+                                      while those partials take at most 4 GB        */
+#define SAKURA_FLAG_GROUPS 64u     /* symmetric FP64 step: always the row-group
+                                      kernel (blocks of warps sweep column blocks
+                                      together, column sums reduced per block:
+                                      n^2 / 2.7 bytes), the default beyond; the
+                                      mixed form always uses row groups            */
 
 #define SAKURA_BATCH_MAX_N 64     /* largest system of sakura_step_batched       */
 

@@ -210,10 +210,12 @@ int step_device_mixed_grp(const double *src, double *dst, const double *masses, 
                           double dt, int order)
 {
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
-    int64_t blocks = g.cfg.grid_blocks > 0
-                         ? g.cfg.grid_blocks
-                         : (int64_t)g.sm_count * sakura::pair_step_grp_mixed_blocks_per_sm(stats);
-    const sakura::GrpLayout L = sakura::make_grp_layout(n, blocks);
+    const bool seed = g.cfg.guess == SAKURA_GUESS_FP32;
+    int64_t blocks =
+        g.cfg.grid_blocks > 0
+            ? g.cfg.grid_blocks
+            : (int64_t)g.sm_count * sakura::pair_step_grp_mixed_blocks_per_sm(stats, seed);
+    const sakura::GrpLayout L = sakura::make_grp_layout(n, sakura::kMixedGrpWarps, blocks);
     // scratch: X[7][n] doubles, row partials [Hmax][6][n], column partials
     // [ng][6][n], then X32[10][n] floats
     int rc = grow(g.partial, (size_t)(7 * n + (int64_t)(L.Hmax + L.ng) * 6 * n + 5 * n) *
@@ -237,6 +239,9 @@ int step_device_mixed_grp(const double *src, double *dst, const double *masses, 
     a.max_iter = g.cfg.kepler_max_iter;
     a.bisection = g.cfg.kepler_bisection;
     a.guess = (g.cfg.guess == SAKURA_GUESS_TAYLOR || g.cfg.guess == SAKURA_GUESS_FP32) ? 2 : 0;
+    a.X32 = seed ? X32 : nullptr;
+    a.ptau32 = (float)(a.pre * dt);
+    a.t32 = (float)dt;
     a.status = g.d_status;
     a.stats = g.d_stats;
     sakura::MixedArgs ma;
@@ -255,8 +260,102 @@ int step_device_mixed_grp(const double *src, double *dst, const double *masses, 
         cudaEventRecord(tm.second, g.stream);
         g.timers.push_back(tm);
     }
-    sakura::launch_apply_grp(dst, X, rowpart, colpart, n, L, blocks, post_drift, g.d_status,
-                             g.stream);
+    sakura::launch_apply_grp(dst, X, nullptr, rowpart, colpart, n, L, blocks, post_drift, false,
+                             0.0, g.d_status, g.stream);
+    rc = launch_error();
+    if (rc) return rc;
+    g.steps += 1;
+    g.pairs += n * (n - 1);
+    int64_t diag = 0;  // ordered pairs inside diagonal tiles
+    for (int64_t b = 0; b < L.nb; ++b) {
+        const int64_t nbk = std::min<int64_t>(32, n - 32 * b);
+        diag += nbk * (nbk - 1);
+    }
+    g.solves += (n * (n - 1) - diag) / 2 + diag;
+    return SAKURA_OK;
+}
+
+// Scratch of the two symmetric layouts: the systolic tile kernels keep
+// 6 doubles per particle per (other block, tile segment) slot, at most
+// 8 nb n of them; the row-group kernels one 6-vector per particle per group
+// (nb / G groups) plus a few row pieces.
+double tile_partial_bytes(int64_t n) { return 8.0 * 6.0 * 8.0 * (double)((n + 31) / 32) * n; }
+double group_partial_bytes(int64_t n, int G)
+{
+    return 48.0 * (double)n * (double)(((n + 31) / 32 + G - 1) / G + 16);
+}
+
+// The symmetric FP64 form runs on systolic tiles (step_sym.cu), measured
+// fastest at every size (16384 bodies: 27.3 ms per step against 28.0 in row
+// groups), while their partials take at most kTileMaxBytes; beyond that in
+// row-group phases (step_grp.cu), whose scratch is 8 times smaller.  The
+// flags force either kernel.
+constexpr double kTileMaxBytes = 4.0 * 1024 * 1024 * 1024;
+
+bool fp64_groups(int64_t n)
+{
+    if (g.cfg.flags & SAKURA_FLAG_GROUPS) return true;
+    if (g.cfg.flags & SAKURA_FLAG_TILES) return false;
+    return tile_partial_bytes(n) > kTileMaxBytes;
+}
+
+// The FP64 form with each unordered pair once, in row-group phases
+// (step_grp.cu).  prepped: X (and X32) already hold this sub-step's drifted
+// state, written by the previous apply kernel; fuse: the apply kernel also
+// applies the next sub-step's drift next_drift and writes its X (and X32).
+int step_device_fp64_grp(const double *src, double *dst, const double *masses, int64_t n,
+                         double dt, int order, bool prepped, bool fuse, double next_drift)
+{
+    const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
+    const bool learned = g.cfg.guess == SAKURA_GUESS_LEARNED;
+    const bool seed = g.cfg.guess == SAKURA_GUESS_FP32;
+    int64_t blocks = g.cfg.grid_blocks > 0
+                         ? g.cfg.grid_blocks
+                         : (int64_t)g.sm_count *
+                               sakura::pair_step_grp_blocks_per_sm(stats, learned, seed);
+    const sakura::GrpLayout L = sakura::make_grp_layout(n, sakura::kFp64GrpWarps, blocks);
+    // scratch: X[7][n] doubles, row partials [Hmax][6][n], column partials
+    // [ng][6][n], then X32[10][n] floats (single-precision seed)
+    int rc = grow(g.partial, (size_t)(7 * n + (int64_t)(L.Hmax + L.ng) * 6 * n + 5 * n) *
+                                 sizeof(double));
+    if (rc) return rc;
+    double *X = (double *)g.partial.ptr;
+    double *rowpart = X + 7 * n;
+    double *colpart = rowpart + (int64_t)L.Hmax * 6 * n;
+    float *X32 = seed ? (float *)(colpart + (int64_t)L.ng * 6 * n) : nullptr;
+    const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
+    const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
+    if (!prepped) sakura::launch_prep_step(src, masses, X, X32, n, drift, g.d_status, g.stream);
+    sakura::StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.X = X;
+    a.X32 = X32;
+    a.n = n;
+    a.tau = dt;
+    a.pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
+    a.post = 1.0 - a.pre;
+    a.ptau32 = (float)(a.pre * dt);
+    a.t32 = (float)dt;
+    a.tol = g.cfg.kepler_tol * DBL_EPSILON;
+    a.max_iter = g.cfg.kepler_max_iter;
+    a.bisection = g.cfg.kepler_bisection;
+    a.guess = (g.cfg.guess == SAKURA_GUESS_TAYLOR || g.cfg.guess == SAKURA_GUESS_FP32) ? 2 : 0;
+    a.mlp = learned ? (const sakura::MlpWeights *)g.mlp.ptr : nullptr;
+    a.status = g.d_status;
+    a.stats = g.d_stats;
+    const bool timing = (g.cfg.flags & SAKURA_FLAG_TIMING) != 0;
+    std::pair<cudaEvent_t, cudaEvent_t> tm{nullptr, nullptr};
+    if (timing) {
+        tm = take_timer();
+        cudaEventRecord(tm.first, g.stream);
+    }
+    sakura::launch_pair_step_grp(a, L, rowpart, colpart, (int)blocks, stats, g.stream);
+    if (timing) {
+        cudaEventRecord(tm.second, g.stream);
+        g.timers.push_back(tm);
+    }
+    sakura::launch_apply_grp(dst, X, X32, rowpart, colpart, n, L, blocks, post_drift, fuse,
+                             next_drift, g.d_status, g.stream);
     rc = launch_error();
     if (rc) return rc;
     g.steps += 1;
@@ -280,6 +379,8 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
                     double next_drift = 0.0)
 {
     if (mixed) return step_device_mixed_grp(src, dst, masses, n, dt, order);
+    if (!df64 && fp64_groups(n))
+        return step_device_fp64_grp(src, dst, masses, n, dt, order, prepped, fuse, next_drift);
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
     const bool learned = !df64 && g.cfg.guess == SAKURA_GUESS_LEARNED;
     const bool seed = !df64 && g.cfg.guess == SAKURA_GUESS_FP32;
@@ -369,8 +470,8 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
     return SAKURA_OK;
 }
 
-// The symmetric mode keeps 32 n (n/32 + 1) doubles of tile partials; beyond
-// kSymMaxBytes the ordered-pair kernel (O(n) scratch) is used instead.
+// The symmetric mode keeps O(n^2 / 32) partial sums; beyond kSymMaxBytes the
+// ordered-pair kernel (O(n) scratch) is used instead.
 constexpr double kSymMaxBytes = 16.0 * 1024 * 1024 * 1024;
 
 // One step of the given order from src to dst (the same buffer, or two
@@ -379,8 +480,12 @@ constexpr double kSymMaxBytes = 16.0 * 1024 * 1024 * 1024;
 // drifted state X[7][n] at the start of the scratch buffer (step_masses).
 bool sym_path(int64_t n)
 {
-    return g.cfg.pair_mode == SAKURA_PAIRS_SYMMETRIC && n > 1 &&
-           8.0 * 6.0 * 8.0 * (double)((n + 31) / 32) * (double)n <= kSymMaxBytes;
+    if (g.cfg.pair_mode != SAKURA_PAIRS_SYMMETRIC || n < 2) return false;
+    if (g.cfg.precision == SAKURA_PREC_DF64) return tile_partial_bytes(n) <= kSymMaxBytes;
+    if (g.cfg.precision == SAKURA_PREC_MIXED)
+        return group_partial_bytes(n, sakura::kMixedGrpWarps) <= kSymMaxBytes;
+    return (fp64_groups(n) ? group_partial_bytes(n, sakura::kFp64GrpWarps)
+                           : tile_partial_bytes(n)) <= kSymMaxBytes;
 }
 
 // Sub-steps whose apply kernel can also drift for the next one: the FP64

@@ -234,22 +234,13 @@ __global__ void __launch_bounds__(WARPS * 32)
 // the end of each window, so every queued pair belongs to the current
 // window (drained at every phase, the lone-lane solves before each barrier
 // cost 12 % on GB300).
-constexpr int kGrpWarps = 8;
-// column blocks per window: the block synchronises and reduces its column
-// sums once per window
-constexpr int kGrpWindow = 4;
 
-__host__ __device__ __forceinline__ int64_t grp_start(int64_t g, int64_t nb)
-{
-    return g * nb - (int64_t)kGrpWarps * (g * (g - 1) / 2);
-}
+// SEED: the FP64-class pairs start their FP64 iteration from the root of a
+// single-precision solve of the same pair and finish by the Taylor carry, as
+// in the symmetric FP64 kernel (step_sym.cu); otherwise from a.guess.
+constexpr int kGrpWarps = kMixedGrpWarps;
 
-__host__ __device__ __forceinline__ int64_t grp_owner(int64_t p, int64_t B, int64_t P)
-{
-    return ((p + 1) * B - 1) / P;
-}
-
-template <bool STATS>
+template <bool STATS, bool SEED>
 __global__ void __launch_bounds__(kGrpWarps * 32, 2)
     pair_step_grp_mixed_kernel(StepArgs a, MixedArgs ma, GrpLayout L, double *rowpart,
                                double *colpart)
@@ -282,13 +273,13 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
     const float *X32 = ma.X32;
     const KeplerParams kp{a.tol, a.max_iter, a.bisection};
     unsigned status = 0;
-    long long it_sum = 0, slots = 0, fallbacks = 0, n32 = 0;
+    long long it_sum = 0, slots = 0, fallbacks = 0, n32 = 0, carries = 0;
     int it_max = 0;
 
     const int64_t p0 = b * P / B, p1 = (b + 1) * P / B;
     int64_t g = 0;
-    while (g + 1 < L.ng && grp_start(g + 1, nb) <= p0) ++g;
-    int64_t J = g * kGrpWarps + (p0 - grp_start(g, nb));
+    while (g + 1 < L.ng && grp_start(g + 1, nb, kGrpWarps) <= p0) ++g;
+    int64_t J = g * kGrpWarps + (p0 - grp_start(g, nb, kGrpWarps));
     int64_t p = p0;
     // a window: up to kGrpWindow consecutive phases of one group within the
     // block's range
@@ -337,7 +328,28 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
             pair_setup(ps, a.tau, miq + mjq, X[iq] - X[jq], X[n + iq] - X[n + jq],
                        X[2 * n + iq] - X[2 * n + jq], X[3 * n + iq] - X[3 * n + jq],
                        X[4 * n + iq] - X[4 * n + jq], X[5 * n + iq] - X[5 * n + jq], a.pre,
-                       a.guess);
+                       SEED ? -1 : a.guess);
+            if (SEED) {
+                // the root of the single-precision solve of the pair (unless
+                // t was reduced modulo the period), else the second-order guess
+                float dr[3], dv[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    dr[q] = __fadd_rn(__fsub_rn(X32[q * n + iq], X32[q * n + jq]),
+                                      __fsub_rn(X32[(3 + q) * n + iq], X32[(3 + q) * n + jq]));
+                    dv[q] = __fsub_rn(X32[(6 + q) * n + iq], X32[(6 + q) * n + jq]);
+                }
+                const K32 o = k32_phase1(dr, dv, X32[9 * n + iq] + X32[9 * n + jq], a.ptau32,
+                                         a.t32, 2);
+                if (o.ok && __double_as_longlong(ps.t) == __double_as_longlong(a.tau) &&
+                    !ps.done) {
+                    ps.s = f2d(o.s);
+                } else if (!ps.done) {
+                    ps.s = ps.t * ps.ir0;
+                    const double cq = 0.5 * ps.s * (ps.eta0 * ps.ir0);
+                    if (magbits(cq) < 0x3fe0000000000000LL) ps.s = fma(-cq, ps.s, ps.s);
+                }
+            }
         } else {
             ps.done = true;
             ps.beta = ps.s = 0.0;
@@ -346,7 +358,7 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
         }
         double d[6];
         int iters = 0, fb = 0;
-        fp64_solve_warp(ps, vq, a.tau, a.post * a.tau, kp, d, iters, fb);
+        fp64_solve_warp<SEED>(ps, vq, a.tau, a.post * a.tau, kp, d, iters, fb);
         if (vq) {
             status |= ps.status;
             // converted to double-words here, with every lane active
@@ -359,6 +371,7 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
             }
         }
         if (STATS) {
+            carries += (vq && ps.carried) ? 1 : 0;
             it_sum += iters;
             fallbacks += fb;
             it_max = max(it_max, iters);
@@ -511,7 +524,7 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
         // leaving the group (or the block's range): this piece's row partial
         if (gn != g || pn == p1) {
             if (irow) {
-                const int64_t h = b - grp_owner(grp_start(g, nb), B, P);
+                const int64_t h = b - grp_owner(grp_start(g, nb, kGrpWarps), B, P);
                 double *dst = rowpart + h * 6 * n;
 #pragma unroll
                 for (int q = 0; q < 6; ++q) dst[q * n + i] = (double)racc[q].h + (double)racc[q].l;
@@ -528,13 +541,14 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
     status = __reduce_or_sync(0xffffffffu, status);
     if (lane == 0 && status) atomicOr(a.status, status);
     if (STATS) {
-        long long s1 = it_sum, s2 = slots, s3 = fallbacks, s4 = n32;
+        long long s1 = it_sum, s2 = slots, s3 = fallbacks, s4 = n32, s5 = carries;
         int mx = it_max;
         for (int o = 16; o > 0; o >>= 1) {
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
             s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             s3 += __shfl_xor_sync(0xffffffffu, s3, o);
             s4 += __shfl_xor_sync(0xffffffffu, s4, o);
+            s5 += __shfl_xor_sync(0xffffffffu, s5, o);
             mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         }
         if (lane == 0) {
@@ -542,6 +556,7 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
             atomicAdd(&a.stats[kStatSlots], (unsigned long long)s2);
             atomicAdd(&a.stats[kStatFallbacks], (unsigned long long)s3);
             atomicAdd(&a.stats[kStatFp32Pairs], (unsigned long long)s4);
+            atomicAdd(&a.stats[kStatCarries], (unsigned long long)s5);
             atomicMax(&a.stats[kStatMaxIters], (unsigned long long)mx);
         }
     }
@@ -551,82 +566,13 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
 constexpr size_t kGrpSmem = sizeof(float4) * (kGrpWarps + 2) * kGrpWindow * 3 * 32 +
                             sizeof(int) * 2 * kGrpWarps * 64 + sizeof(float2) * kGrpWarps * 32 * 12;
 
-// Eqs. 27b-d for the row-group layout.  Particle i of row block I (group
-// gi = I / kGrpWarps) adds its group's row pieces h = 0 .. npieces - 1 and the
-// column partials of groups g = 0 .. gi (the phases (g, I)), in that fixed
-// order, spread over the block's warps (slot s to warp s mod
-// kGrpApplyWarps, alternately into two sums) and then added in warp order.  Block (x, y) takes 32 particles and the component pair (y, 3 + y).
-constexpr int kGrpApplyWarps = 8;
-
-__global__ void __launch_bounds__(32 * kGrpApplyWarps)
-    apply_grp_kernel(double *state, const double *X, const double *rowpart,
-                     const double *colpart, int64_t n, GrpLayout L, int64_t B,
-                     double post_drift, unsigned *status)
+const void *grp_kernel(bool stats, bool seed)
 {
-    __shared__ double red[kGrpApplyWarps][2][32];
-    griddep_wait();    // the pair kernel's partials
-    griddep_launch();  // what follows waits for this grid or is launched plainly
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int q = blockIdx.y;
-    const int64_t Ib = blockIdx.x;
-    const int64_t i = Ib * 32 + lane;
-    const int64_t gi = Ib / kGrpWarps;
-    const int64_t s0 = grp_start(gi, L.nb), s1 = grp_start(gi + 1, L.nb);
-    const int npieces = (int)(grp_owner(s1 - 1, B, L.P) - grp_owner(s0, B, L.P)) + 1;
-    const int nslots = npieces + (int)gi + 1;
-    double dr = 0.0, dv = 0.0;
-    if (i < n) {
-        auto slot = [&](int sl) {
-            return sl < npieces ? rowpart + (int64_t)sl * 6 * n
-                                : colpart + (int64_t)(sl - npieces) * 6 * n;
-        };
-        double er0 = 0, er1 = 0, ev0 = 0, ev1 = 0;
-        int sl = wid;
-        for (; sl + kGrpApplyWarps < nslots; sl += 2 * kGrpApplyWarps) {
-            const double *b0 = slot(sl), *b1 = slot(sl + kGrpApplyWarps);
-            er0 += b0[q * n + i];
-            ev0 += b0[(3 + q) * n + i];
-            er1 += b1[q * n + i];
-            ev1 += b1[(3 + q) * n + i];
-        }
-        if (sl < nslots) {
-            const double *b0 = slot(sl);
-            er0 += b0[q * n + i];
-            ev0 += b0[(3 + q) * n + i];
-        }
-        dr = er0 + er1;
-        dv = ev0 + ev1;
-    }
-    red[wid][0][lane] = dr;
-    red[wid][1][lane] = dv;
-    __syncthreads();
-    if (wid != 0 || i >= n) return;
-    double tr = red[0][0][lane], tv = red[0][1][lane];
-    for (int w = 1; w < kGrpApplyWarps; ++w) {
-        tr += red[w][0][lane];
-        tv += red[w][1][lane];
-    }
-    const double v1 = X[(3 + q) * n + i] + tv;
-    const double x1 = fma(v1, post_drift, X[q * n + i] + tr);
-    if (!isfinite(x1) || !isfinite(v1)) atomicOr(status, kStatusNonfinite);
-    state[q * n + i] = x1;
-    state[(3 + q) * n + i] = v1;
-}
-
-GrpLayout make_grp_layout(int64_t n, int64_t &blocks)
-{
-    GrpLayout L;
-    L.nb = (n + 31) / 32;
-    L.ng = (int)((L.nb + kGrpWarps - 1) / kGrpWarps);
-    L.P = grp_start(L.ng, L.nb);
-    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, L.P));
-    L.Hmax = 1;
-    for (int64_t g = 0; g < L.ng; ++g) {
-        const int64_t s0 = grp_start(g, L.nb), s1 = grp_start(g + 1, L.nb);
-        const int64_t h = grp_owner(s1 - 1, blocks, L.P) - grp_owner(s0, blocks, L.P) + 1;
-        L.Hmax = std::max<int>(L.Hmax, (int)h);
-    }
-    return L;
+    if (seed)
+        return stats ? (const void *)pair_step_grp_mixed_kernel<true, true>
+                     : (const void *)pair_step_grp_mixed_kernel<false, true>;
+    return stats ? (const void *)pair_step_grp_mixed_kernel<true, false>
+                 : (const void *)pair_step_grp_mixed_kernel<false, false>;
 }
 
 void launch_pair_step_grp_mixed(const StepArgs &a, const MixedArgs &ma, const GrpLayout &L,
@@ -635,17 +581,15 @@ void launch_pair_step_grp_mixed(const StepArgs &a, const MixedArgs &ma, const Gr
 {
     GrpLayout Lv = L;
     void *args[] = {(void *)&a, (void *)&ma, (void *)&Lv, (void *)&rowpart, (void *)&colpart};
-    const void *fn = stats ? (const void *)pair_step_grp_mixed_kernel<true>
-                           : (const void *)pair_step_grp_mixed_kernel<false>;
+    const void *fn = grp_kernel(stats, a.X32 != nullptr);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGrpSmem);
     launch_pdl(fn, dim3(blocks), dim3(kGrpWarps * 32), args, kGrpSmem, s);
 }
 
-int pair_step_grp_mixed_blocks_per_sm(bool stats)
+int pair_step_grp_mixed_blocks_per_sm(bool stats, bool seed)
 {
     int b = 0;
-    const void *fn = stats ? (const void *)pair_step_grp_mixed_kernel<true>
-                           : (const void *)pair_step_grp_mixed_kernel<false>;
+    const void *fn = grp_kernel(stats, seed);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGrpSmem);
     const cudaError_t e =
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kGrpWarps * 32, kGrpSmem);
@@ -654,19 +598,6 @@ int pair_step_grp_mixed_blocks_per_sm(bool stats)
         return 1;
     }
     return b > 0 ? b : 1;
-}
-
-void launch_apply_grp(double *state, const double *X, const double *rowpart,
-                      const double *colpart, int64_t n, const GrpLayout &L, int64_t blocks,
-                      double post_drift, unsigned *status, cudaStream_t s)
-{
-    GrpLayout Lv = L;
-    int64_t B = blocks;
-    void *args[] = {(void *)&state,   (void *)&X, (void *)&rowpart,    (void *)&colpart,
-                    (void *)&n,       (void *)&Lv, (void *)&B, (void *)&post_drift,
-                    (void *)&status};
-    launch_pdl((const void *)apply_grp_kernel, dim3((unsigned)((n + 31) / 32), 3),
-               dim3(32 * kGrpApplyWarps), args, 0, s);
 }
 
 // The class of every ordered pair (i, j) as the mixed kernels decide it

@@ -45,6 +45,8 @@ FLAG_STATS = 2
 FLAG_TIMING = 4
 FLAG_NO_AUTOTUNE = 8
 FLAG_NO_SMALL = 16
+FLAG_TILES = 32
+FLAG_GROUPS = 64
 # largest system of the single-block kernel (csrc/step_small.cuh)
 SMALL_MAX_N = 20
 BATCH_MAX_N = 64

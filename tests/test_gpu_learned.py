@@ -185,3 +185,23 @@ def test_load_rejects_bad_blobs():
     assert lib.sakura_load_mlp(bad.ctypes.data, bad.nbytes) == sk.E_ARG
     short = np.ones(100, dtype=np.float32)
     assert lib.sakura_load_mlp(short.ctypes.data, short.nbytes) == sk.E_ARG
+
+
+@pytest.mark.parametrize("order", [2, -1])
+def test_learned_guess_in_the_row_group_kernel(trained, order):
+    # the network inside the row-group kernel (the default from 8192
+    # particles), forced on a small system
+    blob, _ = trained
+    s = ics.random_cluster(700, seed=3, mass_spread=2.0)
+    with configured(guess=sk.GUESS_LEARNED, flags=sk.FLAG_STATS | sk.FLAG_GROUPS):
+        sk.load_mlp(blob)
+        st = dev(s.soa())
+        sk.step(st, dev(s.m), s.dt, order)
+        sk.check()
+        r, v = ics.from_soa(st.cpu().numpy())
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, order, nthreads=NCPU)
+    R = np.sqrt((rr ** 2).sum(1).mean())
+    V = np.sqrt((vr ** 2).sum(1).mean())
+    er = np.linalg.norm(r - rr, axis=1) / np.maximum(np.linalg.norm(rr, axis=1), R)
+    ev = np.linalg.norm(v - vr, axis=1) / np.maximum(np.linalg.norm(vr, axis=1), V)
+    assert er.max() <= TOL and ev.max() <= TOL

@@ -156,14 +156,15 @@ def test_mixed_energy_drift_bh_cluster(pairs):
     assert abs(Em - Ef) <= 1e-9 * abs(E0)
 
 
+@pytest.mark.parametrize("guess", [sk.GUESS_TAYLOR, sk.GUESS_FP32], ids=["taylor", "seed"])
 @pytest.mark.parametrize("blocks", [1, 7])
 @pytest.mark.parametrize("rule", [0, 1], ids=["literal", "hyp"])
-def test_mixed_queue_across_segments(rule, blocks):
-    # few warps, each over many tiles: FP64-class pairs queued in one
-    # segment are solved in a later one and added to the earlier segment's
-    # partials (in queue order where two meet the same element)
+def test_mixed_queue_across_segments(rule, blocks, guess):
+    # few blocks, each over many windows and groups: FP64-class pairs queued
+    # across the tiles of a window are solved together and added in queue
+    # order; with the seed they start from a single-precision solve
     s = ics.bh_cluster(2048, seed=11)
-    with mixed(mixed_rule=rule, guess=sk.GUESS_TAYLOR, pair_mode=sk.PAIRS_SYMMETRIC,
+    with mixed(mixed_rule=rule, guess=guess, pair_mode=sk.PAIRS_SYMMETRIC,
                grid_blocks=blocks):
         r, v, st = step_gpu(s, 2)
         r2, v2, _ = step_gpu(s, 2)
@@ -176,11 +177,13 @@ def test_mixed_queue_across_segments(rule, blocks):
     np.testing.assert_array_equal(v, v2)
 
 
-@pytest.mark.parametrize("blocks", [1, 5])
-def test_mixed_all_fp64_queue_across_segments_is_fp64_exact(blocks):
-    # every pair through the FP64 queue, whose entries cross segment ends
+@pytest.mark.parametrize("guess", [sk.GUESS_STANDARD, sk.GUESS_FP32], ids=["standard", "seed"])
+@pytest.mark.parametrize("blocks", [1, 5, 0])
+def test_mixed_all_fp64_queue_across_segments_is_fp64_exact(blocks, guess):
+    # every pair through the FP64 queue, whose entries span the tiles of a
+    # window; the FP64 solves match the oracle to the FP64 bound
     s = ics.random_cluster(700, seed=12, mass_spread=2.0)
-    with mixed(mixed_r_min=1e6, pair_mode=sk.PAIRS_SYMMETRIC, grid_blocks=blocks):
+    with mixed(mixed_r_min=1e6, pair_mode=sk.PAIRS_SYMMETRIC, grid_blocks=blocks, guess=guess):
         r, v, st = step_gpu(s, 2)
     assert st["fp32_pairs"] == 0
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)

@@ -7,7 +7,8 @@ scale 1, circular velocities, dt = 2^-10), judged against the FP64 oracle.
   single-precision decision's rounding band of a threshold.
 * One step, sampled: 48 particles (the black hole, the stars nearest to it,
   the rest spread over the cluster) against oracle.step_sample, within the
-  mixed form's per-step bound, under both class rules.
+  mixed form's per-step bound, under both class rules (the configuration
+  the benchmark times: FP64-class pairs seeded by a single-precision solve).
 * The whole run of 256 steps against the oracle's cached run
   (tests/golden/bh16384_oracle_run.json, written by
   tests/golden/make_bh16384_oracle_run.py): positions and velocities of the
@@ -109,7 +110,7 @@ def test_bh16384_classes_match_oracle(system, rule):
 def test_bh16384_mixed_step_sampled_against_oracle(system, rule):
     s = system
     idx = sample48(s)
-    r, v, _, st = run_gpu(s, 1, precision=sk.PREC_MIXED, mixed_rule=rule)
+    r, v, _, st = run_gpu(s, 1, precision=sk.PREC_MIXED, mixed_rule=rule, guess=sk.GUESS_FP32)
     rc, rr, vr = oracle.step_sample(s.m, s.r, s.v, s.dt, idx, 2, nthreads=NCPU)
     assert rc == oracle.OK
     R, V = scales(s)
@@ -131,8 +132,10 @@ def golden(system):
 
 
 @pytest.mark.parametrize("form,opts,bound,ebound", [
-    ("mixed-literal", dict(precision=sk.PREC_MIXED, mixed_rule=0), 256 * STEP_BOUND, 1e-8),
-    ("mixed-hyp", dict(precision=sk.PREC_MIXED, mixed_rule=1), 256 * STEP_BOUND, 1e-8),
+    ("mixed-literal", dict(precision=sk.PREC_MIXED, mixed_rule=0, guess=sk.GUESS_FP32),
+     256 * STEP_BOUND, 1e-8),
+    ("mixed-hyp", dict(precision=sk.PREC_MIXED, mixed_rule=1, guess=sk.GUESS_FP32),
+     256 * STEP_BOUND, 1e-8),
     ("fp64", dict(guess=sk.GUESS_FP32), 256 * 1e-12, 1e-12),
 ], ids=["mixed-literal", "mixed-hyp", "fp64"])
 def test_bh16384_256_steps_against_cached_oracle_run(system, golden, form, opts, bound, ebound):

@@ -464,3 +464,70 @@ def test_headline_evolve_32_steps_matches_oracle_and_single_steps():
     assert er <= 32 * TOL and ev <= 32 * TOL
     np.testing.assert_array_equal(r, r1)
     np.testing.assert_array_equal(v, v1)
+
+
+# --- the row-group kernel (the default from 8192 particles), forced on small systems ---
+
+@pytest.mark.parametrize("guess", [sk.GUESS_STANDARD, sk.GUESS_TAYLOR, sk.GUESS_FP32])
+@pytest.mark.parametrize("order", [2, 1, -1])
+@pytest.mark.parametrize("name,s", SMALL, ids=[n for n, _ in SMALL])
+def test_row_group_step_matches_oracle(name, s, order, guess):
+    with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=guess,
+                    flags=sk.FLAG_STATS | sk.FLAG_GROUPS | sk.FLAG_NO_SMALL):
+        r, v = gpu_step(s, s.dt, order)
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, order, nthreads=NCPU)
+    er, ev = rel_err(r, v, rr, vr)
+    assert er <= TOL and ev <= TOL, (er, ev)
+
+
+@pytest.mark.parametrize("blocks", [0, 1, 3, 7, 143, 144, 5000])
+def test_row_group_grid_shapes_agree_with_oracle(blocks):
+    # any grid: a block's phase range may start or end inside a group, and a
+    # group's row sums then come in several pieces (1024 particles: 8 groups,
+    # 144 phases)
+    s = ics.plummer(1024, seed=0)
+    with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=sk.GUESS_FP32, grid_blocks=blocks,
+                    flags=sk.FLAG_STATS | sk.FLAG_GROUPS):
+        sk.get_stats(reset=True)
+        r, v = gpu_step(s, s.dt, 2)
+        st = sk.get_stats(reset=True)
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
+    er, ev = rel_err(r, v, rr, vr)
+    assert er <= TOL and ev <= TOL, (er, ev)
+    assert st["carries"] == st["solves"]
+
+
+def test_row_group_and_tile_kernels_agree_and_are_deterministic():
+    # the two symmetric kernels differ only in summation order; each repeats
+    # its own result bit for bit
+    s = ics.random_cluster(3001, seed=4, mass_spread=2.0)
+    out = {}
+    for name, flag in (("tiles", sk.FLAG_TILES), ("groups", sk.FLAG_GROUPS)):
+        with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=sk.GUESS_FP32,
+                        flags=sk.FLAG_STATS | flag):
+            out[name] = gpu_step(s, s.dt, 2)
+            again = gpu_step(s, s.dt, 2)
+        np.testing.assert_array_equal(out[name][0], again[0])
+        np.testing.assert_array_equal(out[name][1], again[1])
+    er, ev = rel_err(*out["groups"], *out["tiles"])
+    assert er <= TOL and ev <= TOL, (er, ev)
+
+
+def test_row_group_evolve_matches_single_steps():
+    # calls of several steps: each apply kernel drifts for the next step, and
+    # the next row-group pair kernel starts only after it completes
+    s = ics.plummer(2048, seed=1)
+    with configured(guess=sk.GUESS_FP32, pair_mode=sk.PAIRS_SYMMETRIC,
+                    flags=sk.FLAG_STATS | sk.FLAG_GROUPS):
+        st = dev(s.soa())
+        m = dev(s.m)
+        sk.evolve(st, m, s.dt, 2, 8)
+        st1 = dev(s.soa())
+        for _ in range(8):
+            sk.step(st1, m, s.dt, 2)
+        sk.check()
+        np.testing.assert_array_equal(st.cpu().numpy(), st1.cpu().numpy())
+    rc, rr, vr = oracle.evolve(s.m, s.r, s.v, s.dt, 8, 2, nthreads=NCPU)
+    r, v = ics.from_soa(st.cpu().numpy())
+    er, ev = rel_err(r, v, rr, vr)
+    assert er <= 8 * TOL and ev <= 8 * TOL, (er, ev)
