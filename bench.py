@@ -612,8 +612,12 @@ def _roofline(workload, form, pairs, guess, n, small, m):
         peak, pipe, src = FP32_PEAK_GFLOPS / 1e3, "fp32", fp32_peak_src + "; flops counted by hand"
         kname = "pair_step_sym_mixed"
     elif form == "mixed" and pairs == "symmetric":
-        # mostly FP64-class pairs (through the FP64 queue): their FP64 solves
-        flops = (1.0 - share) * (C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP + C_SYM)
+        # mostly FP64-class pairs (through the FP64 queue): their FP64 solves,
+        # counted as in the symmetric FP64 kernel (single-precision seed and
+        # Taylor carry with guess fp32)
+        flops = (1.0 - share) * (C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP +
+                                 carried * (C_STEP + C_CARRY) + C_SYM -
+                                 (C_SEED_SAVED if guess == "fp32" else 0))
         peak, pipe, src = FP64_PEAK_GFLOPS / 1e3, "fp64", fp64_peak_src
         kname = "pair_step_sym_mixed"
     elif form == "mixed":
@@ -856,9 +860,9 @@ def main():
         V = lambda *a, **k: _variant(args, sk, s, device, stream, flush, per_call, small,  # noqa
                                      *a, **k)
         variants = {
-            "mixed_literal": V("mixed", "symmetric", "taylor", "literal",
+            "mixed_literal": V("mixed", "symmetric", "fp32", "literal",
                                "the class rule as stated for this workload"),
-            "mixed_hyp": V("mixed", "symmetric", "taylor", "hyp",
+            "mixed_hyp": V("mixed", "symmetric", "fp32", "hyp",
                            "the class rule with strong hyperbolae (e > 10) also in FP32"),
             "fp64_learned_guess": V("fp64", "symmetric", "learned",
                                     note="FP64 form, second-order guess refined by the"
