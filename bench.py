@@ -209,10 +209,10 @@ class ClockSampler:
 
 
 # the source file of each profiled kernel
-KERNEL_SOURCES = {"pair_step_sym": "step_sym.cu", "pair_step_fp64": "step_fp64.cu",
-                  "pair_step_sym_df64": "step_df64.cu", "pair_step_sym_mixed": "step_mixed.cu",
-                  "pair_step_mixed": "step_mixed.cu", "small": "step_small.cu",
-                  "batched": "step_batched.cu"}
+KERNEL_SOURCES = {"pair_step_sym": "step_sym.cu", "pair_step_grp": "step_grp.cu",
+                  "pair_step_fp64": "step_fp64.cu", "pair_step_sym_df64": "step_df64.cu",
+                  "pair_step_grp_mixed": "step_mixed.cu", "pair_step_mixed": "step_mixed.cu",
+                  "small": "step_small.cu", "batched": "step_batched.cu"}
 
 
 def _kernel_sources_hash(kernel: str = "pair_step_sym") -> str:
@@ -610,7 +610,7 @@ def _roofline(workload, form, pairs, guess, n, small, m):
         # single-precision iterations per solve
         flops = share * (C_MIX32_FIX + kbar * C_MIX32_ITER)
         peak, pipe, src = FP32_PEAK_GFLOPS / 1e3, "fp32", fp32_peak_src + "; flops counted by hand"
-        kname = "pair_step_sym_mixed"
+        kname = "pair_step_grp_mixed"
     elif form == "mixed" and pairs == "symmetric":
         # mostly FP64-class pairs (through the FP64 queue): their FP64 solves,
         # counted as in the symmetric FP64 kernel (single-precision seed and
@@ -619,7 +619,7 @@ def _roofline(workload, form, pairs, guess, n, small, m):
                                  carried * (C_STEP + C_CARRY) + C_SYM -
                                  (C_SEED_SAVED if guess == "fp32" else 0))
         peak, pipe, src = FP64_PEAK_GFLOPS / 1e3, "fp64", fp64_peak_src
-        kname = "pair_step_sym_mixed"
+        kname = "pair_step_grp_mixed"
     elif form == "mixed":
         # FP64 flops per ordered pair: the FP64 accumulation (6 FMA) of an
         # FP32-class pair, the full FP64 solve of the others
