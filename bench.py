@@ -612,14 +612,15 @@ def _roofline(workload, form, pairs, guess, n, small, m):
         peak, pipe, src = FP32_PEAK_GFLOPS / 1e3, "fp32", fp32_peak_src + "; flops counted by hand"
         kname = "pair_step_grp_mixed"
     elif form == "mixed" and pairs == "symmetric":
-        # mostly FP64-class pairs (through the FP64 queue): their FP64 solves,
-        # counted as in the symmetric FP64 kernel (single-precision seed and
-        # Taylor carry with guess fp32)
+        # mostly FP64-class pairs (the literal rule: the FP64 tile kernel with
+        # an inline class test): their FP64 solves, counted as in the
+        # symmetric FP64 kernel (single-precision seed and Taylor carry with
+        # guess fp32)
         flops = (1.0 - share) * (C_FIX + kbar * C_EVAL + (kbar - 1.0) * C_STEP +
                                  carried * (C_STEP + C_CARRY) + C_SYM -
                                  (C_SEED_SAVED if guess == "fp32" else 0))
         peak, pipe, src = FP64_PEAK_GFLOPS / 1e3, "fp64", fp64_peak_src
-        kname = "pair_step_grp_mixed"
+        kname = "pair_step_sym"
     elif form == "mixed":
         # FP64 flops per ordered pair: the FP64 accumulation (6 FMA) of an
         # FP32-class pair, the full FP64 solve of the others

@@ -292,6 +292,17 @@ double group_partial_bytes(int64_t n, int G)
 // flags force either kernel.
 constexpr double kTileMaxBytes = 4.0 * 1024 * 1024 * 1024;
 
+// The mixed form runs in the FP64 tile kernel with an inline class test
+// (step_sym.cu) when its rule admits few pairs, as the literal rule does in
+// clusters (the black-hole cluster: 0.01 % of the pairs), and in the
+// row-group mixed kernel (step_mixed.cu) otherwise; the flags force either.
+bool mixed_tiles(int64_t n)
+{
+    if (g.cfg.flags & SAKURA_FLAG_TILES) return true;
+    if (g.cfg.flags & SAKURA_FLAG_GROUPS) return false;
+    return g.cfg.mixed_rule == SAKURA_MIXED_RULE_LITERAL && tile_partial_bytes(n) <= kTileMaxBytes;
+}
+
 bool fp64_groups(int64_t n)
 {
     if (g.cfg.flags & SAKURA_FLAG_GROUPS) return true;
@@ -378,16 +389,16 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
                     int order, bool df64, bool mixed, bool prepped = false, bool fuse = false,
                     double next_drift = 0.0)
 {
-    if (mixed) return step_device_mixed_grp(src, dst, masses, n, dt, order);
+    if (mixed && !mixed_tiles(n)) return step_device_mixed_grp(src, dst, masses, n, dt, order);
     if (!df64 && fp64_groups(n))
         return step_device_fp64_grp(src, dst, masses, n, dt, order, prepped, fuse, next_drift);
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
-    const bool learned = !df64 && g.cfg.guess == SAKURA_GUESS_LEARNED;
+    const bool learned = !df64 && !mixed && g.cfg.guess == SAKURA_GUESS_LEARNED;
     const bool seed = !df64 && g.cfg.guess == SAKURA_GUESS_FP32;
     const int64_t nb = (n + 31) / 32;
     const int64_t tiles = nb * (nb + 1) / 2;
     const int bps = df64 ? sakura::pair_step_df64_blocks_per_sm(stats)
-                         : sakura::pair_step_sym_blocks_per_sm(stats, learned, seed);
+                         : sakura::pair_step_sym_blocks_per_sm(stats, learned, seed, mixed);
     // contiguous tile-step ranges for W <= T warps (step_common.cuh)
     const int64_t T = tiles * 32;
     int64_t blocks = g.cfg.grid_blocks > 0 ? g.cfg.grid_blocks : (int64_t)g.sm_count * bps;
@@ -404,7 +415,7 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
     double *X = (double *)g.partial.ptr;
     double *partial = X + 7 * n;
     float *X3 = (float *)(partial + nslots * 6 * n);
-    float *X32 = seed ? X3 : nullptr;
+    float *X32 = (seed || mixed) ? X3 : nullptr;
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
     if (df64)
@@ -429,6 +440,11 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
     a.mlp = learned ? (const sakura::MlpWeights *)g.mlp.ptr : nullptr;
     a.status = g.d_status;
     a.stats = g.d_stats;
+    if (mixed) {
+        a.mixed = seed ? 2 : 1;
+        a.rule = class_rule(a.pre * dt);
+        a.post32 = (float)a.post;
+    }
     const bool timing = (g.cfg.flags & SAKURA_FLAG_TIMING) != 0;
     std::pair<cudaEvent_t, cudaEvent_t> tm{nullptr, nullptr};
     if (timing) {
@@ -456,7 +472,7 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
                                   g.stream);
     else
         sakura::launch_apply_sym(dst, X, X32, partial, n, Smax, W, T, post_drift,
-                                 fuse, next_drift, g.d_status, g.stream);
+                                 fuse && !mixed, next_drift, g.d_status, g.stream);
     rc = launch_error();
     if (rc) return rc;
     g.steps += 1;
@@ -483,7 +499,7 @@ bool sym_path(int64_t n)
     if (g.cfg.pair_mode != SAKURA_PAIRS_SYMMETRIC || n < 2) return false;
     if (g.cfg.precision == SAKURA_PREC_DF64) return tile_partial_bytes(n) <= kSymMaxBytes;
     if (g.cfg.precision == SAKURA_PREC_MIXED)
-        return group_partial_bytes(n, sakura::kMixedGrpWarps) <= kSymMaxBytes;
+        return mixed_tiles(n) || group_partial_bytes(n, sakura::kMixedGrpWarps) <= kSymMaxBytes;
     return (fp64_groups(n) ? group_partial_bytes(n, sakura::kFp64GrpWarps)
                            : tile_partial_bytes(n)) <= kSymMaxBytes;
 }

@@ -65,6 +65,12 @@ struct StepArgs {
     float ptau32, t32;     // (float)(pre tau), (float)tau for the seed
     unsigned *status;
     unsigned long long *stats;
+    // mixed form in the FP64 tile kernel (mixed = 1; 2 with the FP64-class
+    // pairs seeded): pairs the class rule admits are solved in FP32 (t32,
+    // post32) and accumulated in FP64
+    int mixed;
+    ClassRule rule;
+    float post32;
 };
 
 // extra arguments of the mixed-precision pair kernel
@@ -206,7 +212,8 @@ void launch_mlp_pack(const float *blob, MlpWeights *W, cudaStream_t s);
 void launch_mlp_eval(const MlpWeights *W, const float *feat, int64_t count, float *out,
                      cudaStream_t s);
 // symmetric (Newton's third law) pair kernel: items = tiles * S
-int pair_step_sym_blocks_per_sm(bool stats, bool learned, bool seed = false);
+int pair_step_sym_blocks_per_sm(bool stats, bool learned, bool seed = false,
+                                bool mixed = false);
 void launch_pair_step_sym(const StepArgs &a, int Smax, int64_t T, int blocks, bool stats,
                           cudaStream_t s);
 // fuse: also apply the next sub-step's drift next_drift and write its

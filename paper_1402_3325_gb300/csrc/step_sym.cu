@@ -31,8 +31,13 @@
 
 namespace sakura {
 
-template <bool STATS, bool LEARNED, bool SEED>
-__global__ void __launch_bounds__(128, (LEARNED || SEED) ? 2 : 4)
+// MIXED: the mixed form for class rules that admit few pairs (the literal
+// rule): each pair's class is decided as in the row-group mixed kernel
+// (kepler_fp32.cuh); a pair the rule admits is solved in FP32 and its
+// increments, converted to double, are accumulated in FP64 with the rest;
+// every other pair takes the FP64 solve (seeded with SEED).
+template <bool STATS, bool LEARNED, bool SEED, bool MIXED>
+__global__ void __launch_bounds__(128, (LEARNED || SEED || MIXED) ? 2 : 4)
     pair_step_sym_kernel(StepArgs a, int Smax, int64_t T)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -49,7 +54,7 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED) ? 2 : 4)
     const double *X = a.X;
     const KeplerParams kp{a.tol, a.max_iter, a.bisection};
     unsigned status = 0;
-    long long it_sum = 0, slots = 0, fallbacks = 0, carries = 0;
+    long long it_sum = 0, slots = 0, fallbacks = 0, carries = 0, n32 = 0;
     int it_max = 0;
     const float *X32 = a.X32;
 
@@ -76,7 +81,7 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED) ? 2 : 4)
             mi = X[6 * n + i];
         }
         float hi_i[3] = {0, 0, 0}, lo_i[3] = {0, 0, 0}, v_i[3] = {0, 0, 0}, m32i = 0.0f;
-        if (SEED && irow) {
+        if ((SEED || MIXED) && irow) {
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 hi_i[q] = X32[q * n + i];
@@ -92,12 +97,30 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED) ? 2 : 4)
             const bool valid = irow && j < n && (!diag || c != lane);
             PairSolve p;
             double mj = 0.0;
+            bool lane32 = false;  // MIXED: solved in FP32
+            float d32[6];
             if (valid) {
                 mj = X[6 * n + j];
                 pair_setup(p, a.tau, mi + mj, xi - X[j], yi - X[n + j], zi - X[2 * n + j],
                            vxi - X[3 * n + j], vyi - X[4 * n + j], vzi - X[5 * n + j], a.pre,
                            LEARNED ? 2 : (SEED ? -1 : a.guess));
-                if (SEED) {
+                if (MIXED) {
+                    float hi_j[3], lo_j[3], v_j[3];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        hi_j[q] = X32[q * n + j];
+                        lo_j[q] = X32[(3 + q) * n + j];
+                        v_j[q] = X32[(6 + q) * n + j];
+                    }
+                    Pair32 pr;
+                    pair32_setup(pr, hi_i, lo_i, v_i, m32i, hi_j, lo_j, v_j, X32[9 * n + j],
+                                 a.rule);
+                    if (pr.fp32) {
+                        int it32 = 0;
+                        lane32 = pair32_solve(pr, a.t32, a.post32, a.guess, d32, it32);
+                    }
+                }
+                if (SEED && !lane32) {
                     // single-precision seed: the root of the FP32 solve of the
                     // same pair (unless t was reduced modulo the period)
                     float dr[3], dv[3];
@@ -125,10 +148,15 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED) ? 2 : 4)
                 p.iters = 0;
                 p.status = 0;
             }
+            if (lane32) p.done = true;
             if (LEARNED) learned_guess_warp(p, valid, *mlpW, mlpStage + wib * 32 * 16);
             double d[6];
             int iters = 0, fb = 0;
-            fp64_solve_warp<SEED>(p, valid, a.tau, a.post * a.tau, kp, d, iters, fb);
+            fp64_solve_warp<SEED>(p, valid && !lane32, a.tau, a.post * a.tau, kp, d, iters, fb);
+            if (MIXED && lane32) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) d[q] = (double)d32[q];
+            }
             if (valid) {
 #pragma unroll
                 for (int q = 0; q < 6; ++q) {
@@ -139,6 +167,7 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED) ? 2 : 4)
             }
             if (STATS) {
                 carries += (valid && p.carried) ? 1 : 0;
+                n32 += lane32 ? (diag ? 1 : 2) : 0;  // in ordered pairs
                 it_sum += iters;
                 fallbacks += fb;
                 it_max = max(it_max, iters);
@@ -183,6 +212,11 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED) ? 2 : 4)
             atomicAdd(&a.stats[kStatFallbacks], (unsigned long long)s3);
             atomicAdd(&a.stats[kStatCarries], (unsigned long long)s4);
             atomicMax(&a.stats[kStatMaxIters], (unsigned long long)mx);
+        }
+        if (MIXED) {
+            long long s5 = n32;
+            for (int o = 16; o > 0; o >>= 1) s5 += __shfl_xor_sync(0xffffffffu, s5, o);
+            if (lane == 0) atomicAdd(&a.stats[kStatFp32Pairs], (unsigned long long)s5);
         }
     }
 }
@@ -268,34 +302,41 @@ __global__ void __launch_bounds__(32 * kApplyWarps)
 
 namespace {
 
-const void *sym_kernel(bool stats, bool learned, bool seed)
+const void *sym_kernel(bool stats, bool learned, bool seed, bool mixed)
 {
+    if (mixed) {
+        if (seed)
+            return stats ? (const void *)pair_step_sym_kernel<true, false, true, true>
+                         : (const void *)pair_step_sym_kernel<false, false, true, true>;
+        return stats ? (const void *)pair_step_sym_kernel<true, false, false, true>
+                     : (const void *)pair_step_sym_kernel<false, false, false, true>;
+    }
     if (learned)
-        return stats ? (const void *)pair_step_sym_kernel<true, true, false>
-                     : (const void *)pair_step_sym_kernel<false, true, false>;
+        return stats ? (const void *)pair_step_sym_kernel<true, true, false, false>
+                     : (const void *)pair_step_sym_kernel<false, true, false, false>;
     if (seed)
-        return stats ? (const void *)pair_step_sym_kernel<true, false, true>
-                     : (const void *)pair_step_sym_kernel<false, false, true>;
-    return stats ? (const void *)pair_step_sym_kernel<true, false, false>
-                 : (const void *)pair_step_sym_kernel<false, false, false>;
+        return stats ? (const void *)pair_step_sym_kernel<true, false, true, false>
+                     : (const void *)pair_step_sym_kernel<false, false, true, false>;
+    return stats ? (const void *)pair_step_sym_kernel<true, false, false, false>
+                 : (const void *)pair_step_sym_kernel<false, false, false, false>;
 }
 
 size_t sym_smem(bool learned) { return learned ? sizeof(MlpWeights) + 4 * 32 * 16 * 2 : 0; }
 
 }  // namespace
 
-int pair_step_sym_blocks_per_sm(bool stats, bool learned, bool seed)
+int pair_step_sym_blocks_per_sm(bool stats, bool learned, bool seed, bool mixed)
 {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sym_kernel(stats, learned, seed), 128,
-                                                      sym_smem(learned)) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, sym_kernel(stats, learned, seed, mixed),
+                                                      128, sym_smem(learned)) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
     // the seeded kernel runs fastest with 8 warps per SM (measured on GB300:
     // 120.8 us at 2 blocks per SM against 123.1 at 3 and 139 at 1, Plummer
     // N = 1024); the others with as many as fit
-    if (seed && b > 2) b = 2;
+    if ((seed || mixed) && b > 2) b = 2;
     return b > 0 ? b : 1;
 }
 
@@ -303,12 +344,13 @@ void launch_pair_step_sym(const StepArgs &a, int Smax, int64_t T, int blocks, bo
                           cudaStream_t s)
 {
     const bool learned = a.mlp != nullptr;
-    const bool seed = !learned && a.X32 != nullptr;
+    const bool mixed = a.mixed != 0;
+    const bool seed = !learned && a.X32 != nullptr && (!mixed || a.mixed == 2);
     int Sv = Smax;
     int64_t it = T;
     void *args[] = {(void *)&a, (void *)&Sv, (void *)&it};
-    launch_pdl(sym_kernel(stats, learned, seed), dim3(blocks), dim3(128), args, sym_smem(learned),
-               s);
+    launch_pdl(sym_kernel(stats, learned, seed, mixed), dim3(blocks), dim3(128), args,
+               sym_smem(learned), s);
 }
 
 void launch_apply_sym(double *state, double *X, float *X32, const double *partial, int64_t n,

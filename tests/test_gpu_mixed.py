@@ -189,3 +189,29 @@ def test_mixed_all_fp64_queue_across_segments_is_fp64_exact(blocks, guess):
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
     er, ev = rel_err(r, v, rr, vr)
     assert er <= 1e-12 and ev <= 1e-12, (er, ev)
+
+
+@pytest.mark.parametrize("guess", [sk.GUESS_TAYLOR, sk.GUESS_FP32], ids=["taylor", "seed"])
+@pytest.mark.parametrize("kernel", [sk.FLAG_TILES, sk.FLAG_GROUPS], ids=["tiles", "groups"])
+@pytest.mark.parametrize("rule", [0, 1], ids=["literal", "hyp"])
+def test_mixed_tile_and_row_group_kernels(rule, kernel, guess):
+    # the FP64 tile kernel with an inline class test (the literal rule's
+    # default) and the row-group mixed kernel (the hyperbolic rule's), each
+    # forced under both rules: same classes, oracle within the step bound,
+    # repeat runs bit-identical
+    s = ics.bh_cluster(2048, seed=3)
+    sk.init(0, flags=sk.FLAG_STATS | kernel, precision=sk.PREC_MIXED, mixed_rule=rule,
+            guess=guess)
+    try:
+        got = classes_checked(s, rule, 2)
+        r, v, st = step_gpu(s, 2)
+        r2, v2, _ = step_gpu(s, 2)
+    finally:
+        sk.init(0, flags=sk.FLAG_STATS)
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
+    er, ev = rel_err(r, v, rr, vr)
+    print(f"rule {rule} kernel {kernel}: fp32 pairs {st['fp32_pairs']}, err r {er:.2e} v {ev:.2e}")
+    assert st["fp32_pairs"] == int(got.sum())
+    assert er <= STEP_BOUND and ev <= STEP_BOUND
+    np.testing.assert_array_equal(r, r2)
+    np.testing.assert_array_equal(v, v2)
