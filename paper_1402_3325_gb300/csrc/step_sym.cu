@@ -101,9 +101,6 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED || MIXED) ? 2 : 4)
             float d32[6];
             if (valid) {
                 mj = X[6 * n + j];
-                pair_setup(p, a.tau, mi + mj, xi - X[j], yi - X[n + j], zi - X[2 * n + j],
-                           vxi - X[3 * n + j], vyi - X[4 * n + j], vzi - X[5 * n + j], a.pre,
-                           LEARNED ? 2 : (SEED ? -1 : a.guess));
                 if (MIXED) {
                     float hi_j[3], lo_j[3], v_j[3];
 #pragma unroll
@@ -120,6 +117,10 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED || MIXED) ? 2 : 4)
                         lane32 = pair32_solve(pr, a.t32, a.post32, a.guess, d32, it32);
                     }
                 }
+                if (!lane32)
+                    pair_setup(p, a.tau, mi + mj, xi - X[j], yi - X[n + j], zi - X[2 * n + j],
+                               vxi - X[3 * n + j], vyi - X[4 * n + j], vzi - X[5 * n + j],
+                               a.pre, LEARNED ? 2 : (SEED ? -1 : a.guess));
                 if (SEED && !lane32) {
                     // single-precision seed: the root of the FP32 solve of the
                     // same pair (unless t was reduced modulo the period)
@@ -142,20 +143,21 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED || MIXED) ? 2 : 4)
                         if (magbits(cq) < 0x3fe0000000000000LL) p.s = fma(-cq, p.s, p.s);
                     }
                 }
-            } else {
+            }
+            if (!valid || lane32) {
                 p.done = true;
                 p.beta = p.s = 0.0;
                 p.iters = 0;
                 p.status = 0;
             }
-            if (lane32) p.done = true;
             if (LEARNED) learned_guess_warp(p, valid, *mlpW, mlpStage + wib * 32 * 16);
             double d[6];
             int iters = 0, fb = 0;
             fp64_solve_warp<SEED>(p, valid && !lane32, a.tau, a.post * a.tau, kp, d, iters, fb);
             if (MIXED && lane32) {
+                // exact conversions on the integer pipe
 #pragma unroll
-                for (int q = 0; q < 6; ++q) d[q] = (double)d32[q];
+                for (int q = 0; q < 6; ++q) d[q] = f2d(d32[q]);
             }
             if (valid) {
 #pragma unroll
