@@ -205,3 +205,27 @@ def test_learned_guess_in_the_row_group_kernel(trained, order):
     er = np.linalg.norm(r - rr, axis=1) / np.maximum(np.linalg.norm(rr, axis=1), R)
     ev = np.linalg.norm(v - vr, axis=1) / np.maximum(np.linalg.norm(vr, axis=1), V)
     assert er.max() <= TOL and ev.max() <= TOL
+
+
+def test_learned_guess_against_the_single_precision_seed(trained):
+    # The shipped FP64 default starts each FP64 iteration from the root of a
+    # single-precision solve of the pair (within ~1e-7 of the FP64 root) and
+    # finishes with one FP64 evaluation and the Taylor carry: one evaluation
+    # is the least the convergence test allows.  The network's guess carries
+    # its BF16 output error (~1e-3 of the correction), too far for the carry,
+    # so every pair it guesses takes a second evaluation.  The network can
+    # therefore beat the method without a seed (t / r0, asserted above) but
+    # not the seeded form; this records the evaluation counts that say why.
+    blob, _ = trained
+    system = ics.plummer_binaries(4096, seed=11)
+    seed, _, _ = _stats_for(system, sk.GUESS_FP32)
+    lrn, _, _ = _stats_for(system, sk.GUESS_LEARNED, blob)
+    std, _, _ = _stats_for(system, sk.GUESS_STANDARD)
+    m_seed = seed["iters"] / seed["solves"]
+    m_lrn = lrn["iters"] / lrn["solves"]
+    m_std = std["iters"] / std["solves"]
+    print(f"FP64 evaluations per solve: seed {m_seed:.4f} (carried"
+          f" {seed['carries'] / seed['solves']:.4f}), learned {m_lrn:.4f}, standard {m_std:.4f}")
+    assert m_seed < 1.01 and seed["carries"] >= 0.99 * seed["solves"]
+    assert m_lrn > 1.99
+    assert m_seed < m_lrn < m_std
