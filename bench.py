@@ -550,7 +550,8 @@ def _pair_kernel_ms(args, sk, s, state, mass, device, stream, flush, guess, opts
     the library around each pair-kernel launch on its stream (for the
     single-block kernel of small systems: the launch that runs the call)."""
     import torch
-    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_TIMING, guess=guess, **opts)
+    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_TIMING | EXTRA_FLAGS,
+            guess=guess, **opts)
     sk.get_stats(reset=True)
     torch.cuda.synchronize(device)
     for k in range(args.steps // per_call):
@@ -571,6 +572,10 @@ GUESSES = ("standard", "taylor", "learned", "fp32")
 def _guess_code(sk, name):
     return {"taylor": sk.GUESS_TAYLOR, "standard": sk.GUESS_STANDARD,
             "learned": sk.GUESS_LEARNED, "fp32": sk.GUESS_FP32}[name]
+
+
+KERNEL_FLAG = {"auto": 0, "tiles": 32, "groups": 64}  # SAKURA_FLAG_TILES / _GROUPS
+EXTRA_FLAGS = 0  # library flags of --kernel, added to every measured configuration
 
 
 def _form_options(sk, form, pairs, mixed_rule):
@@ -635,7 +640,9 @@ def _roofline(workload, form, pairs, guess, n, small, m):
                  (C_SYM if symmetric else 0) -
                  (C_SEED_SAVED if (guess == "fp32" and symmetric) else 0))
         peak, pipe, src = FP64_PEAK_GFLOPS / 1e3, "fp64", fp64_peak_src
-        kname = "small" if small else ("pair_step_sym" if symmetric else "pair_step_fp64")
+        kname = "small" if small else (
+            ("pair_step_grp" if EXTRA_FLAGS == KERNEL_FLAG["groups"] else "pair_step_sym")
+            if symmetric else "pair_step_fp64")
     solves = n * (n - 1) * m["solves_per_pair"]
     pair_ms = m["pair_kernel_ms"]
     achieved = solves * flops / (pair_ms * 1e-3) / 1e12 if flops and pair_ms > 0 else None
@@ -665,7 +672,8 @@ def _measure(args, sk, s, device, stream, flush, guess, opts, per_call, clocks=N
     state0 = torch.tensor(s.soa(), device=device)
     state = state0.clone()
     gcode = _guess_code(sk, guess)
-    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_STATS, guess=gcode, **opts)
+    sk.init(device.index, stream=stream.cuda_stream, flags=sk.FLAG_STATS | EXTRA_FLAGS,
+            guess=gcode, **opts)
     sk.get_stats(reset=True)  # counters of earlier calls
     for _ in range(args.warmup):
         sk.step(state, mass, s.dt, 2)
@@ -680,7 +688,7 @@ def _measure(args, sk, s, device, stream, flush, guess, opts, per_call, clocks=N
          "fp32_pair_share": st["fp32_pairs"] / max(1, st["pairs"])}
     m["fp64_evals_per_fp64_pair"] = (float(st["iters"]) / max(
         1.0, st["solves"] * (1.0 - m["fp32_pair_share"])))
-    sk.init(device.index, stream=stream.cuda_stream, guess=gcode, **opts)
+    sk.init(device.index, stream=stream.cuda_stream, flags=EXTRA_FLAGS, guess=gcode, **opts)
     state.copy_(state0)
     E0 = sk.energy(state, mass)
     nt = args.steps // per_call
@@ -763,6 +771,9 @@ def main():
                          " the FP32 pipe (symmetric pairs)")
     ap.add_argument("--mixed-rule", default="hyp", choices=["literal", "hyp"],
                     help="literal: FP32 iff r > 0.1 and e < 0.9; hyp: ... or e > 10")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "tiles", "groups"],
+                    help="symmetric FP64 and mixed forms: the library's choice, or force the"
+                         " systolic-tile or the row-group kernel")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the other forms reported beside the FP64 headline")
     ap.add_argument("--steps-per-call", type=int, default=None,
@@ -781,6 +792,8 @@ def main():
     if args.steps is None:
         args.steps = _workload(args.workload, 0)[1]
     args.warmup = max(3, args.warmup)
+    global EXTRA_FLAGS
+    EXTRA_FLAGS = KERNEL_FLAG[args.kernel]
 
     if args.impl == "reference":
         return run_reference(args, rank)
@@ -838,8 +851,8 @@ def main():
         host_mass = torch.empty((n,), dtype=torch.float64).pin_memory().numpy()
         host_state[...] = s.soa()
         host_mass[...] = s.m
-        sk.init(device.index, stream=stream.cuda_stream, guess=_guess_code(sk, args.guess),
-                **opts)
+        sk.init(device.index, stream=stream.cuda_stream, flags=EXTRA_FLAGS,
+                guess=_guess_code(sk, args.guess), **opts)
         for _ in range(2):
             sk.evolve_host(host_state, host_mass, s.dt, 2, 1)
         host_state[...] = s.soa()
@@ -897,7 +910,7 @@ def main():
                       if args.form == "mixed" else "f64"),
             "data": "synthetic",
             "config": {"workload": desc, "n": n, "dt": s.dt, "order": 2, "form": args.form,
-                       "pairs": args.pairs,
+                       "pairs": args.pairs, "kernel_choice": args.kernel,
                        "kepler_guess": args.guess,
                        "fp32_pair_share": m["fp32_pair_share"],
                        "pairs_counted_per_step": n * n,
