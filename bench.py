@@ -281,9 +281,20 @@ def _cpu_baseline(s, dt, budget_s=10.0, max_steps=256, min_s=2.0):
             break
     what = (f"{steps} consecutive steps" if passes == 1 else
             f"{passes} passes of {max_steps} consecutive steps")
-    return {"value": s.n ** 2 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{what} of the same workload (N={s.n}) from its initial state,"
-                      f" OpenMP over i on {cores} threads, {el:.1f} s"}
+    out = {"value": s.n ** 2 * steps / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{what} of the same workload (N={s.n}) from its initial state,"
+                     f" OpenMP over i on {cores} threads, {el:.1f} s"}
+    # the same oracle on one core: rows of the first step (each summing over
+    # all n columns), about a second of work
+    import numpy as np
+    rows = max(1, min(s.n, int(4e6 // s.n)))
+    t1 = time.perf_counter()
+    oracle.step_sample(s.m, s.r, s.v, dt, np.arange(rows), 2, nthreads=1)
+    el1 = time.perf_counter() - t1
+    out["one_core"] = {"value": rows * s.n / el1, "unit": UNIT,
+                       "sample": f"{rows} rows of the first step (oracle.step_sample),"
+                                 f" {rows * s.n} ordered pairs, 1 thread, {el1:.2f} s"}
+    return out
 
 
 # the reference arm's steps on large workloads: this many rows of the
