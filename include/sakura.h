@@ -170,9 +170,14 @@ int sakura_set_stream(void *stream);
  * Kepler flow (Eq. 18) and its increments are summed mass-weighted into
  * particle i (Eq. 23).  With cfg.pair_mode = SAKURA_PAIRS_SYMMETRIC (the
  * default) each unordered pair is solved once, its two ordered increments
- * being exact negatives; the library scratch then grows to at most
- * 8 x 6 x 8 ceil(n/32) n bytes (12 MB at n = 1024, 400 MB at 16384), and
- * above 16 GB the ordered kernel is used.  Systems of 2 <= n <= 20 in the
+ * being exact negatives.  The symmetric FP64 step runs on systolic tiles,
+ * whose partial sums take up to 8 x 6 x 8 ceil(n/32) n bytes of library
+ * scratch (12 MB at n = 1024, 0.8 GB at 16384); beyond 4 GB of them it
+ * runs in row-group phases, whose partials take about n^2 / 2.7 bytes; the
+ * mixed form uses row groups under SAKURA_MIXED_RULE_HYP and the tile kernel
+ * with an inline class test under the literal rule (SAKURA_FLAG_TILES /
+ * SAKURA_FLAG_GROUPS force either kernel).  Where the symmetric scratch
+ * would pass 16 GB the ordered kernel is used.  Systems of 2 <= n <= 20 in the
  * FP64 form with symmetric pairs and a non-learned guess run in one launch
  * of a single-block kernel that keeps the system in shared memory and packs
  * the pairs densely over its lanes (no scratch; SAKURA_FLAG_NO_SMALL turns

@@ -40,7 +40,6 @@ constexpr int kFp32MaxIter = 12;
 struct Pair32 {
     float x0, y0, z0, vx, vy, vz;  // r0 (backward-drifted) and v0
     float r2, v2, eta, m;
-    float ir0;                      // 1 / |r0| (hardware reciprocal square root)
     bool fp32;                      // admitted by the FP32 class rule
 };
 
@@ -81,8 +80,7 @@ __device__ __forceinline__ void pair32_setup(Pair32 &p, const float hi_i[3], con
     p.eta = fmaf(x[0], u[0], fmaf(x[1], u[1], x[2] * u[2]));
     p.m = m_i + m_j;
     const float h2 = fmaf(p.r2, p.v2, -(p.eta * p.eta));
-    p.ir0 = rsqrtf(p.r2);
-    const float twoE = fmaf(-2.0f * p.m, p.ir0, p.v2);
+    const float twoE = fmaf(-2.0f * p.m, rsqrtf(p.r2), p.v2);
     const float lhs = twoE * h2;
     const float m2 = p.m * p.m;
     const bool far = p.r2 > cr.rmin2;
@@ -124,15 +122,12 @@ __device__ __forceinline__ Stumpff32 stumpff_fp32(float x)
 
 // FP32 Kepler solve and increments divided by m; returns false when the
 // iteration did not converge (the pair then goes to the FP64 solver).
-// guess: 0 = t/r0, 2 = second order; qtau = post * tau.  out[0..2] =
-// delta_r/m, out[3..5] = delta_v/m.  Where the Laguerre step's correction is
-// small (|q F''/F'| < 2^-8, q = F/F') the step is taken in Halley's form
-// q (1 + q F''/(2 F')), which agrees with it to O(q u^2) and needs no square
-// root or reciprocal; the iteration continues to the same stopping rule.
-__device__ __forceinline__ bool pair32_solve(const Pair32 &p, float tau, float qtau, int guess,
+// guess: 0 = t/r0, 2 = second order.  out[0..2] = delta_r/m,
+// out[3..5] = delta_v/m.
+__device__ __forceinline__ bool pair32_solve(const Pair32 &p, float tau, float post, int guess,
                                              float out[6], int &iters)
 {
-    const float ir0 = p.ir0;
+    const float ir0 = rsqrtf(p.r2);
     const float r0 = p.r2 * ir0;
     const float beta = fmaf(2.0f * p.m, ir0, -p.v2);
     const float zeta0 = fmaf(-beta, r0, p.m);
@@ -162,14 +157,9 @@ __device__ __forceinline__ bool pair32_solve(const Pair32 &p, float tau, float q
         ir = rcp_approx(Fp);
         const float q = F * ir;
         ++iters;
-        const float qh = q * Fpp * ir;  // = u / 1.25
-        float step;
-        if (fabsf(qh) < 0x1p-8f) {
-            step = fmaf(0.5f * q, qh, q);
-        } else {
-            const float den = 1.0f + 4.0f * fsqrt_approx(fabsf(1.0f - 1.25f * qh));
-            step = 5.0f * q * rcp_approx(den);
-        }
+        const float u = 1.25f * q * Fpp * ir;
+        const float den = 1.0f + 4.0f * fsqrt_approx(fabsf(1.0f - u));
+        const float step = 5.0f * q * rcp_approx(den);
         s = s - step;
         // a Laguerre step below 2^-11 of the scale: the root is reached to
         // single-precision round-off, so carry G1..G3 and F' = r to it by
@@ -196,6 +186,7 @@ __device__ __forceinline__ bool pair32_solve(const Pair32 &p, float tau, float q
     if (t != tau) gmt += (t - tau) / p.m;
     const float fd = -G1 * ir0 * ir;
     const float gdm1 = -G2 * ir;
+    const float qtau = post * tau;
     const float A = fmaf(-qtau, fd, fm1);
     const float B = fmaf(-qtau, gdm1, gmt);
     out[3] = fmaf(fd, p.x0, gdm1 * p.vx);

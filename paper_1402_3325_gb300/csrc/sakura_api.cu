@@ -248,7 +248,7 @@ int step_device_mixed_grp(const double *src, double *dst, const double *masses, 
     ma.X32 = X32;
     ma.rule = class_rule(a.pre * dt);
     ma.tau32 = (float)dt;
-    ma.qtau32 = (float)(a.post * dt);
+    ma.post32 = (float)a.post;
     const bool timing = (g.cfg.flags & SAKURA_FLAG_TIMING) != 0;
     std::pair<cudaEvent_t, cudaEvent_t> tm{nullptr, nullptr};
     if (timing) {
@@ -443,7 +443,7 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
     if (mixed) {
         a.mixed = seed ? 2 : 1;
         a.rule = class_rule(a.pre * dt);
-        a.qtau32 = (float)(a.post * dt);
+        a.post32 = (float)a.post;
     }
     const bool timing = (g.cfg.flags & SAKURA_FLAG_TIMING) != 0;
     std::pair<cudaEvent_t, cudaEvent_t> tm{nullptr, nullptr};
@@ -564,7 +564,7 @@ int step_device(const double *src, double *dst, const double *masses, int64_t n,
             ma.X32 = X32;
             ma.rule = class_rule(a.pre * dt);
             ma.tau32 = (float)dt;
-            ma.qtau32 = (float)(a.post * dt);
+            ma.post32 = (float)a.post;
             sakura::launch_pair_step_mixed(a, ma, p.blocks, stats, g.stream);
         } else {
             sakura::launch_pair_step_fp64(a, p.warps, p.blocks, stats, g.stream);

@@ -67,17 +67,17 @@ struct StepArgs {
     unsigned long long *stats;
     // mixed form in the FP64 tile kernel (mixed = 1; 2 with the FP64-class
     // pairs seeded): pairs the class rule admits are solved in FP32 (t32,
-    // qtau32 = (float)(post tau)) and accumulated in FP64
+    // post32) and accumulated in FP64
     int mixed;
     ClassRule rule;
-    float qtau32;
+    float post32;
 };
 
 // extra arguments of the mixed-precision pair kernel
 struct MixedArgs {
     const float *X32;     // [10][n] hi xyz, lo xyz, v xyz, m (floats)
     ClassRule rule;       // FP32 class rule (kepler_fp32.cuh)
-    float tau32, qtau32;  // tau and post tau in FP32
+    float tau32, post32;  // tau and the post-drift fraction in FP32
 };
 
 void launch_prep_mixed(const double *state, const double *mass, double *X, float *X32,

@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(WARPS * 32)
             if (p.fp32) {
                 float d[6];
                 int it32 = 0;
-                solved32 = pair32_solve(p, ma.tau32, ma.qtau32, a.guess, d, it32);
+                solved32 = pair32_solve(p, ma.tau32, ma.post32, a.guess, d, it32);
                 if (solved32) {
                     const double mj = X[6 * n + j];
 #pragma unroll
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
                     pair32_setup(pr, hi_i, lo_i, v_i, mfi, hi_j, lo_j, v_j, mfj, ma.rule);
                     if (pr.fp32) {
                         float d[6];
-                        solved32 = pair32_solve(pr, ma.tau32, ma.qtau32, a.guess, d, it32);
+                        solved32 = pair32_solve(pr, ma.tau32, ma.post32, a.guess, d, it32);
                         if (solved32) {
 #pragma unroll
                             for (int q = 0; q < 6; ++q) dw_acc(racc[q], two_prod(mfj, d[q]));

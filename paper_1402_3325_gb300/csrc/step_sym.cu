@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED || MIXED) ? 2 : 4)
                                  a.rule);
                     if (pr.fp32) {
                         int it32 = 0;
-                        lane32 = pair32_solve(pr, a.t32, a.qtau32, a.guess, d32, it32);
+                        lane32 = pair32_solve(pr, a.t32, a.post32, a.guess, d32, it32);
                     }
                 }
                 if (!lane32)
