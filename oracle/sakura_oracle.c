@@ -4,7 +4,7 @@
  * A plain, slow, deliberately obvious FP64 CPU statement of the Sakura
  * Keplerian-splitting integrator (Goncalves Ferrari, Boekholt & Portegies
  * Zwart 2014, "A Keplerian-based Hamiltonian splitting for gravitational
- * N-body simulations").  It exists to judge the CUDA library: only the test
+ * N-body simulations").  It exists to check the CUDA library: only the test
  * suite, the smoke check and the benchmark's CPU-baseline leg may load it.
  * It shares no code, header or constant with the CUDA path.
  *

@@ -1,7 +1,7 @@
 """Write tests/golden/bh16384_oracle_run.json: the oracle's own run of the
 black-hole cluster (black hole of mass 1 plus 16383 stars of total mass 1e-2,
 Plummer scale 1, circular velocities; seed 0), dt = 2^-10, 256 second-order
-steps (Eqs. 27a-d), so that the mixed-precision form on the GPU can be judged
+steps (Eqs. 27a-d), so that the mixed-precision form on the GPU can be checked
 against the FP64 method over the whole run without repeating hours of CPU
 work in every test.
 

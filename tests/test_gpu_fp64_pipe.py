@@ -3,7 +3,7 @@
 Two facts the FP64 kernels' design and roofline rest on:
 * a warp instruction costs the pipe the same whatever number of its lanes is
   active, so lanes left idle by a schedule are lost throughput (the batched
-  kernel's packing is judged by its lane fill);
+  kernel's packing is measured by its lane fill);
 * the sustained FMA rate, against which the pair kernel's FP64 instruction
   count sets its speed of light.
 Run with -s to see the figures.

@@ -1,6 +1,6 @@
 """The mixed-precision form on its own workload, the black-hole cluster at
 full size (black hole of mass 1 plus 16383 stars of total mass 1e-2, Plummer
-scale 1, circular velocities, dt = 2^-10), judged against the FP64 oracle.
+scale 1, circular velocities, dt = 2^-10), checked against the FP64 oracle.
 
 * Pair classes: every one of the 16384^2 ordered pairs is classed as the
   oracle's double-precision rule classes it, except pairs within the
