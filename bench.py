@@ -626,7 +626,7 @@ def _roofline(workload, form, pairs, guess, n, small, m):
         # single-precision iterations per solve
         flops = share * (C_MIX32_FIX + kbar * C_MIX32_ITER)
         peak, pipe, src = FP32_PEAK_GFLOPS / 1e3, "fp32", fp32_peak_src + "; flops counted by hand"
-        kname = "pair_step_grp_mixed"
+        kname = "pair_step_grp_mixed" if m["row_groups"] else "pair_step_sym"
     elif form == "mixed" and pairs == "symmetric":
         # mostly FP64-class pairs (the literal rule: the FP64 tile kernel with
         # an inline class test): their FP64 solves, counted as in the
@@ -636,7 +636,7 @@ def _roofline(workload, form, pairs, guess, n, small, m):
                                  carried * (C_STEP + C_CARRY) + C_SYM -
                                  (C_SEED_SAVED if guess == "fp32" else 0))
         peak, pipe, src = FP64_PEAK_GFLOPS / 1e3, "fp64", fp64_peak_src
-        kname = "pair_step_sym"
+        kname = "pair_step_grp_mixed" if m["row_groups"] else "pair_step_sym"
     elif form == "mixed":
         # FP64 flops per ordered pair: the FP64 accumulation (6 FMA) of an
         # FP32-class pair, the full FP64 solve of the others
@@ -652,7 +652,7 @@ def _roofline(workload, form, pairs, guess, n, small, m):
                  (C_SEED_SAVED if (guess == "fp32" and symmetric) else 0))
         peak, pipe, src = FP64_PEAK_GFLOPS / 1e3, "fp64", fp64_peak_src
         kname = "small" if small else (
-            ("pair_step_grp" if EXTRA_FLAGS == KERNEL_FLAG["groups"] else "pair_step_sym")
+            ("pair_step_grp" if m["row_groups"] else "pair_step_sym")
             if symmetric else "pair_step_fp64")
     solves = n * (n - 1) * m["solves_per_pair"]
     pair_ms = m["pair_kernel_ms"]
@@ -696,7 +696,9 @@ def _measure(args, sk, s, device, stream, flush, guess, opts, per_call, clocks=N
          "iteration_lane_efficiency": st["iters"] / max(1, st["warp_slots"]),
          "carried_share": st.get("carries", 0) / max(1, st["solves"]),
          "solves_per_pair": st["solves"] / max(1, st["pairs"]),
-         "fp32_pair_share": st["fp32_pairs"] / max(1, st["pairs"])}
+         "fp32_pair_share": st["fp32_pairs"] / max(1, st["pairs"]),
+         # the pair kernel the library chose: the row-group layout or not
+         "row_groups": st.get("group_launches", 0) > 0}
     m["fp64_evals_per_fp64_pair"] = (float(st["iters"]) / max(
         1.0, st["solves"] * (1.0 - m["fp32_pair_share"])))
     sk.init(device.index, stream=stream.cuda_stream, flags=EXTRA_FLAGS, guess=gcode, **opts)

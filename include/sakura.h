@@ -84,15 +84,18 @@ extern "C" {
 #define SAKURA_FLAG_NO_AUTOTUNE 8u /* batched path: skip the block-shape autotuner  */
 #define SAKURA_FLAG_NO_SMALL 16u   /* n <= 20: use the multi-kernel step instead of  */
                                    /* the single-block kernel (for comparisons)      */
-#define SAKURA_FLAG_TILES 32u      /* symmetric FP64 step: always the systolic tile
-                                      kernel (per-warp tile segments, partials per
-                                      segment: 3 n^2 bytes of scratch), the default
-                                      while those partials take at most 4 GB        */
-#define SAKURA_FLAG_GROUPS 64u     /* symmetric FP64 step: always the row-group
-                                      kernel (blocks of warps sweep column blocks
-                                      together, column sums reduced per block:
-                                      n^2 / 2.7 bytes), the default beyond; the
-                                      mixed form always uses row groups            */
+#define SAKURA_FLAG_TILES 32u      /* symmetric FP64 and mixed steps: always the
+                                      systolic tile kernel (per-warp tile segments,
+                                      partials per segment: up to 12 n^2 bytes of
+                                      scratch), the FP64 default up to about 13400
+                                      bodies, the mixed form's under the literal
+                                      rule up to about 18900                       */
+#define SAKURA_FLAG_GROUPS 64u     /* symmetric FP64 and mixed steps: always the
+                                      row-group kernel (blocks of warps sweep column
+                                      blocks together, column sums reduced per
+                                      block: about n^2 / 2.7 bytes), the default
+                                      beyond, and the mixed form's under
+                                      SAKURA_MIXED_RULE_HYP                        */
 
 #define SAKURA_BATCH_MAX_N 64     /* largest system of sakura_step_batched       */
 
@@ -135,6 +138,9 @@ typedef struct sakura_stats {
     int64_t carries;      /* FP64 solves finished by a Laguerre step below 2^-20 of
                              the scale with G1..G3 and r carried to the root by
                              their Taylor series (symmetric FP64 step)          */
+    int64_t group_launches; /* pair-kernel launches in the row-group layout (the
+                               others: systolic tiles, ordered pairs, the
+                               single-block or batched kernels)                 */
 } sakura_stats;
 
 /* Fill *cfg with the defaults listed above. */
@@ -172,11 +178,12 @@ int sakura_set_stream(void *stream);
  * default) each unordered pair is solved once, its two ordered increments
  * being exact negatives.  The symmetric FP64 step runs on systolic tiles,
  * whose partial sums take up to 8 x 6 x 8 ceil(n/32) n bytes of library
- * scratch (12 MB at n = 1024, 0.8 GB at 16384); beyond 4 GB of them it
- * runs in row-group phases, whose partials take about n^2 / 2.7 bytes; the
- * mixed form uses row groups under SAKURA_MIXED_RULE_HYP and the tile kernel
- * with an inline class test under the literal rule (SAKURA_FLAG_TILES /
- * SAKURA_FLAG_GROUPS force either kernel).  Where the symmetric scratch
+ * scratch (12 MB at n = 1024), while that bound stays within 2 GB (up to
+ * about 13400 bodies), and in row-group phases beyond, whose partials take
+ * about n^2 / 2.7 bytes (0.1 GB at 16384); the mixed form uses row groups
+ * under SAKURA_MIXED_RULE_HYP and the tile kernel with an inline class test
+ * under the literal rule while the bound stays within 4 GB
+ * (SAKURA_FLAG_TILES / SAKURA_FLAG_GROUPS force either kernel).  Where the symmetric scratch
  * would pass 16 GB the ordered kernel is used.  Systems of 2 <= n <= 20 in the
  * FP64 form with symmetric pairs and a non-learned guess run in one launch
  * of a single-block kernel that keeps the system in shared memory and packs

@@ -60,6 +60,7 @@ struct Context {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spare;
     double timed_ms = 0.0;
     int64_t timed_launches = 0;
+    int64_t group_launches = 0;
     BatchCache batch;
     Buffer mlp, mlp_blob, mlp_scratch, mlp_adam;  // learned-guess network and training
     bool mlp_loaded = false;
@@ -215,16 +216,20 @@ int step_device_mixed_grp(const double *src, double *dst, const double *masses, 
         g.cfg.grid_blocks > 0
             ? g.cfg.grid_blocks
             : (int64_t)g.sm_count * sakura::pair_step_grp_mixed_blocks_per_sm(stats, seed);
-    const sakura::GrpLayout L = sakura::make_grp_layout(n, sakura::kMixedGrpWarps, blocks);
+    const sakura::GrpLayout L = sakura::make_grp_layout(n, sakura::kMixedGrpWarps, sakura::kMixedGrpChunk, false,
+                                                        blocks);
     // scratch: X[7][n] doubles, row partials [Hmax][6][n], column partials
-    // [ng][6][n], then X32[10][n] floats
-    int rc = grow(g.partial, (size_t)(7 * n + (int64_t)(L.Hmax + L.ng) * 6 * n + 5 * n) *
+    // [ng][6][n] and [blocks][6][32], then X32[10][n] floats
+    int rc = grow(g.partial, (size_t)(7 * n + (int64_t)(L.Hmax + L.ng) * 6 * n + blocks * 192 +
+                                      5 * n) *
                                  sizeof(double));
     if (rc) return rc;
     double *X = (double *)g.partial.ptr;
-    double *rowpart = X + 7 * n;
-    double *colpart = rowpart + (int64_t)L.Hmax * 6 * n;
-    float *X32 = (float *)(colpart + (int64_t)L.ng * 6 * n);
+    sakura::GrpParts parts;
+    parts.row = X + 7 * n;
+    parts.col = parts.row + (int64_t)L.Hmax * 6 * n;
+    parts.colx = parts.col + (int64_t)L.ng * 6 * n;
+    float *X32 = (float *)(parts.colx + blocks * 192);
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
     sakura::launch_prep_mixed(src, masses, X, X32, n, drift, g.d_status, g.stream);
@@ -255,13 +260,14 @@ int step_device_mixed_grp(const double *src, double *dst, const double *masses, 
         tm = take_timer();
         cudaEventRecord(tm.first, g.stream);
     }
-    sakura::launch_pair_step_grp_mixed(a, ma, L, rowpart, colpart, (int)blocks, stats, g.stream);
+    sakura::launch_pair_step_grp_mixed(a, ma, L, parts, (int)blocks, stats, g.stream);
+    g.group_launches += 1;
     if (timing) {
         cudaEventRecord(tm.second, g.stream);
         g.timers.push_back(tm);
     }
-    sakura::launch_apply_grp(dst, X, nullptr, rowpart, colpart, n, L, blocks, post_drift, false,
-                             0.0, g.d_status, g.stream);
+    sakura::launch_apply_grp(dst, X, nullptr, parts, n, L, blocks, post_drift, false, 0.0,
+                             g.d_status, g.stream);
     rc = launch_error();
     if (rc) return rc;
     g.steps += 1;
@@ -285,11 +291,17 @@ double group_partial_bytes(int64_t n, int G)
     return 48.0 * (double)n * (double)(((n + 31) / 32 + G - 1) / G + 16);
 }
 
-// The symmetric FP64 form runs on systolic tiles (step_sym.cu), measured
-// fastest at every size (16384 bodies: 27.3 ms per step against 28.0 in row
-// groups), while their partials take at most kTileMaxBytes; beyond that in
-// row-group phases (step_grp.cu), whose scratch is 8 times smaller.  The
-// flags force either kernel.
+// The symmetric FP64 form runs on systolic tiles (step_sym.cu) while their
+// partials take at most kFp64TileMaxBytes (about 13400 bodies), in row-group
+// phases (step_grp.cu) beyond, where the two are level or the row groups
+// faster and write about a hundredth of the tile kernel's partial traffic
+// (measured with the single-precision seed, ms per step, tiles / row groups:
+// black hole + 12287 stars 15.40 / 15.48, + 16383 stars 27.37 / 27.42,
+// + 24575 stars 61.62 / 61.50, + 32767 stars 114.2 / 109.1; Plummer 24576
+// bodies 62.61 / 62.55; at 16384 bodies with the learned guess 36.07 / 35.42
+// and the standard guess 38.67 / 38.27).  The flags force either kernel.
+constexpr double kFp64TileMaxBytes = 2.0 * 1024 * 1024 * 1024;
+// The mixed form's tile kernel (the literal rule) is used up to this size.
 constexpr double kTileMaxBytes = 4.0 * 1024 * 1024 * 1024;
 
 // The mixed form runs in the FP64 tile kernel with an inline class test
@@ -307,7 +319,7 @@ bool fp64_groups(int64_t n)
 {
     if (g.cfg.flags & SAKURA_FLAG_GROUPS) return true;
     if (g.cfg.flags & SAKURA_FLAG_TILES) return false;
-    return tile_partial_bytes(n) > kTileMaxBytes;
+    return tile_partial_bytes(n) > kFp64TileMaxBytes;
 }
 
 // The FP64 form with each unordered pair once, in row-group phases
@@ -324,16 +336,21 @@ int step_device_fp64_grp(const double *src, double *dst, const double *masses, i
                          ? g.cfg.grid_blocks
                          : (int64_t)g.sm_count *
                                sakura::pair_step_grp_blocks_per_sm(stats, learned, seed);
-    const sakura::GrpLayout L = sakura::make_grp_layout(n, sakura::kFp64GrpWarps, blocks);
+    const sakura::GrpLayout L = sakura::make_grp_layout(n, sakura::kFp64GrpWarps, sakura::kFp64GrpChunk, true,
+                                                        blocks);
     // scratch: X[7][n] doubles, row partials [Hmax][6][n], column partials
-    // [ng][6][n], then X32[10][n] floats (single-precision seed)
-    int rc = grow(g.partial, (size_t)(7 * n + (int64_t)(L.Hmax + L.ng) * 6 * n + 5 * n) *
+    // [ng][6][n] and [blocks][6][32], then X32[10][n] floats (single-precision
+    // seed)
+    int rc = grow(g.partial, (size_t)(7 * n + (int64_t)(L.Hmax + L.ng) * 6 * n + blocks * 192 +
+                                      5 * n) *
                                  sizeof(double));
     if (rc) return rc;
     double *X = (double *)g.partial.ptr;
-    double *rowpart = X + 7 * n;
-    double *colpart = rowpart + (int64_t)L.Hmax * 6 * n;
-    float *X32 = seed ? (float *)(colpart + (int64_t)L.ng * 6 * n) : nullptr;
+    sakura::GrpParts parts;
+    parts.row = X + 7 * n;
+    parts.col = parts.row + (int64_t)L.Hmax * 6 * n;
+    parts.colx = parts.col + (int64_t)L.ng * 6 * n;
+    float *X32 = seed ? (float *)(parts.colx + blocks * 192) : nullptr;
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
     if (!prepped) sakura::launch_prep_step(src, masses, X, X32, n, drift, g.d_status, g.stream);
@@ -360,13 +377,14 @@ int step_device_fp64_grp(const double *src, double *dst, const double *masses, i
         tm = take_timer();
         cudaEventRecord(tm.first, g.stream);
     }
-    sakura::launch_pair_step_grp(a, L, rowpart, colpart, (int)blocks, stats, g.stream);
+    sakura::launch_pair_step_grp(a, L, parts, (int)blocks, stats, g.stream);
+    g.group_launches += 1;
     if (timing) {
         cudaEventRecord(tm.second, g.stream);
         g.timers.push_back(tm);
     }
-    sakura::launch_apply_grp(dst, X, X32, rowpart, colpart, n, L, blocks, post_drift, fuse,
-                             next_drift, g.d_status, g.stream);
+    sakura::launch_apply_grp(dst, X, X32, parts, n, L, blocks, post_drift, fuse, next_drift,
+                             g.d_status, g.stream);
     rc = launch_error();
     if (rc) return rc;
     g.steps += 1;
@@ -390,7 +408,7 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
                     double next_drift = 0.0)
 {
     if (mixed && !mixed_tiles(n)) return step_device_mixed_grp(src, dst, masses, n, dt, order);
-    if (!df64 && fp64_groups(n))
+    if (!df64 && !mixed && fp64_groups(n))
         return step_device_fp64_grp(src, dst, masses, n, dt, order, prepped, fuse, next_drift);
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
     const bool learned = !df64 && !mixed && g.cfg.guess == SAKURA_GUESS_LEARNED;
@@ -1277,12 +1295,14 @@ int sakura_get_stats(sakura_stats *out, int reset)
     collect_timers();
     out->timed_launches = g.timed_launches;
     out->pair_kernel_ms = g.timed_ms;
+    out->group_launches = g.group_launches;
     if (reset) {
         if (cudaMemsetAsync(g.d_stats, 0, sizeof(h), g.stream) != cudaSuccess)
             return SAKURA_E_CUDA;
         g.steps = g.pairs = g.solves = 0;
         g.timed_ms = 0.0;
         g.timed_launches = 0;
+        g.group_launches = 0;
     }
     return SAKURA_OK;
 }

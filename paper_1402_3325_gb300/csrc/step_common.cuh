@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "df64.cuh"
+#include "grp_layout.cuh"
 #include "kepler_fp32.cuh"
 
 namespace sakura {
@@ -85,62 +86,29 @@ void launch_prep_mixed(const double *state, const double *mass, double *X, float
 void launch_pair_step_mixed(const StepArgs &a, const MixedArgs &ma, int blocks, bool stats,
                             cudaStream_t s);
 int pair_step_mixed_blocks_per_sm(bool stats);
-// Row-group phases of the symmetric (Newton's third law) FP64 and mixed
-// kernels (step_grp.cu, step_mixed.cu).  The n particles form nb blocks of
-// 32; a group is G consecutive row blocks, one per warp of a block (G = 8 for
-// the mixed kernel, 4 for the FP64 one); group g meets the column blocks
-// J = g G .. nb - 1 in nb - g G phases.  The phases of all groups are
-// numbered group by group (J ascending): group g's first phase is
-// grp_start(g).  A persistent grid of B blocks takes contiguous ranges
-// [b P / B, (b + 1) P / B) of the P phases; grp_owner(p) is the block whose
-// range holds phase p.  A block works its range in windows of up to
-// kGrpWindow phases of one group, with one block barrier and one reduction of
-// the warps' column sums per window.  Partials: one column partial per
-// particle per group that meets its block, colpart[g][6][n], and one row
-// partial per block that holds phases of its group, rowpart[h][6][n],
-// h = b - grp_owner(grp_start(g)) < Hmax.
-constexpr int kGrpWindow = 4;
-constexpr int kMixedGrpWarps = 8;  // G of the mixed kernel (2 blocks of 8 warps per SM)
-constexpr int kFp64GrpWarps = 4;   // G of the FP64 kernel (2 blocks of 4 warps per SM)
+// Row-group layout: grp_layout.cuh.
 
-__host__ __device__ __forceinline__ int64_t grp_start(int64_t g, int64_t nb, int64_t G)
-{
-    return g * nb - G * (g * (g - 1) / 2);
-}
-
-__host__ __device__ __forceinline__ int64_t grp_owner(int64_t p, int64_t B, int64_t P)
-{
-    return ((p + 1) * B - 1) / P;
-}
-
-struct GrpLayout {
-    int64_t nb;  // blocks of 32 particles
-    int64_t P;   // phases
-    int ng;      // groups
-    int G;       // row blocks per group (warps per block)
-    int Hmax;    // most row pieces of a group for the grid it was made for
+// the partial sums of a row-group step: row [Hmax][6][n], col [ng][6][n],
+// colx [blocks][6][32] (see above)
+struct GrpParts {
+    double *row, *col, *colx;
 };
-// the layout for n particles; clamps blocks to the phase count
-GrpLayout make_grp_layout(int64_t n, int G, int64_t &blocks);
-// rowpart: [Hmax][6][n] row partials; colpart: [ng][6][n] column partials;
 // a.X32 (the float copy, as ma.X32) set: FP64-class pairs seeded by a
 // single-precision solve
 void launch_pair_step_grp_mixed(const StepArgs &a, const MixedArgs &ma, const GrpLayout &L,
-                                double *rowpart, double *colpart, int blocks, bool stats,
-                                cudaStream_t s);
+                                const GrpParts &parts, int blocks, bool stats, cudaStream_t s);
 int pair_step_grp_mixed_blocks_per_sm(bool stats, bool seed);
 // Eqs. 27b-d for the row-group layout; fuse: also the next sub-step's drift
 // (next_drift), writing its drifted copy to X (and X32, if not null) as the
 // prep kernel would, so that a run of steps needs no prep kernel after its
 // first
-void launch_apply_grp(double *state, double *X, float *X32, const double *rowpart,
-                      const double *colpart, int64_t n, const GrpLayout &L, int64_t blocks,
-                      double post_drift, bool fuse, double next_drift, unsigned *status,
-                      cudaStream_t s);
+void launch_apply_grp(double *state, double *X, float *X32, const GrpParts &parts, int64_t n,
+                      const GrpLayout &L, int64_t blocks, double post_drift, bool fuse,
+                      double next_drift, unsigned *status, cudaStream_t s);
 // the symmetric FP64 pair kernel in row-group phases (a.mlp: learned guess;
 // a.X32: single-precision seed)
-void launch_pair_step_grp(const StepArgs &a, const GrpLayout &L, double *rowpart,
-                          double *colpart, int blocks, bool stats, cudaStream_t s);
+void launch_pair_step_grp(const StepArgs &a, const GrpLayout &L, const GrpParts &parts,
+                          int blocks, bool stats, cudaStream_t s);
 int pair_step_grp_blocks_per_sm(bool stats, bool learned, bool seed);
 // the FP32 class of every ordered pair as the mixed kernels decide it
 // (out: n x n bytes), from the float copy that launch_prep_mixed writes

@@ -9,21 +9,29 @@
 // So each pair is solved once and adds  m_j delta/m_ij  to particle i and
 // -m_i delta/m_ij  to particle j (Eq. 23 with 1/m_i folded in).
 //
-// Work (step_common.cuh): a block of kFp64GrpWarps warps owns a group of as
-// many row blocks of 32 particles, warp w the row block I = g G + w, and its
-// warps sweep the column blocks J >= g G together.  In phase J warp w solves the 32 x 32 tile (I, J) (nothing when
-// I > J; the ordered pairs of the diagonal tile when I = J) on a systolic
-// schedule: lane l owns row i = 32 I + l and at step k solves column
-// c = (l + k) mod 32, so the 32 lanes always hold 32 different columns.  The
-// column blocks of a window of up to 8 (or 4) phases are staged in shared
-// memory for all warps.  Row sums stay in the lane's registers for the whole
-// group; each warp adds its column sums into its own shared-memory
-// accumulators of the window, and after the window's block barrier the
-// block adds the warps' accumulators in warp order and writes one column
-// partial per particle.  Every (slot, particle) is written exactly once and
-// the apply kernel adds a particle's slots in a fixed order (deterministic,
-// no atomics).  Partials per step: about 30 MB at n = 16384, which stay in
-// L2 (the earlier per-tile-segment slots were 0.4 GB).
+// Work (step_common.cuh): a block of kFp64GrpWarps = G warps takes the
+// tile-steps of a group of G row blocks, which meets the column blocks
+// J >= g G one phase per J, and the grid's blocks take equal contiguous
+// ranges of all groups' tile-steps.  In phase J the tiles (g G + r, J),
+// r <= J - g G, are solved one per warp, warp w taking row block
+// r = (w + J) mod G: the row blocks rotate over the warps from phase to phase,
+// so a row whose pairs cost more (a black hole's, whose orbits take more
+// series terms and seed iterations) slows each warp in turn rather than one
+// warp of the block, which the others would wait for at every window
+// barrier.  A tile is solved on a systolic schedule: lane l owns row
+// i = 32 I + l and at step k solves column c = (l + k) mod 32, so the 32
+// lanes always hold 32 different columns.  The column blocks of a window of
+// up to 8 (or 4) phases are staged in shared memory for all warps.  Each
+// warp sums a phase's row sums in registers and adds them to its own
+// shared-memory row sums of the group, and adds its column sums into its own
+// shared-memory accumulators of the window; after the window's block barrier
+// the block adds the warps' column sums in warp order and writes one column
+// partial per particle (colpart, or colx for a phase the block entered after
+// its step 0), and on leaving the group the warps' row sums in warp order
+// (one row piece).  Every slot is written exactly once and the apply kernel
+// adds a particle's slots in a fixed order (deterministic, no atomics).
+// Partials per step: about 30 MB at n = 16384, which stay in L2 (the
+// systolic tile kernel's per-tile-segment slots are 0.4 GB).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,38 +44,23 @@
 
 namespace sakura {
 
-GrpLayout make_grp_layout(int64_t n, int G, int64_t &blocks)
-{
-    GrpLayout L;
-    L.nb = (n + 31) / 32;
-    L.G = G;
-    L.ng = (int)((L.nb + G - 1) / G);
-    L.P = grp_start(L.ng, L.nb, G);
-    blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, L.P));
-    L.Hmax = 1;
-    for (int64_t g = 0; g < L.ng; ++g) {
-        const int64_t s0 = grp_start(g, L.nb, G), s1 = grp_start(g + 1, L.nb, G);
-        const int64_t h = grp_owner(s1 - 1, blocks, L.P) - grp_owner(s0, blocks, L.P) + 1;
-        L.Hmax = std::max<int>(L.Hmax, (int)h);
-    }
-    return L;
-}
-
-// Eqs. 27b-d for the row-group layout.  Particle i of row block I (group
-// gi = I / G) adds its group's row pieces h = 0 .. npieces - 1 and the
-// column partials of groups g = 0 .. gi (the phases (g, I)), in that fixed
-// order, spread over the block's warps (slot s to warp s mod
-// kGrpApplyWarps, alternately into two sums) and then added in warp order.
-// Block (x, y) takes 32 particles and the component pair (y, 3 + y).
+// Eqs. 27b-d for the row-group layout.  Layout index i (particle
+// grp_particle(i)) of row block I (group gi = I / G) adds its group's row
+// pieces h = 0 .. npieces - 1 and the
+// column sums of the phases (g, I), g = 0 .. gi (colpart[g], then the colx
+// slots of the blocks that start inside that phase), in that fixed order,
+// spread over the block's warps (slot s to warp s mod kGrpApplyWarps,
+// alternately into two sums) and then added in warp order.  Block (x, y)
+// takes 32 particles and the component pair (y, 3 + y).
 // fuse: the next sub-step's drift (Eq. 27a, next_drift) is applied too and
 // its drifted copy written to X (and X32), as the prep kernel would write it
 // from the new state.
 constexpr int kGrpApplyWarps = 8;
 
 __global__ void __launch_bounds__(32 * kGrpApplyWarps)
-    apply_grp_kernel(double *state, double *X, float *X32, const double *rowpart,
-                     const double *colpart, int64_t n, GrpLayout L, int64_t B,
-                     double post_drift, int fuse, double next_drift, unsigned *status)
+    apply_grp_kernel(double *state, double *X, float *X32, GrpParts parts, int64_t n,
+                     GrpLayout L, int64_t B, double post_drift, int fuse, double next_drift,
+                     unsigned *status)
 {
     __shared__ double red[kGrpApplyWarps][2][32];
     griddep_wait();  // the pair kernel's partials
@@ -76,37 +69,46 @@ __global__ void __launch_bounds__(32 * kGrpApplyWarps)
     // now.  With fuse the next kernel is a persistent pair kernel whose
     // blocks must be spread evenly over the SMs: launched while this grid's
     // blocks still hold SM resources, some SMs could receive an extra block
-    // and the static phase ranges would then run slower there; it waits for
-    // this grid to complete instead.
+    // and the static ranges would then run slower there; it waits for this
+    // grid to complete instead.
     if (!fuse) griddep_launch();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int q = blockIdx.y;
     const int64_t Ib = blockIdx.x;
     const int64_t i = Ib * 32 + lane;
     const int64_t gi = Ib / L.G;
-    const int64_t s0 = grp_start(gi, L.nb, L.G), s1 = grp_start(gi + 1, L.nb, L.G);
-    const int npieces = (int)(grp_owner(s1 - 1, B, L.P) - grp_owner(s0, B, L.P)) + 1;
+    const int64_t u0 = 32 * grp_before(L, gi), u1 = 32 * grp_before(L, gi + 1) - 1;
+    const int npieces = (int)(grp_owner(u1, B, L) - grp_owner(u0, B, L)) + 1;
     const int nslots = npieces + (int)gi + 1;
     double dr = 0.0, dv = 0.0;
     if (i < n) {
-        auto slot = [&](int sl) {
-            return sl < npieces ? rowpart + (int64_t)sl * 6 * n
-                                : colpart + (int64_t)(sl - npieces) * 6 * n;
+        // slot sl: row piece sl, or the column sums of phase (sl - npieces, Ib)
+        auto add = [&](int sl, double &er, double &ev) {
+            if (sl < npieces) {
+                const double *p = parts.row + (int64_t)sl * 6 * n;
+                er += p[q * n + i];
+                ev += p[(3 + q) * n + i];
+                return;
+            }
+            const int64_t gg = sl - npieces;
+            const double *p = parts.col + gg * 6 * n;
+            er += p[q * n + i];
+            ev += p[(3 + q) * n + i];
+            if (L.S == 32) return;  // whole phases: no phase is split
+            const int64_t up = 32 * (grp_before(L, gg) + Ib - gg * L.G);
+            const int64_t bl = grp_owner(up + 31, B, L);
+            for (int64_t bb = grp_owner(up, B, L) + 1; bb <= bl; ++bb) {
+                er += parts.colx[(bb * 6 + q) * 32 + lane];
+                ev += parts.colx[(bb * 6 + 3 + q) * 32 + lane];
+            }
         };
         double er0 = 0, er1 = 0, ev0 = 0, ev1 = 0;
         int sl = wid;
         for (; sl + kGrpApplyWarps < nslots; sl += 2 * kGrpApplyWarps) {
-            const double *b0 = slot(sl), *b1 = slot(sl + kGrpApplyWarps);
-            er0 += b0[q * n + i];
-            ev0 += b0[(3 + q) * n + i];
-            er1 += b1[q * n + i];
-            ev1 += b1[(3 + q) * n + i];
+            add(sl, er0, ev0);
+            add(sl + kGrpApplyWarps, er1, ev1);
         }
-        if (sl < nslots) {
-            const double *b0 = slot(sl);
-            er0 += b0[q * n + i];
-            ev0 += b0[(3 + q) * n + i];
-        }
+        if (sl < nslots) add(sl, er0, ev0);
         dr = er0 + er1;
         dv = ev0 + ev1;
     }
@@ -119,63 +121,69 @@ __global__ void __launch_bounds__(32 * kGrpApplyWarps)
         tr += red[w][0][lane];
         tv += red[w][1][lane];
     }
-    const double v1 = X[(3 + q) * n + i] + tv;
-    const double x1 = fma(v1, post_drift, X[q * n + i] + tr);
-    if (!isfinite(x1) || !isfinite(v1)) atomicOr(status, kStatusNonfinite);
-    state[q * n + i] = x1;
-    state[(3 + q) * n + i] = v1;
+    const int64_t ip = grp_particle(L, n, i);  // the particle of layout index i
+    const double v1 = X[(3 + q) * n + ip] + tv;
+    const double x1n = fma(v1, post_drift, X[q * n + ip] + tr);
+    if (!isfinite(x1n) || !isfinite(v1)) atomicOr(status, kStatusNonfinite);
+    state[q * n + ip] = x1n;
+    state[(3 + q) * n + ip] = v1;
     if (fuse) {
-        const double x = fma(v1, next_drift, x1);
-        X[q * n + i] = x;
-        X[(3 + q) * n + i] = v1;
+        const double x = fma(v1, next_drift, x1n);
+        X[q * n + ip] = x;
+        X[(3 + q) * n + ip] = v1;
         if (X32) {
             const float hi = __double2float_rn(x);
-            X32[q * n + i] = hi;
-            X32[(3 + q) * n + i] = __double2float_rn(x - (double)hi);
-            X32[(6 + q) * n + i] = __double2float_rn(v1);
+            X32[q * n + ip] = hi;
+            X32[(3 + q) * n + ip] = __double2float_rn(x - (double)hi);
+            X32[(6 + q) * n + ip] = __double2float_rn(v1);
         }
     }
 }
 
-void launch_apply_grp(double *state, double *X, float *X32, const double *rowpart,
-                      const double *colpart, int64_t n, const GrpLayout &L, int64_t blocks,
-                      double post_drift, bool fuse, double next_drift, unsigned *status,
-                      cudaStream_t s)
+void launch_apply_grp(double *state, double *X, float *X32, const GrpParts &parts, int64_t n,
+                      const GrpLayout &L, int64_t blocks, double post_drift, bool fuse,
+                      double next_drift, unsigned *status, cudaStream_t s)
 {
+    GrpParts pv = parts;
     GrpLayout Lv = L;
     int64_t B = blocks;
     int f = fuse ? 1 : 0;
-    void *args[] = {(void *)&state,      (void *)&X,    (void *)&X32,       (void *)&rowpart,
-                    (void *)&colpart,    (void *)&n,    (void *)&Lv,        (void *)&B,
-                    (void *)&post_drift, (void *)&f,    (void *)&next_drift, (void *)&status};
+    void *args[] = {(void *)&state,      (void *)&X, (void *)&X32,        (void *)&pv,
+                    (void *)&n,          (void *)&Lv, (void *)&B,         (void *)&post_drift,
+                    (void *)&f,          (void *)&next_drift, (void *)&status};
     launch_pdl((const void *)apply_grp_kernel, dim3((unsigned)((n + 31) / 32), 3),
                dim3(32 * kGrpApplyWarps), args, 0, s);
 }
 
 // shared memory of the pair kernel: the warps' column sums of the window
-// (double [kFp64GrpWarps][WIN][6][32]), the window's column blocks double
-// buffered (double [2][WIN][7][32]: x, y, z, vx, vy, vz, m of the drifted
-// state; float [2][WIN][10][32]: the float copy for the seed), then (learned
-// guess) the network and the warps' staging
-// (kFp64GrpWarps = 4 warps per block and two blocks per SM: one block's
-// warps keep the SM's FP64 pipes busy while the other block waits at a
-// window barrier)
-// The window: 8 phases with the seed (two blocks of 4 warps per SM), 4
-// otherwise (the network's weights take shared memory; without either, four
-// blocks per SM fit).
+// (double [G][WIN][6][32]), the window's column blocks (double [WIN][7][32]:
+// x, y, z, vx, vy, vz, m of the drifted state; float [WIN][10][32]: the float
+// copy for the seed), the warps' row sums of the group (double [G][G][6][32]:
+// warp, row block of the group), then (learned guess) the network and the
+// warps' staging.  G = kFp64GrpWarps = 4 warps per block and two blocks per
+// SM: one block's warps keep the SM's FP64 pipes busy while the other block
+// waits at a window barrier.  The window: 8 phases with the seed (two blocks
+// per SM), 4 otherwise (the network's weights take shared memory; without
+// either, more blocks per SM fit).  The column blocks are loaded between the
+// window's two barriers, after every warp has finished with the previous
+// ones, so one buffer serves.
 __host__ __device__ constexpr int grp_window(bool seed) { return seed ? 8 : 4; }
 __host__ __device__ constexpr size_t grp_cs_bytes(int win)
 {
     return sizeof(double) * kFp64GrpWarps * win * 6 * 32;
 }
-__host__ __device__ constexpr size_t grp_cd_bytes(int win) { return sizeof(double) * 2 * win * 7 * 32; }
+__host__ __device__ constexpr size_t grp_cd_bytes(int win) { return sizeof(double) * win * 7 * 32; }
 __host__ __device__ constexpr size_t grp_cf_bytes(int win, bool seed)
 {
-    return seed ? sizeof(float) * 2 * win * 10 * 32 : 0;
+    return seed ? sizeof(float) * win * 10 * 32 : 0;
+}
+__host__ __device__ constexpr size_t grp_rs_bytes()
+{
+    return sizeof(double) * kFp64GrpWarps * kFp64GrpWarps * 6 * 32;
 }
 __host__ __device__ constexpr size_t grp_base_smem(int win, bool seed)
 {
-    return grp_cs_bytes(win) + grp_cd_bytes(win) + grp_cf_bytes(win, seed);
+    return grp_cs_bytes(win) + grp_cd_bytes(win) + grp_cf_bytes(win, seed) + grp_rs_bytes();
 }
 
 size_t grp_smem(bool learned, bool seed)
@@ -187,14 +195,17 @@ size_t grp_smem(bool learned, bool seed)
 
 template <bool STATS, bool LEARNED, bool SEED>
 __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
-    pair_step_grp_kernel(StepArgs a, GrpLayout L, double *rowpart, double *colpart)
+    pair_step_grp_kernel(StepArgs a, GrpLayout L, GrpParts parts)
 {
+    constexpr int G = kFp64GrpWarps;
     constexpr int WIN = grp_window(SEED);
     extern __shared__ __align__(16) unsigned char gsm[];
     double(*cs)[WIN][6][32] = reinterpret_cast<double(*)[WIN][6][32]>(gsm);
-    double(*cd)[WIN][7][32] = reinterpret_cast<double(*)[WIN][7][32]>(gsm + grp_cs_bytes(WIN));
-    float(*cf)[WIN][10][32] =
-        reinterpret_cast<float(*)[WIN][10][32]>(gsm + grp_cs_bytes(WIN) + grp_cd_bytes(WIN));
+    double(*cd)[7][32] = reinterpret_cast<double(*)[7][32]>(gsm + grp_cs_bytes(WIN));
+    float(*cf)[10][32] =
+        reinterpret_cast<float(*)[10][32]>(gsm + grp_cs_bytes(WIN) + grp_cd_bytes(WIN));
+    double(*rs)[G][6][32] = reinterpret_cast<double(*)[G][6][32]>(
+        gsm + grp_cs_bytes(WIN) + grp_cd_bytes(WIN) + grp_cf_bytes(WIN, SEED));
     MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(gsm + grp_base_smem(WIN, SEED));
     __nv_bfloat16 *mlpStage =
         reinterpret_cast<__nv_bfloat16 *>(gsm + grp_base_smem(WIN, SEED) + sizeof(MlpWeights));
@@ -206,7 +217,6 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
     const int tid = threadIdx.x;
     const int64_t n = a.n;
     const int64_t nb = L.nb;
-    const int64_t P = L.P;
     const int64_t B = gridDim.x;
     const int64_t b = blockIdx.x;
     const double *X = a.X;
@@ -216,100 +226,107 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
     long long it_sum = 0, slots = 0, fallbacks = 0, carries = 0;
     int it_max = 0;
 
-    const int64_t p0 = b * P / B, p1 = (b + 1) * P / B;
-    int64_t g = 0;
-    while (g + 1 < L.ng && grp_start(g + 1, nb, kFp64GrpWarps) <= p0) ++g;
-    int64_t J = g * kFp64GrpWarps + (p0 - grp_start(g, nb, kFp64GrpWarps));
-    int64_t p = p0;
-    // a window: up to WIN consecutive phases of one group within the
-    // block's range
-    auto window_len = [&](int64_t pw, int64_t Jw) {
-        const int64_t m = nb - Jw < p1 - pw ? nb - Jw : p1 - pw;
+    GrpPos cur = grp_block_start(L, b, B);
+    // the range's end, block-uniform, kept in shared memory (read once per
+    // window) rather than in registers
+    __shared__ GrpPos s_end;
+    if (tid == 0) s_end = grp_block_start(L, b + 1, B);
+    __syncthreads();
+    auto in_range = [&](const GrpPos &p) {
+        const GrpPos e = s_end;
+        return p.g < e.g || (p.g == e.g && (p.t < e.t || (p.t == e.t && p.k < e.k)));
+    };
+    // a window: up to WIN consecutive phases of one group within the range
+    auto window_len = [&](const GrpPos &p) {
+        const GrpPos e = s_end;
+        const int64_t m = p.g < e.g ? nb - p.g * G - p.t : e.t - p.t + (e.k > 0 ? 1 : 0);
         return (int)(m < WIN ? m : WIN);
     };
-    // the window's column blocks Jw .. Jw + len - 1 into buffer buf
-    auto load_cols = [&](int buf, int64_t Jw, int len) {
-        for (int e = tid; e < len * 32; e += kFp64GrpWarps * 32) {
+    // the window's column blocks Jw .. Jw + len - 1
+    auto load_cols = [&](int64_t Jw, int len) {
+        for (int e = tid; e < len * 32; e += G * 32) {
             const int cb = e >> 5, c = e & 31;
             const int64_t j = 32 * (Jw + cb) + c;
             const bool ok = j < n;
+            const int64_t jp = ok ? grp_particle(L, n, j) : 0;
 #pragma unroll
-            for (int f = 0; f < 7; ++f) cd[buf][cb][f][c] = ok ? X[f * n + j] : 0.0;
+            for (int f = 0; f < 7; ++f) cd[cb][f][c] = ok ? X[f * n + jp] : 0.0;
             if (SEED) {
 #pragma unroll
-                for (int f = 0; f < 10; ++f) cf[buf][cb][f][c] = ok ? X32[f * n + j] : 0.0f;
+                for (int f = 0; f < 10; ++f) cf[cb][f][c] = ok ? X32[f * n + jp] : 0.0f;
             }
         }
     };
-    int wl = p < p1 ? window_len(p, J) : 0;
-    if (wl > 0) load_cols(0, J, wl);
+    for (int e = tid; e < G * G * 6 * 32; e += G * 32) (&rs[0][0][0][0])[e] = 0.0;
+    int wl = in_range(cur) ? window_len(cur) : 0;
+    if (wl > 0) load_cols(cur.g * G + cur.t, wl);
     __syncthreads();
 
-    double xi = 0, yi = 0, zi = 0, vxi = 0, vyi = 0, vzi = 0, mi = 1;
-    float hi_i[3] = {0, 0, 0}, lo_i[3] = {0, 0, 0}, v_i[3] = {0, 0, 0}, m32i = 0.0f;
-    double racc[6];
-    bool new_group = true;
-    int buf = 0;
     while (wl > 0) {
-        const int64_t I = g * kFp64GrpWarps + wib;
-        const int64_t i = 32 * I + lane;
-        const bool irow = I < nb && i < n;
-        if (new_group) {
-#pragma unroll
-            for (int q = 0; q < 6; ++q) racc[q] = 0.0;
-            if (irow) {
-                xi = X[i];
-                yi = X[n + i];
-                zi = X[2 * n + i];
-                vxi = X[3 * n + i];
-                vyi = X[4 * n + i];
-                vzi = X[5 * n + i];
-                mi = X[6 * n + i];
-                if (SEED) {
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        hi_i[q] = X32[q * n + i];
-                        lo_i[q] = X32[(3 + q) * n + i];
-                        v_i[q] = X32[(6 + q) * n + i];
-                    }
-                    m32i = X32[9 * n + i];
-                }
-            }
-            new_group = false;
-        }
+        const int64_t g = cur.g, R = grp_rows(L, g), J0 = g * G + cur.t;
+        // the steps of the window's first and last phases
+        const int kfirst = cur.k;
+        const int klast = (g == s_end.g && cur.t + wl - 1 == s_end.t) ? s_end.k : 32;
         for (int cb = 0; cb < wl; ++cb) {
 #pragma unroll
             for (int q = 0; q < 6; ++q) cs[wib][cb][q][lane] = 0.0;
         }
         __syncwarp();
         for (int cb = 0; cb < wl; ++cb) {
-            const int64_t Jt = J + cb;
-            if (!(I <= Jt && I < nb)) continue;  // warp-uniform: no tile (I, Jt)
+            const int64_t t = cur.t + cb;
+            const int r = (int)((wib + t) % G);  // this warp's row block of the phase
+            if (!(r <= t && r < R)) continue;     // warp-uniform: no tile
+            const int64_t I = g * G + r, Jt = J0 + cb;
             const bool diag = I == Jt;
-            for (int k = 0; k < 32; ++k) {
+            const int64_t i = 32 * I + lane;
+            const bool irow = i < n;
+            const int kb = cb == 0 ? kfirst : 0;
+            const int ke = cb == wl - 1 ? klast : 32;
+            double xi = 0, yi = 0, zi = 0, vxi = 0, vyi = 0, vzi = 0, mi = 1;
+            float hi_i[3] = {0, 0, 0}, lo_i[3] = {0, 0, 0}, v_i[3] = {0, 0, 0}, m32i = 0.0f;
+            if (irow) {
+                const int64_t ip = grp_particle(L, n, i);
+                xi = X[ip];
+                yi = X[n + ip];
+                zi = X[2 * n + ip];
+                vxi = X[3 * n + ip];
+                vyi = X[4 * n + ip];
+                vzi = X[5 * n + ip];
+                mi = X[6 * n + ip];
+                if (SEED) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        hi_i[q] = X32[q * n + ip];
+                        lo_i[q] = X32[(3 + q) * n + ip];
+                        v_i[q] = X32[(6 + q) * n + ip];
+                    }
+                    m32i = X32[9 * n + ip];
+                }
+            }
+            double racc[6] = {0, 0, 0, 0, 0, 0};
+            for (int k = kb; k < ke; ++k) {
                 const int c = (lane + k) & 31;
                 const int64_t j = 32 * Jt + c;
                 const bool valid = irow && j < n && (!diag || c != lane);
                 PairSolve ps;
                 double mj = 0.0;
                 if (valid) {
-                    mj = cd[buf][cb][6][c];
-                    pair_setup(ps, a.tau, mi + mj, xi - cd[buf][cb][0][c], yi - cd[buf][cb][1][c],
-                               zi - cd[buf][cb][2][c], vxi - cd[buf][cb][3][c],
-                               vyi - cd[buf][cb][4][c], vzi - cd[buf][cb][5][c], a.pre,
-                               LEARNED ? 2 : (SEED ? -1 : a.guess));
+                    mj = cd[cb][6][c];
+                    pair_setup(ps, a.tau, mi + mj, xi - cd[cb][0][c], yi - cd[cb][1][c],
+                               zi - cd[cb][2][c], vxi - cd[cb][3][c], vyi - cd[cb][4][c],
+                               vzi - cd[cb][5][c], a.pre, LEARNED ? 2 : (SEED ? -1 : a.guess));
                     if (SEED) {
                         // single-precision seed: the root of the FP32 solve of
                         // the same pair (unless t was reduced modulo the period)
                         float dr[3], dv[3];
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
-                            dr[q] = __fadd_rn(__fsub_rn(hi_i[q], cf[buf][cb][q][c]),
-                                              __fsub_rn(lo_i[q], cf[buf][cb][3 + q][c]));
-                            dv[q] = __fsub_rn(v_i[q], cf[buf][cb][6 + q][c]);
+                            dr[q] = __fadd_rn(__fsub_rn(hi_i[q], cf[cb][q][c]),
+                                              __fsub_rn(lo_i[q], cf[cb][3 + q][c]));
+                            dv[q] = __fsub_rn(v_i[q], cf[cb][6 + q][c]);
                         }
-                        const K32 o = k32_phase1(dr, dv, m32i + cf[buf][cb][9][c], a.ptau32,
-                                                 a.t32, 2);
+                        const K32 o =
+                            k32_phase1(dr, dv, m32i + cf[cb][9][c], a.ptau32, a.t32, 2);
                         if (o.ok && __double_as_longlong(ps.t) == __double_as_longlong(a.tau) &&
                             !ps.done) {
                             ps.s = f2d(o.s);
@@ -349,44 +366,53 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
                     if (lane == 0) slots += 32LL * wmax;
                 }
             }
+            // the phase's row sums into the warp's row sums of the group
+#pragma unroll
+            for (int q = 0; q < 6; ++q) rs[wib][r][q][lane] += racc[q];
         }
-        __syncthreads();  // every warp's column sums of the window are complete
-        // the next window; its column blocks are loaded now
-        const int64_t pn = p + wl;
-        int64_t gn = g, Jn = J + wl;
-        if (Jn == nb) {
-            gn = g + 1;
-            Jn = gn * kFp64GrpWarps;
+        __syncthreads();  // every warp's sums of the window are complete
+        GrpPos nxt{g, cur.t + wl, 0};
+        if (nxt.t == nb - g * G) {
+            nxt.g = g + 1;
+            nxt.t = 0;
         }
-        const int wln = pn < p1 ? window_len(pn, Jn) : 0;
-        if (wln > 0) load_cols(buf ^ 1, Jn, wln);
-        // the window's column partials: the warps' sums added in warp order
-        for (int e = tid; e < wl * 192; e += kFp64GrpWarps * 32) {
+        const int wln = in_range(nxt) ? window_len(nxt) : 0;
+        // the window's column partials: the warps' sums added in warp order;
+        // a phase entered after its step 0 goes to the block's colx slot
+        for (int e = tid; e < wl * 192; e += G * 32) {
             const int cb = e / 192, rem = e - cb * 192, c = rem & 31, q = rem >> 5;
-            const int64_t j = 32 * (J + cb) + c;
-            if (j < n) {
-                double sum = cs[0][cb][q][c];
+            double sum = cs[0][cb][q][c];
 #pragma unroll
-                for (int w = 1; w < kFp64GrpWarps; ++w) sum += cs[w][cb][q][c];
-                colpart[(g * 6 + q) * n + j] = sum;
+            for (int w = 1; w < G; ++w) sum += cs[w][cb][q][c];
+            if (cb == 0 && kfirst > 0) {
+                parts.colx[(b * 6 + q) * 32 + c] = sum;
+            } else {
+                const int64_t j = 32 * (J0 + cb) + c;
+                if (j < n) parts.col[(g * 6 + q) * n + j] = sum;
             }
         }
-        // leaving the group (or the block's range): this piece's row partial
-        if (gn != g || pn == p1) {
-            if (irow) {
-                const int64_t h = b - grp_owner(grp_start(g, nb, kFp64GrpWarps), B, P);
-                double *dst = rowpart + h * 6 * n;
+        // leaving the group (or the range): the block's row piece of the
+        // group, the warps' sums added in warp order (and cleared)
+        if (nxt.g != g || wln == 0) {
+            const int64_t h = b - grp_owner(32 * grp_before(L, g), B, L);
+            double *dst = parts.row + h * 6 * n;
+            for (int e = tid; e < R * 192; e += G * 32) {
+                const int r = e / 192, rem = e - r * 192, l = rem & 31, q = rem >> 5;
+                const int64_t i = 32 * (g * G + r) + l;
+                double sum = rs[0][r][q][l];
+                rs[0][r][q][l] = 0.0;
 #pragma unroll
-                for (int q = 0; q < 6; ++q) dst[q * n + i] = racc[q];
+                for (int w = 1; w < G; ++w) {
+                    sum += rs[w][r][q][l];
+                    rs[w][r][q][l] = 0.0;
+                }
+                if (i < n) dst[q * n + i] = sum;
             }
-            new_group = true;
         }
+        if (wln > 0) load_cols(nxt.g * G + nxt.t, wln);
         __syncthreads();  // the sums are read and the next column blocks stored
-        p = pn;
-        g = gn;
-        J = Jn;
+        cur = nxt;
         wl = wln;
-        buf ^= 1;
     }
     status = __reduce_or_sync(0xffffffffu, status);
     if (lane == 0 && status) atomicOr(a.status, status);
@@ -441,8 +467,8 @@ int pair_step_grp_blocks_per_sm(bool stats, bool learned, bool seed)
     return b > 0 ? b : 1;
 }
 
-void launch_pair_step_grp(const StepArgs &a, const GrpLayout &L, double *rowpart,
-                          double *colpart, int blocks, bool stats, cudaStream_t s)
+void launch_pair_step_grp(const StepArgs &a, const GrpLayout &L, const GrpParts &parts,
+                          int blocks, bool stats, cudaStream_t s)
 {
     const bool learned = a.mlp != nullptr;
     const bool seed = !learned && a.X32 != nullptr;
@@ -450,7 +476,8 @@ void launch_pair_step_grp(const StepArgs &a, const GrpLayout &L, double *rowpart
     const size_t smem = grp_smem(learned, seed);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     GrpLayout Lv = L;
-    void *args[] = {(void *)&a, (void *)&Lv, (void *)&rowpart, (void *)&colpart};
+    GrpParts pv = parts;
+    void *args[] = {(void *)&a, (void *)&Lv, (void *)&pv};
     launch_pdl(fn, dim3(blocks), dim3(kFp64GrpWarps * 32), args, smem, s);
 }
 

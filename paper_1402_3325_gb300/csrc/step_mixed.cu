@@ -213,13 +213,13 @@ __global__ void __launch_bounds__(WARPS * 32)
 // step_sym.cu, lane l owning row i = 32 I + l and solving column
 // (l + k) mod 32 at step k.  Row sums stay in the lane's registers for the
 // whole group; column sums go to the warp's shared-memory accumulators of
-// the phase.  The phases of all groups are numbered group by group (J
-// ascending) and split into contiguous, equal ranges over the persistent
-// grid.  A block takes its phases in windows of up to kGrpWindow phases of
-// one group: after each window a block barrier, then the block adds the
-// warps' column sums of each phase in warp order and writes one column
-// partial per particle of each block J; a block writes one row partial per
-// group it meets.  So the partial sums written per step are one 6-vector per
+// the phase.  The phases of all groups are split into contiguous, equal
+// ranges of whole phases over the persistent grid (grp_layout.cuh, chunks of
+// kMixedGrpChunk = 32 steps).  A block takes its phases in windows of up to
+// kGrpWindow phases of one group: after each window a block barrier, then
+// the block adds the warps' column sums of each phase in warp order and
+// writes one column partial per particle of each block J; a block writes one
+// row partial per group it meets.  So the partial sums written per step are one 6-vector per
 // particle per group that covers its column block, plus one per row piece:
 // about 30 MB at n = 16384, which stays in L2, against a 6-vector per
 // particle per tile segment in the earlier contiguous-range kernel (369 MB).
@@ -242,8 +242,7 @@ constexpr int kGrpWarps = kMixedGrpWarps;
 
 template <bool STATS, bool SEED>
 __global__ void __launch_bounds__(kGrpWarps * 32, 2)
-    pair_step_grp_mixed_kernel(StepArgs a, MixedArgs ma, GrpLayout L, double *rowpart,
-                               double *colpart)
+    pair_step_grp_mixed_kernel(StepArgs a, MixedArgs ma, GrpLayout L, GrpParts parts)
 {
     // dynamic shared memory (grp_smem_bytes): the warps' column sums of the
     // window, float4 q2 of column block slot cb holding components 2 q2 and
@@ -267,7 +266,6 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
     const unsigned lt_mask = (1u << lane) - 1u;
     const int64_t n = a.n;
     const int64_t nb = L.nb;
-    const int64_t P = L.P;
     const int64_t B = gridDim.x;
     const int64_t b = blockIdx.x;
     const float *X32 = ma.X32;
@@ -276,15 +274,24 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
     long long it_sum = 0, slots = 0, fallbacks = 0, n32 = 0, carries = 0;
     int it_max = 0;
 
-    const int64_t p0 = b * P / B, p1 = (b + 1) * P / B;
-    int64_t g = 0;
-    while (g + 1 < L.ng && grp_start(g + 1, nb, kGrpWarps) <= p0) ++g;
-    int64_t J = g * kGrpWarps + (p0 - grp_start(g, nb, kGrpWarps));
-    int64_t p = p0;
+    // the layout is made with the particles in array order (L.rev = 0):
+    // layout indices are particle indices throughout this kernel.
+    // the range: whole phases (L.S = 32), so every position has k = 0; its
+    // end is block-uniform and kept in shared memory (read once per window)
+    // rather than in registers
+    GrpPos cur = grp_block_start(L, b, B);
+    __shared__ GrpPos s_end;
+    if (tid == 0) s_end = grp_block_start(L, b + 1, B);
+    __syncthreads();
+    auto in_range = [&](const GrpPos &p) {
+        const GrpPos e = s_end;
+        return p.g < e.g || (p.g == e.g && p.t < e.t);
+    };
     // a window: up to kGrpWindow consecutive phases of one group within the
     // block's range
-    auto window_len = [&](int64_t pw, int64_t Jw) {
-        const int64_t m = nb - Jw < p1 - pw ? nb - Jw : p1 - pw;
+    auto window_len = [&](const GrpPos &p) {
+        const GrpPos e = s_end;
+        const int64_t m = p.g < e.g ? nb - p.g * kGrpWarps - p.t : e.t - p.t;
         return (int)(m < kGrpWindow ? m : kGrpWindow);
     };
     // the window's column blocks Jw .. Jw + len - 1 into cx[buf]
@@ -304,8 +311,8 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
             cx[buf][cb][r][c] = v;
         }
     };
-    int wl = p < p1 ? window_len(p, J) : 0;
-    if (wl > 0) load_cols(0, J, wl);
+    int wl = in_range(cur) ? window_len(cur) : 0;
+    if (wl > 0) load_cols(0, cur.g * kGrpWarps + cur.t, wl);
     __syncthreads();
 
     float hi_i[3] = {0, 0, 0}, lo_i[3] = {0, 0, 0}, v_i[3] = {0, 0, 0}, mfi = 1.0f;
@@ -407,6 +414,7 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
     };
 
     while (wl > 0) {
+        const int64_t g = cur.g, J = g * kGrpWarps + cur.t;
         const int64_t I = g * kGrpWarps + wib;
         const int64_t i = 32 * I + lane;
         const bool irow = I < nb && i < n;
@@ -499,14 +507,13 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
         if (tail > 0) flush(J, tail);
         __syncthreads();  // every warp's column sums of the window are complete
         // the next window; its column blocks are loaded now
-        const int64_t pn = p + wl;
-        int64_t gn = g, Jn = J + wl;
-        if (Jn == nb) {
-            gn = g + 1;
-            Jn = gn * kGrpWarps;
+        GrpPos nxt{g, cur.t + wl, 0};
+        if (nxt.t == nb - g * kGrpWarps) {
+            nxt.g = g + 1;
+            nxt.t = 0;
         }
-        const int wln = pn < p1 ? window_len(pn, Jn) : 0;
-        if (wln > 0) load_cols(buf ^ 1, Jn, wln);
+        const int wln = in_range(nxt) ? window_len(nxt) : 0;
+        if (wln > 0) load_cols(buf ^ 1, nxt.g * kGrpWarps + nxt.t, wln);
         // the window's column partials: the warps' sums added in warp order
         for (int e = tid; e < wl * 192; e += kGrpWarps * 32) {
             const int cb = e / 192, rem = e - cb * 192, c = rem & 31, q = rem >> 5;
@@ -518,23 +525,21 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
                     const float4 x = cacc[w][cb][q >> 1][c];
                     sum += (q & 1) ? ((double)x.z + (double)x.w) : ((double)x.x + (double)x.y);
                 }
-                colpart[(g * 6 + q) * n + j] = sum;
+                parts.col[(g * 6 + q) * n + j] = sum;
             }
         }
         // leaving the group (or the block's range): this piece's row partial
-        if (gn != g || pn == p1) {
+        if (nxt.g != g || wln == 0) {
             if (irow) {
-                const int64_t h = b - grp_owner(grp_start(g, nb, kGrpWarps), B, P);
-                double *dst = rowpart + h * 6 * n;
+                const int64_t h = b - grp_owner(32 * grp_before(L, g), B, L);
+                double *dst = parts.row + h * 6 * n;
 #pragma unroll
                 for (int q = 0; q < 6; ++q) dst[q * n + i] = (double)racc[q].h + (double)racc[q].l;
             }
             new_group = true;
         }
         __syncthreads();  // the sums are read and the next column blocks stored
-        p = pn;
-        g = gn;
-        J = Jn;
+        cur = nxt;
         wl = wln;
         buf ^= 1;
     }
@@ -576,11 +581,11 @@ const void *grp_kernel(bool stats, bool seed)
 }
 
 void launch_pair_step_grp_mixed(const StepArgs &a, const MixedArgs &ma, const GrpLayout &L,
-                                double *rowpart, double *colpart, int blocks, bool stats,
-                                cudaStream_t s)
+                                const GrpParts &parts, int blocks, bool stats, cudaStream_t s)
 {
     GrpLayout Lv = L;
-    void *args[] = {(void *)&a, (void *)&ma, (void *)&Lv, (void *)&rowpart, (void *)&colpart};
+    GrpParts pv = parts;
+    void *args[] = {(void *)&a, (void *)&ma, (void *)&Lv, (void *)&pv};
     const void *fn = grp_kernel(stats, a.X32 != nullptr);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGrpSmem);
     launch_pdl(fn, dim3(blocks), dim3(kGrpWarps * 32), args, kGrpSmem, s);

@@ -78,7 +78,8 @@ class Stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in
                 ("steps", "pairs", "iters", "max_iters", "warp_slots", "fp32_pairs",
                  "fallbacks", "solves", "timed_launches")] + [
-                     ("pair_kernel_ms", ctypes.c_double), ("carries", ctypes.c_int64)]
+                     ("pair_kernel_ms", ctypes.c_double), ("carries", ctypes.c_int64),
+                     ("group_launches", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: int(getattr(self, k)) for k, t in self._fields_ if t is ctypes.c_int64}

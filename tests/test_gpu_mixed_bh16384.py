@@ -124,6 +124,10 @@ def test_bh16384_mixed_step_sampled_against_oracle(system, rule):
     print(f"rule {rule}: fp32 share {st['fp32_pairs'] / st['pairs']:.4f},"
           f" one step vs oracle: r {er:.2e} v {ev:.2e}")
     assert er <= STEP_BOUND and ev <= STEP_BOUND
+    # the mixed form ran: single-precision pairs were solved, in the tile
+    # kernel with the inline class test (literal rule) or in row groups
+    assert st["fp32_pairs"] > 0
+    assert st["group_launches"] == (1 if rule == 1 else 0)
 
 
 @pytest.fixture(scope="module")
@@ -158,6 +162,7 @@ def _compare(form, s, golden, r, v, E, st, bound, ebound):
 ], ids=["mixed-literal", "mixed-hyp"])
 def test_bh16384_256_steps_against_cached_oracle_run(system, golden, form, opts):
     r, v, E, st = run_gpu(system, golden["steps"], **opts)
+    assert st["fp32_pairs"] > 0
     _compare(form, system, golden, r, v, E, st, 256 * STEP_BOUND, 1e-8)
 
 
@@ -165,6 +170,7 @@ def test_bh16384_fp64_256_steps_against_cached_oracle_run(system, golden):
     s = system
     steps = golden["steps"]
     r, v, E, st = run_gpu(s, steps, guess=sk.GUESS_FP32)
+    assert st["group_launches"] == steps  # the FP64 default at this size: row groups
     # the same run from a state moved by 1e-12 of each particle's scale
     R, V = scales(s)
     rng = np.random.default_rng(7)

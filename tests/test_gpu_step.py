@@ -466,7 +466,8 @@ def test_headline_evolve_32_steps_matches_oracle_and_single_steps():
     np.testing.assert_array_equal(v, v1)
 
 
-# --- the row-group kernel (the default from 8192 particles), forced on small systems ---
+# --- the row-group kernel (the FP64 default beyond about 13400 particles), forced on
+# small systems ---
 
 @pytest.mark.parametrize("guess", [sk.GUESS_STANDARD, sk.GUESS_TAYLOR, sk.GUESS_FP32])
 @pytest.mark.parametrize("order", [2, 1, -1])
@@ -482,9 +483,11 @@ def test_row_group_step_matches_oracle(name, s, order, guess):
 
 @pytest.mark.parametrize("blocks", [0, 1, 3, 7, 143, 144, 5000])
 def test_row_group_grid_shapes_agree_with_oracle(blocks):
-    # any grid: a block's phase range may start or end inside a group, and a
-    # group's row sums then come in several pieces (1024 particles: 8 groups,
-    # 144 phases)
+    # any grid: a block's range of phase-steps may start or end inside a
+    # group or inside a phase (7 or 143 blocks over 144 phases), a group's row
+    # sums then come in several pieces and a split phase's column sums in two
+    # or more slots (1024 particles: 8 groups, 144 phases; 5000 blocks are
+    # clamped to one phase each)
     s = ics.plummer(1024, seed=0)
     with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=sk.GUESS_FP32, grid_blocks=blocks,
                     flags=sk.FLAG_STATS | sk.FLAG_GROUPS):
@@ -495,6 +498,7 @@ def test_row_group_grid_shapes_agree_with_oracle(blocks):
     er, ev = rel_err(r, v, rr, vr)
     assert er <= TOL and ev <= TOL, (er, ev)
     assert st["carries"] == st["solves"]
+    assert st["group_launches"] == 1
 
 
 def test_row_group_and_tile_kernels_agree_and_are_deterministic():
@@ -505,8 +509,10 @@ def test_row_group_and_tile_kernels_agree_and_are_deterministic():
     for name, flag in (("tiles", sk.FLAG_TILES), ("groups", sk.FLAG_GROUPS)):
         with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=sk.GUESS_FP32,
                         flags=sk.FLAG_STATS | flag):
+            sk.get_stats(reset=True)
             out[name] = gpu_step(s, s.dt, 2)
             again = gpu_step(s, s.dt, 2)
+            assert sk.get_stats(reset=True)["group_launches"] == (2 if name == "groups" else 0)
         np.testing.assert_array_equal(out[name][0], again[0])
         np.testing.assert_array_equal(out[name][1], again[1])
     er, ev = rel_err(*out["groups"], *out["tiles"])
