@@ -16,6 +16,7 @@
 #include "mlp_infer.cuh"
 #include "step_batched.cuh"
 #include "step_common.cuh"
+#include "step_grp.cuh"
 #include "step_small.cuh"
 
 namespace {
@@ -216,8 +217,7 @@ int step_device_mixed_grp(const double *src, double *dst, const double *masses, 
         g.cfg.grid_blocks > 0
             ? g.cfg.grid_blocks
             : (int64_t)g.sm_count * sakura::pair_step_grp_mixed_blocks_per_sm(stats, seed);
-    const sakura::GrpLayout L = sakura::make_grp_layout(n, sakura::kMixedGrpWarps, sakura::kMixedGrpChunk, false,
-                                                        blocks);
+    const sakura::GrpLayout L = sakura::make_grp_layout(n, sakura::kMixedGrpShape, blocks);
     // scratch: X[7][n] doubles, row partials [Hmax][6][n], column partials
     // [ng][6][n] and [blocks][6][32], then X32[10][n] floats
     int rc = grow(g.partial, (size_t)(7 * n + (int64_t)(L.Hmax + L.ng) * 6 * n + blocks * 192 +
@@ -336,8 +336,7 @@ int step_device_fp64_grp(const double *src, double *dst, const double *masses, i
                          ? g.cfg.grid_blocks
                          : (int64_t)g.sm_count *
                                sakura::pair_step_grp_blocks_per_sm(stats, learned, seed);
-    const sakura::GrpLayout L = sakura::make_grp_layout(n, sakura::kFp64GrpWarps, sakura::kFp64GrpChunk, true,
-                                                        blocks);
+    const sakura::GrpLayout L = sakura::make_grp_layout(n, sakura::kFp64GrpShape, blocks);
     // scratch: X[7][n] doubles, row partials [Hmax][6][n], column partials
     // [ng][6][n] and [blocks][6][32], then X32[10][n] floats (single-precision
     // seed)

@@ -6,7 +6,6 @@
 #include <cstdint>
 
 #include "df64.cuh"
-#include "grp_layout.cuh"
 #include "kepler_fp32.cuh"
 
 namespace sakura {
@@ -86,30 +85,7 @@ void launch_prep_mixed(const double *state, const double *mass, double *X, float
 void launch_pair_step_mixed(const StepArgs &a, const MixedArgs &ma, int blocks, bool stats,
                             cudaStream_t s);
 int pair_step_mixed_blocks_per_sm(bool stats);
-// Row-group layout: grp_layout.cuh.
-
-// the partial sums of a row-group step: row [Hmax][6][n], col [ng][6][n],
-// colx [blocks][6][32] (see above)
-struct GrpParts {
-    double *row, *col, *colx;
-};
-// a.X32 (the float copy, as ma.X32) set: FP64-class pairs seeded by a
-// single-precision solve
-void launch_pair_step_grp_mixed(const StepArgs &a, const MixedArgs &ma, const GrpLayout &L,
-                                const GrpParts &parts, int blocks, bool stats, cudaStream_t s);
-int pair_step_grp_mixed_blocks_per_sm(bool stats, bool seed);
-// Eqs. 27b-d for the row-group layout; fuse: also the next sub-step's drift
-// (next_drift), writing its drifted copy to X (and X32, if not null) as the
-// prep kernel would, so that a run of steps needs no prep kernel after its
-// first
-void launch_apply_grp(double *state, double *X, float *X32, const GrpParts &parts, int64_t n,
-                      const GrpLayout &L, int64_t blocks, double post_drift, bool fuse,
-                      double next_drift, unsigned *status, cudaStream_t s);
-// the symmetric FP64 pair kernel in row-group phases (a.mlp: learned guess;
-// a.X32: single-precision seed)
-void launch_pair_step_grp(const StepArgs &a, const GrpLayout &L, const GrpParts &parts,
-                          int blocks, bool stats, cudaStream_t s);
-int pair_step_grp_blocks_per_sm(bool stats, bool learned, bool seed);
+// The row-group kernels' declarations: step_grp.cuh.
 // the FP32 class of every ordered pair as the mixed kernels decide it
 // (out: n x n bytes), from the float copy that launch_prep_mixed writes
 void launch_pair_classes(const float *X32, int64_t n, const ClassRule &rule, unsigned char *out,

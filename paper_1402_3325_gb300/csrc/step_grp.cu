@@ -41,6 +41,7 @@
 #include "mlp_infer.cuh"
 #include "pair_batch_fp64.cuh"
 #include "step_common.cuh"
+#include "step_grp.cuh"
 
 namespace sakura {
 
@@ -77,8 +78,8 @@ __global__ void __launch_bounds__(32 * kGrpApplyWarps)
     const int64_t Ib = blockIdx.x;
     const int64_t i = Ib * 32 + lane;
     const int64_t gi = Ib / L.G;
-    const int64_t u0 = 32 * grp_before(L, gi), u1 = 32 * grp_before(L, gi + 1) - 1;
-    const int npieces = (int)(grp_owner(u1, B, L) - grp_owner(u0, B, L)) + 1;
+    const int64_t x0 = grp_phase_x(L, gi, 0), x1 = grp_phase_last_x(L, gi, L.nb - gi * L.G - 1);
+    const int npieces = (int)(grp_owner(x1, B, L) - grp_owner(x0, B, L)) + 1;
     const int nslots = npieces + (int)gi + 1;
     double dr = 0.0, dv = 0.0;
     if (i < n) {
@@ -95,9 +96,9 @@ __global__ void __launch_bounds__(32 * kGrpApplyWarps)
             er += p[q * n + i];
             ev += p[(3 + q) * n + i];
             if (L.S == 32) return;  // whole phases: no phase is split
-            const int64_t up = 32 * (grp_before(L, gg) + Ib - gg * L.G);
-            const int64_t bl = grp_owner(up + 31, B, L);
-            for (int64_t bb = grp_owner(up, B, L) + 1; bb <= bl; ++bb) {
+            const int64_t t = Ib - gg * L.G;
+            const int64_t bl = grp_owner(grp_phase_last_x(L, gg, t), B, L);
+            for (int64_t bb = grp_owner(grp_phase_x(L, gg, t), B, L) + 1; bb <= bl; ++bb) {
                 er += parts.colx[(bb * 6 + q) * 32 + lane];
                 ev += parts.colx[(bb * 6 + 3 + q) * 32 + lane];
             }
@@ -394,7 +395,7 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
         // leaving the group (or the range): the block's row piece of the
         // group, the warps' sums added in warp order (and cleared)
         if (nxt.g != g || wln == 0) {
-            const int64_t h = b - grp_owner(32 * grp_before(L, g), B, L);
+            const int64_t h = b - grp_owner(grp_phase_x(L, g, 0), B, L);
             double *dst = parts.row + h * 6 * n;
             for (int e = tid; e < R * 192; e += G * 32) {
                 const int r = e / 192, rem = e - r * 192, l = rem & 31, q = rem >> 5;

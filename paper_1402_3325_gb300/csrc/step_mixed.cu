@@ -23,6 +23,7 @@
 #include "kepler_fp64.cuh"
 #include "pair_batch_fp64.cuh"
 #include "step_common.cuh"
+#include "step_grp.cuh"
 
 namespace sakura {
 
@@ -214,12 +215,13 @@ __global__ void __launch_bounds__(WARPS * 32)
 // (l + k) mod 32 at step k.  Row sums stay in the lane's registers for the
 // whole group; column sums go to the warp's shared-memory accumulators of
 // the phase.  The phases of all groups are split into contiguous, equal
-// ranges of whole phases over the persistent grid (grp_layout.cuh, chunks of
-// kMixedGrpChunk = 32 steps).  A block takes its phases in windows of up to
-// kGrpWindow phases of one group: after each window a block barrier, then
-// the block adds the warps' column sums of each phase in warp order and
-// writes one column partial per particle of each block J; a block writes one
-// row partial per group it meets.  So the partial sums written per step are one 6-vector per
+// ranges of whole phases over the persistent grid (grp_layout.cuh,
+// kMixedGrpShape: whole phases, each of the same cost).  A block takes its
+// phases in windows of up to kGrpWindow phases of one group: after each
+// window a block barrier, then the block adds the warps' column sums of each
+// phase in warp order and writes one column partial per particle of each
+// block J; a block writes one row partial per group it meets.  So the
+// partial sums written per step are one 6-vector per
 // particle per group that covers its column block, plus one per row piece:
 // about 30 MB at n = 16384, which stays in L2, against a 6-vector per
 // particle per tile segment in the earlier contiguous-range kernel (369 MB).
@@ -531,7 +533,7 @@ __global__ void __launch_bounds__(kGrpWarps * 32, 2)
         // leaving the group (or the block's range): this piece's row partial
         if (nxt.g != g || wln == 0) {
             if (irow) {
-                const int64_t h = b - grp_owner(32 * grp_before(L, g), B, L);
+                const int64_t h = b - grp_owner(grp_phase_x(L, g, 0), B, L);
                 double *dst = parts.row + h * 6 * n;
 #pragma unroll
                 for (int q = 0; q < 6; ++q) dst[q * n + i] = (double)racc[q].h + (double)racc[q].l;
