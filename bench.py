@@ -211,6 +211,7 @@ class ClockSampler:
 # the source file of each profiled kernel
 KERNEL_SOURCES = {"pair_step_sym": "step_sym.cu", "pair_step_grp": "step_grp.cu",
                   "pair_step_fp64": "step_fp64.cu", "pair_step_sym_df64": "step_df64.cu",
+                  "pair_step_grp_df64": "step_df64.cu",
                   "pair_step_grp_mixed": "step_mixed.cu", "pair_step_mixed": "step_mixed.cu",
                   "small": "step_small.cu", "batched": "step_batched.cu"}
 
@@ -615,7 +616,8 @@ def _roofline(workload, form, pairs, guess, n, small, m):
         peak, pipe, src = FP32_PEAK_GFLOPS / 1e3, "fp32", fp32_peak_src + (
             "; flops per solve counted by running the double-word code on the host with an"
             " operation tally")
-        kname = "small" if small else "pair_step_sym_df64"
+        kname = "small" if small else (
+            "pair_step_grp_df64" if m["row_groups"] else "pair_step_sym_df64")
     elif form == "mixed" and pairs == "symmetric" and share >= 0.5:
         # FP32 flops of an FP32-class unordered pair (hand count from
         # csrc/kepler_fp32.cuh and csrc/step_mixed.cu, FMA = 2): class test

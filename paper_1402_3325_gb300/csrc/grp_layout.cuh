@@ -82,6 +82,11 @@ struct GrpShape {
 };
 constexpr GrpShape kFp64GrpShape{kFp64GrpWarps, 1, 2, 1, true};
 constexpr GrpShape kMixedGrpShape{kMixedGrpWarps, 32, 1, 0, false};
+// the double-word form (step_df64.cu): 4 warps per block, 3 blocks per SM;
+// whole phases (its loop, FP32-issue-bound like the mixed kernel's, stays
+// free of range tests), weighted like the FP64 kernel's, particles reversed
+constexpr int kDf64GrpWarps = 4;
+constexpr GrpShape kDf64GrpShape{kDf64GrpWarps, 32, 2, 1, true};
 
 // row blocks of group g (0 past the last group)
 GRP_HD int64_t grp_rows(const GrpLayout &L, int64_t g)

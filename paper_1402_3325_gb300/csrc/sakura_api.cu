@@ -322,6 +322,87 @@ bool fp64_groups(int64_t n)
     return tile_partial_bytes(n) > kFp64TileMaxBytes;
 }
 
+// The double-word form: tiles below kFp64TileMaxBytes of tile partials, row
+// groups beyond; the flags force either.
+bool df64_groups(int64_t n)
+{
+    if (g.cfg.flags & SAKURA_FLAG_GROUPS) return true;
+    if (g.cfg.flags & SAKURA_FLAG_TILES) return false;
+    return tile_partial_bytes(n) > kFp64TileMaxBytes;
+}
+
+// The double-word form in row-group phases (step_df64.cu): prep (drift and
+// three-float copy), pair and apply kernels.
+int step_device_df64_grp(const double *src, double *dst, const double *masses, int64_t n,
+                         double dt, int order)
+{
+    const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
+    int64_t blocks = g.cfg.grid_blocks > 0
+                         ? g.cfg.grid_blocks
+                         : (int64_t)g.sm_count * sakura::pair_step_grp_df64_blocks_per_sm(stats);
+    const sakura::GrpLayout L = sakura::make_grp_layout(n, sakura::kDf64GrpShape, blocks);
+    // scratch: X[7][n] doubles, row partials [Hmax][6][n], column partials
+    // [ng][6][n] and [blocks][6][32], then X3[20][n] floats
+    int rc = grow(g.partial, (size_t)(7 * n + (int64_t)(L.Hmax + L.ng) * 6 * n + blocks * 192 +
+                                      10 * n) *
+                                 sizeof(double));
+    if (rc) return rc;
+    double *X = (double *)g.partial.ptr;
+    sakura::GrpParts parts;
+    parts.row = X + 7 * n;
+    parts.col = parts.row + (int64_t)L.Hmax * 6 * n;
+    parts.colx = parts.col + (int64_t)L.ng * 6 * n;
+    float *X3 = (float *)(parts.colx + blocks * 192);
+    const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
+    const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
+    sakura::launch_prep_df64(src, masses, X, X3, n, drift, g.d_status, g.stream);
+    sakura::StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.X = X;
+    a.n = n;
+    a.tau = dt;
+    a.pre = order == 2 ? 0.5 : (order == 1 ? 0.0 : 1.0);
+    a.post = 1.0 - a.pre;
+    a.tol = g.cfg.kepler_tol * DBL_EPSILON;
+    a.max_iter = g.cfg.kepler_max_iter;
+    a.bisection = g.cfg.kepler_bisection;
+    a.guess = (g.cfg.guess == SAKURA_GUESS_TAYLOR || g.cfg.guess == SAKURA_GUESS_FP32) ? 2 : 0;
+    a.status = g.d_status;
+    a.stats = g.d_stats;
+    sakura::DwArgs da;
+    da.X3 = X3;
+    da.ptau32 = (float)(a.pre * dt);
+    da.t32 = (float)dt;
+    da.ptau = split_dw(a.pre * dt);
+    da.t = split_dw(dt);
+    da.qtau = split_dw(a.post * dt);
+    const bool timing = (g.cfg.flags & SAKURA_FLAG_TIMING) != 0;
+    std::pair<cudaEvent_t, cudaEvent_t> tm{nullptr, nullptr};
+    if (timing) {
+        tm = take_timer();
+        cudaEventRecord(tm.first, g.stream);
+    }
+    sakura::launch_pair_step_grp_df64(a, da, L, parts, (int)blocks, stats, g.stream);
+    g.group_launches += 1;
+    if (timing) {
+        cudaEventRecord(tm.second, g.stream);
+        g.timers.push_back(tm);
+    }
+    sakura::launch_apply_grp(dst, X, nullptr, parts, n, L, blocks, post_drift, false, 0.0,
+                             g.d_status, g.stream);
+    rc = launch_error();
+    if (rc) return rc;
+    g.steps += 1;
+    g.pairs += n * (n - 1);
+    int64_t diag = 0;  // ordered pairs inside diagonal tiles
+    for (int64_t b = 0; b < L.nb; ++b) {
+        const int64_t nbk = std::min<int64_t>(32, n - 32 * b);
+        diag += nbk * (nbk - 1);
+    }
+    g.solves += (n * (n - 1) - diag) / 2 + diag;
+    return SAKURA_OK;
+}
+
 // The FP64 form with each unordered pair once, in row-group phases
 // (step_grp.cu).  prepped: X (and X32) already hold this sub-step's drifted
 // state, written by the previous apply kernel; fuse: the apply kernel also
@@ -407,6 +488,7 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
                     double next_drift = 0.0)
 {
     if (mixed && !mixed_tiles(n)) return step_device_mixed_grp(src, dst, masses, n, dt, order);
+    if (df64 && df64_groups(n)) return step_device_df64_grp(src, dst, masses, n, dt, order);
     if (!df64 && !mixed && fp64_groups(n))
         return step_device_fp64_grp(src, dst, masses, n, dt, order, prepped, fuse, next_drift);
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
@@ -514,7 +596,9 @@ constexpr double kSymMaxBytes = 16.0 * 1024 * 1024 * 1024;
 bool sym_path(int64_t n)
 {
     if (g.cfg.pair_mode != SAKURA_PAIRS_SYMMETRIC || n < 2) return false;
-    if (g.cfg.precision == SAKURA_PREC_DF64) return tile_partial_bytes(n) <= kSymMaxBytes;
+    if (g.cfg.precision == SAKURA_PREC_DF64)
+        return (df64_groups(n) ? group_partial_bytes(n, sakura::kDf64GrpWarps)
+                               : tile_partial_bytes(n)) <= kSymMaxBytes;
     if (g.cfg.precision == SAKURA_PREC_MIXED)
         return mixed_tiles(n) || group_partial_bytes(n, sakura::kMixedGrpWarps) <= kSymMaxBytes;
     return (fp64_groups(n) ? group_partial_bytes(n, sakura::kFp64GrpWarps)

@@ -18,6 +18,12 @@
 //   (contiguous tile-step ranges per warp, step_common.cuh).
 // apply kernel: Eqs. 27b-d with the slots added in double-word arithmetic
 //   and converted to FP64 once per particle.
+// Row-group form (pair_step_grp_df64_kernel, the default where the tile
+//   partials would pass 2 GB): the same pair solves in the row-group phases
+//   of the mixed kernel (step_mixed.cu): 4 warps per block, column sums as
+//   double-words in shared memory reduced per window, row sums in registers;
+//   the partial sums go out in FP64 (a double-word is a double exactly) to
+//   the row-group apply kernel (step_grp.cu).
 #include <cuda_runtime.h>
 
 #include "df64.cuh"
@@ -25,6 +31,7 @@
 #include "kepler_fp64.cuh"
 #include "pair_batch_fp64.cuh"
 #include "step_common.cuh"
+#include "step_grp.cuh"
 
 namespace sakura {
 
@@ -334,6 +341,334 @@ __global__ void __launch_bounds__(32 * kApplyDwWarps)
     state[(3 + q) * n + i] = v1;
 }
 
+// Row-group form.  A block of kDf64GrpWarps warps takes a group of as many
+// row blocks (warp w: row block I = g G + w in layout order, particle
+// grp_particle(i)) and sweeps the column blocks J >= g G with them, one
+// phase per J, in windows of up to kGrpWindow phases of one group (whole
+// phases, grp_layout.cuh).  Column blocks of a window are staged in shared
+// memory (20 floats per particle, double buffered); each warp adds its column
+// sums of the window as double-words into its own shared-memory
+// accumulators, which the block adds in warp order after the window's
+// barrier; row sums stay in registers for the whole group.  Pairs the
+// double-word solve rejects join the warp's FP64 queue, solved 32 at a time
+// and drained at the end of each window.
+constexpr int kDf64GrpWin = kGrpWindow;
+constexpr size_t kDf64GrpSmem = sizeof(float4) * (kDf64GrpWarps * 3 + 2 * 5) * kDf64GrpWin * 32 +
+                                sizeof(int) * 2 * kDf64GrpWarps * 64 +
+                                sizeof(float2) * kDf64GrpWarps * 32 * 12;
+
+template <bool STATS>
+__global__ void __launch_bounds__(kDf64GrpWarps * 32, 3)
+    pair_step_grp_df64_kernel(StepArgs a, DwArgs da, GrpLayout L, GrpParts parts)
+{
+    constexpr int G = kDf64GrpWarps;
+    constexpr int WIN = kDf64GrpWin;
+    // dynamic shared memory: the warps' column sums of the window (float4
+    // q2 of column block slot cb: components 2 q2 and 2 q2 + 1 as
+    // double-words h, l, h, l); the window's column blocks, double buffered
+    // (rows 0..19 of X3 as five float4); the FP64 queues and their results
+    extern __shared__ __align__(16) unsigned char gsm[];
+    float4(*cacc)[WIN][3][32] = reinterpret_cast<float4(*)[WIN][3][32]>(gsm);
+    float4(*cx)[WIN][5][32] =
+        reinterpret_cast<float4(*)[WIN][5][32]>(gsm + sizeof(float4) * G * WIN * 3 * 32);
+    int(*queue_i)[64] =
+        reinterpret_cast<int(*)[64]>(gsm + sizeof(float4) * (G * 3 + 2 * 5) * WIN * 32);
+    int(*queue_j)[64] = queue_i + G;
+    float2(*qres)[32][12] = reinterpret_cast<float2(*)[32][12]>(queue_j + G);
+    griddep_wait();    // X and X3 from the prep kernel
+    griddep_launch();  // the apply kernel may begin launching
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int tid = threadIdx.x;
+    int *qi = queue_i[wib], *qj = queue_j[wib];
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int64_t n = a.n;
+    const int64_t nb = L.nb;
+    const int64_t B = gridDim.x;
+    const int64_t b = blockIdx.x;
+    const float *X3 = da.X3;
+    const KeplerParams kp{a.tol, a.max_iter, a.bisection};
+    const int guess = a.guess == 1 ? 2 : a.guess;
+    unsigned status = 0;
+    long long it_sum = 0, slots = 0, fallbacks = 0, ndw = 0;
+    int it_max = 0;
+
+    // the range: whole phases (L.S = 32); its end is block-uniform and kept
+    // in shared memory
+    GrpPos cur = grp_block_start(L, b, B);
+    __shared__ GrpPos s_end;
+    if (tid == 0) s_end = grp_block_start(L, b + 1, B);
+    __syncthreads();
+    auto in_range = [&](const GrpPos &p) {
+        const GrpPos e = s_end;
+        return p.g < e.g || (p.g == e.g && p.t < e.t);
+    };
+    auto window_len = [&](const GrpPos &p) {
+        const GrpPos e = s_end;
+        const int64_t m = p.g < e.g ? nb - p.g * G - p.t : e.t - p.t;
+        return (int)(m < WIN ? m : WIN);
+    };
+    // the window's column blocks Jw .. Jw + len - 1 into cx[buf]
+    auto load_cols = [&](int buf, int64_t Jw, int len) {
+        for (int e = tid; e < len * 160; e += G * 32) {
+            const int cb = e / 160, r = (e >> 5) % 5, c = e & 31;
+            const int64_t j = 32 * (Jw + cb) + c;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (j < n) {
+                const int64_t jp = grp_particle(L, n, j);
+                v = make_float4(X3[(4 * r) * n + jp], X3[(4 * r + 1) * n + jp],
+                                X3[(4 * r + 2) * n + jp], X3[(4 * r + 3) * n + jp]);
+            }
+            cx[buf][cb][r][c] = v;
+        }
+    };
+    int wl = in_range(cur) ? window_len(cur) : 0;
+    if (wl > 0) load_cols(0, cur.g * G + cur.t, wl);
+    __syncthreads();
+
+    float xi[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) xi[q] = 0.0f;
+    dw mi = {1.0f, 0.0f};
+    dw racc[6];
+    bool new_group = true;
+    int buf = 0;
+
+    // FP64 solve of queue entries 0..cnt-1 (layout indices), all of the
+    // current window (column blocks Jw ..); their increments are added in
+    // queue order to the row owners' sums and the warp's column sums
+    auto flush = [&](int64_t Jw, int cnt) {
+        const bool vq = lane < cnt;
+        const int64_t iq = vq ? qi[lane] : 0, jq = vq ? qj[lane] : 0;
+        PairSolve ps;
+        double miq = 0.0, mjq = 0.0;
+        if (vq) {
+            const double *X = a.X;
+            const int64_t ip = grp_particle(L, n, iq), jp = grp_particle(L, n, jq);
+            miq = X[6 * n + ip];
+            mjq = X[6 * n + jp];
+            pair_setup(ps, a.tau, miq + mjq, X[ip] - X[jp], X[n + ip] - X[n + jp],
+                       X[2 * n + ip] - X[2 * n + jp], X[3 * n + ip] - X[3 * n + jp],
+                       X[4 * n + ip] - X[4 * n + jp], X[5 * n + ip] - X[5 * n + jp], a.pre,
+                       guess);
+        } else {
+            ps.done = true;
+            ps.beta = ps.s = 0.0;
+            ps.iters = 0;
+            ps.status = 0;
+        }
+        double d[6];
+        int iters = 0, fb = 0;
+        fp64_solve_warp(ps, vq, a.tau, a.post * a.tau, kp, d, iters, fb);
+        if (vq) {
+            status |= ps.status;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const double xr = mjq * d[q], xc = -miq * d[q];
+                const float rh = __double2float_rn(xr), ch = __double2float_rn(xc);
+                qres[wib][lane][q] = make_float2(rh, __double2float_rn(xr - (double)rh));
+                qres[wib][lane][6 + q] = make_float2(ch, __double2float_rn(xc - (double)ch));
+            }
+        }
+        if (STATS) {
+            it_sum += iters;
+            fallbacks += fb;
+            it_max = max(it_max, iters);
+            const int wmax = __reduce_max_sync(0xffffffffu, iters);
+            if (lane == 0) slots += 32LL * wmax;
+        }
+        __syncwarp();
+        for (int e = 0; e < cnt; ++e) {
+            const int ie = qi[e], je = qj[e];
+            if ((ie & 31) == lane) {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const float2 x = qres[wib][e][q];
+                    dw_acc(racc[q], dw{x.x, x.y});
+                }
+            }
+            // the diagonal tile keeps row sums only
+            if ((ie >> 5) != (je >> 5) && (je & 31) == lane) {
+                const int cb = (int)((je >> 5) - Jw);
+#pragma unroll
+                for (int q2 = 0; q2 < 3; ++q2) {
+                    const float4 x = cacc[wib][cb][q2][lane];
+                    dw a0{x.x, x.y}, a1{x.z, x.w};
+                    const float2 y0 = qres[wib][e][6 + 2 * q2], y1 = qres[wib][e][7 + 2 * q2];
+                    dw_acc(a0, dw{y0.x, y0.y});
+                    dw_acc(a1, dw{y1.x, y1.y});
+                    cacc[wib][cb][q2][lane] = make_float4(a0.h, a0.l, a1.h, a1.l);
+                }
+            }
+        }
+        __syncwarp();
+    };
+
+    while (wl > 0) {
+        const int64_t g = cur.g, J = g * G + cur.t;
+        const int64_t I = g * G + wib;
+        const int64_t i = 32 * I + lane;
+        const bool irow = I < nb && i < n;
+        if (new_group) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) racc[q] = dw{0.0f, 0.0f};
+            if (irow) {
+                const int64_t ip = grp_particle(L, n, i);
+#pragma unroll
+                for (int q = 0; q < 18; ++q) xi[q] = X3[q * n + ip];
+                mi = {X3[18 * n + ip], X3[19 * n + ip]};
+            }
+            new_group = false;
+        }
+        for (int cb = 0; cb < wl; ++cb) {
+#pragma unroll
+            for (int q2 = 0; q2 < 3; ++q2)
+                cacc[wib][cb][q2][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+        int tail = 0;
+        for (int cb = 0; cb < wl; ++cb) {
+            const int64_t Jt = J + cb;
+            if (!(I <= Jt && I < nb)) continue;  // warp-uniform: no tile (I, Jt)
+            const bool diag = I == Jt;
+            for (int k = 0; k < 32; ++k) {
+                const int c = (lane + k) & 31;
+                const int64_t j = 32 * Jt + c;
+                const bool valid = irow && j < n && (!diag || c != lane);
+                dw rr[3], vv[3], mj = {0.0f, 0.0f};
+                K32 o;
+                o.ok = false;
+                o.x = 0.0f;
+                o.s = 0.0f;
+                o.iters = 0;
+                if (valid) {
+                    const float4 c0 = cx[buf][cb][0][c], c1 = cx[buf][cb][1][c],
+                                 c2 = cx[buf][cb][2][c], c3 = cx[buf][cb][3][c],
+                                 c4 = cx[buf][cb][4][c];
+                    const float cj[20] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z,
+                                          c1.w, c2.x, c2.y, c2.z, c2.w, c3.x, c3.y,
+                                          c3.z, c3.w, c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        rr[q] = tf_diff(xi[3 * q], xi[3 * q + 1], xi[3 * q + 2], cj[3 * q],
+                                        cj[3 * q + 1], cj[3 * q + 2]);
+                        vv[q] = tf_diff(xi[9 + 3 * q], xi[10 + 3 * q], xi[11 + 3 * q],
+                                        cj[9 + 3 * q], cj[10 + 3 * q], cj[11 + 3 * q]);
+                    }
+                    mj = {cj[18], cj[19]};
+                    o = dw_phase1(rr, vv, dw_add(mi, mj), da.ptau32, da.t32, guess);
+                }
+                const bool big = __any_sync(0xffffffffu, o.ok && fabsf(o.x) > 0x1p-8f);
+                bool solved = false;
+                int evals = 0;
+                dw d[6];
+                if (o.ok)
+                    solved = dw_phase2(rr, vv, dw_add(mi, mj), da.ptau, da.t, da.qtau, o.s, big,
+                                       d, evals);
+                if (solved) {
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) dw_acc(racc[q], dw_mul(mj, d[q]));
+                    if (!diag) {
+                        const dw nmi = dw_neg(mi);
+#pragma unroll
+                        for (int q2 = 0; q2 < 3; ++q2) {
+                            const float4 x = cacc[wib][cb][q2][c];
+                            dw a0{x.x, x.y}, a1{x.z, x.w};
+                            dw_acc(a0, dw_mul(nmi, d[2 * q2]));
+                            dw_acc(a1, dw_mul(nmi, d[2 * q2 + 1]));
+                            cacc[wib][cb][q2][c] = make_float4(a0.h, a0.l, a1.h, a1.l);
+                        }
+                    }
+                }
+                if (STATS) {
+                    const int it = o.iters + evals;
+                    it_sum += it;
+                    it_max = max(it_max, it);
+                    ndw += solved ? 1 : 0;
+                    const int wmax = __reduce_max_sync(0xffffffffu, it);
+                    if (lane == 0) slots += 32LL * wmax;
+                }
+                const bool need64 = valid && !solved;
+                const unsigned mask = __ballot_sync(0xffffffffu, need64);
+                if (need64) {
+                    qi[tail + __popc(mask & lt_mask)] = (int)i;
+                    qj[tail + __popc(mask & lt_mask)] = (int)j;
+                }
+                tail += __popc(mask);
+                __syncwarp();
+                if (tail >= 32) {
+                    flush(J, 32);
+                    if (lane < tail - 32) {
+                        qi[lane] = qi[32 + lane];
+                        qj[lane] = qj[32 + lane];
+                    }
+                    __syncwarp();
+                    tail -= 32;
+                }
+            }
+        }
+        if (tail > 0) flush(J, tail);
+        __syncthreads();  // every warp's column sums of the window are complete
+        // the next window; its column blocks are loaded now
+        GrpPos nxt{g, cur.t + wl, 0};
+        if (nxt.t == nb - g * G) {
+            nxt.g = g + 1;
+            nxt.t = 0;
+        }
+        const int wln = in_range(nxt) ? window_len(nxt) : 0;
+        if (wln > 0) load_cols(buf ^ 1, nxt.g * G + nxt.t, wln);
+        // the window's column partials: the warps' double-words added in
+        // warp order, in FP64
+        for (int e = tid; e < wl * 192; e += G * 32) {
+            const int cb = e / 192, rem = e - cb * 192, c = rem & 31, q = rem >> 5;
+            const int64_t j = 32 * (J + cb) + c;
+            if (j < n) {
+                double sum = 0.0;
+#pragma unroll
+                for (int w = 0; w < G; ++w) {
+                    const float4 x = cacc[w][cb][q >> 1][c];
+                    sum += (q & 1) ? ((double)x.z + (double)x.w) : ((double)x.x + (double)x.y);
+                }
+                parts.col[(g * 6 + q) * n + j] = sum;
+            }
+        }
+        // leaving the group (or the block's range): this piece's row partial
+        if (nxt.g != g || wln == 0) {
+            if (irow) {
+                const int64_t h = b - grp_owner(grp_phase_x(L, g, 0), B, L);
+                double *dst = parts.row + h * 6 * n;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) dst[q * n + i] = (double)racc[q].h + (double)racc[q].l;
+            }
+            new_group = true;
+        }
+        __syncthreads();  // the sums are read and the next column blocks stored
+        cur = nxt;
+        wl = wln;
+        buf ^= 1;
+    }
+    status = __reduce_or_sync(0xffffffffu, status);
+    if (lane == 0 && status) atomicOr(a.status, status);
+    if (STATS) {
+        long long s1 = it_sum, s2 = slots, s3 = fallbacks, s4 = ndw;
+        int mx = it_max;
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+            s4 += __shfl_xor_sync(0xffffffffu, s4, o);
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        if (lane == 0) {
+            atomicAdd(&a.stats[kStatIters], (unsigned long long)s1);
+            atomicAdd(&a.stats[kStatSlots], (unsigned long long)s2);
+            atomicAdd(&a.stats[kStatFallbacks], (unsigned long long)s3);
+            atomicAdd(&a.stats[kStatFp32Pairs], (unsigned long long)s4);
+            atomicMax(&a.stats[kStatMaxIters], (unsigned long long)mx);
+        }
+    }
+}
+
 namespace {
 
 const void *df64_kernel(bool stats)
@@ -381,6 +716,41 @@ void launch_apply_df64(double *state, const double *X, const void *partial, int6
                     (void *)&status};
     launch_pdl((const void *)apply_df64_kernel, dim3((unsigned)((n + 31) / 32), 3),
                dim3(32 * kApplyDwWarps), args, 0, s);
+}
+
+namespace {
+
+const void *grp_df64_kernel(bool stats)
+{
+    return stats ? (const void *)pair_step_grp_df64_kernel<true>
+                 : (const void *)pair_step_grp_df64_kernel<false>;
+}
+
+}  // namespace
+
+int pair_step_grp_df64_blocks_per_sm(bool stats)
+{
+    const void *fn = grp_df64_kernel(stats);
+    int b = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDf64GrpSmem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kDf64GrpWarps * 32, kDf64GrpSmem) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return b > 0 ? b : 1;
+}
+
+void launch_pair_step_grp_df64(const StepArgs &a, const DwArgs &da, const GrpLayout &L,
+                               const GrpParts &parts, int blocks, bool stats, cudaStream_t s)
+{
+    const void *fn = grp_df64_kernel(stats);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDf64GrpSmem);
+    GrpLayout Lv = L;
+    GrpParts pv = parts;
+    void *args[] = {(void *)&a, (void *)&da, (void *)&Lv, (void *)&pv};
+    launch_pdl(fn, dim3(blocks), dim3(kDf64GrpWarps * 32), args, kDf64GrpSmem, s);
 }
 
 }  // namespace sakura

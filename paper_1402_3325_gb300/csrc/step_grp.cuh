@@ -31,5 +31,10 @@ void launch_apply_grp(double *state, double *X, float *X32, const GrpParts &part
 void launch_pair_step_grp(const StepArgs &a, const GrpLayout &L, const GrpParts &parts,
                           int blocks, bool stats, cudaStream_t s);
 int pair_step_grp_blocks_per_sm(bool stats, bool learned, bool seed);
+// the double-word form in row-group phases (step_df64.cu): X3 from
+// launch_prep_df64, partial sums in FP64 for launch_apply_grp
+void launch_pair_step_grp_df64(const StepArgs &a, const DwArgs &da, const GrpLayout &L,
+                               const GrpParts &parts, int blocks, bool stats, cudaStream_t s);
+int pair_step_grp_df64_blocks_per_sm(bool stats);
 
 }  // namespace sakura

@@ -51,7 +51,8 @@ def test_profile_summaries_match_the_current_kernel_sources(path):
         pytest.skip("summary without a source hash")
     name = os.path.basename(path)[:-3]
     kernel = next(k for k in ("small", "batched", "pair_step_sym_df64", "pair_step_fp64",
-                              "pair_step_grp_mixed", "pair_step_grp", "pair_step_sym")
+                              "pair_step_grp_mixed", "pair_step_grp_df64", "pair_step_grp",
+                              "pair_step_sym")
                   if name.startswith(k + "_"))
     assert vals["kernel_sources_sha256_16"] == bench._kernel_sources_hash(kernel), (
         f"{name}: the kernel changed since this summary was taken")

@@ -7,7 +7,10 @@ Covers every order, N from 2 to 16384 (ragged tiles, diagonal tiles, a
 single tile), grid shapes down to one block, the FP64 fallback queue (a
 swarm of fast flybys whose pairs leave single-precision range, tight
 binaries whose step exceeds the period), composed orders, determinism and
-the statistics of the double-word solves.
+the statistics of the double-word solves; for both symmetric kernels, the
+systolic tiles (the default below about 13400 bodies) and the row-group
+phases (the default beyond, forced with SAKURA_FLAG_GROUPS on the small
+cases).
 """
 import contextlib
 import os
@@ -94,6 +97,50 @@ def test_df64_plummer_1024_and_grid_shapes(blocks):
     assert er <= TOL and ev <= TOL, (er, ev)
 
 
+KERNELS = [(sk.FLAG_TILES, 0), (sk.FLAG_GROUPS, 1)]
+
+
+@pytest.mark.parametrize("order", [2, 1, -1])
+@pytest.mark.parametrize("name,s", SMALL, ids=[n for n, _ in SMALL])
+def test_df64_row_groups_match_oracle(name, s, order):
+    # (systems of up to 20 bodies otherwise run in the single-block kernel)
+    with configured(flags=sk.FLAG_STATS | sk.FLAG_GROUPS | sk.FLAG_NO_SMALL):
+        sk.get_stats(reset=True)
+        r, v = gpu_step(s, s.dt, order)
+        st = sk.get_stats(reset=True)
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, order, nthreads=NCPU)
+    assert rc == oracle.OK
+    er, ev = rel_err(r, v, rr, vr)
+    assert er <= TOL and ev <= TOL, (er, ev)
+    assert st["group_launches"] == 1
+
+
+@pytest.mark.parametrize("blocks", [0, 1, 7, 143, 5000])
+def test_df64_row_group_grid_shapes(blocks):
+    # 1024 particles: 8 groups of 4 row blocks, 144 phases dealt whole; a
+    # block's range may start or end inside a group (7 or 143 blocks), 5000
+    # are clamped
+    s = ics.plummer(1024, seed=0)
+    with configured(grid_blocks=blocks, flags=sk.FLAG_STATS | sk.FLAG_GROUPS):
+        r, v = gpu_step(s, s.dt, 2)
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
+    er, ev = rel_err(r, v, rr, vr)
+    assert er <= TOL and ev <= TOL, (er, ev)
+
+
+def test_df64_tiles_and_row_groups_agree_and_are_deterministic():
+    s = ics.random_cluster(3001, seed=4, mass_spread=2.0)
+    out = {}
+    for flag, _ in KERNELS:
+        with configured(flags=sk.FLAG_STATS | flag):
+            out[flag] = gpu_step(s, s.dt, 2)
+            again = gpu_step(s, s.dt, 2)
+        np.testing.assert_array_equal(out[flag][0], again[0])
+        np.testing.assert_array_equal(out[flag][1], again[1])
+    er, ev = rel_err(*out[sk.FLAG_GROUPS], *out[sk.FLAG_TILES])
+    assert er <= TOL and ev <= TOL, (er, ev)
+
+
 def _full_size_sample(s, k=48, seed=0):
     rng = np.random.default_rng(seed)
     idx = np.unique(np.concatenate([[0, s.n - 1], rng.choice(s.n, k, replace=False)]))
@@ -107,33 +154,49 @@ def _full_size_sample(s, k=48, seed=0):
     return float(er.max()), float(ev.max())
 
 
-def test_df64_full_size_bh_cluster_sampled():
-    er, ev = _full_size_sample(ics.bh_cluster(16384, seed=0))
+@pytest.mark.parametrize("flag,groups", KERNELS, ids=["tiles", "groups"])
+def test_df64_full_size_bh_cluster_sampled(flag, groups):
+    with configured(flags=sk.FLAG_STATS | flag):
+        sk.get_stats(reset=True)
+        er, ev = _full_size_sample(ics.bh_cluster(16384, seed=0))
+        assert (sk.get_stats(reset=True)["group_launches"] > 0) == bool(groups)
     assert er <= TOL and ev <= TOL, (er, ev)
 
 
-def test_df64_full_size_binaries_sampled():
+@pytest.mark.parametrize("flag,groups", KERNELS, ids=["tiles", "groups"])
+def test_df64_full_size_binaries_sampled(flag, groups):
     # the binaries with periods below the step go to the FP64 queue
     s = ics.plummer_binaries(16384, seed=0)
     # sample the binary members as well as random particles
-    er, ev = _full_size_sample(s, seed=3)
+    with configured(flags=sk.FLAG_STATS | flag):
+        er, ev = _full_size_sample(s, seed=3)
     assert er <= TOL and ev <= TOL, (er, ev)
 
 
-def test_df64_fast_swarm_uses_the_fp64_queue():
+def test_df64_default_kernel_at_16384_is_row_groups():
+    s = ics.bh_cluster(16384, seed=0)
+    sk.get_stats(reset=True)
+    gpu_step(s, s.dt, 2)
+    assert sk.get_stats(reset=True)["group_launches"] == 1
+
+
+@pytest.mark.parametrize("flag,groups", KERNELS, ids=["tiles", "groups"])
+def test_df64_fast_swarm_uses_the_fp64_queue(flag, groups):
     rng = np.random.default_rng(0)
     n = 64
     m = np.full(n, 1e-6)
     r = rng.uniform(-2.5e-4, 2.5e-4, (n, 3))
     v = rng.normal(0.0, 300.0, (n, 3))
     s = ics.System(m, r, v, 1e-3, "fast-swarm")
-    sk.get_stats(reset=True)
-    r1, v1 = gpu_step(s, s.dt, 2)
-    st = sk.get_stats(reset=True)
+    with configured(flags=sk.FLAG_STATS | flag):
+        sk.get_stats(reset=True)
+        r1, v1 = gpu_step(s, s.dt, 2)
+        st = sk.get_stats(reset=True)
     rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
     er, ev = rel_err(r1, v1, rr, vr)
     assert er <= TOL and ev <= TOL, (er, ev)
     assert st["fp32_pairs"] < st["solves"]  # some pairs went to FP64
+    assert st["group_launches"] == groups
 
 
 @pytest.mark.parametrize("order", [4, 6])
@@ -153,11 +216,13 @@ def test_df64_is_deterministic():
     np.testing.assert_array_equal(a[1], b[1])
 
 
-def test_df64_counts_double_word_solves():
+@pytest.mark.parametrize("flag,groups", KERNELS, ids=["tiles", "groups"])
+def test_df64_counts_double_word_solves(flag, groups):
     s = ics.plummer(1024, seed=2)
-    sk.get_stats(reset=True)
-    gpu_step(s, s.dt, 2)
-    st = sk.get_stats(reset=True)
+    with configured(flags=sk.FLAG_STATS | flag):
+        sk.get_stats(reset=True)
+        gpu_step(s, s.dt, 2)
+        st = sk.get_stats(reset=True)
     # a Plummer sphere has no pair outside the double-word class
     assert st["fp32_pairs"] == st["solves"]
     assert st["fallbacks"] == 0
