@@ -638,7 +638,9 @@ def _roofline(workload, form, pairs, guess, n, small, m):
                                  carried * (C_STEP + C_CARRY) + C_SYM -
                                  (C_SEED_SAVED if guess == "fp32" else 0))
         peak, pipe, src = FP64_PEAK_GFLOPS / 1e3, "fp64", fp64_peak_src
-        kname = "pair_step_grp_mixed" if m["row_groups"] else "pair_step_sym"
+        # the FP64 kernels with the inline class test (literal rule): in row
+        # groups or on tiles
+        kname = "pair_step_grp" if m["row_groups"] else "pair_step_sym"
     elif form == "mixed":
         # FP64 flops per ordered pair: the FP64 accumulation (6 FMA) of an
         # FP32-class pair, the full FP64 solve of the others

@@ -301,25 +301,27 @@ double group_partial_bytes(int64_t n, int G)
 // bodies 62.61 / 62.55; at 16384 bodies with the learned guess 36.07 / 35.42
 // and the standard guess 38.67 / 38.27).  The flags force either kernel.
 constexpr double kFp64TileMaxBytes = 2.0 * 1024 * 1024 * 1024;
-// The mixed form's tile kernel (the literal rule) is used up to this size.
-constexpr double kTileMaxBytes = 4.0 * 1024 * 1024 * 1024;
-
-// The mixed form runs in the FP64 tile kernel with an inline class test
-// (step_sym.cu) when its rule admits few pairs, as the literal rule does in
-// clusters (the black-hole cluster: 0.01 % of the pairs), and in the
-// row-group mixed kernel (step_mixed.cu) otherwise; the flags force either.
-bool mixed_tiles(int64_t n)
-{
-    if (g.cfg.flags & SAKURA_FLAG_TILES) return true;
-    if (g.cfg.flags & SAKURA_FLAG_GROUPS) return false;
-    return g.cfg.mixed_rule == SAKURA_MIXED_RULE_LITERAL && tile_partial_bytes(n) <= kTileMaxBytes;
-}
-
 bool fp64_groups(int64_t n)
 {
     if (g.cfg.flags & SAKURA_FLAG_GROUPS) return true;
     if (g.cfg.flags & SAKURA_FLAG_TILES) return false;
     return tile_partial_bytes(n) > kFp64TileMaxBytes;
+}
+
+// The mixed form's kernels.  Under the literal rule, which admits few pairs
+// in clusters (the black-hole cluster: 0.01 % of them), the FP64 kernels
+// with an inline class test: on tiles (step_sym.cu) or in row groups
+// (step_grp.cu) as for the FP64 form.  Under the hyperbolic rule the
+// row-group mixed kernel (step_mixed.cu), or the tile kernel with the inline
+// test when SAKURA_FLAG_TILES forces it.
+enum class MixedKernel { Tiles, Fp64Groups, MixedGroups };
+
+MixedKernel mixed_kernel(int64_t n)
+{
+    if (g.cfg.mixed_rule == SAKURA_MIXED_RULE_LITERAL)
+        return fp64_groups(n) ? MixedKernel::Fp64Groups : MixedKernel::Tiles;
+    if (g.cfg.flags & SAKURA_FLAG_TILES) return MixedKernel::Tiles;
+    return MixedKernel::MixedGroups;
 }
 
 // The double-word form: tiles below kFp64TileMaxBytes of tile partials, row
@@ -408,15 +410,16 @@ int step_device_df64_grp(const double *src, double *dst, const double *masses, i
 // state, written by the previous apply kernel; fuse: the apply kernel also
 // applies the next sub-step's drift next_drift and writes its X (and X32).
 int step_device_fp64_grp(const double *src, double *dst, const double *masses, int64_t n,
-                         double dt, int order, bool prepped, bool fuse, double next_drift)
+                         double dt, int order, bool prepped, bool fuse, double next_drift,
+                         bool mixed = false)
 {
     const bool stats = (g.cfg.flags & SAKURA_FLAG_STATS) != 0;
-    const bool learned = g.cfg.guess == SAKURA_GUESS_LEARNED;
+    const bool learned = !mixed && g.cfg.guess == SAKURA_GUESS_LEARNED;
     const bool seed = g.cfg.guess == SAKURA_GUESS_FP32;
     int64_t blocks = g.cfg.grid_blocks > 0
                          ? g.cfg.grid_blocks
                          : (int64_t)g.sm_count *
-                               sakura::pair_step_grp_blocks_per_sm(stats, learned, seed);
+                               sakura::pair_step_grp_blocks_per_sm(stats, learned, seed, mixed);
     const sakura::GrpLayout L = sakura::make_grp_layout(n, sakura::kFp64GrpShape, blocks);
     // scratch: X[7][n] doubles, row partials [Hmax][6][n], column partials
     // [ng][6][n] and [blocks][6][32], then X32[10][n] floats (single-precision
@@ -430,7 +433,7 @@ int step_device_fp64_grp(const double *src, double *dst, const double *masses, i
     parts.row = X + 7 * n;
     parts.col = parts.row + (int64_t)L.Hmax * 6 * n;
     parts.colx = parts.col + (int64_t)L.ng * 6 * n;
-    float *X32 = seed ? (float *)(parts.colx + blocks * 192) : nullptr;
+    float *X32 = (seed || mixed) ? (float *)(parts.colx + blocks * 192) : nullptr;
     const double drift = order == 2 ? 0.5 * dt : (order == 1 ? 0.0 : dt);
     const double post_drift = order == 2 ? 0.5 * dt : (order == 1 ? dt : 0.0);
     if (!prepped) sakura::launch_prep_step(src, masses, X, X32, n, drift, g.d_status, g.stream);
@@ -451,6 +454,11 @@ int step_device_fp64_grp(const double *src, double *dst, const double *masses, i
     a.mlp = learned ? (const sakura::MlpWeights *)g.mlp.ptr : nullptr;
     a.status = g.d_status;
     a.stats = g.d_stats;
+    if (mixed) {
+        a.mixed = seed ? 2 : 1;
+        a.rule = class_rule(a.pre * dt);
+        a.post32 = (float)a.post;
+    }
     const bool timing = (g.cfg.flags & SAKURA_FLAG_TIMING) != 0;
     std::pair<cudaEvent_t, cudaEvent_t> tm{nullptr, nullptr};
     if (timing) {
@@ -487,7 +495,13 @@ int step_device_sym(const double *src, double *dst, const double *masses, int64_
                     int order, bool df64, bool mixed, bool prepped = false, bool fuse = false,
                     double next_drift = 0.0)
 {
-    if (mixed && !mixed_tiles(n)) return step_device_mixed_grp(src, dst, masses, n, dt, order);
+    if (mixed) {
+        const MixedKernel k = mixed_kernel(n);
+        if (k == MixedKernel::MixedGroups)
+            return step_device_mixed_grp(src, dst, masses, n, dt, order);
+        if (k == MixedKernel::Fp64Groups)
+            return step_device_fp64_grp(src, dst, masses, n, dt, order, false, false, 0.0, true);
+    }
     if (df64 && df64_groups(n)) return step_device_df64_grp(src, dst, masses, n, dt, order);
     if (!df64 && !mixed && fp64_groups(n))
         return step_device_fp64_grp(src, dst, masses, n, dt, order, prepped, fuse, next_drift);
@@ -600,7 +614,12 @@ bool sym_path(int64_t n)
         return (df64_groups(n) ? group_partial_bytes(n, sakura::kDf64GrpWarps)
                                : tile_partial_bytes(n)) <= kSymMaxBytes;
     if (g.cfg.precision == SAKURA_PREC_MIXED)
-        return mixed_tiles(n) || group_partial_bytes(n, sakura::kMixedGrpWarps) <= kSymMaxBytes;
+        switch (mixed_kernel(n)) {
+        case MixedKernel::Tiles: return tile_partial_bytes(n) <= kSymMaxBytes;
+        case MixedKernel::Fp64Groups:
+            return group_partial_bytes(n, sakura::kFp64GrpWarps) <= kSymMaxBytes;
+        default: return group_partial_bytes(n, sakura::kMixedGrpWarps) <= kSymMaxBytes;
+        }
     return (fp64_groups(n) ? group_partial_bytes(n, sakura::kFp64GrpWarps)
                            : tile_partial_bytes(n)) <= kSymMaxBytes;
 }

@@ -37,6 +37,7 @@
 #include <algorithm>
 
 #include "kepler_df64.cuh"
+#include "kepler_fp32.cuh"
 #include "kepler_fp64.cuh"
 #include "mlp_infer.cuh"
 #include "pair_batch_fp64.cuh"
@@ -187,29 +188,36 @@ __host__ __device__ constexpr size_t grp_base_smem(int win, bool seed)
     return grp_cs_bytes(win) + grp_cd_bytes(win) + grp_cf_bytes(win, seed) + grp_rs_bytes();
 }
 
-size_t grp_smem(bool learned, bool seed)
+// f32: the float copy is staged (the seed, or the inline class test)
+size_t grp_smem(bool learned, bool f32)
 {
-    const int win = grp_window(seed);
-    return grp_base_smem(win, seed) +
+    const int win = grp_window(f32);
+    return grp_base_smem(win, f32) +
            (learned ? sizeof(MlpWeights) + kFp64GrpWarps * 32 * 16 * 2 : 0);
 }
 
-template <bool STATS, bool LEARNED, bool SEED>
-__global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
+// MIXED: the mixed form for class rules that admit few pairs (the literal
+// rule), as in the tile kernel (step_sym.cu): each pair's class is decided
+// from the float copy (kepler_fp32.cuh); a pair the rule admits is solved in
+// FP32 and its increments, converted to double, are accumulated in FP64 with
+// the rest; every other pair takes the FP64 solve (seeded with SEED).
+template <bool STATS, bool LEARNED, bool SEED, bool MIXED>
+__global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED || MIXED) ? 2 : 4)
     pair_step_grp_kernel(StepArgs a, GrpLayout L, GrpParts parts)
 {
     constexpr int G = kFp64GrpWarps;
-    constexpr int WIN = grp_window(SEED);
+    constexpr bool F32 = SEED || MIXED;  // the float copy is staged
+    constexpr int WIN = grp_window(F32);
     extern __shared__ __align__(16) unsigned char gsm[];
     double(*cs)[WIN][6][32] = reinterpret_cast<double(*)[WIN][6][32]>(gsm);
     double(*cd)[7][32] = reinterpret_cast<double(*)[7][32]>(gsm + grp_cs_bytes(WIN));
     float(*cf)[10][32] =
         reinterpret_cast<float(*)[10][32]>(gsm + grp_cs_bytes(WIN) + grp_cd_bytes(WIN));
     double(*rs)[G][6][32] = reinterpret_cast<double(*)[G][6][32]>(
-        gsm + grp_cs_bytes(WIN) + grp_cd_bytes(WIN) + grp_cf_bytes(WIN, SEED));
-    MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(gsm + grp_base_smem(WIN, SEED));
+        gsm + grp_cs_bytes(WIN) + grp_cd_bytes(WIN) + grp_cf_bytes(WIN, F32));
+    MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(gsm + grp_base_smem(WIN, F32));
     __nv_bfloat16 *mlpStage =
-        reinterpret_cast<__nv_bfloat16 *>(gsm + grp_base_smem(WIN, SEED) + sizeof(MlpWeights));
+        reinterpret_cast<__nv_bfloat16 *>(gsm + grp_base_smem(WIN, F32) + sizeof(MlpWeights));
     griddep_wait();    // X (and X32) from the prep kernel or the previous apply kernel
     griddep_launch();  // the apply kernel may begin launching
     if (LEARNED) mlp_load_shared(*mlpW, a.mlp);
@@ -224,7 +232,7 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
     const float *X32 = a.X32;
     const KeplerParams kp{a.tol, a.max_iter, a.bisection};
     unsigned status = 0;
-    long long it_sum = 0, slots = 0, fallbacks = 0, carries = 0;
+    long long it_sum = 0, slots = 0, fallbacks = 0, carries = 0, n32 = 0;
     int it_max = 0;
 
     GrpPos cur = grp_block_start(L, b, B);
@@ -252,7 +260,7 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
             const int64_t jp = ok ? grp_particle(L, n, j) : 0;
 #pragma unroll
             for (int f = 0; f < 7; ++f) cd[cb][f][c] = ok ? X[f * n + jp] : 0.0;
-            if (SEED) {
+            if (F32) {
 #pragma unroll
                 for (int f = 0; f < 10; ++f) cf[cb][f][c] = ok ? X32[f * n + jp] : 0.0f;
             }
@@ -294,7 +302,7 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
                 vyi = X[4 * n + ip];
                 vzi = X[5 * n + ip];
                 mi = X[6 * n + ip];
-                if (SEED) {
+                if (F32) {
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         hi_i[q] = X32[q * n + ip];
@@ -311,12 +319,28 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
                 const bool valid = irow && j < n && (!diag || c != lane);
                 PairSolve ps;
                 double mj = 0.0;
+                bool lane32 = false;  // MIXED: solved in FP32
+                float d32[6];
                 if (valid) {
                     mj = cd[cb][6][c];
-                    pair_setup(ps, a.tau, mi + mj, xi - cd[cb][0][c], yi - cd[cb][1][c],
-                               zi - cd[cb][2][c], vxi - cd[cb][3][c], vyi - cd[cb][4][c],
-                               vzi - cd[cb][5][c], a.pre, LEARNED ? 2 : (SEED ? -1 : a.guess));
-                    if (SEED) {
+                    if (MIXED) {
+                        const float hi_j[3] = {cf[cb][0][c], cf[cb][1][c], cf[cb][2][c]};
+                        const float lo_j[3] = {cf[cb][3][c], cf[cb][4][c], cf[cb][5][c]};
+                        const float v_j[3] = {cf[cb][6][c], cf[cb][7][c], cf[cb][8][c]};
+                        Pair32 pr;
+                        pair32_setup(pr, hi_i, lo_i, v_i, m32i, hi_j, lo_j, v_j, cf[cb][9][c],
+                                     a.rule);
+                        if (pr.fp32) {
+                            int it32 = 0;
+                            lane32 = pair32_solve(pr, a.t32, a.post32, a.guess, d32, it32);
+                        }
+                    }
+                    if (!lane32)
+                        pair_setup(ps, a.tau, mi + mj, xi - cd[cb][0][c], yi - cd[cb][1][c],
+                                   zi - cd[cb][2][c], vxi - cd[cb][3][c], vyi - cd[cb][4][c],
+                                   vzi - cd[cb][5][c], a.pre,
+                                   LEARNED ? 2 : (SEED ? -1 : a.guess));
+                    if (SEED && !lane32) {
                         // single-precision seed: the root of the FP32 solve of
                         // the same pair (unless t was reduced modulo the period)
                         float dr[3], dv[3];
@@ -339,7 +363,8 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
                             if (magbits(cq) < 0x3fe0000000000000LL) ps.s = fma(-cq, ps.s, ps.s);
                         }
                     }
-                } else {
+                }
+                if (!valid || lane32) {
                     ps.done = true;
                     ps.beta = ps.s = 0.0;
                     ps.iters = 0;
@@ -348,7 +373,13 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
                 if (LEARNED) learned_guess_warp(ps, valid, *mlpW, mlpStage + wib * 32 * 16);
                 double d[6];
                 int iters = 0, fb = 0;
-                fp64_solve_warp<SEED>(ps, valid, a.tau, a.post * a.tau, kp, d, iters, fb);
+                fp64_solve_warp<SEED>(ps, valid && !lane32, a.tau, a.post * a.tau, kp, d, iters,
+                                      fb);
+                if (MIXED && lane32) {
+                    // exact conversions on the integer pipe
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) d[q] = f2d(d32[q]);
+                }
                 if (valid) {
 #pragma unroll
                     for (int q = 0; q < 6; ++q) racc[q] = fma(mj, d[q], racc[q]);
@@ -360,6 +391,7 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
                 }
                 if (STATS) {
                     carries += (valid && ps.carried) ? 1 : 0;
+                    n32 += lane32 ? (diag ? 1 : 2) : 0;  // in ordered pairs
                     it_sum += iters;
                     fallbacks += fb;
                     it_max = max(it_max, iters);
@@ -434,29 +466,43 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED) ? 2 : 4)
             atomicAdd(&a.stats[kStatCarries], (unsigned long long)s4);
             atomicMax(&a.stats[kStatMaxIters], (unsigned long long)mx);
         }
+        if (MIXED) {
+            long long s5 = n32;
+            for (int o = 16; o > 0; o >>= 1) s5 += __shfl_xor_sync(0xffffffffu, s5, o);
+            if (lane == 0) atomicAdd(&a.stats[kStatFp32Pairs], (unsigned long long)s5);
+        }
     }
 }
 
 namespace {
 
-const void *grp_fp64_kernel(bool stats, bool learned, bool seed)
+const void *grp_fp64_kernel(bool stats, bool learned, bool seed, bool mixed)
 {
+    if (mixed) {
+        if (seed)
+            return stats ? (const void *)pair_step_grp_kernel<true, false, true, true>
+                         : (const void *)pair_step_grp_kernel<false, false, true, true>;
+        return stats ? (const void *)pair_step_grp_kernel<true, false, false, true>
+                     : (const void *)pair_step_grp_kernel<false, false, false, true>;
+    }
     if (learned)
-        return stats ? (const void *)pair_step_grp_kernel<true, true, false>
-                     : (const void *)pair_step_grp_kernel<false, true, false>;
+        return stats ? (const void *)pair_step_grp_kernel<true, true, false, false>
+                     : (const void *)pair_step_grp_kernel<false, true, false, false>;
     if (seed)
-        return stats ? (const void *)pair_step_grp_kernel<true, false, true>
-                     : (const void *)pair_step_grp_kernel<false, false, true>;
-    return stats ? (const void *)pair_step_grp_kernel<true, false, false>
-                 : (const void *)pair_step_grp_kernel<false, false, false>;
+        return stats ? (const void *)pair_step_grp_kernel<true, false, true, false>
+                     : (const void *)pair_step_grp_kernel<false, false, true, false>;
+    return stats ? (const void *)pair_step_grp_kernel<true, false, false, false>
+                 : (const void *)pair_step_grp_kernel<false, false, false, false>;
 }
 
 }  // namespace
 
-int pair_step_grp_blocks_per_sm(bool stats, bool learned, bool seed)
+int pair_step_grp_blocks_per_sm(bool stats, bool learned, bool seed, bool mixed)
 {
-    const void *fn = grp_fp64_kernel(stats, learned, seed);
-    const size_t smem = grp_smem(learned, seed && !learned);
+    learned = learned && !mixed;
+    seed = seed && !learned;
+    const void *fn = grp_fp64_kernel(stats, learned, seed, mixed);
+    const size_t smem = grp_smem(learned, seed || mixed);
     int b = 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
@@ -471,10 +517,11 @@ int pair_step_grp_blocks_per_sm(bool stats, bool learned, bool seed)
 void launch_pair_step_grp(const StepArgs &a, const GrpLayout &L, const GrpParts &parts,
                           int blocks, bool stats, cudaStream_t s)
 {
-    const bool learned = a.mlp != nullptr;
-    const bool seed = !learned && a.X32 != nullptr;
-    const void *fn = grp_fp64_kernel(stats, learned, seed);
-    const size_t smem = grp_smem(learned, seed);
+    const bool mixed = a.mixed != 0;
+    const bool learned = !mixed && a.mlp != nullptr;
+    const bool seed = !learned && a.X32 != nullptr && (!mixed || a.mixed == 2);
+    const void *fn = grp_fp64_kernel(stats, learned, seed, mixed);
+    const size_t smem = grp_smem(learned, seed || mixed);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     GrpLayout Lv = L;
     GrpParts pv = parts;

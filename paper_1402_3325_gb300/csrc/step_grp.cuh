@@ -27,10 +27,11 @@ void launch_apply_grp(double *state, double *X, float *X32, const GrpParts &part
                       const GrpLayout &L, int64_t blocks, double post_drift, bool fuse,
                       double next_drift, unsigned *status, cudaStream_t s);
 // the symmetric FP64 pair kernel in row-group phases (a.mlp: learned guess;
-// a.X32: single-precision seed)
+// a.X32: single-precision seed; a.mixed: the mixed form's inline class test,
+// a.mixed == 2 with the seed, as in launch_pair_step_sym)
 void launch_pair_step_grp(const StepArgs &a, const GrpLayout &L, const GrpParts &parts,
                           int blocks, bool stats, cudaStream_t s);
-int pair_step_grp_blocks_per_sm(bool stats, bool learned, bool seed);
+int pair_step_grp_blocks_per_sm(bool stats, bool learned, bool seed, bool mixed = false);
 // the double-word form in row-group phases (step_df64.cu): X3 from
 // launch_prep_df64, partial sums in FP64 for launch_apply_grp
 void launch_pair_step_grp_df64(const StepArgs &a, const DwArgs &da, const GrpLayout &L,

@@ -195,10 +195,12 @@ def test_mixed_all_fp64_queue_across_segments_is_fp64_exact(blocks, guess):
 @pytest.mark.parametrize("kernel", [sk.FLAG_TILES, sk.FLAG_GROUPS], ids=["tiles", "groups"])
 @pytest.mark.parametrize("rule", [0, 1], ids=["literal", "hyp"])
 def test_mixed_tile_and_row_group_kernels(rule, kernel, guess):
-    # the FP64 tile kernel with an inline class test (the literal rule's
-    # default) and the row-group mixed kernel (the hyperbolic rule's), each
-    # forced under both rules: same classes, oracle within the step bound,
-    # repeat runs bit-identical
+    # the FP64 tile kernel with an inline class test (forced with
+    # SAKURA_FLAG_TILES under either rule), and in row groups
+    # (SAKURA_FLAG_GROUPS): the FP64 row-group kernel with the inline test
+    # under the literal rule, the row-group mixed kernel under the
+    # hyperbolic rule: same classes, oracle within the step bound, repeat
+    # runs bit-identical
     s = ics.bh_cluster(2048, seed=3)
     sk.init(0, flags=sk.FLAG_STATS | kernel, precision=sk.PREC_MIXED, mixed_rule=rule,
             guess=guess)
@@ -212,6 +214,38 @@ def test_mixed_tile_and_row_group_kernels(rule, kernel, guess):
     er, ev = rel_err(r, v, rr, vr)
     print(f"rule {rule} kernel {kernel}: fp32 pairs {st['fp32_pairs']}, err r {er:.2e} v {ev:.2e}")
     assert st["fp32_pairs"] == int(got.sum())
+    assert st["group_launches"] == (1 if kernel == sk.FLAG_GROUPS else 0)
+    assert er <= STEP_BOUND and ev <= STEP_BOUND
+    np.testing.assert_array_equal(r, r2)
+    np.testing.assert_array_equal(v, v2)
+
+
+@pytest.mark.parametrize("guess", [sk.GUESS_TAYLOR, sk.GUESS_FP32], ids=["taylor", "seed"])
+@pytest.mark.parametrize("kernel", [sk.FLAG_TILES, sk.FLAG_GROUPS], ids=["tiles", "groups"])
+def test_literal_rule_inline_test_with_most_pairs_single_precision(kernel, guess):
+    # a wide literal rule (e_max = 1e15: every pair beyond r_min) sends most
+    # pairs through the inline FP32 solve of the FP64 kernels, on tiles and
+    # in row groups, at a ragged size
+    s = ics.random_cluster(1000, seed=17, mass_spread=2.0)
+    emax = 1e15
+    sk.init(0, flags=sk.FLAG_STATS | kernel, precision=sk.PREC_MIXED, mixed_rule=0,
+            mixed_e_max=emax, guess=guess)
+    try:
+        got = classes_gpu(s, 2)
+        r, v, st = step_gpu(s, 2)
+        r2, v2, _ = step_gpu(s, 2)
+    finally:
+        sk.init(0, flags=sk.FLAG_STATS)
+    cnt, orc = oracle.pair_classes(s.m, s.r, s.v, s.dt, rule=0, e_max=emax, want_matrix=True)
+    k = check_classes(got, orc, s.m, s.r, s.v, s.dt, 2, 0, e_max=emax)
+    rc, rr, vr = oracle.step(s.m, s.r, s.v, s.dt, 2, nthreads=NCPU)
+    er, ev = rel_err(r, v, rr, vr)
+    n = s.n
+    print(f"kernel {kernel}: classes {int(got.sum())} of {n * (n - 1)} ({k} boundary pairs"
+          f" differ), fp32 pairs {st['fp32_pairs']}, err r {er:.2e} v {ev:.2e}")
+    assert got.sum() > 0.5 * n * (n - 1)
+    assert st["fp32_pairs"] == int(got.sum())
+    assert st["group_launches"] == (1 if kernel == sk.FLAG_GROUPS else 0)
     assert er <= STEP_BOUND and ev <= STEP_BOUND
     np.testing.assert_array_equal(r, r2)
     np.testing.assert_array_equal(v, v2)
