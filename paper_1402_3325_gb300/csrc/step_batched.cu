@@ -55,6 +55,9 @@
 
 namespace sakura {
 
+// the sign bit of a double, flipped by an integer XOR
+constexpr long long kSignBit = (long long)0x8000000000000000ULL;
+
 constexpr int kBatchMaxN = 64;                                      // particles of a task
 constexpr int kBatchMaxPairs = kBatchMaxN * (kBatchMaxN - 1) / 2;  // 2016
 
@@ -225,10 +228,13 @@ __global__ void __launch_bounds__(WARPS * 32)
                 double sr = 0.0, sv = 0.0;
                 for (int aj = 0; aj < N; ++aj) {
                     if (aj == ai) continue;
-                    // the pair (j, i) for j < i gives -m_j d, the pair (i, j) +m_j d
+                    // the pair (j, i) for j < i gives -m_j d, the pair (i, j)
+                    // +m_j d; the sign set by an integer XOR of the sign bit
+                    // (the same bits as -m_j, without an FP64 instruction;
+                    // one loop, so the lanes of a warp do not diverge)
                     const int p = pb + local_pair(min(ai, aj), max(ai, aj), N);
-                    const double mj = S[6][b0 + aj];
-                    const double wj = aj < ai ? -mj : mj;
+                    const double wj = __longlong_as_double(
+                        __double_as_longlong(S[6][b0 + aj]) ^ (aj < ai ? kSignBit : 0LL));
                     sr = fma(wj, D[c][p], sr);
                     sv = fma(wj, D[3 + c][p], sv);
                 }

@@ -44,6 +44,9 @@
 
 namespace sakura {
 
+// the sign bit of a double, flipped by an integer XOR
+constexpr long long kSignBit = (long long)0x8000000000000000ULL;
+
 namespace {
 
 __device__ __forceinline__ dw split_dw(double x)
@@ -225,7 +228,10 @@ __global__ void __launch_bounds__(32 * kSmallMaxWarps, 1) small_kernel(SmallArgs
                 // the pair (j, i) for j < i gives -m_j d, the pair (i, j) +m_j d
                 const int lo = min(i, j), hi = max(i, j);
                 const int p = lo * n - lo * (lo + 1) / 2 + hi - lo - 1;
-                const double w = j < i ? -S[6][j] : S[6][j];
+                // -m_j as the same bits by an integer XOR of the sign bit
+                // (no FP64 instruction)
+                const double w = __longlong_as_double(__double_as_longlong(S[6][j]) ^
+                                                      (j < i ? kSignBit : 0LL));
                 sr = fma(w, D[c][p], sr);
                 sv = fma(w, D[3 + c][p], sv);
             }
