@@ -166,34 +166,35 @@ __device__ __forceinline__ Stumpff stumpff_fp64(double x, int nt)
         ++k;
     }
     if (k > 0) nt = 6;
-    const double y = -x;
+    // Horner in y = -x from the highest kept term; 1/(2n+2)! and 1/(2n+3)!.
+    // Each step c y + a is written fma(-c, x, a): the same value, with the
+    // sign an operand of the FMA rather than a separate FP64 negation of x.
     double c2, c3;
-    // Horner from the highest kept term; 1/(2n+2)! and 1/(2n+3)!
     if (nt >= 6) {
-        c2 = fma(1.0 / 479001600.0, y, 1.0 / 3628800.0);
-        c3 = fma(1.0 / 6227020800.0, y, 1.0 / 39916800.0);
-        c2 = fma(c2, y, 1.0 / 40320.0);
-        c3 = fma(c3, y, 1.0 / 362880.0);
-        c2 = fma(c2, y, 1.0 / 720.0);
-        c3 = fma(c3, y, 1.0 / 5040.0);
+        c2 = fma(-1.0 / 479001600.0, x, 1.0 / 3628800.0);
+        c3 = fma(-1.0 / 6227020800.0, x, 1.0 / 39916800.0);
+        c2 = fma(-c2, x, 1.0 / 40320.0);
+        c3 = fma(-c3, x, 1.0 / 362880.0);
+        c2 = fma(-c2, x, 1.0 / 720.0);
+        c3 = fma(-c3, x, 1.0 / 5040.0);
     } else if (nt == 5) {
-        c2 = fma(1.0 / 3628800.0, y, 1.0 / 40320.0);
-        c3 = fma(1.0 / 39916800.0, y, 1.0 / 362880.0);
-        c2 = fma(c2, y, 1.0 / 720.0);
-        c3 = fma(c3, y, 1.0 / 5040.0);
+        c2 = fma(-1.0 / 3628800.0, x, 1.0 / 40320.0);
+        c3 = fma(-1.0 / 39916800.0, x, 1.0 / 362880.0);
+        c2 = fma(-c2, x, 1.0 / 720.0);
+        c3 = fma(-c3, x, 1.0 / 5040.0);
     } else if (nt == 4) {
-        c2 = fma(1.0 / 40320.0, y, 1.0 / 720.0);
-        c3 = fma(1.0 / 362880.0, y, 1.0 / 5040.0);
+        c2 = fma(-1.0 / 40320.0, x, 1.0 / 720.0);
+        c3 = fma(-1.0 / 362880.0, x, 1.0 / 5040.0);
     } else {
         c2 = 1.0 / 720.0;
         c3 = 1.0 / 5040.0;
     }
-    c2 = fma(c2, y, 1.0 / 24.0);
-    c3 = fma(c3, y, 1.0 / 120.0);
-    c2 = fma(c2, y, 0.5);
-    c3 = fma(c3, y, 1.0 / 6.0);
-    double c0 = fma(y, c2, 1.0);
-    double c1 = fma(y, c3, 1.0);
+    c2 = fma(-c2, x, 1.0 / 24.0);
+    c3 = fma(-c3, x, 1.0 / 120.0);
+    c2 = fma(-c2, x, 0.5);
+    c3 = fma(-c3, x, 1.0 / 6.0);
+    double c0 = fma(-x, c2, 1.0);
+    double c1 = fma(-x, c3, 1.0);
     for (; k > 0; --k) {
         const double n3 = 0.25 * fma(c0, c3, c2);
         const double n2 = 0.5 * c1 * c1;
@@ -449,12 +450,14 @@ __device__ __forceinline__ void pair_increment_over_m(const PairSolve &p, double
 {
     const double ir = p.ir;
     const double fm1 = -p.G2 * p.ir0;
-    double gmt = -p.G3;
-    if (__double_as_longlong(p.t) != __double_as_longlong(tau)) gmt += (p.t - tau) * rcp_nr(p.m);
+    // g - tau = -m G3 / m ... with t reduced modulo the period, + (t - tau) / m;
+    // kept as its negation g3 so that B's addend takes the sign as an operand
+    double g3 = p.G3;
+    if (__double_as_longlong(p.t) != __double_as_longlong(tau)) g3 -= (p.t - tau) * rcp_nr(p.m);
     const double fd = -p.G1 * p.ir0 * ir;
     const double gdm1 = -p.G2 * ir;
     const double A = fma(-qtau, fd, fm1);
-    const double B = fma(-qtau, gdm1, gmt);
+    const double B = fma(-qtau, gdm1, -g3);
     out[3] = fma(fd, p.x0, gdm1 * p.vx);
     out[4] = fma(fd, p.y0, gdm1 * p.vy);
     out[5] = fma(fd, p.z0, gdm1 * p.vz);
