@@ -82,10 +82,13 @@ struct GrpShape {
 };
 constexpr GrpShape kFp64GrpShape{kFp64GrpWarps, 1, 2, 1, true};
 constexpr GrpShape kMixedGrpShape{kMixedGrpWarps, 32, 1, 0, false};
-// the double-word form (step_df64.cu): 4 warps per block, 3 blocks per SM;
-// whole phases (its loop, FP32-issue-bound like the mixed kernel's, stays
-// free of range tests), weighted like the FP64 kernel's, particles reversed
-constexpr int kDf64GrpWarps = 4;
+// the double-word form (step_df64.cu): one block of 12 warps per SM, whose
+// window barrier keeps the SM's warps together (in three blocks of 4 warps
+// the warp scheduler's preference let one block end up to 1.4 ms before
+// another on the same SM, the last then running alone at a low issue rate
+// in this FP32-issue-bound kernel); whole phases (its loop stays free of
+// range tests), weighted like the FP64 kernel's, particles reversed
+constexpr int kDf64GrpWarps = 12;
 constexpr GrpShape kDf64GrpShape{kDf64GrpWarps, 32, 2, 1, true};
 
 // row blocks of group g (0 past the last group)

@@ -20,8 +20,9 @@
 //   and converted to FP64 once per particle.
 // Row-group form (pair_step_grp_df64_kernel, the default where the tile
 //   partials would pass 2 GB): the same pair solves in the row-group phases
-//   of the mixed kernel (step_mixed.cu): 4 warps per block, column sums as
-//   double-words in shared memory reduced per window, row sums in registers;
+//   of the mixed kernel (step_mixed.cu): one block of 12 warps per SM,
+//   column sums as double-words in shared memory reduced per window, row
+//   sums in registers;
 //   the partial sums go out in FP64 (a double-word is a double exactly) to
 //   the row-group apply kernel (step_grp.cu).
 #include <cuda_runtime.h>
@@ -358,7 +359,7 @@ constexpr size_t kDf64GrpSmem = sizeof(float4) * (kDf64GrpWarps * 3 + 2 * 5) * k
                                 sizeof(float2) * kDf64GrpWarps * 32 * 12;
 
 template <bool STATS>
-__global__ void __launch_bounds__(kDf64GrpWarps * 32, 3)
+__global__ void __launch_bounds__(kDf64GrpWarps * 32, 1)
     pair_step_grp_df64_kernel(StepArgs a, DwArgs da, GrpLayout L, GrpParts parts)
 {
     constexpr int G = kDf64GrpWarps;

@@ -36,10 +36,10 @@ def lib(tmp_path_factory):
 
 SIZES = [1, 2, 31, 32, 33, 100, 255, 256, 257, 1000, 1023, 1024, 1025, 2049, 4096, 5000, 16384]
 GRIDS = [1, 2, 3, 7, 152, 304, 608, 1_000_000]
-# (G, S, wA, wB, rev): the FP64 kernel's shape, the mixed kernel's, and the
-# others the arithmetic allows
-SHAPES = [(4, 1, 2, 1, 1), (8, 32, 1, 0, 0), (4, 1, 1, 1, 1), (4, 32, 1, 1, 0), (8, 1, 1, 0, 1),
-          (8, 1, 2, 3, 0)]
+# (G, S, wA, wB, rev): the FP64 kernel's shape, the mixed kernel's, the
+# double-word kernel's, and others the arithmetic allows
+SHAPES = [(4, 1, 2, 1, 1), (8, 32, 1, 0, 0), (12, 32, 2, 1, 1), (4, 1, 1, 1, 1), (4, 32, 1, 1, 0),
+          (8, 1, 1, 0, 1), (8, 1, 2, 3, 0)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda sh: "G%d-S%d-w%d%d-r%d" % sh)
