@@ -90,6 +90,25 @@ C_CARRY = 28
 # the carry test by |s| (1) and forms the step's 1/F' by one quadratic
 # refinement (2)
 C_SEED_SAVED = 10
+# FP64 multiplies per solve that the FP64 kernels form on the integer pipes
+# instead (csrc/fp64_emu.cuh; the same IEEE results, counted in the flops
+# above all the same): the increments' 10 in the row-group kernel with the
+# seed or learned guess and in the batched kernel with the seed; with the
+# standard (or Taylor) guess, in the row-group, tile and batched kernels, also
+# the 10 of each Laguerre evaluation
+EMU_INC_MULS = 10
+EMU_ITER_MULS = 10
+
+
+def _integer_pipe_flops(kernel, guess, kbar):
+    if guess in ("standard", "taylor") and kernel in ("pair_step_grp", "pair_step_sym", "batched"):
+        return EMU_INC_MULS + kbar * EMU_ITER_MULS
+    if (kernel == "pair_step_grp" and guess in ("fp32", "learned")) or (
+            kernel == "batched" and guess == "fp32"):
+        return EMU_INC_MULS
+    return 0
+
+
 # FP32-class pair of the symmetric mixed form (see the roofline code below)
 C_MIX32_FIX = 44 + 44 + 168
 C_MIX32_ITER = 71
@@ -477,6 +496,8 @@ def run_ensemble(args, rank, world, device, stream, dist):
                          "unit": "TFLOP/s", "frac": ach / (FP64_PEAK_GFLOPS / 1e3),
                          "traffic": None, "kernel": "batched_kernel (learned guess)",
                          "pipe": "fp64", "flops_per_solve": fl,
+                         "integer_pipe_flops_per_solve": _integer_pipe_flops(
+                             "batched", "learned", hl["kepler_evals_per_solve"]),
                          "kepler_evals_per_solve": hl["kepler_evals_per_solve"],
                          "iteration_lane_efficiency": hl["iteration_lane_efficiency"]}}}
         ps_steps = min(args.steps, 10)
@@ -513,7 +534,10 @@ def run_ensemble(args, rank, world, device, stream, dist):
                          # a launch reads the state once, whatever its step count
                          "traffic": _profiled_traffic(args.workload, "batched"),
                          "kernel": "batched_kernel", "pipe": "fp64",
-                         "flops_per_solve": flops_solve, "kepler_evals_per_solve": kbar,
+                         "flops_per_solve": flops_solve,
+                         "integer_pipe_flops_per_solve": _integer_pipe_flops("batched", args.guess,
+                                                                             kbar),
+                         "kepler_evals_per_solve": kbar,
                          "iteration_lane_efficiency": h["iteration_lane_efficiency"]},
             "clocks": clocks.summary(),
             "e2e": {"value": world * n2 * args.steps / el, "unit": UNIT,
@@ -665,7 +689,11 @@ def _roofline(workload, form, pairs, guess, n, small, m):
             "frac": achieved / peak if achieved else None,
             "traffic": _profiled_traffic(workload, kname),
             "kernel": kname + "_kernel", "pipe": pipe, "peak_source": src,
-            "flops_per_solve": flops, "kepler_evals_per_solve": kbar,
+            "flops_per_solve": flops,
+            "integer_pipe_flops_per_solve": (
+                (1.0 - share if form == "mixed" else 1.0) * _integer_pipe_flops(kname, guess, kbar)
+                if form in ("fp64", "mixed") and pipe.startswith("fp64") and not small else 0.0),
+            "kepler_evals_per_solve": kbar,
             "carried_share": carried, "iteration_lane_efficiency": m["iteration_lane_efficiency"],
             "solves_per_step": solves, "pair_kernel_ms": pair_ms,
             "pair_kernel_share": pair_ms / m["ms_per_step"],

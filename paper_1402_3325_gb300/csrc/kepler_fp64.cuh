@@ -48,19 +48,51 @@
 //   c3(4x) = (c2 + c0 c3) / 4.
 // No trigonometric or hyperbolic function is called.
 //
-// Reciprocals and reciprocal square roots use the hardware approximation
-// (rcp/rsqrt.approx.ftz.f64, relative error below 2^-19) refined by one
-// third-order step of the Newton-Raphson family (Householder order 2),
+// Reciprocals and reciprocal square roots start from the single-precision
+// hardware approximation of the operand truncated to float (relative error
+// about 2^-22; the FP64 approximations, rcp/rsqrt.approx.ftz.f64 with error
+// below 2^-19, only for operands outside float's range: they measured about
+// 5 % of the pair kernel's time as seeds) and take one third-order step of
+// the Newton-Raphson family (Householder order 2),
 //   y <- y (1 + e + e^2),          e = 1 - x y,
 //   y <- y (1 + e/2 + 3 e^2 / 8),  e = 1 - x y^2,
 // which takes the error from d to O(d^3).
+//
+// Part of a solve's multiplies (and, where it pays, adds) can be formed on
+// the integer pipes instead of the FP64 pipe (fp64_emu.cuh), chosen per
+// kernel by the template argument EMU; the IEEE results are the same.
 #pragma once
 
 #include <cstdint>
 
+#include "fp64_emu.cuh"
 #include "fp_bits.cuh"
 
 namespace sakura {
+
+// Which FP64 operations of a solve are formed on the integer pipes
+// (fp64_emu.cuh) instead of the FP64 pipe: a kernel passes the OR of these
+// bits as the template argument EMU of the solver functions.  The results are
+// the same IEEE values either way; only the pipes that compute them differ.
+constexpr int kEmuIncMul = 1;    // the increments' multiplies
+constexpr int kEmuSetupMul = 2;  // the setup's multiplies
+constexpr int kEmuIterMul = 4;   // the multiplies of a Laguerre iteration
+constexpr int kEmuCarryMul = 8;  // the Taylor carry's multiplies
+
+template <int EMU, int BIT>
+__device__ __forceinline__ double xmul(double a, double b)
+{
+    if constexpr ((EMU & BIT) != 0) return emu::mul(a, b);
+    else return a * b;
+}
+
+// -a b, the sign an operand in either form
+template <int EMU, int BIT>
+__device__ __forceinline__ double xmul_neg(double a, double b)
+{
+    if constexpr ((EMU & BIT) != 0) return emu::mul_neg(a, b);
+    else return -a * b;
+}
 
 constexpr double kPi = 3.14159265358979323846;
 
@@ -71,8 +103,55 @@ constexpr unsigned kStatusKepler = 4u;
 constexpr unsigned kStatusMass = 8u;
 constexpr unsigned kStatusTimeout = 16u;
 
+// The bit pattern of a double, read through an opaque move.  Tests of a
+// pattern read with a plain bit cast are turned back into FP64 instructions
+// by the compiler: a zero test or an exponent-field test into an FP64
+// comparison, a sign flip into an FP64 negation, each a slot of the narrow
+// FP64 pipe.
+__device__ __forceinline__ long long dbits(double a)
+{
+    long long b;
+    asm("mov.b64 %0, %1;" : "=l"(b) : "d"(a));
+    return b;
+}
+
+// The seeds of 1/x and 1/sqrt(x) come from the FP32 approximations of x
+// truncated to float, formed and widened on the integer pipe (the FP64 pipe
+// bounds the solver): relative error about 2^-22 (the truncation 2^-23 plus
+// the approximation's).  Operands with |x| outside [2^-126, 2^126), where the
+// float or its reciprocal would not be a normal float, take the FP64
+// approximations (error <= 2^-19).
+__device__ __forceinline__ bool f32_range(long long b)
+{
+    const int e = (int)((b >> 52) & 0x7ff);
+    return e >= 1023 - 126 && e < 1023 + 126;
+}
+
+__device__ __forceinline__ float trunc_to_f32(long long b)
+{
+    const unsigned e = (unsigned)((b >> 52) & 0x7ff) - 1023u + 127u;
+    const unsigned m = (unsigned)(b >> 29) & 0x7fffffu;
+    const unsigned sign = (unsigned)((unsigned long long)b >> 32) & 0x80000000u;
+    return __uint_as_float(sign | (e << 23) | m);
+}
+
+__device__ __forceinline__ double widen_f32(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    return __longlong_as_double((long long)((((unsigned long long)(u & 0x80000000u)) << 32) |
+                                            ((unsigned long long)(((u >> 23) & 0xffu) + 896u)
+                                             << 52) |
+                                            ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
 __device__ __forceinline__ double rcp_seed(double x)
 {
+    const long long b = dbits(x);
+    if (f32_range(b)) {
+        float y;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(trunc_to_f32(b)));
+        return widen_f32(y);
+    }
     double y;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
     return y;
@@ -80,6 +159,12 @@ __device__ __forceinline__ double rcp_seed(double x)
 
 __device__ __forceinline__ double rsqrt_seed(double x)
 {
+    const long long b = dbits(x);
+    if (f32_range(b)) {
+        float y;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(trunc_to_f32(b)));
+        return widen_f32(y);
+    }
     double y;
     asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
     return y;
@@ -103,11 +188,12 @@ __device__ __forceinline__ double rcp_nr2(double x)
 
 // 1/sqrt(x) to about one ulp (x > 0 normal and finite): one cubic step
 // y (1 + e/2 + 3 e^2 / 8), e = 1 - x y^2, from a seed with error <= 2^-19.
+template <int EMU = 0>
 __device__ __forceinline__ double rsqrt_nr(double x)
 {
     const double y = rsqrt_seed(x);
-    const double e = fma(-x, y * y, 1.0);
-    return fma(y * e, fma(0.375, e, 0.5), y);
+    const double e = fma(-x, xmul<EMU, kEmuSetupMul>(y, y), 1.0);
+    return fma(xmul<EMU, kEmuSetupMul>(y, e), fma(0.375, e, 0.5), y);
 }
 
 __device__ __forceinline__ float sqrt_approx(float x)
@@ -123,16 +209,13 @@ __device__ __forceinline__ float sqrt_approx(float x)
 // in |a| (NaN compares above +inf).
 __device__ __forceinline__ long long okey(double a)
 {
-    const long long b = __double_as_longlong(a);
+    const long long b = dbits(a);
     return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
 
-__device__ __forceinline__ long long magbits(double a)
-{
-    return __double_as_longlong(a) & 0x7fffffffffffffffLL;
-}
+__device__ __forceinline__ long long magbits(double a) { return dbits(a) & 0x7fffffffffffffffLL; }
 
-__device__ __forceinline__ bool is_neg(double a) { return __double_as_longlong(a) < 0; }
+__device__ __forceinline__ bool is_neg(double a) { return dbits(a) < 0; }
 
 constexpr long long kInfBits = 0x7ff0000000000000LL;
 constexpr long long kBits0p1 = 0x3fb999999999999aLL;  // 0.1
@@ -233,6 +316,7 @@ struct PairSolve {
 // eta0 t / (2 r0^2)), from ds/dt = 1/r and d2s/dt2 = -eta0/r0^3 at t = 0;
 // when the correction exceeds 1/2 in size (fast radial motion over the
 // step) the expansion is not trusted and the standard guess is used.
+template <int EMU = 0>
 __device__ __forceinline__ void pair_setup(PairSolve &p, double tau, double m, double rx,
                                            double ry, double rz, double vx, double vy,
                                            double vz, double pre, int guess)
@@ -248,11 +332,11 @@ __device__ __forceinline__ void pair_setup(PairSolve &p, double tau, double m, d
     p.x0 = fma(-ptau, vx, rx);
     p.y0 = fma(-ptau, vy, ry);
     p.z0 = fma(-ptau, vz, rz);
-    const double r0sq = fma(p.x0, p.x0, fma(p.y0, p.y0, p.z0 * p.z0));
+    const double r0sq = fma(p.x0, p.x0, fma(p.y0, p.y0, xmul<EMU, kEmuSetupMul>(p.z0, p.z0)));
     p.G1 = p.G2 = p.G3 = 0.0;
-    const long long rb = __double_as_longlong(r0sq);
+    const long long rb = dbits(r0sq);
     if (!(rb > 0 && rb < 0x7e37e43c8800759cLL)) {  // 0 < r0^2 < 1e300, not NaN
-        p.status = (r0sq == 0.0) ? kStatusCoincident : kStatusNonfinite;
+        p.status = magbits(r0sq) == 0 ? kStatusCoincident : kStatusNonfinite;
         p.done = true;
         p.r0 = p.ir0 = 1.0;
         p.Fp = p.ir = 1.0;
@@ -261,25 +345,27 @@ __device__ __forceinline__ void pair_setup(PairSolve &p, double tau, double m, d
         p.lo = p.hi = 0.0;
         return;
     }
-    p.ir0 = rsqrt_nr(r0sq);
-    p.r0 = r0sq * p.ir0;
+    p.ir0 = rsqrt_nr<EMU>(r0sq);
+    p.r0 = xmul<EMU, kEmuSetupMul>(r0sq, p.ir0);
     p.Fp = p.r0;
     p.ir = p.ir0;
-    p.eta0 = fma(p.x0, vx, fma(p.y0, vy, p.z0 * vz));
-    const double v2 = fma(vx, vx, fma(vy, vy, vz * vz));
+    p.eta0 = fma(p.x0, vx, fma(p.y0, vy, xmul<EMU, kEmuSetupMul>(p.z0, vz)));
+    const double v2 = fma(vx, vx, fma(vy, vy, xmul<EMU, kEmuSetupMul>(vz, vz)));
     p.beta = fma(scale2(m, 1), p.ir0, -v2);
     p.zeta0 = fma(-p.beta, p.r0, m);
     p.t = tau;
     // bound orbit with |t| > P = 2 pi m / beta^1.5  <=>  t^2 beta^3 > (2 pi m)^2
-    if (__double_as_longlong(p.beta) > 0) {
-        const double b3 = p.beta * p.beta * p.beta;
-        const double tm = 2.0 * kPi * m;
-        if (okey(tau * tau * b3) > okey(tm * tm)) {
-            const double P = tm * rsqrt_nr(b3);
+    if (dbits(p.beta) > 0) {
+        const double b3 =
+            xmul<EMU, kEmuSetupMul>(xmul<EMU, kEmuSetupMul>(p.beta, p.beta), p.beta);
+        const double tm = xmul<EMU, kEmuSetupMul>(2.0 * kPi, m);
+        const double tt = xmul<EMU, kEmuSetupMul>(tau, tau);
+        if (okey(xmul<EMU, kEmuSetupMul>(tt, b3)) > okey(xmul<EMU, kEmuSetupMul>(tm, tm))) {
+            const double P = xmul<EMU, kEmuSetupMul>(tm, rsqrt_nr<EMU>(b3));
             p.t = fmod(tau, P);
         }
     }
-    p.s = guess < 0 ? 0.0 : p.t * p.ir0;  // standard initial guess
+    p.s = guess < 0 ? 0.0 : xmul<EMU, kEmuSetupMul>(p.t, p.ir0);  // standard initial guess
     if (guess == 2) {
         const double c = 0.5 * p.s * (p.eta0 * p.ir0);  // eta0 t / (2 r0^2)
         if (magbits(c) < 0x3fe0000000000000LL) p.s = fma(-c, p.s, p.s);  // |c| < 1/2
@@ -302,20 +388,20 @@ __device__ __forceinline__ void pair_setup(PairSolve &p, double tau, double m, d
 // warps finish after one evaluation).  With the carry, 1/F' at the iterate
 // only forms the step (to 2^-38, a relative error that vanishes with the
 // step) and is recomputed in full at the accepted root.
-template <bool CARRY>
+template <bool CARRY, int EMU = 0>
 __device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, double s2, int nt,
                                              const KeplerParams &kp)
 {
     const double s = p.s;
     const Stumpff c = stumpff_fp64(x, nt);
-    const double G1 = s * c.c1;
-    const double G2 = s2 * c.c2;
-    const double G3 = s2 * s * c.c3;
+    const double G1 = xmul<EMU, kEmuIterMul>(s, c.c1);
+    const double G2 = xmul<EMU, kEmuIterMul>(s2, c.c2);
+    const double G3 = xmul<EMU, kEmuIterMul>(xmul<EMU, kEmuIterMul>(s2, s), c.c3);
     const double F = fma(p.r0, s, fma(p.eta0, G2, fma(p.zeta0, G3, -p.t)));
     const double Fp = fma(p.eta0, G1, fma(p.zeta0, G2, p.r0));
-    const double Fpp = fma(p.eta0, c.c0, p.zeta0 * G1);
+    const double Fpp = fma(p.eta0, c.c0, xmul<EMU, kEmuIterMul>(p.zeta0, G1));
     const double ip = CARRY ? rcp_nr2(Fp) : rcp_nr(Fp);
-    const double q = F * ip;
+    const double q = xmul<EMU, kEmuIterMul>(F, ip);
     p.G1 = G1;
     p.G2 = G2;
     p.G3 = G3;
@@ -326,7 +412,7 @@ __device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, double s2, 
     // F' passed 2^1000 (its reciprocal would flush to zero and fake
     // convergence): r at the root is the pair's separation, so the root lies
     // between the iterate and the origin and the iterate bounds the bracket
-    if ((__double_as_longlong(F) & kInfBits) == kInfBits || magbits(Fp) >= kBits2p1000) {
+    if ((dbits(F) & kInfBits) == kInfBits || magbits(Fp) >= kBits2p1000) {
         if (is_neg(s))
             p.lo = s;
         else
@@ -344,7 +430,7 @@ __device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, double s2, 
         p.lo = s;
     else
         p.hi = s;
-    const double qh = q * (Fpp * ip);  // = u / 1.25
+    const double qh = xmul<EMU, kEmuIterMul>(q, xmul<EMU, kEmuIterMul>(Fpp, ip));  // = u / 1.25
     double step;
     if (CARRY && magbits(qh) < 0x3f50000000000000LL) {
         // |u| < 2^-10 (a root next to the seed): the Laguerre step
@@ -367,11 +453,12 @@ __device__ __forceinline__ bool pair_iterate(PairSolve &p, double x, double s2, 
     // evaluating at the new point
     const long long sc20 = sc > (20LL << 52) ? sc - (20LL << 52) : 0;
     if (CARRY && magbits(step) <= sc20) {
-        const double h2 = scale2(step * step, -1);
-        const double F3 = fma(-p.eta0 * p.beta, G1, p.zeta0 * c.c0);  // dF''/ds
+        const double h2 = scale2(xmul<EMU, kEmuCarryMul>(step, step), -1);
+        const double F3 = fma(xmul_neg<EMU, kEmuCarryMul>(p.eta0, p.beta), G1,
+                              xmul<EMU, kEmuCarryMul>(p.zeta0, c.c0));  // dF''/ds
         p.G3 = fma(h2, G1, fma(-step, G2, G3));
         p.G2 = fma(h2, c.c0, fma(-step, G1, G2));
-        p.G1 = fma(h2, -p.beta * G1, fma(-step, c.c0, G1));
+        p.G1 = fma(h2, xmul_neg<EMU, kEmuCarryMul>(p.beta, G1), fma(-step, c.c0, G1));
         p.Fp = fma(h2, F3, fma(-step, Fpp, Fp));
         p.ir = rcp_nr(p.Fp);
         p.s = sn;
@@ -445,25 +532,26 @@ __device__ __forceinline__ void pair_bisect(PairSolve &p)
 
 // Increments divided by m = m_i + m_j: out[0..2] = delta_r / m,
 // out[3..5] = delta_v / m; qtau = post * tau.
+template <int EMU = 0>
 __device__ __forceinline__ void pair_increment_over_m(const PairSolve &p, double tau, double qtau,
                                                       double out[6])
 {
     const double ir = p.ir;
-    const double fm1 = -p.G2 * p.ir0;
+    const double fm1 = xmul_neg<EMU, kEmuIncMul>(p.G2, p.ir0);
     // g - tau = -m G3 / m ... with t reduced modulo the period, + (t - tau) / m;
     // kept as its negation g3 so that B's addend takes the sign as an operand
     double g3 = p.G3;
-    if (__double_as_longlong(p.t) != __double_as_longlong(tau)) g3 -= (p.t - tau) * rcp_nr(p.m);
-    const double fd = -p.G1 * p.ir0 * ir;
-    const double gdm1 = -p.G2 * ir;
+    if (dbits(p.t) != dbits(tau)) g3 -= (p.t - tau) * rcp_nr(p.m);
+    const double fd = xmul<EMU, kEmuIncMul>(xmul_neg<EMU, kEmuIncMul>(p.G1, p.ir0), ir);
+    const double gdm1 = xmul_neg<EMU, kEmuIncMul>(p.G2, ir);
     const double A = fma(-qtau, fd, fm1);
     const double B = fma(-qtau, gdm1, -g3);
-    out[3] = fma(fd, p.x0, gdm1 * p.vx);
-    out[4] = fma(fd, p.y0, gdm1 * p.vy);
-    out[5] = fma(fd, p.z0, gdm1 * p.vz);
-    out[0] = fma(A, p.x0, B * p.vx);
-    out[1] = fma(A, p.y0, B * p.vy);
-    out[2] = fma(A, p.z0, B * p.vz);
+    out[3] = fma(fd, p.x0, xmul<EMU, kEmuIncMul>(gdm1, p.vx));
+    out[4] = fma(fd, p.y0, xmul<EMU, kEmuIncMul>(gdm1, p.vy));
+    out[5] = fma(fd, p.z0, xmul<EMU, kEmuIncMul>(gdm1, p.vz));
+    out[0] = fma(A, p.x0, xmul<EMU, kEmuIncMul>(B, p.vx));
+    out[1] = fma(A, p.y0, xmul<EMU, kEmuIncMul>(B, p.vy));
+    out[2] = fma(A, p.z0, xmul<EMU, kEmuIncMul>(B, p.vz));
 }
 
 }  // namespace sakura

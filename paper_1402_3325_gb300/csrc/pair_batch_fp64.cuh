@@ -12,19 +12,19 @@ namespace sakura {
 // call this.  tau, qtau: this lane's step and post-drift time (post * tau).  Writes
 // the increments divided by m_ij to d (only meaningful when valid), returns
 // the lane's evaluation count and whether it needed bisection.
-template <bool CARRY = false>
+template <bool CARRY = false, int EMU = 0>
 __device__ __forceinline__ void fp64_solve_warp(PairSolve &p, bool valid, double tau,
                                                 double qtau, const KeplerParams &kp,
                                                 double d[6], int &iters, int &fb)
 {
     for (int it = 0; it < kp.max_iter; ++it) {
         if (__all_sync(0xffffffffu, p.done)) break;
-        const double s2 = p.s * p.s;
-        const double x = p.beta * s2;
+        const double s2 = xmul<EMU, kEmuIterMul>(p.s, p.s);
+        const double x = xmul<EMU, kEmuIterMul>(p.beta, s2);
         const unsigned hx = p.done ? 0u : abs_hiword(x);
         const int nt = stumpff_terms(__reduce_max_sync(0xffffffffu, hx));
         bool oob = false;
-        if (!p.done) oob = pair_iterate<CARRY>(p, x, s2, nt, kp);
+        if (!p.done) oob = pair_iterate<CARRY, EMU>(p, x, s2, nt, kp);
         if (__any_sync(0xffffffffu, oob)) {
             if (oob) pair_safeguard(p);
         }
@@ -39,7 +39,7 @@ __device__ __forceinline__ void fp64_solve_warp(PairSolve &p, bool valid, double
         }
     }
     iters = valid ? p.iters : 0;
-    if (valid) pair_increment_over_m(p, tau, qtau, d);
+    if (valid) pair_increment_over_m<EMU>(p, tau, qtau, d);
 }
 
 // Learned initial guess for the 32 lanes (every lane calls): replaces the

@@ -46,6 +46,17 @@
 
 namespace sakura {
 
+// The FP64 operations formed on the integer pipes (kepler_fp64.cuh), per
+// initial guess, as measured at 16384 bodies: with the seed or the learned
+// guess the increments' multiplies (ms per step 25.72 -> 24.89 seeded; every
+// other set measured was slower: the solve's own multiplies lengthen the
+// chain that the two blocks of 4 warps on an SM must hide); with the
+// standard guess, whose several iterations per solve fill the FP64 pipe
+// more, also the iterations' multiplies (36.69 -> 30.53).
+constexpr int kGrpEmuSeed = kEmuIncMul;
+constexpr int kGrpEmuLearned = kEmuIncMul;
+constexpr int kGrpEmuStandard = kEmuIncMul | kEmuIterMul;
+
 // Eqs. 27b-d for the row-group layout.  Layout index i (particle
 // grp_particle(i)) of row block I (group gi = I / G) adds its group's row
 // pieces h = 0 .. npieces - 1 and the
@@ -207,6 +218,7 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED || MIXED)
 {
     constexpr int G = kFp64GrpWarps;
     constexpr bool F32 = SEED || MIXED;  // the float copy is staged
+    constexpr int kGrpEmu = SEED ? kGrpEmuSeed : (LEARNED ? kGrpEmuLearned : kGrpEmuStandard);
     constexpr int WIN = grp_window(F32);
     extern __shared__ __align__(16) unsigned char gsm[];
     double(*cs)[WIN][6][32] = reinterpret_cast<double(*)[WIN][6][32]>(gsm);
@@ -336,10 +348,11 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED || MIXED)
                         }
                     }
                     if (!lane32)
-                        pair_setup(ps, a.tau, mi + mj, xi - cd[cb][0][c], yi - cd[cb][1][c],
-                                   zi - cd[cb][2][c], vxi - cd[cb][3][c], vyi - cd[cb][4][c],
-                                   vzi - cd[cb][5][c], a.pre,
-                                   LEARNED ? 2 : (SEED ? -1 : a.guess));
+                        pair_setup<kGrpEmu>(ps, a.tau, mi + mj, xi - cd[cb][0][c],
+                                            yi - cd[cb][1][c], zi - cd[cb][2][c],
+                                            vxi - cd[cb][3][c], vyi - cd[cb][4][c],
+                                            vzi - cd[cb][5][c], a.pre,
+                                            LEARNED ? 2 : (SEED ? -1 : a.guess));
                     if (SEED && !lane32) {
                         // single-precision seed: the root of the FP32 solve of
                         // the same pair (unless t was reduced modulo the period)
@@ -352,7 +365,7 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED || MIXED)
                         }
                         const K32 o =
                             k32_phase1(dr, dv, m32i + cf[cb][9][c], a.ptau32, a.t32, 2);
-                        if (o.ok && __double_as_longlong(ps.t) == __double_as_longlong(a.tau) &&
+                        if (o.ok && dbits(ps.t) == dbits(a.tau) &&
                             !ps.done) {
                             ps.s = f2d(o.s);
                         } else if (!ps.done) {
@@ -373,8 +386,8 @@ __global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED || MIXED)
                 if (LEARNED) learned_guess_warp(ps, valid, *mlpW, mlpStage + wib * 32 * 16);
                 double d[6];
                 int iters = 0, fb = 0;
-                fp64_solve_warp<SEED>(ps, valid && !lane32, a.tau, a.post * a.tau, kp, d, iters,
-                                      fb);
+                fp64_solve_warp<SEED, kGrpEmu>(ps, valid && !lane32, a.tau, a.post * a.tau, kp,
+                                               d, iters, fb);
                 if (MIXED && lane32) {
                     // exact conversions on the integer pipe
 #pragma unroll

@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(32 * kSmallMaxWarps, 1) small_kernel(SmallArgs
                            S[2][i] - S[2][j], S[3][i] - S[3][j], S[4][i] - S[4][j],
                            S[5][i] - S[5][j], a.pre, SEED ? -1 : a.guess);
                 if (SEED) {
-                    if (o.ok && __double_as_longlong(ps.t) == __double_as_longlong(tau) &&
+                    if (o.ok && dbits(ps.t) == dbits(tau) &&
                         !ps.done) {
                         ps.s = f2d(o.s);
                     } else if (!ps.done) {
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(32 * kSmallMaxWarps, 1) small_kernel(SmallArgs
                 const int p = lo * n - lo * (lo + 1) / 2 + hi - lo - 1;
                 // -m_j as the same bits by an integer XOR of the sign bit
                 // (no FP64 instruction)
-                const double w = __longlong_as_double(__double_as_longlong(S[6][j]) ^
+                const double w = __longlong_as_double(dbits(S[6][j]) ^
                                                       (j < i ? kSignBit : 0LL));
                 sr = fma(w, D[c][p], sr);
                 sv = fma(w, D[3 + c][p], sv);

@@ -31,6 +31,17 @@
 
 namespace sakura {
 
+// The FP64 operations formed on the integer pipes (kepler_fp64.cuh), per
+// initial guess, as measured on Plummer spheres of 1024 to 8192 bodies: none
+// with the seed or the learned guess (the increments' multiplies measured
+// 3.5 % slower at 1024 bodies, level at 4096, 1.5 % faster at 8192; 5 %
+// slower with the learned guess at 4096), the increments' and the
+// iterations' multiplies with the standard guess (13 % and 16 % faster at
+// 1024 and 4096 bodies).
+constexpr int kSymEmuSeed = 0;
+constexpr int kSymEmuLearned = 0;
+constexpr int kSymEmuStandard = kEmuIncMul | kEmuIterMul;
+
 // MIXED: the mixed form for class rules that admit few pairs (the literal
 // rule): each pair's class is decided as in the row-group mixed kernel
 // (kepler_fp32.cuh); a pair the rule admits is solved in FP32 and its
@@ -40,6 +51,7 @@ template <bool STATS, bool LEARNED, bool SEED, bool MIXED>
 __global__ void __launch_bounds__(128, (LEARNED || SEED || MIXED) ? 2 : 4)
     pair_step_sym_kernel(StepArgs a, int Smax, int64_t T)
 {
+    constexpr int kSymEmu = SEED ? kSymEmuSeed : (LEARNED ? kSymEmuLearned : kSymEmuStandard);
     extern __shared__ __align__(16) unsigned char dsm[];
     MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(dsm);
     __nv_bfloat16 *mlpStage = reinterpret_cast<__nv_bfloat16 *>(dsm + sizeof(MlpWeights));
@@ -118,9 +130,10 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED || MIXED) ? 2 : 4)
                     }
                 }
                 if (!lane32)
-                    pair_setup(p, a.tau, mi + mj, xi - X[j], yi - X[n + j], zi - X[2 * n + j],
-                               vxi - X[3 * n + j], vyi - X[4 * n + j], vzi - X[5 * n + j],
-                               a.pre, LEARNED ? 2 : (SEED ? -1 : a.guess));
+                    pair_setup<kSymEmu>(p, a.tau, mi + mj, xi - X[j], yi - X[n + j],
+                                        zi - X[2 * n + j], vxi - X[3 * n + j], vyi - X[4 * n + j],
+                                        vzi - X[5 * n + j], a.pre,
+                                        LEARNED ? 2 : (SEED ? -1 : a.guess));
                 if (SEED && !lane32) {
                     // single-precision seed: the root of the FP32 solve of the
                     // same pair (unless t was reduced modulo the period)
@@ -132,7 +145,7 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED || MIXED) ? 2 : 4)
                         dv[q] = __fsub_rn(v_i[q], X32[(6 + q) * n + j]);
                     }
                     const K32 o = k32_phase1(dr, dv, m32i + X32[9 * n + j], a.ptau32, a.t32, 2);
-                    if (o.ok && __double_as_longlong(p.t) == __double_as_longlong(a.tau) &&
+                    if (o.ok && dbits(p.t) == dbits(a.tau) &&
                         !p.done) {
                         p.s = f2d(o.s);
                     } else if (!p.done) {
@@ -153,7 +166,8 @@ __global__ void __launch_bounds__(128, (LEARNED || SEED || MIXED) ? 2 : 4)
             if (LEARNED) learned_guess_warp(p, valid, *mlpW, mlpStage + wib * 32 * 16);
             double d[6];
             int iters = 0, fb = 0;
-            fp64_solve_warp<SEED>(p, valid && !lane32, a.tau, a.post * a.tau, kp, d, iters, fb);
+            fp64_solve_warp<SEED, kSymEmu>(p, valid && !lane32, a.tau, a.post * a.tau, kp, d, iters,
+                                           fb);
             if (MIXED && lane32) {
                 // exact conversions on the integer pipe
 #pragma unroll
