@@ -92,21 +92,25 @@ C_CARRY = 28
 C_SEED_SAVED = 10
 # FP64 multiplies per solve that the FP64 kernels form on the integer pipes
 # instead (csrc/fp64_emu.cuh; the same IEEE results, counted in the flops
-# above all the same): the increments' 10 in the row-group kernel with the
-# seed or learned guess and in the batched kernel with the seed; with the
-# standard (or Taylor) guess, in the row-group, tile and batched kernels, also
-# the 10 of each Laguerre evaluation
+# above all the same), per kernel and guess (the EMU sets of step_grp.cu,
+# step_sym.cu and step_batched.cu): the increments' 10, the setup's 6, the
+# carry's 4 and the 10 of each Laguerre evaluation
 EMU_INC_MULS = 10
+EMU_SETUP_MULS = 6
+EMU_CARRY_MULS = 4
 EMU_ITER_MULS = 10
 
 
-def _integer_pipe_flops(kernel, guess, kbar):
-    if guess in ("standard", "taylor") and kernel in ("pair_step_grp", "pair_step_sym", "batched"):
+def _integer_pipe_flops(kernel, guess, kbar, mixed=False):
+    if kernel not in ("pair_step_grp", "pair_step_sym", "batched"):
+        return 0
+    if mixed:  # the inline class test: row groups only
+        return (EMU_INC_MULS + EMU_SETUP_MULS + EMU_CARRY_MULS) if kernel == "pair_step_grp" else 0
+    if guess == "fp32":
+        return EMU_INC_MULS + EMU_SETUP_MULS + kbar * EMU_ITER_MULS
+    if guess in ("standard", "taylor"):
         return EMU_INC_MULS + kbar * EMU_ITER_MULS
-    if (kernel == "pair_step_grp" and guess in ("fp32", "learned")) or (
-            kernel == "batched" and guess == "fp32"):
-        return EMU_INC_MULS
-    return 0
+    return EMU_INC_MULS if kernel == "pair_step_grp" else 0
 
 
 # FP32-class pair of the symmetric mixed form (see the roofline code below)
@@ -691,7 +695,8 @@ def _roofline(workload, form, pairs, guess, n, small, m):
             "kernel": kname + "_kernel", "pipe": pipe, "peak_source": src,
             "flops_per_solve": flops,
             "integer_pipe_flops_per_solve": (
-                (1.0 - share if form == "mixed" else 1.0) * _integer_pipe_flops(kname, guess, kbar)
+                (1.0 - share if form == "mixed" else 1.0) *
+                _integer_pipe_flops(kname, guess, kbar, mixed=form == "mixed")
                 if form in ("fp64", "mixed") and pipe.startswith("fp64") and not small else 0.0),
             "kepler_evals_per_solve": kbar,
             "carried_share": carried, "iteration_lane_efficiency": m["iteration_lane_efficiency"],

@@ -25,13 +25,16 @@ namespace sakura {
 // Work is split in steps.  The units (g, t, k), step k of phase t of group
 // g, are ordered group by group, phase by phase.  A step of phase t costs
 // c(g, t) = wA + wB min(t + 1, R_g): wA for the step's time and wB for each
-// of its tiles.  The two blocks on an SM share its FP64 pipe warp by warp,
-// so a block whose phase has idle warps advances faster than one whose
-// warps are all busy, but not in proportion to its tiles: measured on
-// GB300, a step of the phases at a group's start (1 to 3 tiles of 4, two on
-// average) took 0.64 of a full step, which (wA, wB) = (1, 1) gives as 0.6
-// (FP64 kernel; the mixed kernel, whose blocks' times vary with their pairs'
-// classes more than with this, takes (1, 0)).  x(g, t, k), the cost of the
+// of its tiles.  The blocks on an SM share its FP64 pipe warp by warp, so a
+// block whose phase has idle warps advances faster than one whose warps are
+// all busy, but not in proportion to its tiles: measured on GB300, a step of
+// the phases at a group's start (1 to 3 tiles of 4, two on average) took
+// 0.64 of a full step with two blocks per SM (the double-word kernel keeps
+// (wA, wB) = (2, 1)); the FP64 kernel, now four blocks per SM with part of
+// its multiplies on the integer pipes, measured fastest with (3, 1) (20.72
+// ms per step at 16384 bodies against 20.85 with (2, 1) and 21.16 with
+// (1, 1)); the mixed kernel, whose blocks' times vary with their pairs'
+// classes more than with this, takes (1, 0).  x(g, t, k), the cost of the
 // units before (g, t, k), is grp_phase_x(g, t) + k c(g, t); C = x at the
 // end.  The units are dealt in chunks of S consecutive steps of one phase
 // (S = 1: single steps, for the FP64 kernel; S = 32: whole phases, for the
@@ -62,7 +65,7 @@ namespace sakura {
 // every group's blocks.
 constexpr int kGrpWindow = 4;
 constexpr int kMixedGrpWarps = 8;  // G of the mixed kernel (2 blocks of 8 warps per SM)
-constexpr int kFp64GrpWarps = 4;   // G of the FP64 kernel (2 blocks of 4 warps per SM)
+constexpr int kFp64GrpWarps = 4;   // G of the FP64 kernel (blocks of 4 warps, 2 to 4 per SM)
 
 struct GrpLayout {
     int64_t nb;  // blocks of 32 particles
@@ -80,14 +83,14 @@ struct GrpShape {
     int G, S, wA, wB;
     bool rev;
 };
-constexpr GrpShape kFp64GrpShape{kFp64GrpWarps, 1, 2, 1, true};
+constexpr GrpShape kFp64GrpShape{kFp64GrpWarps, 1, 3, 1, true};
 constexpr GrpShape kMixedGrpShape{kMixedGrpWarps, 32, 1, 0, false};
 // the double-word form (step_df64.cu): one block of 12 warps per SM, whose
 // window barrier keeps the SM's warps together (in three blocks of 4 warps
 // the warp scheduler's preference let one block end up to 1.4 ms before
 // another on the same SM, the last then running alone at a low issue rate
 // in this FP32-issue-bound kernel); whole phases (its loop stays free of
-// range tests), weighted like the FP64 kernel's, particles reversed
+// range tests), a step costing 2 + its tiles, particles reversed
 constexpr int kDf64GrpWarps = 12;
 constexpr GrpShape kDf64GrpShape{kDf64GrpWarps, 32, 2, 1, true};
 

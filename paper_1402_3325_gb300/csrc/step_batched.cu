@@ -56,11 +56,13 @@
 namespace sakura {
 
 // The FP64 operations formed on the integer pipes (kepler_fp64.cuh), per
-// initial guess, as measured on 4096 planetary systems: the increments'
-// multiplies with the seed (9.47e9 -> 1.00e10 N^2 steps/s), none with the
-// learned guess (no change measured), the increments' and the iterations'
-// multiplies with the standard guess (6.36e9 -> 7.51e9).
-constexpr int kBatEmuSeed = kEmuIncMul;
+// initial guess, as measured on 4096 planetary systems: the increments', the
+// setup's and the iterations' multiplies with the seed (9.47e9 -> 1.15e10
+// N^2 steps/s; 1.08e10 with the increments' only), none with the learned
+// guess (no change measured), the increments' and the iterations'
+// multiplies with the standard guess (6.36e9 -> 8.53e9; 7.94e9 with the
+// setup's too).
+constexpr int kBatEmuSeed = kEmuIncMul | kEmuSetupMul | kEmuIterMul;
 constexpr int kBatEmuLearned = 0;
 constexpr int kBatEmuStandard = kEmuIncMul | kEmuIterMul;
 

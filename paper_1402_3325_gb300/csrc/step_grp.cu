@@ -46,14 +46,26 @@
 
 namespace sakura {
 
-// The FP64 operations formed on the integer pipes (kepler_fp64.cuh), per
-// initial guess, as measured at 16384 bodies: with the seed or the learned
-// guess the increments' multiplies (ms per step 25.72 -> 24.89 seeded; every
-// other set measured was slower: the solve's own multiplies lengthen the
-// chain that the two blocks of 4 warps on an SM must hide); with the
-// standard guess, whose several iterations per solve fill the FP64 pipe
-// more, also the iterations' multiplies (36.69 -> 30.53).
-constexpr int kGrpEmuSeed = kEmuIncMul;
+// The FP64 operations formed on the integer pipes (kepler_fp64.cuh) and the
+// blocks of 4 warps per SM, per kernel, as measured at 16384 bodies (ms per
+// step).  The emulated multiplies lengthen each warp's dependency chains, so
+// they pay only with enough warps per SM to hide them:
+//   seed: 4 blocks (ptxas fits the kernel in 128 registers, spilling 52
+//     bytes), windows of 2
+//     phases, the increments', the setup's and the iterations' multiplies:
+//     20.72, against 24.03 with 2 blocks and the increments' multiplies
+//     only, 22.15 with 3 blocks and those, 20.85-21.72 with other sets;
+//   mixed form under the literal rule (inline class test): 3 blocks, windows
+//     of 2, the increments', the setup's and the carry's multiplies: 21.57
+//     against 25.43 with 2 blocks;
+//   learned guess (255 registers at 2 blocks, 168 with some spills at 3):
+//     3 blocks, the increments' multiplies: 27.74 against 29.02 with 2
+//     blocks and 35.36 with the iterations' and the setup's too;
+//   standard guess (4 blocks of 128 registers): the increments' and the
+//     iterations' multiplies: 26.47, against 27.09 with the setup's too.
+constexpr int kGrpLearnedBlocks = 3;
+constexpr int kGrpEmuSeed = kEmuIncMul | kEmuSetupMul | kEmuIterMul;
+constexpr int kGrpEmuMixed = kEmuIncMul | kEmuSetupMul | kEmuCarryMul;
 constexpr int kGrpEmuLearned = kEmuIncMul;
 constexpr int kGrpEmuStandard = kEmuIncMul | kEmuIterMul;
 
@@ -173,14 +185,19 @@ void launch_apply_grp(double *state, double *X, float *X32, const GrpParts &part
 // x, y, z, vx, vy, vz, m of the drifted state; float [WIN][10][32]: the float
 // copy for the seed), the warps' row sums of the group (double [G][G][6][32]:
 // warp, row block of the group), then (learned guess) the network and the
-// warps' staging.  G = kFp64GrpWarps = 4 warps per block and two blocks per
-// SM: one block's warps keep the SM's FP64 pipes busy while the other block
-// waits at a window barrier.  The window: 8 phases with the seed (two blocks
-// per SM), 4 otherwise (the network's weights take shared memory; without
-// either, more blocks per SM fit).  The column blocks are loaded between the
-// window's two barriers, after every warp has finished with the previous
-// ones, so one buffer serves.
-__host__ __device__ constexpr int grp_window(bool seed) { return seed ? 8 : 4; }
+// warps' staging.  G = kFp64GrpWarps = 4 warps per block and several blocks
+// per SM: one block's warps keep the SM's FP64 pipes busy while another
+// waits at a window barrier.  The window: 2 phases with the seed or the
+// inline class test (their 4 and 3 blocks per SM must fit in shared memory),
+// 4 otherwise.  The column blocks are loaded between the window's two
+// barriers, after every warp has finished with the previous ones, so one
+// buffer serves.
+constexpr int kGrpSeedBlocks = 4, kGrpSeedWindow = 2;
+constexpr int kGrpMixedBlocks = 3, kGrpMixedWindow = 2;
+__host__ __device__ constexpr int grp_window(bool seed, bool mixed)
+{
+    return mixed ? kGrpMixedWindow : (seed ? kGrpSeedWindow : 4);
+}
 __host__ __device__ constexpr size_t grp_cs_bytes(int win)
 {
     return sizeof(double) * kFp64GrpWarps * win * 6 * 32;
@@ -200,9 +217,10 @@ __host__ __device__ constexpr size_t grp_base_smem(int win, bool seed)
 }
 
 // f32: the float copy is staged (the seed, or the inline class test)
-size_t grp_smem(bool learned, bool f32)
+size_t grp_smem(bool learned, bool seed, bool mixed)
 {
-    const int win = grp_window(f32);
+    const int win = grp_window(seed, mixed);
+    const bool f32 = seed || mixed;
     return grp_base_smem(win, f32) +
            (learned ? sizeof(MlpWeights) + kFp64GrpWarps * 32 * 16 * 2 : 0);
 }
@@ -213,13 +231,16 @@ size_t grp_smem(bool learned, bool f32)
 // FP32 and its increments, converted to double, are accumulated in FP64 with
 // the rest; every other pair takes the FP64 solve (seeded with SEED).
 template <bool STATS, bool LEARNED, bool SEED, bool MIXED>
-__global__ void __launch_bounds__(kFp64GrpWarps * 32, (LEARNED || SEED || MIXED) ? 2 : 4)
+__global__ void __launch_bounds__(kFp64GrpWarps * 32,
+                                  LEARNED ? kGrpLearnedBlocks
+                                          : (MIXED ? kGrpMixedBlocks : (SEED ? kGrpSeedBlocks : 4)))
     pair_step_grp_kernel(StepArgs a, GrpLayout L, GrpParts parts)
 {
     constexpr int G = kFp64GrpWarps;
     constexpr bool F32 = SEED || MIXED;  // the float copy is staged
-    constexpr int kGrpEmu = SEED ? kGrpEmuSeed : (LEARNED ? kGrpEmuLearned : kGrpEmuStandard);
-    constexpr int WIN = grp_window(F32);
+    constexpr int kGrpEmu =
+        MIXED ? kGrpEmuMixed : (SEED ? kGrpEmuSeed : (LEARNED ? kGrpEmuLearned : kGrpEmuStandard));
+    constexpr int WIN = grp_window(SEED, MIXED);
     extern __shared__ __align__(16) unsigned char gsm[];
     double(*cs)[WIN][6][32] = reinterpret_cast<double(*)[WIN][6][32]>(gsm);
     double(*cd)[7][32] = reinterpret_cast<double(*)[7][32]>(gsm + grp_cs_bytes(WIN));
@@ -515,7 +536,7 @@ int pair_step_grp_blocks_per_sm(bool stats, bool learned, bool seed, bool mixed)
     learned = learned && !mixed;
     seed = seed && !learned;
     const void *fn = grp_fp64_kernel(stats, learned, seed, mixed);
-    const size_t smem = grp_smem(learned, seed || mixed);
+    const size_t smem = grp_smem(learned, seed, mixed);
     int b = 0;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess ||
@@ -534,7 +555,7 @@ void launch_pair_step_grp(const StepArgs &a, const GrpLayout &L, const GrpParts 
     const bool learned = !mixed && a.mlp != nullptr;
     const bool seed = !learned && a.X32 != nullptr && (!mixed || a.mixed == 2);
     const void *fn = grp_fp64_kernel(stats, learned, seed, mixed);
-    const size_t smem = grp_smem(learned, seed || mixed);
+    const size_t smem = grp_smem(learned, seed, mixed);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     GrpLayout Lv = L;
     GrpParts pv = parts;

@@ -32,13 +32,16 @@
 namespace sakura {
 
 // The FP64 operations formed on the integer pipes (kepler_fp64.cuh), per
-// initial guess, as measured on Plummer spheres of 1024 to 8192 bodies: none
-// with the seed or the learned guess (the increments' multiplies measured
-// 3.5 % slower at 1024 bodies, level at 4096, 1.5 % faster at 8192; 5 %
-// slower with the learned guess at 4096), the increments' and the
-// iterations' multiplies with the standard guess (13 % and 16 % faster at
-// 1024 and 4096 bodies).
-constexpr int kSymEmuSeed = 0;
+// initial guess, as measured on Plummer spheres of 1024 to 8192 bodies and
+// the black-hole cluster of 12288: with the seed, 3 blocks per SM (ptxas
+// fits the kernel in 143 registers) and the increments', the setup's and
+// the iterations' multiplies (3 % faster at 1024 bodies, 13-15 % from 2048
+// up, against 2 blocks and none; 3 blocks and none alone were 1 % slower);
+// with the learned guess 3 blocks and none (2 % faster at 4096; the
+// increments' multiplies were 5 % slower); with the standard guess the
+// increments' and the iterations' multiplies (13 % and 16 % faster at 1024
+// and 4096 bodies).
+constexpr int kSymEmuSeed = kEmuIncMul | kEmuSetupMul | kEmuIterMul;
 constexpr int kSymEmuLearned = 0;
 constexpr int kSymEmuStandard = kEmuIncMul | kEmuIterMul;
 
@@ -48,7 +51,7 @@ constexpr int kSymEmuStandard = kEmuIncMul | kEmuIterMul;
 // increments, converted to double, are accumulated in FP64 with the rest;
 // every other pair takes the FP64 solve (seeded with SEED).
 template <bool STATS, bool LEARNED, bool SEED, bool MIXED>
-__global__ void __launch_bounds__(128, (LEARNED || SEED || MIXED) ? 2 : 4)
+__global__ void __launch_bounds__(128, MIXED ? 2 : ((SEED || LEARNED) ? 3 : 4))
     pair_step_sym_kernel(StepArgs a, int Smax, int64_t T)
 {
     constexpr int kSymEmu = SEED ? kSymEmuSeed : (LEARNED ? kSymEmuLearned : kSymEmuStandard);
@@ -349,10 +352,12 @@ int pair_step_sym_blocks_per_sm(bool stats, bool learned, bool seed, bool mixed)
         cudaGetLastError();
         return 1;
     }
-    // the seeded kernel runs fastest with 8 warps per SM (measured on GB300:
-    // 120.8 us at 2 blocks per SM against 123.1 at 3 and 139 at 1, Plummer
-    // N = 1024); the others with as many as fit
-    if ((seed || mixed) && b > 2) b = 2;
+    // the seeded kernel runs fastest with 3 blocks per SM since part of its
+    // multiplies moved to the integer pipes (before that, 2: 120.8 us against
+    // 123.1 at 3, Plummer N = 1024); the mixed form's with 2; the others with
+    // as many as fit
+    if (mixed && b > 2) b = 2;
+    if (seed && b > 3) b = 3;
     return b > 0 ? b : 1;
 }
 
