@@ -30,11 +30,12 @@ namespace sakura {
 // all busy, but not in proportion to its tiles: measured on GB300, a step of
 // the phases at a group's start (1 to 3 tiles of 4, two on average) took
 // 0.64 of a full step with two blocks per SM (the double-word kernel keeps
-// (wA, wB) = (2, 1)); the FP64 kernel, now four blocks per SM with part of
-// its multiplies on the integer pipes, measured fastest with (3, 1) (20.72
-// ms per step at 16384 bodies against 20.85 with (2, 1) and 21.16 with
-// (1, 1)); the mixed kernel, whose blocks' times vary with their pairs'
-// classes more than with this, takes (1, 0).  x(g, t, k), the cost of the
+// (wA, wB) = (2, 1)).  The FP64 kernel, now four blocks per SM with part of
+// its multiplies on the integer pipes, measured fastest with steps counted
+// alike, (1, 0): 20.43 ms per step at 16384 bodies, against 20.45 with
+// (8, 1), 20.56 with (5, 1), 20.73 with (3, 1), 20.85 with (2, 1) and 21.16
+// with (1, 1).  The mixed kernel, whose blocks' times vary with their
+// pairs' classes more than with this, takes (1, 0) as well.  x(g, t, k), the cost of the
 // units before (g, t, k), is grp_phase_x(g, t) + k c(g, t); C = x at the
 // end.  The units are dealt in chunks of S consecutive steps of one phase
 // (S = 1: single steps, for the FP64 kernel; S = 32: whole phases, for the
@@ -83,7 +84,7 @@ struct GrpShape {
     int G, S, wA, wB;
     bool rev;
 };
-constexpr GrpShape kFp64GrpShape{kFp64GrpWarps, 1, 3, 1, true};
+constexpr GrpShape kFp64GrpShape{kFp64GrpWarps, 1, 1, 0, true};
 constexpr GrpShape kMixedGrpShape{kMixedGrpWarps, 32, 1, 0, false};
 // the double-word form (step_df64.cu): one block of 12 warps per SM, whose
 // window barrier keeps the SM's warps together (in three blocks of 4 warps

@@ -53,8 +53,9 @@ namespace sakura {
 //   seed: 4 blocks (ptxas fits the kernel in 128 registers, spilling 52
 //     bytes), windows of 2
 //     phases, the increments', the setup's and the iterations' multiplies:
-//     20.72, against 24.03 with 2 blocks and the increments' multiplies
-//     only, 22.15 with 3 blocks and those, 20.85-21.72 with other sets;
+//     20.43 (20.72 with the steps weighted 3 + tiles in the layout), against
+//     24.03 with 2 blocks and the increments' multiplies only, 22.15 with 3
+//     blocks and those, 20.85-21.72 with other sets;
 //   mixed form under the literal rule (inline class test): 3 blocks, windows
 //     of 2, the increments', the setup's and the carry's multiplies: 21.57
 //     against 25.43 with 2 blocks;
