@@ -87,9 +87,10 @@ extern "C" {
 #define SAKURA_FLAG_TILES 32u      /* symmetric FP64 and mixed steps: always the
                                       systolic tile kernel (per-warp tile segments,
                                       partials per segment: up to 12 n^2 bytes of
-                                      scratch), the FP64 default up to about 13400
-                                      bodies, the mixed form's under the literal
-                                      rule up to about 18900                       */
+                                      scratch), the FP64 default below 4096
+                                      bodies (the mixed form's under the literal
+                                      rule too; the double-word form's up to about
+                                      13400)                                       */
 #define SAKURA_FLAG_GROUPS 64u     /* symmetric FP64 and mixed steps: always the
                                       row-group kernel (blocks of warps sweep column
                                       blocks together, column sums reduced per
@@ -178,11 +179,10 @@ int sakura_set_stream(void *stream);
  * default) each unordered pair is solved once, its two ordered increments
  * being exact negatives.  The symmetric FP64 step runs on systolic tiles,
  * whose partial sums take up to 8 x 6 x 8 ceil(n/32) n bytes of library
- * scratch (12 MB at n = 1024), while that bound stays within 2 GB (up to
- * about 13400 bodies), and in row-group phases beyond, whose partials take
- * about n^2 / 2.7 bytes (0.1 GB at 16384); the mixed form uses row groups
- * under SAKURA_MIXED_RULE_HYP and the tile kernel with an inline class test
- * under the literal rule while the bound stays within 4 GB
+ * scratch (12 MB at n = 1024), below 4096 bodies, and in row-group phases
+ * from there, whose partials take about n^2 / 2.7 bytes (0.1 GB at 16384);
+ * the mixed form uses row groups under SAKURA_MIXED_RULE_HYP, and under the
+ * literal rule the FP64 kernel of its size with an inline class test
  * (SAKURA_FLAG_TILES / SAKURA_FLAG_GROUPS force either kernel).  Where the symmetric scratch
  * would pass 16 GB the ordered kernel is used.  Systems of 2 <= n <= 20 in the
  * FP64 form with symmetric pairs and a non-learned guess run in one launch

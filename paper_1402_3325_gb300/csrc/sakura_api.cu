@@ -291,21 +291,21 @@ double group_partial_bytes(int64_t n, int G)
     return 48.0 * (double)n * (double)(((n + 31) / 32 + G - 1) / G + 16);
 }
 
-// The symmetric FP64 form runs on systolic tiles (step_sym.cu) while their
-// partials take at most kFp64TileMaxBytes (about 13400 bodies), in row-group
-// phases (step_grp.cu) beyond, where the two are level or the row groups
-// faster and write about a hundredth of the tile kernel's partial traffic
-// (measured with the single-precision seed, ms per step, tiles / row groups:
-// black hole + 12287 stars 15.40 / 15.48, + 16383 stars 27.37 / 27.42,
-// + 24575 stars 61.62 / 61.50, + 32767 stars 114.2 / 109.1; Plummer 24576
-// bodies 62.61 / 62.55; at 16384 bodies with the learned guess 36.07 / 35.42
-// and the standard guess 38.67 / 38.27).  The flags force either kernel.
-constexpr double kFp64TileMaxBytes = 2.0 * 1024 * 1024 * 1024;
+// The symmetric FP64 form runs on systolic tiles (step_sym.cu) below
+// kFp64GroupsMinN bodies and in row-group phases (step_grp.cu) from there,
+// where the row groups are level or faster and write about a hundredth of
+// the tile kernel's partial traffic (measured with the single-precision
+// seed, ms per step, tiles / row groups: black hole + 2047 stars 0.380 /
+// 0.412, + 4095 stars 1.376 / 1.351, + 8191 stars 5.378 / 5.182, + 12287
+// stars 12.07 / 11.54, + 16383 stars 21.58 / 20.41; Plummer 2048 bodies
+// 0.358 / 0.393, 4096 1.354 / 1.357, 8192 5.350 / 5.262, 12288 12.02 /
+// 11.71, 16384 21.47 / 20.73).  The flags force either kernel.
+constexpr int64_t kFp64GroupsMinN = 4096;
 bool fp64_groups(int64_t n)
 {
     if (g.cfg.flags & SAKURA_FLAG_GROUPS) return true;
     if (g.cfg.flags & SAKURA_FLAG_TILES) return false;
-    return tile_partial_bytes(n) > kFp64TileMaxBytes;
+    return n >= kFp64GroupsMinN;
 }
 
 // The mixed form's kernels.  Under the literal rule, which admits few pairs
@@ -324,13 +324,16 @@ MixedKernel mixed_kernel(int64_t n)
     return MixedKernel::MixedGroups;
 }
 
-// The double-word form: tiles below kFp64TileMaxBytes of tile partials, row
-// groups beyond; the flags force either.
+// The double-word form: tiles while their partials take at most
+// kDf64TileMaxBytes (about 13400 bodies; at 8192 bodies the tiles measured
+// 2.15 ms per step against 2.24 in row groups), row groups beyond; the
+// flags force either.
+constexpr double kDf64TileMaxBytes = 2.0 * 1024 * 1024 * 1024;
 bool df64_groups(int64_t n)
 {
     if (g.cfg.flags & SAKURA_FLAG_GROUPS) return true;
     if (g.cfg.flags & SAKURA_FLAG_TILES) return false;
-    return tile_partial_bytes(n) > kFp64TileMaxBytes;
+    return tile_partial_bytes(n) > kDf64TileMaxBytes;
 }
 
 // The double-word form in row-group phases (step_df64.cu): prep (drift and

@@ -466,7 +466,7 @@ def test_headline_evolve_32_steps_matches_oracle_and_single_steps():
     np.testing.assert_array_equal(v, v1)
 
 
-# --- the row-group kernel (the FP64 default beyond about 13400 particles), forced on
+# --- the row-group kernel (the FP64 default from 4096 particles), forced on
 # small systems ---
 
 @pytest.mark.parametrize("guess", [sk.GUESS_STANDARD, sk.GUESS_TAYLOR, sk.GUESS_FP32])
