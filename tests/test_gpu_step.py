@@ -519,6 +519,23 @@ def test_row_group_and_tile_kernels_agree_and_are_deterministic():
     assert er <= TOL and ev <= TOL, (er, ev)
 
 
+@pytest.mark.parametrize("n,groups", [(4095, False), (4096, True)])
+def test_default_fp64_kernel_choice_by_size(n, groups):
+    # without a flag the symmetric FP64 step runs on tiles below 4096 bodies
+    # and in row groups from there; either way within the oracle's tolerance
+    # on a sample of rows
+    s = ics.plummer(n, seed=3)
+    with configured(pair_mode=sk.PAIRS_SYMMETRIC, guess=sk.GUESS_FP32):
+        sk.get_stats(reset=True)
+        r, v = gpu_step(s, s.dt, 2)
+        assert (sk.get_stats(reset=True)["group_launches"] == 1) == groups
+    rows = np.arange(0, n, 97)
+    rc, rr, vr = oracle.step_sample(s.m, s.r, s.v, s.dt, rows, 2, nthreads=NCPU)
+    assert rc == oracle.OK
+    er, ev = rel_err(r[rows], v[rows], rr, vr)
+    assert er <= TOL and ev <= TOL, (er, ev)
+
+
 def test_row_group_evolve_matches_single_steps():
     # calls of several steps: each apply kernel drifts for the next step, and
     # the next row-group pair kernel starts only after it completes
