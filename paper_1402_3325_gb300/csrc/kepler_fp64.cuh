@@ -58,9 +58,10 @@
 //   y <- y (1 + e/2 + 3 e^2 / 8),  e = 1 - x y^2,
 // which takes the error from d to O(d^3).
 //
-// Part of a solve's multiplies (and, where it pays, adds) can be formed on
-// the integer pipes instead of the FP64 pipe (fp64_emu.cuh), chosen per
-// kernel by the template argument EMU; the IEEE results are the same.
+// Part of a solve's multiplies can be formed on the integer pipes instead of
+// the FP64 pipe (fp64_emu.cuh), chosen per kernel by the template argument
+// EMU; the IEEE results are the same.  (Adds and FMAs formed there measured
+// slower than on the FP64 pipe, so none of the kernels moves them.)
 #pragma once
 
 #include <cstdint>
