@@ -104,10 +104,8 @@ EMU_ITER_MULS = 10
 def _integer_pipe_flops(kernel, guess, kbar, mixed=False):
     if kernel not in ("pair_step_grp", "pair_step_sym", "batched"):
         return 0
-    if mixed:  # the inline class test: its own set in row groups, the seed's on tiles
-        if kernel == "pair_step_grp":
-            return EMU_INC_MULS + EMU_SETUP_MULS + EMU_CARRY_MULS
-        return EMU_INC_MULS + EMU_SETUP_MULS + kbar * EMU_ITER_MULS if kernel == "pair_step_sym" else 0
+    if mixed:  # the inline class test: row groups only
+        return (EMU_INC_MULS + EMU_SETUP_MULS + EMU_CARRY_MULS) if kernel == "pair_step_grp" else 0
     if guess == "fp32":
         return EMU_INC_MULS + EMU_SETUP_MULS + kbar * EMU_ITER_MULS
     if guess in ("standard", "taylor"):

@@ -40,8 +40,10 @@ namespace sakura {
 // with the learned guess 3 blocks and none (2 % faster at 4096; the
 // increments' multiplies were 5 % slower); with the standard guess the
 // increments' and the iterations' multiplies (13 % and 16 % faster at 1024
-// and 4096 bodies).
+// and 4096 bodies).  The inline class test (2 blocks per SM) moves none: with
+// the seed's set its Plummer-1024 line fell from 8.62e9 to 8.16e9.
 constexpr int kSymEmuSeed = kEmuIncMul | kEmuSetupMul | kEmuIterMul;
+constexpr int kSymEmuMixed = 0;
 constexpr int kSymEmuLearned = 0;
 constexpr int kSymEmuStandard = kEmuIncMul | kEmuIterMul;
 
@@ -54,7 +56,8 @@ template <bool STATS, bool LEARNED, bool SEED, bool MIXED>
 __global__ void __launch_bounds__(128, MIXED ? 2 : ((SEED || LEARNED) ? 3 : 4))
     pair_step_sym_kernel(StepArgs a, int Smax, int64_t T)
 {
-    constexpr int kSymEmu = SEED ? kSymEmuSeed : (LEARNED ? kSymEmuLearned : kSymEmuStandard);
+    constexpr int kSymEmu =
+        MIXED ? kSymEmuMixed : (SEED ? kSymEmuSeed : (LEARNED ? kSymEmuLearned : kSymEmuStandard));
     extern __shared__ __align__(16) unsigned char dsm[];
     MlpWeights *mlpW = reinterpret_cast<MlpWeights *>(dsm);
     __nv_bfloat16 *mlpStage = reinterpret_cast<__nv_bfloat16 *>(dsm + sizeof(MlpWeights));
